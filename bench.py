@@ -1,0 +1,321 @@
+"""Benchmark of the connectivity-aware multigrid solver on GB300.
+
+One step = the whole hot path for one synthetic mesh: assemble M and L of every
+level (A = M + t L), project the right-hand sides (vertex x, y, z), solve
+(M + t L) x = rhs with mixed-precision V-cycles to relative residual 1e-6 for
+all three right-hand sides, and evaluate the solution at the mesh vertices
+(one implicit mean-curvature-flow update, Section 5.3).  The hierarchy is built
+once before timing.  Default workload: (2,3) torus-knot tube, 200k triangles,
+depth 8, t = 1e-4.
+
+Prints one JSON line.  `--impl reference` times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np
+
+METRIC = "unknowns×V-cycles/s; ms to 1e-6 rel. residual, mixed/learned vs plain FP64"
+UNIT = "unknowns*V-cycles/s"
+WORKLOAD = "knot23_200k_d8"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_oracle_sample(V, F, depth, t, f, cycles):
+    """Time `cycles` FP64 V-cycles (3 right-hand sides) of the oracle; returns (unknowns*cycles/s, seconds, n)."""
+    import oracle
+    h = oracle.Hierarchy(V, F, depth)
+    rhs = h.project_rhs(f)
+    t0 = time.perf_counter()
+    h.vcycles(t, rhs, cycles=cycles)
+    dt = time.perf_counter() - t0
+    n = h.ndof(depth)
+    return n * rhs.shape[1] * cycles / dt, dt, n, h
+
+
+def reference_main(args):
+    """Reference arm: the FP64 CPU oracle as it stands, one core."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import meshgen
+    import oracle
+    V, F, depth, t, f, tol, _ = meshgen.config_mesh(WORKLOAD)
+    h = oracle.Hierarchy(V, F, depth)
+    rhs = h.project_rhs(f)
+    n = h.ndof(depth)
+    cyc = 2
+    for _ in range(args.warmup):
+        h.vcycles(t, rhs, cycles=1)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        h.vcycles(t, rhs, cycles=cyc)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = n * rhs.shape[1] * cyc * args.steps / total
+    sample = f"{cyc} FP64 lexicographic-GS V-cycles x 3 right-hand sides per step on the {WORKLOAD} hierarchy (n={n})"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "unknowns": n * 3, "depth": depth, "t": t},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="lbmg")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-cycles", type=int, default=60)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_main(args)
+
+    import torch
+
+    import meshgen
+    import paper_1505_03615_gb300 as L
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    V, F, depth, t, f, tol, _ = meshgen.config_mesh(WORKLOAD)
+    nv = V.shape[0]
+    h = L.lbmg_build_hierarchy(V, F, depth)
+    d0, D = L.lbmg_levels(h)
+    n, nnz, nfrag = L.lbmg_level_info(h, D)
+    nrhs = 3
+    f_dev = torch.tensor(f, dtype=torch.float64, device=dev)
+    rhs = torch.zeros((n, nrhs), dtype=torch.float64, device=dev)
+    x = torch.zeros_like(rhs)
+    u = torch.zeros((nv, nrhs), dtype=torch.float64, device=dev)
+    max_cycles = 2000
+
+    def step(precision=L.LBMG_MIXED):
+        L.lbmg_assemble(h, t)
+        L.lbmg_project_rhs(h, f_dev, rhs)
+        x.zero_()
+        code, st = L.lbmg_solve(h, rhs, x, tol, max_cycles, precision)
+        if code != L.LBMG_OK:
+            raise RuntimeError(f"solve did not converge: {st.rel_residual[:3]}")
+        L.lbmg_eval_vertices(h, x, u)
+        return st
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.25)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    cycles, smooth_ms, rel = 0, 0.0, 0.0
+    for _ in range(args.steps):
+        st = step()
+        cycles += st.cycles
+        smooth_ms += st.ms_fine_smooth
+        rel = max(rel, max(st.rel_residual[:nrhs]))
+    e1.record()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    ms_t = torch.tensor([ms, float(cycles)], dtype=torch.float64, device=dev)
+    if ws > 1:
+        tot = torch.tensor([float(cycles)], dtype=torch.float64, device=dev)
+        dist.all_reduce(ms_t[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+        all_cycles = tot.item()
+    else:
+        all_cycles = float(cycles)
+    ms_max = ms_t[0].item()
+    value = n * nrhs * all_cycles / (ms_max / 1e3)
+    ms_per_step = ms_max / args.steps
+
+    # end to end through the C ABI with host buffers (pinned): H2D of the vertex data,
+    # D2H of the evaluated vertex positions, inside the timed region
+    f_pin = torch.tensor(f, dtype=torch.float64).pin_memory()
+    u_pin = torch.zeros((nv, nrhs), dtype=torch.float64).pin_memory()
+    f_np, u_np = f_pin.numpy(), u_pin.numpy()
+
+    def step_e2e():
+        L.lbmg_assemble(h, t)
+        L.lbmg_project_rhs(h, f_np, rhs)
+        x.zero_()
+        code, st = L.lbmg_solve(h, rhs, x, tol, max_cycles, L.LBMG_MIXED)
+        L.lbmg_eval_vertices(h, x, u_np)
+        return st
+
+    step_e2e()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_cycles = 0
+    for _ in range(args.steps):
+        e2e_cycles += step_e2e().cycles
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_value = n * nrhs * e2e_cycles / e2e_s * (ws if ws > 1 else 1)
+
+    # plain FP64 GPU multigrid on the same mesh: ms to the same tolerance
+    fp64_steps = max(1, min(3, args.steps))
+    step(L.LBMG_FP64)
+    torch.cuda.synchronize()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record()
+    fp64_cycles = 0
+    for _ in range(fp64_steps):
+        fp64_cycles += step(L.LBMG_FP64).cycles
+    g1.record()
+    torch.cuda.synchronize()
+    fp64_ms = g0.elapsed_time(g1) / fp64_steps
+
+    # roofline of the dominant kernel: finest-level coloured Gauss-Seidel (FP32, 4 lanes),
+    # timed live by events recorded inside the cycle graph around the finest sweeps
+    a_cnt, p_cnt, per_cycle, fixed = L.lbmg_launch_counts(h, L.LBMG_MIXED)
+    opts = L.lbmg_default_options()
+    sweeps_per_cycle = opts.nu1 + opts.nu2
+    R = 4
+    bytes_sweep = nnz * 8 + n * (4 + 4 + 3 * R * 4)
+    launches = cycles * sweeps_per_cycle * 8
+    avg_launch_ms = smooth_ms / max(launches, 1)
+    bytes_launch = bytes_sweep / 8
+    peak, peak_kind = _peaks()
+    achieved = bytes_launch / (avg_launch_ms * 1e-3) / 1e9 if avg_launch_ms > 0 else 0.0
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            tr = json.load(fh).get("smooth_colour_knot23_200k_d8")
+            if tr:
+                traffic = tr["bytes_per_launch"]
+    except Exception:
+        pass
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "kernel": "smooth_colour_kernel<float,4,8> (finest level)",
+                "peak_kind": peak_kind, "bytes_per_launch": bytes_launch, "avg_launch_us": avg_launch_ms * 1e3}
+
+    gpu_launches = args.steps * (a_cnt + p_cnt + fixed + 1) + cycles * per_cycle
+
+    cpu_baseline = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        val, dt, n_o, _ = run_oracle_sample(V, F, depth, t, f, args.oracle_cycles)
+        cpu_baseline = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                        "sample": f"{args.oracle_cycles} FP64 lexicographic-GS V-cycles x 3 right-hand sides on the "
+                                  f"same mesh (oracle hierarchy, n={n_o}), {dt:.1f} s on one host core"}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 relax / f64 residual+assembly", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "triangles": int(F.shape[0]), "depth": depth, "min_depth": d0,
+                       "dofs_finest": n, "nnz_finest": nnz, "fragments_finest": nfrag, "nrhs": nrhs, "t": t,
+                       "tol": tol, "precision": "mixed", "l2": "inputs larger than L2 (assembly streams >0.5 GB/step)",
+                       "parallelism": "replicas" if ws > 1 else "single"},
+            "ms_to_tol_mixed": ms_per_step, "ms_to_tol_fp64": fp64_ms,
+            "cycles_per_step": cycles / args.steps, "fp64_cycles_per_step": fp64_cycles / fp64_steps,
+            "max_rel_residual": rel,
+            "roofline": roofline, "cpu_baseline": cpu_baseline,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(nv * nrhs * 8),
+                    "d2h_bytes_per_step": int(nv * nrhs * 8)},
+            "gpu_launches": int(gpu_launches), "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    L.lbmg_destroy(h)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,182 @@
+/*
+ * lbmg.h -- C ABI of the GB300 library for the connectivity-aware multi-level
+ * finite-element system of Chuang & Kazhdan (arXiv 1505.03615).
+ *
+ * The library builds, for a triangle mesh, the hierarchy of connectivity-split
+ * trilinear B-spline spaces of Sections 3.2 and 4 (one function b_k^i per
+ * connected component C_k^i of supp(b_k) restricted to the mesh, on grids of
+ * depth min_depth..depth), assembles the mass matrix M and the stiffness matrix L
+ * of every level (Eq. 2 and Section 5.1), and solves the screened system
+ * (M + t L) x = rhs with multigrid V-cycles (Section 4.3) whose relaxation,
+ * residual, restriction and prolongation run as CUDA kernels for sm_103a.
+ *
+ * Conventions shared by every entry point
+ *  - Every function returns an int status (LBMG_OK = 0 or one of the codes
+ *    below); no exception or abort crosses the ABI.  lbmg_status_string()
+ *    names a code.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Work is enqueued on it; functions return without synchronizing
+ *    unless their comment says otherwise.
+ *  - Vector arguments are dense row-major arrays [n][nrhs] of double, with
+ *    1 <= nrhs <= 4.  Each may be a device pointer (the caller owns it and it
+ *    must stay valid until the stream reaches the call) or a host pointer, in
+ *    which case the library copies through pinned staging memory and the call
+ *    synchronizes the stream before returning.
+ *  - Levels are addressed by depth d, min_depth <= d <= depth; the finest
+ *    level (d = depth) carries right-hand sides and solutions.
+ *  - Dof order on the device: by colour (corner parity (k mod 2)^3), then Morton
+ *    order of the corner, then the smallest triangle index of the component.
+ *    lbmg_get_dofs() gives, per dof, its corner and that triangle, so results
+ *    can be matched with any other numbering of the same functions.
+ *  - A handle is not thread-safe: calls on one handle must be serialized, and
+ *    all its device work must be on one stream at a time.
+ */
+#ifndef LBMG_H
+#define LBMG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    LBMG_OK = 0,
+    LBMG_INVALID_ARG = 1,      /* NaN/inf coordinates, index out of range, bad depth or nrhs, NULL pointer */
+    LBMG_DEGENERATE_MESH = 2,  /* no triangle of positive area inside the grid */
+    LBMG_OUT_OF_MEMORY = 3,    /* host or device allocation failed; the handle is left unchanged */
+    LBMG_NOT_CONVERGED = 4,    /* solve reached max_cycles; x holds the last iterate, stats say how far */
+    LBMG_NOT_ASSEMBLED = 5,    /* solve/vcycle before lbmg_assemble */
+    LBMG_COARSE_FACTOR = 6,    /* coarsest-level Cholesky met a non-positive pivot */
+    LBMG_CUDA_ERROR = 7,       /* a CUDA call failed; lbmg_last_cuda_error() names it */
+    LBMG_DIVERGED = 8          /* residual became NaN or grew by 1e6 */
+};
+
+enum { LBMG_FP64 = 0, LBMG_MIXED = 1 };          /* precision of the V-cycle */
+enum { LBMG_GS_COLOURED = 0, LBMG_JACOBI = 1 };  /* smoother */
+
+typedef struct lbmg_options {
+    int min_depth;      /* coarsest depth; < 0: deepest level with at most coarse_max functions */
+    int coarse_max;     /* default 160 */
+    int nu1, nu2;       /* pre/post smoothing sweeps per level, default 2/2 */
+    int smoother;       /* LBMG_GS_COLOURED (default) or LBMG_JACOBI */
+    double jacobi_omega;/* damping of the weighted Jacobi smoother, default 0.6 */
+    int split;          /* 1 (default): connectivity-aware split of Section 4.2; 0: unsplit space of Section 3.2 */
+    int threads;        /* host threads for the hierarchy build; 0 = all cores */
+} lbmg_options;
+
+typedef struct lbmg_stats {
+    int cycles;              /* V-cycles applied */
+    int converged;           /* 1 if every right-hand side met tol */
+    double rel_residual[4];  /* final ||rhs - A x||_2 / ||rhs||_2 per right-hand side (FP64) */
+    double initial_residual[4];
+    float ms_total;          /* device time of the solve, CUDA events */
+    float ms_fine_smooth;    /* device time of the finest-level smoothing sweeps summed over all cycles,
+                                from CUDA events recorded inside the cycle (0 for lbmg_vcycles) */
+} lbmg_stats;
+
+typedef struct lbmg_ctx *lbmg_handle;
+
+const char *lbmg_status_string(int code);
+const char *lbmg_last_cuda_error(void);
+void lbmg_default_options(lbmg_options *o);
+
+/*
+ * Build the hierarchy (host, then upload).  Sections 3.2, 4.1-4.3.
+ *  V: host double[nv][3] vertex positions; F: host int[nt][3] triangle indices.
+ *  depth: finest grid depth, 1..12 (2^depth voxels per axis).
+ * The mesh's bounding box is centred in a cube of side 1.1 x its largest extent.
+ * For every level: fragments of triangles cut by the voxels (area above
+ * 1e-12 finest voxel faces), the split functions (one per connected component
+ * of supp(b_k) /\ M, two triangles being joined through a shared edge meeting
+ * the open support cube or a shared vertex inside it), the prolongation of
+ * Eq. 4 (parent component via chi, weights from the trilinear stencil
+ * 1/2(1 2 1)), and the contribution lists used by lbmg_assemble.
+ * Synchronous.  *out receives a new handle owned by the caller (lbmg_destroy).
+ */
+int lbmg_build_hierarchy(const double *V, int nv, const int *F, int nt, int depth,
+                         const lbmg_options *opt, lbmg_handle *out);
+void lbmg_destroy(lbmg_handle h);
+
+/* min_depth and depth of the hierarchy. */
+int lbmg_levels(lbmg_handle h, int *min_depth, int *depth);
+/* functions (dofs), stored non-zeros and, for the finest level, fragments of level d */
+int lbmg_level_info(lbmg_handle h, int d, long *ndof, long *nnz, long *nfrag);
+/* cube side S and centre of the embedding (host double[3]) */
+int lbmg_embedding(lbmg_handle h, double *cube_side, double *center);
+
+/*
+ * Assemble A_d = M_d + t L_d for every level (Eq. 2, Section 5.1; positive
+ * stiffness L_ij = int <grad_M b_i, grad_M b_j>).  The finest level is
+ * integrated exactly over each fragment (Gauss-Legendre product rule on a fan
+ * of sub-triangles, exact to degree 6); every coarser level is the Galerkin
+ * product P^T A_{d+1} P, which equals its own quadrature because the spaces nest
+ * (Claim of Section 4.1).  Sums use precomputed contribution lists, no atomics.
+ * Also factors the coarsest level (FP64 Cholesky of A + eps Id, eps =
+ * 1e-12 mean diag, Discussion of Section 5).  Asynchronous on `stream` except
+ * for the coarse-factor status, which it reads back (one synchronization).
+ */
+int lbmg_assemble(lbmg_handle h, double t, void *stream);
+
+/*
+ * rhs_i = int_M f b_i over the finest level, f linear on each triangle from
+ * per-vertex values f_vertex[nv][nrhs] (Section 5.2, s_i; Section 5.3, M_t u_t).
+ * rhs: [n_depth][nrhs].  Needs lbmg_assemble (it reuses the fragment moments).
+ */
+int lbmg_project_rhs(lbmg_handle h, const double *f_vertex, int nrhs, double *rhs, void *stream);
+
+/*
+ * Solve (M + t L) x = rhs by V-cycles: each cycle is ν1 smoothing sweeps per
+ * level on the way down, residual, restriction P^T r, the coarsest solve, then
+ * prolongation x += P e and ν2 sweeps on the way up (Section 4.3).  precision:
+ * LBMG_FP64 runs the whole cycle in FP64; LBMG_MIXED runs it in FP32 inside an
+ * FP64 defect-correction loop (residual and update in FP64).  Stops when
+ * ||rhs - A x||_2 <= tol ||rhs||_2 for every right-hand side, or after
+ * max_cycles.  x: [n_depth][nrhs], in/out (warm start).  stats may be NULL.
+ * Synchronizes once per cycle to read the residual norms.
+ */
+int lbmg_solve(lbmg_handle h, const double *rhs, double *x, int nrhs, double tol, int max_cycles,
+               int precision, lbmg_stats *stats, void *stream);
+
+/* Number of kernels each call launches: lbmg_assemble, lbmg_project_rhs, one
+   V-cycle step of lbmg_solve/lbmg_vcycles in `precision` (cycle + FP64 residual
+   + norms), and the fixed part of lbmg_solve around its cycles.  Host only. */
+int lbmg_launch_counts(lbmg_handle h, int precision, int *assemble, int *project_rhs, int *per_cycle,
+                       int *solve_fixed);
+
+/* Exactly `cycles` V-cycles in the same defect-correction form, with no norm
+   read-back (used for throughput measurement).  x in/out. */
+int lbmg_vcycles(lbmg_handle h, const double *rhs, double *x, int nrhs, int cycles, int precision,
+                 void *stream);
+
+/* r = rhs - A_d x on level d in FP64 (Eq. 2 operator); all [n_d][nrhs]. */
+int lbmg_residual(lbmg_handle h, int d, const double *rhs, const double *x, double *r, int nrhs,
+                  void *stream);
+
+/* `sweeps` smoothing sweeps of the configured smoother on level d, in the
+   given precision, on A_d x = rhs; x in/out.  Colour order 0..7. */
+int lbmg_smooth(lbmg_handle h, int d, const double *rhs, double *x, int nrhs, int sweeps,
+                int precision, void *stream);
+
+/* r_c = P^T r_f from level d to d-1 (FP64). r_f: [n_d][nrhs], r_c: [n_{d-1}][nrhs]. */
+int lbmg_restrict(lbmg_handle h, int d, const double *r_fine, double *r_coarse, int nrhs, void *stream);
+/* x_f += P x_c from level d-1 to d (FP64). */
+int lbmg_prolong_add(lbmg_handle h, int d, const double *x_coarse, double *x_fine, int nrhs, void *stream);
+
+/* u(v) = sum_i x_i b_i(v) at every mesh vertex; x: [n_depth][nrhs], u: [nv][nrhs]. */
+int lbmg_eval_vertices(lbmg_handle h, const double *x, int nrhs, double *u, void *stream);
+
+/*
+ * Host copies for inspection and testing (synchronous).
+ *  lbmg_get_dofs: corner int[n][3] (grid corner index at depth d), mintri int[n].
+ *  lbmg_get_matrix: CSR of level d, rowptr int[n+1], col int[nnz] (sorted per
+ *    row), M, L double[nnz] (either may be NULL); needs lbmg_assemble.
+ *  lbmg_get_prolongation: parents int[n_d][8] (coarse dofs at depth d-1, -1 =
+ *    none) and weights double[n_d][8].
+ */
+int lbmg_get_dofs(lbmg_handle h, int d, int *corner, int *mintri);
+int lbmg_get_matrix(lbmg_handle h, int d, int *rowptr, int *col, double *M, double *L);
+int lbmg_get_prolongation(lbmg_handle h, int d, int *parents, double *weights);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBMG_H */

@@ -1,0 +1,271 @@
+"""Python binding of liblbmg, the GB300 library for the connectivity-aware
+multi-level finite-element system of Chuang & Kazhdan (arXiv 1505.03615).
+
+Every function here has the name of a C entry point in ``include/lbmg.h`` and
+only marshals arguments: numpy arrays and torch tensors are passed as raw
+pointers (host or device), torch streams as ``cudaStream_t``.  All arithmetic
+runs in the library's CUDA kernels; there is no fallback: if the shared
+library is missing or fails to load, importing the functions raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+__all__ = [
+    "LbmgError", "Options", "Stats", "load_library", "exported_symbols",
+    "LBMG_OK", "LBMG_NOT_CONVERGED", "LBMG_FP64", "LBMG_MIXED", "LBMG_GS_COLOURED", "LBMG_JACOBI",
+    "lbmg_build_hierarchy", "lbmg_destroy", "lbmg_levels", "lbmg_level_info", "lbmg_embedding",
+    "lbmg_assemble", "lbmg_project_rhs", "lbmg_solve", "lbmg_vcycles", "lbmg_residual", "lbmg_smooth",
+    "lbmg_restrict", "lbmg_prolong_add", "lbmg_eval_vertices", "lbmg_get_dofs", "lbmg_get_matrix",
+    "lbmg_get_prolongation", "lbmg_launch_counts", "lbmg_status_string", "lbmg_last_cuda_error", "lbmg_default_options",
+]
+
+LBMG_OK = 0
+LBMG_NOT_CONVERGED = 4
+LBMG_FP64 = 0
+LBMG_MIXED = 1
+LBMG_GS_COLOURED = 0
+LBMG_JACOBI = 1
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_lib = None
+
+
+class LbmgError(RuntimeError):
+    def __init__(self, code, where):
+        msg = f"{where}: {_lib.lbmg_status_string(code).decode()} ({code})" if _lib else f"{where}: status {code}"
+        if _lib is not None and code == 7:
+            msg += " -- " + _lib.lbmg_last_cuda_error().decode()
+        super().__init__(msg)
+        self.code = code
+
+
+class Options(C.Structure):
+    _fields_ = [("min_depth", C.c_int), ("coarse_max", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int),
+                ("smoother", C.c_int), ("jacobi_omega", C.c_double), ("split", C.c_int), ("threads", C.c_int)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("cycles", C.c_int), ("converged", C.c_int), ("rel_residual", C.c_double * 4),
+                ("initial_residual", C.c_double * 4), ("ms_total", C.c_float), ("ms_fine_smooth", C.c_float)]
+
+
+def load_library():
+    """Load (building first if needed) paper_1505_03615_gb300/_build/liblbmg.so."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    from . import build as _build
+    path = _build.build()
+    lib = C.CDLL(path)
+    P, i, l, d = C.c_void_p, C.c_int, C.c_long, C.c_double
+    sig = {
+        "lbmg_status_string": (C.c_char_p, [i]),
+        "lbmg_last_cuda_error": (C.c_char_p, []),
+        "lbmg_default_options": (None, [P]),
+        "lbmg_build_hierarchy": (i, [P, i, P, i, i, P, P]),
+        "lbmg_destroy": (None, [P]),
+        "lbmg_levels": (i, [P, P, P]),
+        "lbmg_level_info": (i, [P, i, P, P, P]),
+        "lbmg_embedding": (i, [P, P, P]),
+        "lbmg_assemble": (i, [P, d, P]),
+        "lbmg_project_rhs": (i, [P, P, i, P, P]),
+        "lbmg_solve": (i, [P, P, P, i, d, i, i, P, P]),
+        "lbmg_vcycles": (i, [P, P, P, i, i, i, P]),
+        "lbmg_residual": (i, [P, i, P, P, P, i, P]),
+        "lbmg_smooth": (i, [P, i, P, P, i, i, i, P]),
+        "lbmg_restrict": (i, [P, i, P, P, i, P]),
+        "lbmg_prolong_add": (i, [P, i, P, P, i, P]),
+        "lbmg_eval_vertices": (i, [P, P, i, P, P]),
+        "lbmg_get_dofs": (i, [P, i, P, P]),
+        "lbmg_launch_counts": (i, [P, i, P, P, P, P]),
+        "lbmg_get_matrix": (i, [P, i, P, P, P, P]),
+        "lbmg_get_prolongation": (i, [P, i, P, P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    """Names declared in include/lbmg.h (parsed from the header)."""
+    import re
+    hdr = os.path.join(os.path.dirname(_HERE), "include", "lbmg.h")
+    text = open(hdr).read()
+    return sorted(set(re.findall(r"\b(lbmg_[a-z_0-9]+)\s*\(", text)))
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("arrays must be C-contiguous")
+        return C.c_void_p(a.ctypes.data)
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return C.c_void_p(a.data_ptr())
+    raise TypeError(f"unsupported argument type {type(a)}")
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def _nrhs(a):
+    return 1 if len(a.shape) == 1 else int(a.shape[1])
+
+
+def _check(code, where, allow=()):
+    if code != LBMG_OK and code not in allow:
+        raise LbmgError(code, where)
+    return code
+
+
+def lbmg_status_string(code):
+    return load_library().lbmg_status_string(int(code)).decode()
+
+
+def lbmg_last_cuda_error():
+    return load_library().lbmg_last_cuda_error().decode()
+
+
+def lbmg_default_options():
+    o = Options()
+    load_library().lbmg_default_options(C.byref(o))
+    return o
+
+
+def lbmg_build_hierarchy(V, F, depth, **opts):
+    """Build the hierarchy; V float64 [nv,3], F int32 [nt,3] on the host.  Returns the handle."""
+    lib = load_library()
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    F = np.ascontiguousarray(F, dtype=np.int32)
+    o = lbmg_default_options()
+    for k, v in opts.items():
+        setattr(o, k, v)
+    h = C.c_void_p()
+    _check(lib.lbmg_build_hierarchy(_ptr(V), V.shape[0], _ptr(F), F.shape[0], int(depth), C.byref(o), C.byref(h)),
+           "lbmg_build_hierarchy")
+    return h
+
+
+def lbmg_destroy(h):
+    load_library().lbmg_destroy(h)
+
+
+def lbmg_levels(h):
+    a, b = C.c_int(), C.c_int()
+    _check(load_library().lbmg_levels(h, C.byref(a), C.byref(b)), "lbmg_levels")
+    return a.value, b.value
+
+
+def lbmg_level_info(h, d):
+    n, z, f = C.c_long(), C.c_long(), C.c_long()
+    _check(load_library().lbmg_level_info(h, int(d), C.byref(n), C.byref(z), C.byref(f)), "lbmg_level_info")
+    return n.value, z.value, f.value
+
+
+def lbmg_embedding(h):
+    s = C.c_double()
+    c = np.zeros(3)
+    _check(load_library().lbmg_embedding(h, C.byref(s), _ptr(c)), "lbmg_embedding")
+    return s.value, c
+
+
+def lbmg_assemble(h, t, stream=None):
+    return _check(load_library().lbmg_assemble(h, float(t), _stream(stream)), "lbmg_assemble")
+
+
+def lbmg_project_rhs(h, f_vertex, rhs, stream=None):
+    return _check(load_library().lbmg_project_rhs(h, _ptr(f_vertex), _nrhs(f_vertex), _ptr(rhs), _stream(stream)),
+                  "lbmg_project_rhs")
+
+
+def lbmg_solve(h, rhs, x, tol, max_cycles, precision, stream=None, raise_not_converged=False):
+    """Returns (status, Stats); status is LBMG_OK or LBMG_NOT_CONVERGED."""
+    st = Stats()
+    code = load_library().lbmg_solve(h, _ptr(rhs), _ptr(x), _nrhs(rhs), float(tol), int(max_cycles), int(precision),
+                                     C.byref(st), _stream(stream))
+    _check(code, "lbmg_solve", allow=() if raise_not_converged else (LBMG_NOT_CONVERGED,))
+    return code, st
+
+
+def lbmg_vcycles(h, rhs, x, cycles, precision, stream=None):
+    return _check(load_library().lbmg_vcycles(h, _ptr(rhs), _ptr(x), _nrhs(rhs), int(cycles), int(precision),
+                                              _stream(stream)), "lbmg_vcycles")
+
+
+def lbmg_residual(h, d, rhs, x, r, stream=None):
+    return _check(load_library().lbmg_residual(h, int(d), _ptr(rhs), _ptr(x), _ptr(r), _nrhs(rhs), _stream(stream)),
+                  "lbmg_residual")
+
+
+def lbmg_smooth(h, d, rhs, x, sweeps, precision, stream=None):
+    return _check(load_library().lbmg_smooth(h, int(d), _ptr(rhs), _ptr(x), _nrhs(rhs), int(sweeps), int(precision),
+                                             _stream(stream)), "lbmg_smooth")
+
+
+def lbmg_restrict(h, d, r_fine, r_coarse, stream=None):
+    return _check(load_library().lbmg_restrict(h, int(d), _ptr(r_fine), _ptr(r_coarse), _nrhs(r_fine),
+                                               _stream(stream)), "lbmg_restrict")
+
+
+def lbmg_prolong_add(h, d, x_coarse, x_fine, stream=None):
+    return _check(load_library().lbmg_prolong_add(h, int(d), _ptr(x_coarse), _ptr(x_fine), _nrhs(x_coarse),
+                                                  _stream(stream)), "lbmg_prolong_add")
+
+
+def lbmg_eval_vertices(h, x, u, stream=None):
+    return _check(load_library().lbmg_eval_vertices(h, _ptr(x), _nrhs(x), _ptr(u), _stream(stream)),
+                  "lbmg_eval_vertices")
+
+
+def lbmg_launch_counts(h, precision):
+    """(assemble, project_rhs, per_cycle, solve_fixed) kernel launch counts."""
+    v = [C.c_int() for _ in range(4)]
+    _check(load_library().lbmg_launch_counts(h, int(precision), *[C.byref(x) for x in v]), "lbmg_launch_counts")
+    return tuple(x.value for x in v)
+
+
+def lbmg_get_dofs(h, d):
+    n, _, _ = lbmg_level_info(h, d)
+    corner = np.zeros((n, 3), np.int32)
+    mintri = np.zeros(n, np.int32)
+    _check(load_library().lbmg_get_dofs(h, int(d), _ptr(corner), _ptr(mintri)), "lbmg_get_dofs")
+    return corner, mintri
+
+
+def lbmg_get_matrix(h, d):
+    n, nnz, _ = lbmg_level_info(h, d)
+    rp = np.zeros(n + 1, np.int32)
+    ci = np.zeros(nnz, np.int32)
+    M = np.zeros(nnz)
+    L = np.zeros(nnz)
+    _check(load_library().lbmg_get_matrix(h, int(d), _ptr(rp), _ptr(ci), _ptr(M), _ptr(L)), "lbmg_get_matrix")
+    return rp, ci, M, L
+
+
+def lbmg_get_prolongation(h, d):
+    n, _, _ = lbmg_level_info(h, d)
+    par = np.zeros((n, 8), np.int32)
+    w = np.zeros((n, 8))
+    _check(load_library().lbmg_get_prolongation(h, int(d), _ptr(par), _ptr(w)), "lbmg_get_prolongation")
+    return par, w

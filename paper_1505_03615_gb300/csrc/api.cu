@@ -1,0 +1,688 @@
+// api.cu -- C ABI of the library (declared in include/lbmg.h): handle lifetime,
+// device upload of the hierarchy, assembly, V-cycles and the defect-correction
+// solve loop (Chuang & Kazhdan, Sections 4.3 and 5).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lbmg.h"
+#include "lbmg_internal.h"
+
+using namespace lbmg;
+
+namespace {
+
+thread_local std::string g_cuda_err;
+
+#define LBMG_CK(call)                                                                 \
+    do {                                                                              \
+        cudaError_t e_ = (call);                                                      \
+        if (e_ != cudaSuccess) {                                                      \
+            g_cuda_err = std::string(#call) + ": " + cudaGetErrorString(e_);          \
+            return e_ == cudaErrorMemoryAllocation ? LBMG_OUT_OF_MEMORY : LBMG_CUDA_ERROR; \
+        }                                                                             \
+    } while (0)
+
+#define LBMG_TRY(expr)          \
+    do {                        \
+        int st_ = (expr);       \
+        if (st_) return st_;    \
+    } while (0)
+
+int check_launch() {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        g_cuda_err = std::string("kernel launch: ") + cudaGetErrorString(e);
+        return LBMG_CUDA_ERROR;
+    }
+    return LBMG_OK;
+}
+
+bool on_device(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+inline int stride_for(int nrhs) { return nrhs == 1 ? 1 : (nrhs == 2 ? 2 : 4); }
+
+__global__ void to_double_kernel(const float *__restrict__ a, double *__restrict__ b, int64_t n) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q < n) b[q] = (double)a[q];
+}
+
+}  // namespace
+
+struct lbmg_ctx {
+    Ctx c;
+    std::vector<void *> allocs;
+    size_t io_cap = 0;   // doubles per io slot
+    int *h_flag = nullptr;
+
+    template <class T>
+    int alloc(T **p, size_t count) {
+        if (count == 0) count = 1;
+        cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+        if (e != cudaSuccess) {
+            g_cuda_err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+            cudaGetLastError();
+            *p = nullptr;
+            return LBMG_OUT_OF_MEMORY;
+        }
+        allocs.push_back((void *)*p);
+        return LBMG_OK;
+    }
+    template <class T>
+    int upload(T **p, const std::vector<T> &v) {
+        LBMG_TRY(alloc(p, v.size()));
+        if (!v.empty()) LBMG_CK(cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+        return LBMG_OK;
+    }
+    ~lbmg_ctx() {
+        if (c.graph.exec) cudaGraphExecDestroy(c.graph.exec);
+        for (void *p : allocs) cudaFree(p);
+        if (c.h_norm) cudaFreeHost(c.h_norm);
+        if (h_flag) cudaFreeHost(h_flag);
+        if (c.capture_stream) cudaStreamDestroy(c.capture_stream);
+        if (c.ev0) cudaEventDestroy(c.ev0);
+        if (c.ev1) cudaEventDestroy(c.ev1);
+        for (int q = 0; q < 4; q++) if (c.ev_smooth[q]) cudaEventDestroy(c.ev_smooth[q]);
+    }
+};
+
+namespace {
+
+// device pointer for a user input: copies host data into io slot `slot`
+int input_ptr(lbmg_handle h, const double *user, size_t count, int slot, cudaStream_t s, const double **out) {
+    if (on_device(user)) { *out = user; return LBMG_OK; }
+    if (count > h->io_cap) return LBMG_INVALID_ARG;
+    double *dst = h->c.dev_io + (size_t)slot * h->io_cap;
+    LBMG_CK(cudaMemcpyAsync(dst, user, count * sizeof(double), cudaMemcpyHostToDevice, s));
+    *out = dst;
+    return LBMG_OK;
+}
+
+// device pointer for a user output; *host tells whether finish_output must copy back
+int output_ptr(lbmg_handle h, double *user, size_t count, int slot, double **out, bool *host) {
+    if (on_device(user)) { *out = user; *host = false; return LBMG_OK; }
+    if (count > h->io_cap) return LBMG_INVALID_ARG;
+    *out = h->c.dev_io + (size_t)slot * h->io_cap;
+    *host = true;
+    return LBMG_OK;
+}
+
+int finish_output(double *user, const double *dev, size_t count, bool host, cudaStream_t s) {
+    if (host) {
+        LBMG_CK(cudaMemcpyAsync(user, dev, count * sizeof(double), cudaMemcpyDeviceToHost, s));
+        LBMG_CK(cudaStreamSynchronize(s));
+    }
+    return check_launch();
+}
+
+template <class T> struct P;
+template <> struct P<float> {
+    static float *x(DevLevel &L) { return L.x32; }
+    static float *b(DevLevel &L) { return L.b32; }
+    static float *r(DevLevel &L) { return L.r32; }
+    static const float *A(DevLevel &L) { return L.A32; }
+    static const float *dinv(DevLevel &L) { return L.dinv32; }
+    static const float *inv(Ctx &c) { return c.cinv32; }
+};
+template <> struct P<double> {
+    static double *x(DevLevel &L) { return L.x64; }
+    static double *b(DevLevel &L) { return L.b64; }
+    static double *r(DevLevel &L) { return L.r64; }
+    static const double *A(DevLevel &L) { return L.A64; }
+    static const double *dinv(DevLevel &L) { return L.dinv64; }
+    static const double *inv(Ctx &c) { return c.cinv64; }
+};
+
+template <class T>
+void enqueue_smooth(Ctx &c, DevLevel &L, int R, int sweeps, bool forward, cudaStream_t s) {
+    for (int sw = 0; sw < sweeps; sw++) {
+        if (c.smoother == LBMG_JACOBI) {
+            launch_residual<T>(L, P<T>::A(L), P<T>::b(L), P<T>::x(L), P<T>::r(L), R, s);
+            launch_jacobi_update<T>(L, P<T>::dinv(L), P<T>::r(L), P<T>::x(L), (T)c.omega, R, s);
+        } else {
+            for (int q = 0; q < 8; q++) {
+                const int colour = forward ? q : 7 - q;
+                launch_smooth_colour<T>(L, colour, P<T>::A(L), P<T>::dinv(L), P<T>::b(L), P<T>::x(L), R, s);
+            }
+        }
+    }
+}
+
+// one V-cycle on A e = b at the finest level; e (finest x) must be zero on entry
+template <class T>
+void enqueue_vcycle(Ctx &c, int R, cudaStream_t s, bool timed) {
+    for (int d = c.D; d > c.d0; d--) {
+        DevLevel &L = c.lev[d], &Lc = c.lev[d - 1];
+        if (timed && d == c.D) cudaEventRecord(c.ev_smooth[0], s);
+        enqueue_smooth<T>(c, L, R, c.nu1, true, s);
+        if (timed && d == c.D) cudaEventRecord(c.ev_smooth[1], s);
+        launch_residual<T>(L, P<T>::A(L), P<T>::b(L), P<T>::x(L), P<T>::r(L), R, s);
+        launch_restrict<T>(Lc, P<T>::r(L), P<T>::b(Lc), R, s);
+        if (d - 1 > c.d0) cudaMemsetAsync(P<T>::x(Lc), 0, (size_t)Lc.n * R * sizeof(T), s);
+    }
+    DevLevel &L0 = c.lev[c.d0];
+    launch_coarse_apply<T>(L0.n, P<T>::inv(c), P<T>::b(L0), P<T>::x(L0), R, s);
+    for (int d = c.d0 + 1; d <= c.D; d++) {
+        DevLevel &L = c.lev[d];
+        launch_prolong_add<T>(L, P<T>::x(c.lev[d - 1]), P<T>::x(L), R, s);
+        if (timed && d == c.D) cudaEventRecord(c.ev_smooth[2], s);
+        enqueue_smooth<T>(c, L, R, c.nu2, false, s);
+        if (timed && d == c.D) cudaEventRecord(c.ev_smooth[3], s);
+    }
+}
+
+// one defect-correction step: x += Vcycle(r); r = b - A x; norms(r)
+void enqueue_iteration(Ctx &c, int R, int precision, cudaStream_t s) {
+    DevLevel &F = c.lev[c.D];
+    const int64_t m = (int64_t)F.n * R;
+    if (precision == LBMG_MIXED) {
+        launch_to_float(c.rs, F.b32, m, s);
+        cudaMemsetAsync(F.x32, 0, m * sizeof(float), s);
+        enqueue_vcycle<float>(c, R, s, true);
+        launch_add_float(c.xs, F.x32, m, s);
+    } else {
+        cudaMemcpyAsync(F.b64, c.rs, m * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        cudaMemsetAsync(F.x64, 0, m * sizeof(double), s);
+        enqueue_vcycle<double>(c, R, s, true);
+        launch_add_double(c.xs, F.x64, m, s);
+    }
+    launch_residual<double>(F, F.A64, c.bs, c.xs, c.rs, R, s);
+    launch_norms(c.rs, F.n, R, c.norm_part, c.norm_out, s);
+}
+
+int get_graph(lbmg_handle h, int R, int precision, cudaGraphExec_t *out) {
+    Ctx &c = h->c;
+    GraphCache &g = c.graph;
+    if (g.exec && g.R == R && g.precision == precision && g.nu1 == c.nu1 && g.nu2 == c.nu2 && g.smoother == c.smoother) {
+        *out = g.exec;
+        return LBMG_OK;
+    }
+    if (g.exec) { cudaGraphExecDestroy(g.exec); g.exec = nullptr; }
+    LBMG_CK(cudaStreamBeginCapture(c.capture_stream, cudaStreamCaptureModeThreadLocal));
+    enqueue_iteration(c, R, precision, c.capture_stream);
+    cudaGraph_t graph = nullptr;
+    LBMG_CK(cudaStreamEndCapture(c.capture_stream, &graph));
+    cudaError_t e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        g_cuda_err = std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e);
+        g.exec = nullptr;
+        return LBMG_CUDA_ERROR;
+    }
+    g.R = R; g.precision = precision; g.nu1 = c.nu1; g.nu2 = c.nu2; g.smoother = c.smoother;
+    *out = g.exec;
+    return LBMG_OK;
+}
+
+int read_norms(lbmg_handle h, int R, cudaStream_t s, double *out4) {
+    LBMG_CK(cudaMemcpyAsync(h->c.h_norm, h->c.norm_out, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    LBMG_CK(cudaStreamSynchronize(s));
+    for (int r = 0; r < 4; r++) out4[r] = r < R ? h->c.h_norm[r] : 0.0;
+    return LBMG_OK;
+}
+
+int check_level(lbmg_handle h, int d) {
+    if (!h) return LBMG_INVALID_ARG;
+    if (d < h->c.d0 || d > h->c.D) return LBMG_INVALID_ARG;
+    return LBMG_OK;
+}
+
+int upload_hierarchy(lbmg_handle h) {
+    Ctx &c = h->c;
+    HostHierarchy &H = c.host;
+    c.D = H.D; c.d0 = H.d0; c.nv = H.nv; c.nt = H.nt; c.nfrag = H.nfrag;
+    if (H.lev[H.d0].ndof > kMaxCoarse) return LBMG_INVALID_ARG;
+    for (int d = c.d0; d <= c.D; d++) {
+        HostLevel &hl = H.lev[d];
+        DevLevel &L = c.lev[d];
+        L.d = d;
+        L.n = hl.ndof;
+        L.nnz = hl.rp.empty() ? 0 : hl.rp[hl.ndof];
+        for (int q = 0; q < 9; q++) L.cs[q] = hl.colour_start[q];
+        LBMG_TRY(h->upload(&L.rp, hl.rp));
+        LBMG_TRY(h->upload(&L.ci, hl.ci));
+        LBMG_TRY(h->alloc(&L.M, L.nnz));
+        LBMG_TRY(h->alloc(&L.L, L.nnz));
+        LBMG_TRY(h->alloc(&L.A64, L.nnz));
+        LBMG_TRY(h->alloc(&L.A32, L.nnz));
+        LBMG_TRY(h->alloc(&L.dinv64, L.n));
+        LBMG_TRY(h->alloc(&L.dinv32, L.n));
+        if (d > c.d0) {
+            LBMG_TRY(h->upload(&L.par, hl.par));
+            LBMG_TRY(h->upload(&L.npl2, hl.npar_log2));
+        }
+        if (d < c.D) {
+            LBMG_TRY(h->upload(&L.crp, hl.crp));
+            LBMG_TRY(h->upload(&L.cch, hl.cch));
+            LBMG_TRY(h->upload(&L.grp, hl.grp));
+            LBMG_TRY(h->upload(&L.gidx, hl.gidx));
+        }
+        const size_t v4 = 4 * (size_t)L.n;
+        LBMG_TRY(h->alloc(&L.x64, v4));
+        LBMG_TRY(h->alloc(&L.b64, v4));
+        LBMG_TRY(h->alloc(&L.r64, v4));
+        LBMG_TRY(h->alloc(&L.x32, v4));
+        LBMG_TRY(h->alloc(&L.b32, v4));
+        LBMG_TRY(h->alloc(&L.r32, v4));
+    }
+    LBMG_TRY(h->upload(&c.poly, H.frag_poly));
+    LBMG_TRY(h->upload(&c.pstart, H.frag_pstart));
+    LBMG_TRY(h->upload(&c.ftri, H.frag_tri));
+    LBMG_TRY(h->upload(&c.fvox, H.frag_vox));
+    LBMG_TRY(h->upload(&c.fdof, H.frag_dof));
+    LBMG_TRY(h->upload(&c.tnormal, H.tri_normal));
+    LBMG_TRY(h->upload(&c.Vg, H.Vg));
+    LBMG_TRY(h->upload(&c.F, H.F));
+    LBMG_TRY(h->upload(&c.arp, H.arp));
+    LBMG_TRY(h->upload(&c.aidx, H.aidx));
+    LBMG_TRY(h->upload(&c.rrp, H.rrp));
+    LBMG_TRY(h->upload(&c.ridx, H.ridx));
+    LBMG_TRY(h->upload(&c.vdof, H.vdof));
+    LBMG_TRY(h->upload(&c.vw, H.vw));
+    LBMG_TRY(h->alloc(&c.moments, 27 * (size_t)c.nfrag));
+    LBMG_TRY(h->alloc(&c.stage, 72 * (size_t)c.nfrag));
+    LBMG_TRY(h->alloc(&c.stage_rhs, 32 * (size_t)c.nfrag));
+    const int n0 = c.lev[c.d0].n;
+    LBMG_TRY(h->alloc(&c.cdense, (size_t)n0 * n0));
+    LBMG_TRY(h->alloc(&c.cinv64, (size_t)n0 * n0));
+    LBMG_TRY(h->alloc(&c.cinv32, (size_t)n0 * n0));
+    LBMG_TRY(h->alloc(&c.flag, 1));
+    const size_t nD = (size_t)c.lev[c.D].n;
+    LBMG_TRY(h->alloc(&c.xs, 4 * nD));
+    LBMG_TRY(h->alloc(&c.bs, 4 * nD));
+    LBMG_TRY(h->alloc(&c.rs, 4 * nD));
+    LBMG_TRY(h->alloc(&c.norm_part, 4 * (size_t)kNormBlocks));
+    LBMG_TRY(h->alloc(&c.norm_out, 8));
+    h->io_cap = 4 * std::max(nD, (size_t)c.nv);
+    LBMG_TRY(h->alloc(&c.dev_io, 2 * h->io_cap));
+    LBMG_CK(cudaMallocHost((void **)&c.h_norm, 8 * sizeof(double)));
+    LBMG_CK(cudaMallocHost((void **)&h->h_flag, sizeof(int)));
+    LBMG_CK(cudaStreamCreateWithFlags(&c.capture_stream, cudaStreamNonBlocking));
+    LBMG_CK(cudaEventCreate(&c.ev0));
+    LBMG_CK(cudaEventCreate(&c.ev1));
+    for (int q = 0; q < 4; q++) LBMG_CK(cudaEventCreate(&c.ev_smooth[q]));
+    return LBMG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *lbmg_status_string(int code) {
+    switch (code) {
+        case LBMG_OK: return "ok";
+        case LBMG_INVALID_ARG: return "invalid argument";
+        case LBMG_DEGENERATE_MESH: return "degenerate mesh";
+        case LBMG_OUT_OF_MEMORY: return "out of memory";
+        case LBMG_NOT_CONVERGED: return "not converged";
+        case LBMG_NOT_ASSEMBLED: return "not assembled";
+        case LBMG_COARSE_FACTOR: return "coarse factorisation failed";
+        case LBMG_CUDA_ERROR: return "CUDA error";
+        case LBMG_DIVERGED: return "diverged";
+        default: return "unknown status";
+    }
+}
+
+const char *lbmg_last_cuda_error(void) { return g_cuda_err.c_str(); }
+
+void lbmg_default_options(lbmg_options *o) {
+    if (!o) return;
+    o->min_depth = -1;
+    o->coarse_max = 160;
+    o->nu1 = 2;
+    o->nu2 = 2;
+    o->smoother = LBMG_GS_COLOURED;
+    o->jacobi_omega = 0.6;
+    o->split = 1;
+    o->threads = 0;
+}
+
+int lbmg_build_hierarchy(const double *V, int nv, const int *F, int nt, int depth, const lbmg_options *opt,
+                         lbmg_handle *out) {
+    if (!out || !V || !F) return LBMG_INVALID_ARG;
+    *out = nullptr;
+    lbmg_options o;
+    lbmg_default_options(&o);
+    if (opt) o = *opt;
+    if (o.nu1 < 0 || o.nu2 < 0 || o.coarse_max < 1 || o.coarse_max > kMaxCoarse) return LBMG_INVALID_ARG;
+    if (o.smoother != LBMG_GS_COLOURED && o.smoother != LBMG_JACOBI) return LBMG_INVALID_ARG;
+    lbmg_ctx *h = new (std::nothrow) lbmg_ctx();
+    if (!h) return LBMG_OUT_OF_MEMORY;
+    std::string err;
+    int st;
+    try {
+        st = build_host_hierarchy(V, nv, F, nt, depth, o.min_depth, o.coarse_max, o.split, o.threads, h->c.host, err);
+    } catch (const std::bad_alloc &) {
+        st = LBMG_OUT_OF_MEMORY;
+    } catch (...) {
+        st = LBMG_INVALID_ARG;
+    }
+    if (st != 0) { delete h; return st; }
+    h->c.nu1 = o.nu1;
+    h->c.nu2 = o.nu2;
+    h->c.smoother = o.smoother;
+    h->c.omega = o.jacobi_omega;
+    st = upload_hierarchy(h);
+    if (st != 0) { delete h; return st; }
+    *out = h;
+    return LBMG_OK;
+}
+
+void lbmg_destroy(lbmg_handle h) { delete h; }
+
+int lbmg_levels(lbmg_handle h, int *min_depth, int *depth) {
+    if (!h) return LBMG_INVALID_ARG;
+    if (min_depth) *min_depth = h->c.d0;
+    if (depth) *depth = h->c.D;
+    return LBMG_OK;
+}
+
+int lbmg_level_info(lbmg_handle h, int d, long *ndof, long *nnz, long *nfrag) {
+    LBMG_TRY(check_level(h, d));
+    if (ndof) *ndof = h->c.lev[d].n;
+    if (nnz) *nnz = (long)h->c.lev[d].nnz;
+    if (nfrag) *nfrag = d == h->c.D ? h->c.nfrag : 0;
+    return LBMG_OK;
+}
+
+int lbmg_embedding(lbmg_handle h, double *cube_side, double *center) {
+    if (!h) return LBMG_INVALID_ARG;
+    if (cube_side) *cube_side = h->c.host.S;
+    if (center) for (int a = 0; a < 3; a++) center[a] = h->c.host.center[a];
+    return LBMG_OK;
+}
+
+int lbmg_assemble(lbmg_handle h, double t, void *stream) {
+    if (!h || !(t >= 0) || !std::isfinite(t)) return LBMG_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    Ctx &c = h->c;
+    launch_fragment_moments(c, s);
+    launch_fine_gather(c, t, s);
+    for (int d = c.D - 1; d >= c.d0; d--) launch_galerkin(c, d, t, s);
+    for (int d = c.d0; d <= c.D; d++) launch_inverse_diag(c.lev[d], s);
+    launch_coarse_factor(c, s);
+    LBMG_TRY(check_launch());
+    LBMG_CK(cudaMemcpyAsync(h->h_flag, c.flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    LBMG_CK(cudaStreamSynchronize(s));
+    c.assembled = true;
+    c.t = t;
+    if (*h->h_flag != 0) return LBMG_COARSE_FACTOR;
+    return LBMG_OK;
+}
+
+int lbmg_project_rhs(lbmg_handle h, const double *f_vertex, int nrhs, double *rhs, void *stream) {
+    if (!h || !f_vertex || !rhs || nrhs < 1 || nrhs > 4) return LBMG_INVALID_ARG;
+    if (!h->c.assembled) return LBMG_NOT_ASSEMBLED;
+    cudaStream_t s = (cudaStream_t)stream;
+    const double *fv;
+    double *out;
+    bool host_out;
+    const size_t nD = (size_t)h->c.lev[h->c.D].n;
+    LBMG_TRY(input_ptr(h, f_vertex, (size_t)h->c.nv * nrhs, 0, s, &fv));
+    LBMG_TRY(output_ptr(h, rhs, nD * nrhs, 1, &out, &host_out));
+    launch_project_rhs(h->c, fv, nrhs, out, s);
+    return finish_output(rhs, out, nD * nrhs, host_out, s);
+}
+
+int lbmg_eval_vertices(lbmg_handle h, const double *x, int nrhs, double *u, void *stream) {
+    if (!h || !x || !u || nrhs < 1 || nrhs > 4) return LBMG_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t nD = (size_t)h->c.lev[h->c.D].n;
+    const double *xd;
+    double *ud;
+    bool host_out;
+    LBMG_TRY(input_ptr(h, x, nD * nrhs, 0, s, &xd));
+    LBMG_TRY(output_ptr(h, u, (size_t)h->c.nv * nrhs, 1, &ud, &host_out));
+    launch_eval_vertices(h->c, xd, nrhs, ud, s);
+    return finish_output(u, ud, (size_t)h->c.nv * nrhs, host_out, s);
+}
+
+static int solve_impl(lbmg_handle h, const double *rhs, double *x, int nrhs, double tol, int max_cycles,
+                      int precision, lbmg_stats *stats, void *stream, bool check) {
+    if (!h || !rhs || !x || nrhs < 1 || nrhs > 4 || max_cycles < 0) return LBMG_INVALID_ARG;
+    if (precision != LBMG_FP64 && precision != LBMG_MIXED) return LBMG_INVALID_ARG;
+    if (!h->c.assembled) return LBMG_NOT_ASSEMBLED;
+    Ctx &c = h->c;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int R = stride_for(nrhs);
+    DevLevel &Fl = c.lev[c.D];
+    const size_t cnt = (size_t)Fl.n * nrhs;
+    const double *rd, *xin;
+    double *xout;
+    bool host_out;
+    LBMG_TRY(input_ptr(h, rhs, cnt, 0, s, &rd));
+    LBMG_TRY(input_ptr(h, x, cnt, 1, s, &xin));
+    LBMG_TRY(output_ptr(h, x, cnt, 1, &xout, &host_out));
+    cudaGraphExec_t exec;
+    LBMG_TRY(get_graph(h, R, precision, &exec));
+    LBMG_CK(cudaEventRecord(c.ev0, s));
+    launch_pack(rd, Fl.n, nrhs, R, c.bs, s);
+    launch_pack(xin, Fl.n, nrhs, R, c.xs, s);
+    launch_residual<double>(Fl, Fl.A64, c.bs, c.xs, c.rs, R, s);
+    double nb[4] = {0, 0, 0, 0}, nr[4] = {0, 0, 0, 0}, r0[4] = {0, 0, 0, 0};
+    int cycles = 0, status = LBMG_OK;
+    float smooth_ms = 0.0f;
+    bool conv = false;
+    if (check) {
+        launch_norms(c.bs, Fl.n, R, c.norm_part, c.norm_out, s);
+        LBMG_TRY(read_norms(h, R, s, nb));
+        launch_norms(c.rs, Fl.n, R, c.norm_part, c.norm_out, s);
+        LBMG_TRY(read_norms(h, R, s, nr));
+        auto rel = [&](int r) { return nb[r] > 0 ? std::sqrt(nr[r] / nb[r]) : 0.0; };
+        for (int r = 0; r < nrhs; r++) r0[r] = rel(r);
+        for (;;) {
+            conv = true;
+            bool bad = false;
+            for (int r = 0; r < nrhs; r++) {
+                const double v = rel(r);
+                if (!(v <= tol)) conv = false;
+                if (!std::isfinite(v) || v > 1e6 * std::max(r0[r], 1e-300)) bad = true;
+            }
+            if (bad) { status = LBMG_DIVERGED; break; }
+            if (conv || cycles >= max_cycles) break;
+            LBMG_CK(cudaGraphLaunch(exec, s));
+            LBMG_TRY(read_norms(h, R, s, nr));
+            if (c.D > c.d0) {
+                float a0 = 0, a1 = 0;
+                if (cudaEventElapsedTime(&a0, c.ev_smooth[0], c.ev_smooth[1]) != cudaSuccess ||
+                    cudaEventElapsedTime(&a1, c.ev_smooth[2], c.ev_smooth[3]) != cudaSuccess) {
+                    cudaGetLastError();
+                    a0 = a1 = 0.0f;
+                }
+                smooth_ms += a0 + a1;
+            }
+            cycles++;
+        }
+        if (!conv && status == LBMG_OK) status = LBMG_NOT_CONVERGED;
+        if (stats) {
+            stats->cycles = cycles;
+            stats->converged = conv ? 1 : 0;
+            for (int r = 0; r < 4; r++) {
+                stats->rel_residual[r] = r < nrhs ? rel(r) : 0.0;
+                stats->initial_residual[r] = r < nrhs ? r0[r] : 0.0;
+            }
+        }
+    } else {
+        for (int k = 0; k < max_cycles; k++) LBMG_CK(cudaGraphLaunch(exec, s));
+        cycles = max_cycles;
+    }
+    launch_unpack(c.xs, Fl.n, nrhs, R, xout, s);
+    LBMG_CK(cudaEventRecord(c.ev1, s));
+    LBMG_TRY(finish_output(x, xout, cnt, host_out, s));
+    if (stats) {
+        LBMG_CK(cudaEventSynchronize(c.ev1));
+        float ms = 0;
+        cudaEventElapsedTime(&ms, c.ev0, c.ev1);
+        stats->ms_total = ms;
+        stats->ms_fine_smooth = smooth_ms;
+        if (!check) stats->cycles = cycles;
+    }
+    return status;
+}
+
+int lbmg_solve(lbmg_handle h, const double *rhs, double *x, int nrhs, double tol, int max_cycles, int precision,
+               lbmg_stats *stats, void *stream) {
+    if (!(tol >= 0)) return LBMG_INVALID_ARG;
+    return solve_impl(h, rhs, x, nrhs, tol, max_cycles, precision, stats, stream, true);
+}
+
+int lbmg_vcycles(lbmg_handle h, const double *rhs, double *x, int nrhs, int cycles, int precision, void *stream) {
+    return solve_impl(h, rhs, x, nrhs, 0.0, cycles, precision, nullptr, stream, false);
+}
+
+int lbmg_residual(lbmg_handle h, int d, const double *rhs, const double *x, double *r, int nrhs, void *stream) {
+    LBMG_TRY(check_level(h, d));
+    if (!rhs || !x || !r || nrhs < 1 || nrhs > 4) return LBMG_INVALID_ARG;
+    if (!h->c.assembled) return LBMG_NOT_ASSEMBLED;
+    cudaStream_t s = (cudaStream_t)stream;
+    DevLevel &L = h->c.lev[d];
+    const int R = stride_for(nrhs);
+    const size_t cnt = (size_t)L.n * nrhs;
+    const double *bd, *xd;
+    double *rd;
+    bool host_out;
+    LBMG_TRY(input_ptr(h, rhs, cnt, 0, s, &bd));
+    launch_pack(bd, L.n, nrhs, R, L.b64, s);
+    LBMG_TRY(input_ptr(h, x, cnt, 1, s, &xd));
+    launch_pack(xd, L.n, nrhs, R, L.x64, s);
+    launch_residual<double>(L, L.A64, L.b64, L.x64, L.r64, R, s);
+    LBMG_TRY(output_ptr(h, r, cnt, 0, &rd, &host_out));
+    launch_unpack(L.r64, L.n, nrhs, R, rd, s);
+    return finish_output(r, rd, cnt, host_out, s);
+}
+
+int lbmg_smooth(lbmg_handle h, int d, const double *rhs, double *x, int nrhs, int sweeps, int precision, void *stream) {
+    LBMG_TRY(check_level(h, d));
+    if (!rhs || !x || nrhs < 1 || nrhs > 4 || sweeps < 0) return LBMG_INVALID_ARG;
+    if (precision != LBMG_FP64 && precision != LBMG_MIXED) return LBMG_INVALID_ARG;
+    if (!h->c.assembled) return LBMG_NOT_ASSEMBLED;
+    cudaStream_t s = (cudaStream_t)stream;
+    DevLevel &L = h->c.lev[d];
+    const int R = stride_for(nrhs);
+    const size_t cnt = (size_t)L.n * nrhs;
+    const int64_t m = (int64_t)L.n * R;
+    const double *bd, *xd;
+    LBMG_TRY(input_ptr(h, rhs, cnt, 0, s, &bd));
+    launch_pack(bd, L.n, nrhs, R, L.b64, s);
+    LBMG_TRY(input_ptr(h, x, cnt, 1, s, &xd));
+    launch_pack(xd, L.n, nrhs, R, L.x64, s);
+    if (precision == LBMG_MIXED) {
+        launch_to_float(L.b64, L.b32, m, s);
+        launch_to_float(L.x64, L.x32, m, s);
+        enqueue_smooth<float>(h->c, L, R, sweeps, true, s);
+        if (m) to_double_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(L.x32, L.x64, m);
+    } else {
+        enqueue_smooth<double>(h->c, L, R, sweeps, true, s);
+    }
+    double *xo;
+    bool host_out;
+    LBMG_TRY(output_ptr(h, x, cnt, 1, &xo, &host_out));
+    launch_unpack(L.x64, L.n, nrhs, R, xo, s);
+    return finish_output(x, xo, cnt, host_out, s);
+}
+
+int lbmg_restrict(lbmg_handle h, int d, const double *r_fine, double *r_coarse, int nrhs, void *stream) {
+    LBMG_TRY(check_level(h, d));
+    if (d == h->c.d0 || !r_fine || !r_coarse || nrhs < 1 || nrhs > 4) return LBMG_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    DevLevel &Lf = h->c.lev[d], &Lc = h->c.lev[d - 1];
+    const int R = stride_for(nrhs);
+    const double *rf;
+    LBMG_TRY(input_ptr(h, r_fine, (size_t)Lf.n * nrhs, 0, s, &rf));
+    launch_pack(rf, Lf.n, nrhs, R, Lf.r64, s);
+    launch_restrict<double>(Lc, Lf.r64, Lc.b64, R, s);
+    double *out;
+    bool host_out;
+    LBMG_TRY(output_ptr(h, r_coarse, (size_t)Lc.n * nrhs, 1, &out, &host_out));
+    launch_unpack(Lc.b64, Lc.n, nrhs, R, out, s);
+    return finish_output(r_coarse, out, (size_t)Lc.n * nrhs, host_out, s);
+}
+
+int lbmg_prolong_add(lbmg_handle h, int d, const double *x_coarse, double *x_fine, int nrhs, void *stream) {
+    LBMG_TRY(check_level(h, d));
+    if (d == h->c.d0 || !x_coarse || !x_fine || nrhs < 1 || nrhs > 4) return LBMG_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    DevLevel &Lf = h->c.lev[d], &Lc = h->c.lev[d - 1];
+    const int R = stride_for(nrhs);
+    const double *xc, *xf;
+    LBMG_TRY(input_ptr(h, x_coarse, (size_t)Lc.n * nrhs, 0, s, &xc));
+    launch_pack(xc, Lc.n, nrhs, R, Lc.x64, s);
+    LBMG_TRY(input_ptr(h, x_fine, (size_t)Lf.n * nrhs, 1, s, &xf));
+    launch_pack(xf, Lf.n, nrhs, R, Lf.x64, s);
+    launch_prolong_add<double>(Lf, Lc.x64, Lf.x64, R, s);
+    double *out;
+    bool host_out;
+    LBMG_TRY(output_ptr(h, x_fine, (size_t)Lf.n * nrhs, 1, &out, &host_out));
+    launch_unpack(Lf.x64, Lf.n, nrhs, R, out, s);
+    return finish_output(x_fine, out, (size_t)Lf.n * nrhs, host_out, s);
+}
+
+int lbmg_launch_counts(lbmg_handle h, int precision, int *assemble, int *project_rhs, int *per_cycle,
+                       int *solve_fixed) {
+    if (!h) return LBMG_INVALID_ARG;
+    const Ctx &c = h->c;
+    const int levels = c.D - c.d0;
+    if (assemble) *assemble = 2 + levels + (levels + 1) + 3;
+    if (project_rhs) *project_rhs = 2;
+    int cyc = 1;   // coarse apply
+    for (int d = c.d0 + 1; d <= c.D; d++) {
+        int per_sweep = 2;
+        if (c.smoother != LBMG_JACOBI) {
+            per_sweep = 0;
+            for (int q = 0; q < 8; q++) per_sweep += c.lev[d].cs[q + 1] > c.lev[d].cs[q];
+        }
+        cyc += (c.nu1 + c.nu2) * per_sweep + 3;   // sweeps, residual, restriction, prolongation
+    }
+    cyc += (precision == LBMG_MIXED ? 2 : 1) + 1 + 2;   // conversion/update, FP64 residual, norms
+    if (per_cycle) *per_cycle = cyc;
+    if (solve_fixed) *solve_fixed = 2 + 1 + 2 + 2 + 1;  // packs, residual, two norms, unpack
+    return LBMG_OK;
+}
+
+int lbmg_get_dofs(lbmg_handle h, int d, int *corner, int *mintri) {
+    LBMG_TRY(check_level(h, d));
+    const HostLevel &L = h->c.host.lev[d];
+    if (corner) std::memcpy(corner, L.corner.data(), L.corner.size() * sizeof(int));
+    if (mintri) std::memcpy(mintri, L.mintri.data(), L.mintri.size() * sizeof(int));
+    return LBMG_OK;
+}
+
+int lbmg_get_matrix(lbmg_handle h, int d, int *rowptr, int *col, double *M, double *L) {
+    LBMG_TRY(check_level(h, d));
+    const HostLevel &hl = h->c.host.lev[d];
+    if (rowptr) std::memcpy(rowptr, hl.rp.data(), hl.rp.size() * sizeof(int));
+    if (col) std::memcpy(col, hl.ci.data(), hl.ci.size() * sizeof(int));
+    if (M || L) {
+        if (!h->c.assembled) return LBMG_NOT_ASSEMBLED;
+        const DevLevel &dl = h->c.lev[d];
+        if (M) LBMG_CK(cudaMemcpy(M, dl.M, dl.nnz * sizeof(double), cudaMemcpyDeviceToHost));
+        if (L) LBMG_CK(cudaMemcpy(L, dl.L, dl.nnz * sizeof(double), cudaMemcpyDeviceToHost));
+    }
+    return LBMG_OK;
+}
+
+int lbmg_get_prolongation(lbmg_handle h, int d, int *parents, double *weights) {
+    LBMG_TRY(check_level(h, d));
+    if (d == h->c.d0) return LBMG_INVALID_ARG;
+    const HostLevel &L = h->c.host.lev[d];
+    for (int i = 0; i < L.ndof; i++) {
+        const int np = 1 << L.npar_log2[i];
+        for (int q = 0; q < 8; q++) {
+            if (parents) parents[8 * (size_t)i + q] = q < np ? L.par[8 * (size_t)i + q] : -1;
+            if (weights) weights[8 * (size_t)i + q] = q < np ? 1.0 / np : 0.0;
+        }
+    }
+    return LBMG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,72 @@
+// hier.h -- host-side hierarchy of connectivity-split trilinear B-spline spaces
+// (Chuang & Kazhdan, Sections 3.2 and 4), in the layout the CUDA kernels use.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace lbmg {
+
+constexpr int kMaxDepth = 12;
+constexpr double kFragTau = 1e-12;   // pieces of at most this area (finest voxel faces) are ignored
+constexpr int kPackShift = 28;       // packed list entry: index | (log2 weight denominator << 28)
+constexpr uint32_t kPackMask = (1u << kPackShift) - 1u;
+
+struct HostLevel {
+    int d = 0;
+    int ndof = 0;
+    int colour_start[9] = {0};          // dofs sorted by corner parity colour 0..7
+    std::vector<int32_t> corner;        // [ndof*3] grid corner index at depth d
+    std::vector<int32_t> mintri;        // [ndof] smallest triangle of the component
+    // (corner Morton key, triangle) -> dof, sorted by key then triangle
+    std::vector<uint64_t> ct_key;
+    std::vector<int32_t> ct_tri, ct_dof;
+    // sparsity pattern of A_d, columns sorted per row
+    std::vector<int32_t> rp, ci;
+    // prolongation into this level from depth d-1: parents [ndof*8] (-1 pad), log2 #parents
+    std::vector<int32_t> par;
+    std::vector<int8_t> npar_log2;
+    // as a coarse level: children of each dof, entries fine_dof | (log2 #parents << 28)
+    std::vector<int32_t> crp;
+    std::vector<uint32_t> cch;
+    // as a coarse level: Galerkin contributions per stored entry,
+    // entries fine_nnz | ((log2 np_i + log2 np_l) << 28)
+    std::vector<int64_t> grp;
+    std::vector<uint32_t> gidx;
+};
+
+struct HostHierarchy {
+    int D = 0, d0 = 0, nv = 0, nt = 0, split = 1;
+    double S = 0, center[3] = {0, 0, 0}, sigma = 0;   // cube side, centre, physical length per finest unit
+    std::vector<double> Vg;                           // vertices in finest-grid units
+    std::vector<int32_t> F;
+    std::vector<double> tri_normal;                   // unit normals [nt*3]
+    std::vector<HostLevel> lev;                       // indexed by depth
+    // finest-level fragments, sorted by voxel Morton key then triangle
+    int nfrag = 0;
+    std::vector<int32_t> frag_tri, frag_vox;          // vox [nfrag*3]
+    std::vector<int32_t> frag_pstart;                 // [nfrag+1] into frag_poly (vertices)
+    std::vector<double> frag_poly;                    // polygon vertices in voxel-local coordinates [0,1]^3
+    std::vector<int32_t> frag_dof;                    // [nfrag*8] dof of each voxel corner (bit a = axis)
+    // finest assembly: per stored entry, list of fragment*36 + local pair
+    std::vector<int64_t> arp;
+    std::vector<uint32_t> aidx;
+    // finest right-hand side: per dof, list of fragment*8 + corner
+    std::vector<int64_t> rrp;
+    std::vector<uint32_t> ridx;
+    // vertex evaluation at the finest level: [nv*8] dof (-1 none) and hat value
+    std::vector<int32_t> vdof;
+    std::vector<double> vw;
+};
+
+// Local index of the unordered corner pair (a, b), a <= b, in the 36 upper-triangular pairs.
+inline int pair_index(int a, int b) {
+    if (a > b) { int t = a; a = b; b = t; }
+    return a * 8 - a * (a - 1) / 2 + (b - a);
+}
+
+// Returns 0 on success, else an lbmg status code with a message in err.
+int build_host_hierarchy(const double *V, int nv, const int *F, int nt, int depth, int min_depth,
+                         int coarse_max, int split, int threads, HostHierarchy &H, std::string &err);
+
+}  // namespace lbmg

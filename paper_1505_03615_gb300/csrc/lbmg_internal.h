@@ -1,0 +1,107 @@
+// lbmg_internal.h -- device-side state of a hierarchy and kernel launch wrappers.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+
+#include "hier.h"
+
+namespace lbmg {
+
+constexpr int kNQ = 4;            // Gauss-Legendre points per direction of the collapsed triangle rule
+constexpr int kMaxCoarse = 2048;  // largest coarsest level factored densely
+constexpr int kNormBlocks = 256;  // partial sums of the two-pass norm reduction
+
+struct DevLevel {
+    int d = 0, n = 0;
+    int64_t nnz = 0;
+    int cs[9] = {0};                       // colour ranges
+    int *rp = nullptr, *ci = nullptr;
+    double *M = nullptr, *L = nullptr, *A64 = nullptr;
+    float *A32 = nullptr;
+    double *dinv64 = nullptr;
+    float *dinv32 = nullptr;
+    int *par = nullptr;                    // [n*8] parents at depth d-1, -1 pad
+    int8_t *npl2 = nullptr;                // log2 #parents
+    int *crp = nullptr;                    // children lists (this level as coarse)
+    uint32_t *cch = nullptr;
+    int64_t *grp = nullptr;                // Galerkin lists (this level as coarse)
+    uint32_t *gidx = nullptr;
+    // V-cycle work vectors, room for [n][4]
+    double *x64 = nullptr, *b64 = nullptr, *r64 = nullptr;
+    float *x32 = nullptr, *b32 = nullptr, *r32 = nullptr;
+};
+
+struct GraphCache {
+    cudaGraphExec_t exec = nullptr;
+    int R = 0, precision = -1, nu1 = -1, nu2 = -1, smoother = -1;
+};
+
+struct Ctx {
+    HostHierarchy host;
+    int D = 0, d0 = 0, nv = 0, nt = 0, nfrag = 0;
+    int nu1 = 2, nu2 = 2, smoother = 0;
+    double omega = 0.6;
+    DevLevel lev[kMaxDepth + 1];
+    // finest-level geometry
+    double *poly = nullptr;
+    int *pstart = nullptr, *ftri = nullptr, *fvox = nullptr, *fdof = nullptr;
+    double *tnormal = nullptr, *Vg = nullptr;
+    int *F = nullptr;
+    int64_t *arp = nullptr, *rrp = nullptr;
+    uint32_t *aidx = nullptr, *ridx = nullptr;
+    double *moments = nullptr;   // [nfrag*27]
+    double *stage = nullptr;     // [nfrag*36*2]  (M, L) per local pair
+    double *stage_rhs = nullptr; // [nfrag*8*4]
+    int *vdof = nullptr;
+    double *vw = nullptr;
+    // coarsest level
+    double *cdense = nullptr;    // factor workspace n0*n0
+    double *cinv64 = nullptr;
+    float *cinv32 = nullptr;
+    int *flag = nullptr;         // device status word (coarse factor)
+    // finest FP64 solve vectors, room for [n][4]
+    double *xs = nullptr, *bs = nullptr, *rs = nullptr;
+    double *norm_part = nullptr, *norm_out = nullptr;
+    double *h_norm = nullptr;    // pinned [8]
+    // staging of user vectors (device [n][nrhs]) and pinned host mirrors
+    double *dev_io = nullptr;
+    size_t dev_io_bytes = 0;
+    double *pin_io = nullptr;
+    size_t pin_io_bytes = 0;
+    bool assembled = false;
+    double t = 0;
+    cudaStream_t capture_stream = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEvent_t ev_smooth[4] = {nullptr, nullptr, nullptr, nullptr};   // around finest-level smoothing in the cycle graph
+    GraphCache graph;
+};
+
+// ----- kernels (assemble.cu) -----
+void launch_fragment_moments(const Ctx &c, cudaStream_t s);
+void launch_fine_gather(const Ctx &c, double t, cudaStream_t s);
+void launch_galerkin(const Ctx &c, int dc, double t, cudaStream_t s);
+void launch_inverse_diag(const DevLevel &L, cudaStream_t s);
+void launch_project_rhs(const Ctx &c, const double *fv, int nrhs, double *rhs_out, cudaStream_t s);
+void launch_eval_vertices(const Ctx &c, const double *x, int nrhs, double *u, cudaStream_t s);
+
+// ----- kernels (relax.cu) -----
+// vectors below are [n][R] with stride R in {1, 2, 4} (3 right-hand sides padded to 4)
+template <class T> void launch_smooth_colour(const DevLevel &L, int colour, const T *A, const T *dinv,
+                                             const T *b, T *x, int R, cudaStream_t s);
+template <class T> void launch_residual(const DevLevel &L, const T *A, const T *b, const T *x, T *r, int R,
+                                        cudaStream_t s);
+template <class T> void launch_jacobi_update(const DevLevel &L, const T *dinv, const T *r, T *x, T omega, int R,
+                                             cudaStream_t s);
+template <class T> void launch_restrict(const DevLevel &Lc, const T *rf, T *bc, int R, cudaStream_t s);
+template <class T> void launch_prolong_add(const DevLevel &Lf, const T *xc, T *xf, int R, cudaStream_t s);
+template <class T> void launch_coarse_apply(int n, const T *inv, const T *b, T *x, int R, cudaStream_t s);
+void launch_coarse_factor(const Ctx &c, cudaStream_t s);
+void launch_norms(const double *v, int n, int R, double *part, double *out, cudaStream_t s);
+void launch_pack(const double *user, int n, int nrhs, int R, double *v, cudaStream_t s);
+void launch_unpack(const double *v, int n, int nrhs, int R, double *user, cudaStream_t s);
+void launch_to_float(const double *a, float *b, int64_t n, cudaStream_t s);
+void launch_add_float(double *x, const float *e, int64_t n, cudaStream_t s);
+void launch_add_double(double *x, const double *e, int64_t n, cudaStream_t s);
+
+}  // namespace lbmg

@@ -1,0 +1,417 @@
+// relax.cu -- multigrid kernels of the V-cycle (Chuang & Kazhdan, Sections 4.3
+// and 5.2): coloured Gauss-Seidel and weighted-Jacobi relaxation, residual,
+// restriction P^T r, prolongation x += P e, the coarsest-level dense solve, and
+// small vector kernels.  Vectors are row-major [n][R], R in {1, 2, 4}.
+//
+// Rows of one colour (one corner parity class) never couple, because supports
+// of equal-parity corners are disjoint and the components of one corner are
+// disjoint, so a colour is relaxed in parallel with exact Gauss-Seidel updates.
+// A group of G threads shares one matrix row.
+#include "lbmg_internal.h"
+
+namespace lbmg {
+
+template <class T, int R>
+__device__ __forceinline__ void load_vec(const T *__restrict__ p, T (&v)[R]) {
+#pragma unroll
+    for (int r = 0; r < R; r++) v[r] = p[r];
+}
+template <>
+__device__ __forceinline__ void load_vec<float, 4>(const float *__restrict__ p, float (&v)[4]) {
+    const float4 q = __ldg(reinterpret_cast<const float4 *>(p));
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+template <>
+__device__ __forceinline__ void load_vec<double, 2>(const double *__restrict__ p, double (&v)[2]) {
+    const double2 q = __ldg(reinterpret_cast<const double2 *>(p));
+    v[0] = q.x; v[1] = q.y;
+}
+template <>
+__device__ __forceinline__ void load_vec<double, 4>(const double *__restrict__ p, double (&v)[4]) {
+    const double2 q0 = __ldg(reinterpret_cast<const double2 *>(p));
+    const double2 q1 = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+    v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+}
+
+// x may be written by other rows of the same launch only at rows of the same
+// colour, which this row never reads, so plain (non-__ldg) loads are not needed
+// for correctness; __ldg is avoided anyway for x because the GS kernel writes it.
+template <class T, int R>
+__device__ __forceinline__ void load_x(const T *p, T (&v)[R]) {
+#pragma unroll
+    for (int r = 0; r < R; r++) v[r] = p[r];
+}
+
+template <class T, int R, int G>
+__device__ __forceinline__ void row_dot(int row, const int *__restrict__ rp, const int *__restrict__ ci,
+                                        const T *__restrict__ A, const T *x, int lane, T (&acc)[R]) {
+#pragma unroll
+    for (int r = 0; r < R; r++) acc[r] = T(0);
+    const int k1 = rp[row + 1];
+    for (int k = rp[row] + lane; k < k1; k += G) {
+        const int j = __ldg(ci + k);
+        const T a = __ldg(A + k);
+        T xv[R];
+        load_x<T, R>(x + (size_t)j * R, xv);
+#pragma unroll
+        for (int r = 0; r < R; r++) acc[r] = fma(a, xv[r], acc[r]);
+    }
+}
+
+template <class T, int R, int G>
+__device__ __forceinline__ void group_sum(T (&acc)[R]) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1)
+#pragma unroll
+        for (int r = 0; r < R; r++) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o, G);
+}
+
+template <class T, int R, int G>
+__global__ void __launch_bounds__(256) smooth_colour_kernel(int r0, int r1, const int *__restrict__ rp,
+                                                            const int *__restrict__ ci, const T *__restrict__ A,
+                                                            const T *__restrict__ dinv, const T *__restrict__ b, T *x) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int row = r0 + tid / G, lane = tid % G;
+    T acc[R];
+    if (row < r1) row_dot<T, R, G>(row, rp, ci, A, x, lane, acc);
+    else {
+#pragma unroll
+        for (int r = 0; r < R; r++) acc[r] = T(0);
+    }
+    group_sum<T, R, G>(acc);
+    if (row < r1 && lane == 0) {
+        const T d = dinv[row];
+#pragma unroll
+        for (int r = 0; r < R; r++) x[(size_t)row * R + r] += (b[(size_t)row * R + r] - acc[r]) * d;
+    }
+}
+
+template <class T, int R, int G>
+__global__ void __launch_bounds__(256) residual_kernel(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                                                       const T *__restrict__ A, const T *__restrict__ b,
+                                                       const T *x, T *__restrict__ r) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int row = tid / G, lane = tid % G;
+    T acc[R];
+    if (row < n) row_dot<T, R, G>(row, rp, ci, A, x, lane, acc);
+    else {
+#pragma unroll
+        for (int q = 0; q < R; q++) acc[q] = T(0);
+    }
+    group_sum<T, R, G>(acc);
+    if (row < n && lane == 0) {
+#pragma unroll
+        for (int q = 0; q < R; q++) r[(size_t)row * R + q] = b[(size_t)row * R + q] - acc[q];
+    }
+}
+
+constexpr int kRowGroup = 8;   // threads per matrix row
+
+template <class T>
+void launch_smooth_colour(const DevLevel &L, int colour, const T *A, const T *dinv, const T *b, T *x, int R,
+                          cudaStream_t s) {
+    const int r0 = L.cs[colour], r1 = L.cs[colour + 1];
+    if (r1 <= r0) return;
+    const int threads = 256;
+    const unsigned blocks = (unsigned)(((int64_t)(r1 - r0) * kRowGroup + threads - 1) / threads);
+    if (R == 1) smooth_colour_kernel<T, 1, kRowGroup><<<blocks, threads, 0, s>>>(r0, r1, L.rp, L.ci, A, dinv, b, x);
+    else if (R == 2) smooth_colour_kernel<T, 2, kRowGroup><<<blocks, threads, 0, s>>>(r0, r1, L.rp, L.ci, A, dinv, b, x);
+    else smooth_colour_kernel<T, 4, kRowGroup><<<blocks, threads, 0, s>>>(r0, r1, L.rp, L.ci, A, dinv, b, x);
+}
+
+template <class T>
+void launch_residual(const DevLevel &L, const T *A, const T *b, const T *x, T *r, int R, cudaStream_t s) {
+    if (L.n == 0) return;
+    const int threads = 256;
+    const unsigned blocks = (unsigned)(((int64_t)L.n * kRowGroup + threads - 1) / threads);
+    if (R == 1) residual_kernel<T, 1, kRowGroup><<<blocks, threads, 0, s>>>(L.n, L.rp, L.ci, A, b, x, r);
+    else if (R == 2) residual_kernel<T, 2, kRowGroup><<<blocks, threads, 0, s>>>(L.n, L.rp, L.ci, A, b, x, r);
+    else residual_kernel<T, 4, kRowGroup><<<blocks, threads, 0, s>>>(L.n, L.rp, L.ci, A, b, x, r);
+}
+
+template <class T>
+__global__ void jacobi_update_kernel(int n, int R, const T *__restrict__ dinv, const T *__restrict__ r, T *x, T omega) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= (int64_t)n * R) return;
+    x[q] += omega * dinv[q / R] * r[q];
+}
+
+template <class T>
+void launch_jacobi_update(const DevLevel &L, const T *dinv, const T *r, T *x, T omega, int R, cudaStream_t s) {
+    const int64_t m = (int64_t)L.n * R;
+    if (m == 0) return;
+    jacobi_update_kernel<T><<<(unsigned)((m + 255) / 256), 256, 0, s>>>(L.n, R, dinv, r, x, omega);
+}
+
+// b_c[J] = sum over fine children i of J of r_f[i] / #parents(i)
+template <class T, int R>
+__global__ void restrict_kernel(int nc, const int *__restrict__ crp, const uint32_t *__restrict__ cch,
+                                const T *__restrict__ rf, T *__restrict__ bc) {
+    const int J = blockIdx.x * blockDim.x + threadIdx.x;
+    if (J >= nc) return;
+    T acc[R];
+#pragma unroll
+    for (int r = 0; r < R; r++) acc[r] = T(0);
+    for (int k = crp[J]; k < crp[J + 1]; k++) {
+        const uint32_t e = __ldg(cch + k);
+        const uint32_t i = e & kPackMask;
+        const T w = T(1) / T(1u << (e >> kPackShift));
+        T v[R];
+        load_vec<T, R>(rf + (size_t)i * R, v);
+#pragma unroll
+        for (int r = 0; r < R; r++) acc[r] = fma(w, v[r], acc[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < R; r++) bc[(size_t)J * R + r] = acc[r];
+}
+
+template <class T>
+void launch_restrict(const DevLevel &Lc, const T *rf, T *bc, int R, cudaStream_t s) {
+    if (Lc.n == 0) return;
+    const unsigned blocks = (unsigned)((Lc.n + 255) / 256);
+    if (R == 1) restrict_kernel<T, 1><<<blocks, 256, 0, s>>>(Lc.n, Lc.crp, Lc.cch, rf, bc);
+    else if (R == 2) restrict_kernel<T, 2><<<blocks, 256, 0, s>>>(Lc.n, Lc.crp, Lc.cch, rf, bc);
+    else restrict_kernel<T, 4><<<blocks, 256, 0, s>>>(Lc.n, Lc.crp, Lc.cch, rf, bc);
+}
+
+// x_f[i] += (sum of parent values) / #parents(i)
+template <class T, int R>
+__global__ void prolong_add_kernel(int nf, const int *__restrict__ par, const int8_t *__restrict__ npl2,
+                                   const T *__restrict__ xc, T *__restrict__ xf) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nf) return;
+    const int np = 1 << npl2[i];
+    T acc[R];
+#pragma unroll
+    for (int r = 0; r < R; r++) acc[r] = T(0);
+    for (int q = 0; q < np; q++) {
+        const int p = __ldg(par + 8 * (size_t)i + q);
+        T v[R];
+        load_vec<T, R>(xc + (size_t)p * R, v);
+#pragma unroll
+        for (int r = 0; r < R; r++) acc[r] += v[r];
+    }
+    const T w = T(1) / T(np);
+#pragma unroll
+    for (int r = 0; r < R; r++) xf[(size_t)i * R + r] += w * acc[r];
+}
+
+template <class T>
+void launch_prolong_add(const DevLevel &Lf, const T *xc, T *xf, int R, cudaStream_t s) {
+    if (Lf.n == 0) return;
+    const unsigned blocks = (unsigned)((Lf.n + 255) / 256);
+    if (R == 1) prolong_add_kernel<T, 1><<<blocks, 256, 0, s>>>(Lf.n, Lf.par, Lf.npl2, xc, xf);
+    else if (R == 2) prolong_add_kernel<T, 2><<<blocks, 256, 0, s>>>(Lf.n, Lf.par, Lf.npl2, xc, xf);
+    else prolong_add_kernel<T, 4><<<blocks, 256, 0, s>>>(Lf.n, Lf.par, Lf.npl2, xc, xf);
+}
+
+// x = inv * b at the coarsest level, one warp per row
+template <class T, int R>
+__global__ void coarse_apply_kernel(int n, const T *__restrict__ inv, const T *__restrict__ b, T *__restrict__ x) {
+    const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (row >= n) return;
+    T acc[R];
+#pragma unroll
+    for (int r = 0; r < R; r++) acc[r] = T(0);
+    for (int j = lane; j < n; j += 32) {
+        const T a = inv[(size_t)row * n + j];
+#pragma unroll
+        for (int r = 0; r < R; r++) acc[r] = fma(a, b[(size_t)j * R + r], acc[r]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int r = 0; r < R; r++) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+    if (lane == 0) {
+#pragma unroll
+        for (int r = 0; r < R; r++) x[(size_t)row * R + r] = acc[r];
+    }
+}
+
+template <class T>
+void launch_coarse_apply(int n, const T *inv, const T *b, T *x, int R, cudaStream_t s) {
+    if (n == 0) return;
+    const unsigned blocks = (unsigned)((n * 32 + 255) / 256);
+    if (R == 1) coarse_apply_kernel<T, 1><<<blocks, 256, 0, s>>>(n, inv, b, x);
+    else if (R == 2) coarse_apply_kernel<T, 2><<<blocks, 256, 0, s>>>(n, inv, b, x);
+    else coarse_apply_kernel<T, 4><<<blocks, 256, 0, s>>>(n, inv, b, x);
+}
+
+// ---- coarsest-level dense FP64 Cholesky of A + eps Id, eps = 1e-12 mean diag ----
+__global__ void dense_from_csr_kernel(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                                      const double *__restrict__ A, double *__restrict__ D) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int j = 0; j < n; j++) D[(size_t)i * n + j] = 0.0;
+    for (int k = rp[i]; k < rp[i + 1]; k++) D[(size_t)i * n + ci[k]] = A[k];
+}
+
+__global__ void __launch_bounds__(1024) cholesky_kernel(int n, double *D, int *flag) {
+    __shared__ double s_val;
+    const int tid = threadIdx.x, nthr = blockDim.x, warp = tid >> 5, lane = tid & 31, nw = nthr >> 5;
+    if (tid == 0) {
+        double tr = 0.0;
+        for (int i = 0; i < n; i++) tr += D[(size_t)i * n + i];
+        s_val = 1e-12 * tr / (double)(n > 0 ? n : 1);
+        *flag = 0;
+    }
+    __syncthreads();
+    const double eps = s_val;
+    for (int i = tid; i < n; i += nthr) D[(size_t)i * n + i] += eps;
+    for (int j = 0; j < n; j++) {
+        __syncthreads();
+        if (tid == 0) {
+            double d = D[(size_t)j * n + j];
+            if (!(d > 0.0)) { *flag = 1; d = 1.0; }
+            s_val = sqrt(d);
+            D[(size_t)j * n + j] = s_val;
+        }
+        __syncthreads();
+        const double piv = s_val;
+        for (int i = j + 1 + tid; i < n; i += nthr) D[(size_t)i * n + j] /= piv;
+        __syncthreads();
+        for (int i = j + 1 + warp; i < n; i += nw) {
+            const double lij = D[(size_t)i * n + j];
+            for (int k = j + 1 + lane; k <= i; k += 32) D[(size_t)i * n + k] -= lij * D[(size_t)k * n + j];
+        }
+    }
+}
+
+// column c of (L L^T)^{-1}: forward then backward substitution on e_c
+__global__ void __launch_bounds__(256) cholesky_inverse_kernel(int n, const double *__restrict__ Lf,
+                                                               double *__restrict__ inv64, float *__restrict__ inv32) {
+    extern __shared__ double y[];
+    const int c = blockIdx.x, tid = threadIdx.x, nthr = blockDim.x;
+    for (int i = tid; i < n; i += nthr) y[i] = (i == c) ? 1.0 : 0.0;
+    for (int k = 0; k < n; k++) {
+        __syncthreads();
+        if (tid == 0) y[k] /= Lf[(size_t)k * n + k];
+        __syncthreads();
+        const double yk = y[k];
+        for (int i = k + 1 + tid; i < n; i += nthr) y[i] -= Lf[(size_t)i * n + k] * yk;
+    }
+    for (int k = n - 1; k >= 0; k--) {
+        __syncthreads();
+        if (tid == 0) y[k] /= Lf[(size_t)k * n + k];
+        __syncthreads();
+        const double yk = y[k];
+        for (int i = tid; i < k; i += nthr) y[i] -= Lf[(size_t)k * n + i] * yk;
+    }
+    __syncthreads();
+    for (int i = tid; i < n; i += nthr) {
+        inv64[(size_t)i * n + c] = y[i];
+        inv32[(size_t)i * n + c] = (float)y[i];
+    }
+}
+
+void launch_coarse_factor(const Ctx &c, cudaStream_t s) {
+    const DevLevel &L = c.lev[c.d0];
+    const int n = L.n;
+    dense_from_csr_kernel<<<(n + 127) / 128, 128, 0, s>>>(n, L.rp, L.ci, L.A64, c.cdense);
+    cholesky_kernel<<<1, 1024, 0, s>>>(n, c.cdense, c.flag);
+    cholesky_inverse_kernel<<<n, 256, n * sizeof(double), s>>>(n, c.cdense, c.cinv64, c.cinv32);
+}
+
+// ---- per-right-hand-side sums of squares, two passes (deterministic) ----
+template <int R>
+__global__ void __launch_bounds__(256) norm_partial_kernel(const double *__restrict__ v, int n, double *__restrict__ part) {
+    __shared__ double sh[256][R];
+    double acc[R];
+#pragma unroll
+    for (int r = 0; r < R; r++) acc[r] = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+#pragma unroll
+        for (int r = 0; r < R; r++) { const double x = v[(size_t)i * R + r]; acc[r] = fma(x, x, acc[r]); }
+#pragma unroll
+    for (int r = 0; r < R; r++) sh[threadIdx.x][r] = acc[r];
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o)
+#pragma unroll
+            for (int r = 0; r < R; r++) sh[threadIdx.x][r] += sh[threadIdx.x + o][r];
+        __syncthreads();
+    }
+    if (threadIdx.x < R) part[blockIdx.x * 4 + threadIdx.x] = sh[0][threadIdx.x];
+}
+
+__global__ void __launch_bounds__(256) norm_final_kernel(const double *__restrict__ part, int nblocks, int R,
+                                                         double *__restrict__ out) {
+    __shared__ double sh[256][4];
+    for (int r = 0; r < 4; r++) sh[threadIdx.x][r] = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+        for (int r = 0; r < R; r++) sh[threadIdx.x][r] += part[b * 4 + r];
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o)
+            for (int r = 0; r < 4; r++) sh[threadIdx.x][r] += sh[threadIdx.x + o][r];
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) out[threadIdx.x] = threadIdx.x < R ? sh[0][threadIdx.x] : 0.0;
+}
+
+void launch_norms(const double *v, int n, int R, double *part, double *out, cudaStream_t s) {
+    if (R == 1) norm_partial_kernel<1><<<kNormBlocks, 256, 0, s>>>(v, n, part);
+    else if (R == 2) norm_partial_kernel<2><<<kNormBlocks, 256, 0, s>>>(v, n, part);
+    else norm_partial_kernel<4><<<kNormBlocks, 256, 0, s>>>(v, n, part);
+    norm_final_kernel<<<1, 256, 0, s>>>(part, kNormBlocks, R, out);
+}
+
+// ---- layout and elementwise kernels ----
+__global__ void pack_kernel(const double *__restrict__ u, int n, int nrhs, int R, double *__restrict__ v) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= (int64_t)n * R) return;
+    const int64_t i = q / R;
+    const int r = (int)(q % R);
+    v[q] = r < nrhs ? u[i * nrhs + r] : 0.0;
+}
+__global__ void unpack_kernel(const double *__restrict__ v, int n, int nrhs, int R, double *__restrict__ u) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= (int64_t)n * nrhs) return;
+    const int64_t i = q / nrhs;
+    const int r = (int)(q % nrhs);
+    u[q] = v[i * R + r];
+}
+__global__ void to_float_kernel(const double *__restrict__ a, float *__restrict__ b, int64_t n) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q < n) b[q] = (float)a[q];
+}
+__global__ void add_float_kernel(double *__restrict__ x, const float *__restrict__ e, int64_t n) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q < n) x[q] += (double)e[q];
+}
+__global__ void add_double_kernel(double *__restrict__ x, const double *__restrict__ e, int64_t n) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q < n) x[q] += e[q];
+}
+
+void launch_pack(const double *user, int n, int nrhs, int R, double *v, cudaStream_t s) {
+    const int64_t m = (int64_t)n * R;
+    if (m) pack_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(user, n, nrhs, R, v);
+}
+void launch_unpack(const double *v, int n, int nrhs, int R, double *user, cudaStream_t s) {
+    const int64_t m = (int64_t)n * nrhs;
+    if (m) unpack_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(v, n, nrhs, R, user);
+}
+void launch_to_float(const double *a, float *b, int64_t n, cudaStream_t s) {
+    if (n) to_float_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, b, n);
+}
+void launch_add_float(double *x, const float *e, int64_t n, cudaStream_t s) {
+    if (n) add_float_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, e, n);
+}
+void launch_add_double(double *x, const double *e, int64_t n, cudaStream_t s) {
+    if (n) add_double_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, e, n);
+}
+
+// explicit instantiations
+#define LBMG_INST(T)                                                                                           \
+    template void launch_smooth_colour<T>(const DevLevel &, int, const T *, const T *, const T *, T *, int,   \
+                                          cudaStream_t);                                                       \
+    template void launch_residual<T>(const DevLevel &, const T *, const T *, const T *, T *, int, cudaStream_t); \
+    template void launch_jacobi_update<T>(const DevLevel &, const T *, const T *, T *, T, int, cudaStream_t);   \
+    template void launch_restrict<T>(const DevLevel &, const T *, T *, int, cudaStream_t);                     \
+    template void launch_prolong_add<T>(const DevLevel &, const T *, T *, int, cudaStream_t);                  \
+    template void launch_coarse_apply<T>(int, const T *, const T *, T *, int, cudaStream_t);
+LBMG_INST(float)
+LBMG_INST(double)
+
+}  // namespace lbmg

@@ -1,0 +1,98 @@
+"""Full-size check in the benchmark's launch configuration: (2,3) torus-knot tube,
+200k triangles, depth 8, t = 1e-4, three right-hand sides (vertex x, y, z),
+mixed-precision V-cycles to relative residual 1e-6.
+
+At this size the oracle computes the finest level only; its rows are compared on
+a sample, and the GPU matrices are checked against closed forms that hold at
+any size (area, L 1 = 0, tangential metric, int x^2).  The solve is checked by
+an FP64 residual recomputed on the host from the verified matrices."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import meshgen
+import oracle
+import paper_1505_03615_gb300 as L
+from tests._match import permutation
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def knot():
+    V, F, depth, t, f, tol, _ = meshgen.config_mesh("knot23_200k_d8")
+    h = L.lbmg_build_hierarchy(V, F, depth)
+    L.lbmg_assemble(h, t)
+    yield V, F, depth, t, f, tol, h
+    L.lbmg_destroy(h)
+
+
+def _csr(h, d):
+    rp, ci, M, Lm = L.lbmg_get_matrix(h, d)
+    n = len(rp) - 1
+    return sp.csr_matrix((M, ci, rp), shape=(n, n)), sp.csr_matrix((Lm, ci, rp), shape=(n, n))
+
+
+def test_full_size_closed_forms(knot):
+    V, F, depth, t, f, tol, h = knot
+    P = V[F]
+    cr = np.cross(P[:, 1] - P[:, 0], P[:, 2] - P[:, 0])
+    A = 0.5 * np.linalg.norm(cr, axis=1)
+    nrm = cr / (2 * A[:, None])
+    S, c = L.lbmg_embedding(h)
+    d0, D = L.lbmg_levels(h)
+    for d in (D, D - 1, d0):
+        M, Lm = _csr(h, d)
+        assert abs(M.sum() - A.sum()) <= 1e-11 * A.sum()
+        assert np.abs(Lm @ np.ones(M.shape[0])).max() <= 1e-11 * np.abs(Lm.diagonal()).max()
+        assert abs(M - M.T).max() <= 1e-15 * abs(M).max()
+        corner, _ = L.lbmg_get_dofs(h, d)
+        pos = corner * (S / 2 ** d) - S / 2 + c
+        for a in range(3):
+            expect = (A * (1 - nrm[:, a] ** 2)).sum()
+            assert abs(pos[:, a] @ Lm @ pos[:, a] - expect) <= 1e-10 * expect
+        # int x^2 over each triangle: (A/6)(x1^2 + x2^2 + x3^2 + x1x2 + x1x3 + x2x3)
+        x = P[:, :, 0]
+        ix2 = (A / 6 * (x[:, 0] ** 2 + x[:, 1] ** 2 + x[:, 2] ** 2 + x[:, 0] * x[:, 1] + x[:, 0] * x[:, 2]
+                        + x[:, 1] * x[:, 2])).sum()
+        assert abs(pos[:, 0] @ M @ pos[:, 0] - ix2) <= 1e-10 * ix2
+
+
+def test_full_size_sampled_rows_match_oracle(knot):
+    V, F, depth, t, f, tol, h = knot
+    o = oracle.Hierarchy(V, F, depth, min_depth=depth)
+    c, m = L.lbmg_get_dofs(h, depth)
+    oc, om = o.dofs(depth)
+    perm = permutation(c, m, oc, om, F.shape[0])
+    assert (perm >= 0).all() and len(np.unique(perm)) == len(perm) == len(om)
+    M, Lm = _csr(h, depth)
+    Mo, Lo = o.matrices(depth)
+    rng = np.random.default_rng(0)
+    rows = rng.choice(M.shape[0], size=2000, replace=False)
+    Ms = M[rows][:, np.argsort(perm)]
+    Ls = Lm[rows][:, np.argsort(perm)]
+    Mref, Lref = Mo[perm[rows]], Lo[perm[rows]]
+    assert abs(Ms - Mref).max() <= 1e-12 * abs(Mo).max()
+    assert abs(Ls - Lref).max() <= 1e-12 * abs(Lo).max()
+    n = M.shape[0]
+    rhs = torch.zeros((n, 3), dtype=torch.float64, device="cuda:0")
+    L.lbmg_project_rhs(h, torch.tensor(f, device="cuda:0"), rhs)
+    ro = o.project_rhs(f)
+    assert np.abs(rhs.cpu().numpy() - ro[perm]).max() <= 1e-12 * np.abs(ro).max()
+
+
+def test_full_size_mixed_solve_reaches_tolerance(knot):
+    V, F, depth, t, f, tol, h = knot
+    M, Lm = _csr(h, depth)
+    n = M.shape[0]
+    rhs = torch.zeros((n, 3), dtype=torch.float64, device="cuda:0")
+    L.lbmg_project_rhs(h, torch.tensor(f, device="cuda:0"), rhs)
+    x = torch.zeros_like(rhs)
+    code, st = L.lbmg_solve(h, rhs, x, tol, 2000, L.LBMG_MIXED)
+    assert code == L.LBMG_OK and st.converged
+    b, xx = rhs.cpu().numpy(), x.cpu().numpy()
+    r = b - (M + t * Lm) @ xx
+    rel = np.linalg.norm(r, axis=0) / np.linalg.norm(b, axis=0)
+    assert np.all(rel <= 1.05 * tol)
+    assert np.allclose(rel, st.rel_residual[:3], rtol=1e-3, atol=1e-12)

@@ -1,0 +1,289 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 oracle.
+
+Tolerances: matrices, right-hand sides, residuals, transfers and FP64 smoothing
+are FP64 sums of at most a few hundred terms on both sides, computed in a
+different order (moments + contraction on the GPU, pointwise products in the
+oracle; Galerkin products on coarse GPU levels, direct quadrature in the
+oracle), so they agree to ~1e-14 of the largest entry; the tests allow 1e-12.
+Solves are compared with the oracle's direct solution in the M-norm (the
+function on the surface): FP64 V-cycles to relative residual 1e-10 must match to
+1e-8, mixed-precision V-cycles to 1e-6 must match to 1e-5.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+import meshgen
+import oracle
+import paper_1505_03615_gb300 as L
+from tests._match import permutation
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+DEV = "cuda:0"
+
+
+class Case:
+    def __init__(self, V, F, depth, min_depth, t, split=True, **opts):
+        self.V, self.F, self.t = V, F, t
+        self.h = L.lbmg_build_hierarchy(V, F, depth, min_depth=min_depth, split=int(split), **opts)
+        self.o = oracle.Hierarchy(V, F, depth, min_depth=min_depth, split=split)
+        self.d0, self.D = L.lbmg_levels(self.h)
+        assert (self.d0, self.D) == (self.o.min_depth, self.o.depth)
+        L.lbmg_assemble(self.h, t)
+        self.perm = {}
+        for d in range(self.d0, self.D + 1):
+            c, m = L.lbmg_get_dofs(self.h, d)
+            oc, om = self.o.dofs(d)
+            self.perm[d] = permutation(c, m, oc, om, F.shape[0])
+
+    def n(self, d):
+        return L.lbmg_level_info(self.h, d)[0]
+
+    def lib_matrices(self, d):
+        rp, ci, M, Lm = L.lbmg_get_matrix(self.h, d)
+        n = self.n(d)
+        return sp.csr_matrix((M, ci, rp), shape=(n, n)), sp.csr_matrix((Lm, ci, rp), shape=(n, n))
+
+    def orc_in_lib_order(self, d):
+        """oracle M, L permuted into the library's dof order"""
+        M, Lm = self.o.matrices(d)
+        p = self.perm[d]
+        return M[p][:, p], Lm[p][:, p]
+
+    def close(self):
+        L.lbmg_destroy(self.h)
+
+
+def _cases():
+    return {
+        "sphere": lambda: Case(*meshgen.icosphere(3, 1.0, 1e-3, 1), 5, 2, 1e-3),
+        "knot": lambda: Case(*meshgen.torus_knot_tube(2, 3, 1.0, 0.12, 48, 8, 1e-6, 3), 5, 1, 1e-2),
+        "sheets": lambda: Case(*meshgen.double_sheet(20, 0.05, 6, 0.5, 1e-6, 4), 6, 2, 1e-3),
+    }
+
+
+@pytest.fixture(scope="module", params=["sphere", "knot", "sheets"])
+def case(request):
+    c = _cases()[request.param]()
+    yield c
+    c.close()
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def _dev(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=DEV)
+
+
+def test_same_split_functions_on_every_level(case):
+    for d in range(case.d0, case.D + 1):
+        assert case.n(d) == case.o.ndof(d)
+        assert (case.perm[d] >= 0).all()
+        assert len(np.unique(case.perm[d])) == case.n(d)
+
+
+def test_mass_and_stiffness_match_oracle(case):
+    for d in range(case.d0, case.D + 1):
+        M, Lm = case.lib_matrices(d)
+        Mo, Lo = case.orc_in_lib_order(d)
+        assert abs(M - Mo).max() <= 1e-12 * abs(Mo).max()
+        assert abs(Lm - Lo).max() <= 1e-12 * abs(Lo).max()
+
+
+def test_prolongation_matches_oracle(case):
+    for d in range(case.d0 + 1, case.D + 1):
+        par, w = L.lbmg_get_prolongation(case.h, d)
+        n = case.n(d)
+        rows = np.repeat(np.arange(n), 8)
+        m = par.ravel() >= 0
+        P = sp.csr_matrix((w.ravel()[m], (rows[m], par.ravel()[m])), shape=(n, case.n(d - 1)))
+        Po = case.o.prolongation(d)[case.perm[d]][:, case.perm[d - 1]]
+        assert abs(P - Po).max() == 0
+
+
+@pytest.mark.parametrize("nrhs", [1, 2, 3, 4])
+def test_project_rhs_matches_oracle(case, nrhs):
+    rng = np.random.default_rng(nrhs)
+    f = rng.uniform(-1, 1, size=(case.V.shape[0], nrhs))
+    n = case.n(case.D)
+    rhs = torch.zeros((n, nrhs), dtype=torch.float64, device=DEV)
+    L.lbmg_project_rhs(case.h, _dev(f), rhs)
+    ro = case.o.project_rhs(f)[case.perm[case.D]]
+    assert _rel(rhs.cpu().numpy(), ro) <= 1e-12
+
+
+@pytest.mark.parametrize("nrhs", [1, 3])
+def test_residual_matches_oracle(case, nrhs):
+    rng = np.random.default_rng(7)
+    for d in (case.d0, case.D):
+        n = case.n(d)
+        b, x = rng.normal(size=(n, nrhs)), rng.normal(size=(n, nrhs))
+        r = torch.zeros((n, nrhs), dtype=torch.float64, device=DEV)
+        L.lbmg_residual(case.h, d, _dev(b), _dev(x), r)
+        Mo, Lo = case.orc_in_lib_order(d)
+        A = Mo + case.t * Lo
+        ro = b - A @ x
+        scale = np.abs(b).max() + abs(A).max() * np.abs(x).max()
+        assert np.abs(r.cpu().numpy() - ro).max() <= 1e-12 * scale
+
+
+def test_restriction_and_prolongation_match_oracle(case):
+    rng = np.random.default_rng(3)
+    for d in range(case.d0 + 1, case.D + 1):
+        P = case.o.prolongation(d)[case.perm[d]][:, case.perm[d - 1]]
+        nf, nc = case.n(d), case.n(d - 1)
+        rf = rng.normal(size=(nf, 3))
+        rc = torch.zeros((nc, 3), dtype=torch.float64, device=DEV)
+        L.lbmg_restrict(case.h, d, _dev(rf), rc)
+        assert _rel(rc.cpu().numpy(), P.T @ rf) <= 1e-13
+        xc, xf = rng.normal(size=(nc, 2)), rng.normal(size=(nf, 2))
+        out = _dev(xf)
+        L.lbmg_prolong_add(case.h, d, _dev(xc), out)
+        assert _rel(out.cpu().numpy(), xf + P @ xc) <= 1e-13
+
+
+def _coloured_gs_reference(A, corner, b, x, sweeps):
+    """Gauss-Seidel by corner-parity colour (rows of one colour updated together)."""
+    x = x.copy()
+    colour = (corner[:, 0] & 1) | ((corner[:, 1] & 1) << 1) | ((corner[:, 2] & 1) << 2)
+    dinv = 1.0 / A.diagonal()
+    for _ in range(sweeps):
+        for c in range(8):
+            rows = np.where(colour == c)[0]
+            r = b[rows] - A[rows] @ x
+            x[rows] += dinv[rows, None] * r
+    return x
+
+
+def test_coloured_gauss_seidel_matches_reference(case):
+    rng = np.random.default_rng(11)
+    d = case.D
+    n = case.n(d)
+    Mo, Lo = case.orc_in_lib_order(d)
+    A = (Mo + case.t * Lo).tocsr()
+    corner, _ = L.lbmg_get_dofs(case.h, d)
+    b, x0 = rng.normal(size=(n, 3)), rng.normal(size=(n, 3))
+    x = _dev(x0)
+    L.lbmg_smooth(case.h, d, _dev(b), x, 2, L.LBMG_FP64)
+    xr = _coloured_gs_reference(A, corner, b, x0, 2)
+    assert _rel(x.cpu().numpy(), xr) <= 1e-11
+    # FP32 smoothing stays within single-precision rounding of the FP64 sweep
+    x32 = _dev(x0)
+    L.lbmg_smooth(case.h, d, _dev(b), x32, 2, L.LBMG_MIXED)
+    assert _rel(x32.cpu().numpy(), xr) <= 1e-4
+
+
+def _direct(case, rhs):
+    Mo, Lo = case.orc_in_lib_order(case.D)
+    A = (Mo + case.t * Lo).tocsc()
+    return spla.splu(A).solve(rhs), Mo
+
+
+def _mnorm_err(M, x, xd):
+    e = x - xd
+    return np.sqrt(np.einsum("ij,ij->", e, M @ e) / np.einsum("ij,ij->", xd, M @ xd))
+
+
+@pytest.mark.parametrize("precision,tol,err", [(L.LBMG_FP64, 1e-10, 1e-8), (L.LBMG_MIXED, 1e-6, 1e-5)])
+def test_solve_matches_direct_solution(case, precision, tol, err):
+    f = np.asarray(case.V, dtype=np.float64)          # x, y, z: three right-hand sides
+    n = case.n(case.D)
+    rhs = torch.zeros((n, 3), dtype=torch.float64, device=DEV)
+    L.lbmg_project_rhs(case.h, _dev(f), rhs)
+    x = torch.zeros_like(rhs)
+    code, st = L.lbmg_solve(case.h, rhs, x, tol, 3000, precision)
+    assert code == L.LBMG_OK and st.converged == 1
+    assert max(st.rel_residual[:3]) <= tol
+    xd, Mo = _direct(case, rhs.cpu().numpy())
+    assert _mnorm_err(Mo, x.cpu().numpy(), xd) <= err
+
+
+def test_eval_vertices_matches_oracle(case):
+    rng = np.random.default_rng(5)
+    n = case.n(case.D)
+    x = rng.normal(size=(n, 2))
+    u = torch.zeros((case.V.shape[0], 2), dtype=torch.float64, device=DEV)
+    L.lbmg_eval_vertices(case.h, _dev(x), u)
+    xo = np.zeros_like(x)
+    xo[case.perm[case.D]] = x
+    assert _rel(u.cpu().numpy(), case.o.eval_vertices(xo)) <= 1e-13
+
+
+def test_host_buffers_give_device_results(case):
+    """Host (numpy) arguments are copied by the library and give identical results."""
+    f = np.asarray(case.V[:, :1], dtype=np.float64).copy()
+    n = case.n(case.D)
+    rhs_h = np.zeros((n, 1))
+    L.lbmg_project_rhs(case.h, f, rhs_h)
+    rhs_d = torch.zeros((n, 1), dtype=torch.float64, device=DEV)
+    L.lbmg_project_rhs(case.h, _dev(f), rhs_d)
+    assert np.array_equal(rhs_h, rhs_d.cpu().numpy())
+    x_h = np.zeros((n, 1))
+    L.lbmg_solve(case.h, rhs_h, x_h, 1e-6, 500, L.LBMG_MIXED)
+    x_d = torch.zeros((n, 1), dtype=torch.float64, device=DEV)
+    L.lbmg_solve(case.h, rhs_d, x_d, 1e-6, 500, L.LBMG_MIXED)
+    assert np.array_equal(x_h, x_d.cpu().numpy())
+
+
+def test_not_converged_status_keeps_iterate(case):
+    n = case.n(case.D)
+    rhs = torch.zeros((n, 1), dtype=torch.float64, device=DEV)
+    L.lbmg_project_rhs(case.h, _dev(np.ones((case.V.shape[0], 1))), rhs)
+    x = torch.zeros_like(rhs)
+    code, st = L.lbmg_solve(case.h, rhs, x, 1e-14, 1, L.LBMG_FP64)
+    assert code == L.LBMG_NOT_CONVERGED and st.cycles == 1 and st.converged == 0
+    assert 0 < st.rel_residual[0] < st.initial_residual[0]
+    assert torch.isfinite(x).all() and x.abs().max() > 0
+
+
+def test_unsplit_space_matches_oracle():
+    V, F = meshgen.double_sheet(12, 0.05, 5, 0.5, 1e-6, 4)
+    c = Case(V, F, 5, 2, 1e-3, split=False)
+    try:
+        for d in range(c.d0, c.D + 1):
+            assert (c.perm[d] >= 0).all()
+            M, Lm = c.lib_matrices(d)
+            Mo, Lo = c.orc_in_lib_order(d)
+            assert abs(M - Mo).max() <= 1e-12 * abs(Mo).max()
+            assert abs(Lm - Lo).max() <= 1e-12 * abs(Lo).max()
+    finally:
+        c.close()
+
+
+def test_single_level_hierarchy_solves_directly():
+    """Coarsest level = finest level: the V-cycle reduces to the dense solve."""
+    V, F = meshgen.icosphere(1, 1.0, 1e-3, 2)
+    c = Case(V, F, 2, 2, 1e-2)
+    try:
+        assert c.d0 == c.D
+        n = c.n(c.D)
+        rhs = torch.zeros((n, 1), dtype=torch.float64, device=DEV)
+        L.lbmg_project_rhs(c.h, _dev(V[:, :1]), rhs)
+        x = torch.zeros_like(rhs)
+        code, st = L.lbmg_solve(c.h, rhs, x, 1e-10, 5, L.LBMG_FP64)
+        assert code == L.LBMG_OK and st.cycles <= 2
+        xd, Mo = _direct(c, rhs.cpu().numpy())
+        assert _mnorm_err(Mo, x.cpu().numpy(), xd) <= 1e-8
+    finally:
+        c.close()
+
+
+def test_weighted_jacobi_smoother_converges():
+    V, F = meshgen.icosphere(3, 1.0, 1e-3, 1)
+    c = Case(V, F, 5, 2, 1e-2, smoother=L.LBMG_JACOBI, jacobi_omega=0.6)
+    try:
+        n = c.n(c.D)
+        rhs = torch.zeros((n, 1), dtype=torch.float64, device=DEV)
+        L.lbmg_project_rhs(c.h, _dev(V[:, 2:3]), rhs)
+        x = torch.zeros_like(rhs)
+        code, st = L.lbmg_solve(c.h, rhs, x, 1e-6, 3000, L.LBMG_MIXED)
+        assert code == L.LBMG_OK
+        xd, Mo = _direct(c, rhs.cpu().numpy())
+        assert _mnorm_err(Mo, x.cpu().numpy(), xd) <= 1e-5
+    finally:
+        c.close()

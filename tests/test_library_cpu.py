@@ -1,0 +1,67 @@
+"""Host-only checks of the C-ABI library: it builds, loads without a GPU, exports
+every entry point declared in include/lbmg.h, and rejects bad input on the host
+before touching a device."""
+import ctypes as C
+import os
+
+import numpy as np
+import pytest
+
+import paper_1505_03615_gb300 as L
+
+
+def test_library_loads_and_exports_every_declared_symbol():
+    lib = L.load_library()
+    names = L.exported_symbols()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(lib, name), name
+    # the binding exposes a function of the same name for each entry point
+    for name in names:
+        assert hasattr(L, name), name
+
+
+def test_library_is_built_for_sm_103a():
+    import subprocess
+    from paper_1505_03615_gb300 import build
+    path = build.build()
+    assert os.path.dirname(path).startswith(os.path.dirname(os.path.abspath(L.__file__)))
+    out = subprocess.run(["/usr/local/cuda/bin/cuobjdump", "--list-elf", path], capture_output=True, text=True)
+    if out.returncode == 0:
+        assert "sm_103a" in out.stdout
+
+
+def test_status_strings_and_defaults():
+    assert L.lbmg_status_string(0) == "ok"
+    assert L.lbmg_status_string(4) == "not converged"
+    o = L.lbmg_default_options()
+    assert (o.min_depth, o.coarse_max, o.nu1, o.nu2, o.split) == (-1, 160, 2, 2, 1)
+
+
+@pytest.mark.parametrize("case", ["bad_index", "nan_vertex", "depth0", "depth13", "min_gt_depth", "bad_smoother"])
+def test_invalid_input_rejected_on_host(case):
+    V = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], dtype=np.float64)
+    F = np.array([[0, 1, 2], [0, 1, 3]], dtype=np.int32)
+    depth, opts = 3, {}
+    if case == "bad_index":
+        F = F.copy(); F[1, 2] = 7
+    elif case == "nan_vertex":
+        V = V.copy(); V[2, 1] = np.nan
+    elif case == "depth0":
+        depth = 0
+    elif case == "depth13":
+        depth = 13
+    elif case == "min_gt_depth":
+        opts = {"min_depth": 5}
+    elif case == "bad_smoother":
+        opts = {"smoother": 9}
+    with pytest.raises(L.LbmgError) as e:
+        L.lbmg_build_hierarchy(V, F, depth, **opts)
+    assert e.value.code == 1
+
+
+def test_null_handle_rejected():
+    lib = L.load_library()
+    assert lib.lbmg_assemble(None, 1.0, None) == 1
+    assert lib.lbmg_solve(None, None, None, 1, 1e-6, 10, 0, None, None) == 1
+    assert lib.lbmg_levels(None, None, None) == 1
