@@ -163,9 +163,9 @@ template <class T>
 void enqueue_vcycle(Ctx &c, int R, cudaStream_t s, bool timed) {
     for (int d = c.D; d > c.d0; d--) {
         DevLevel &L = c.lev[d], &Lc = c.lev[d - 1];
-        if (timed && d == c.D) cudaEventRecord(c.ev_smooth[0], s);
+        if (timed && d == c.D) cudaEventRecordWithFlags(c.ev_smooth[0], s, cudaEventRecordExternal);
         enqueue_smooth<T>(c, L, R, c.nu1, true, s);
-        if (timed && d == c.D) cudaEventRecord(c.ev_smooth[1], s);
+        if (timed && d == c.D) cudaEventRecordWithFlags(c.ev_smooth[1], s, cudaEventRecordExternal);
         launch_residual<T>(L, P<T>::A(L), P<T>::b(L), P<T>::x(L), P<T>::r(L), R, s);
         launch_restrict<T>(Lc, P<T>::r(L), P<T>::b(Lc), R, s);
         if (d - 1 > c.d0) cudaMemsetAsync(P<T>::x(Lc), 0, (size_t)Lc.n * R * sizeof(T), s);
@@ -175,9 +175,9 @@ void enqueue_vcycle(Ctx &c, int R, cudaStream_t s, bool timed) {
     for (int d = c.d0 + 1; d <= c.D; d++) {
         DevLevel &L = c.lev[d];
         launch_prolong_add<T>(L, P<T>::x(c.lev[d - 1]), P<T>::x(L), R, s);
-        if (timed && d == c.D) cudaEventRecord(c.ev_smooth[2], s);
+        if (timed && d == c.D) cudaEventRecordWithFlags(c.ev_smooth[2], s, cudaEventRecordExternal);
         enqueue_smooth<T>(c, L, R, c.nu2, false, s);
-        if (timed && d == c.D) cudaEventRecord(c.ev_smooth[3], s);
+        if (timed && d == c.D) cudaEventRecordWithFlags(c.ev_smooth[3], s, cudaEventRecordExternal);
     }
 }
 
