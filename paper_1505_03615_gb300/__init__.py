@@ -16,7 +16,7 @@ import numpy as np
 
 __all__ = [
     "LbmgError", "Options", "Stats", "load_library", "exported_symbols",
-    "LBMG_OK", "LBMG_NOT_CONVERGED", "LBMG_FP64", "LBMG_MIXED", "LBMG_GS_COLOURED", "LBMG_JACOBI",
+    "LBMG_OK", "LBMG_NOT_CONVERGED", "LBMG_DEVICE_TIMEOUT", "LBMG_FP64", "LBMG_MIXED", "LBMG_GS_COLOURED", "LBMG_JACOBI",
     "lbmg_build_hierarchy", "lbmg_destroy", "lbmg_levels", "lbmg_level_info", "lbmg_embedding",
     "lbmg_assemble", "lbmg_project_rhs", "lbmg_solve", "lbmg_vcycles", "lbmg_residual", "lbmg_smooth",
     "lbmg_restrict", "lbmg_prolong_add", "lbmg_eval_vertices", "lbmg_get_dofs", "lbmg_get_matrix",
@@ -25,6 +25,7 @@ __all__ = [
 
 LBMG_OK = 0
 LBMG_NOT_CONVERGED = 4
+LBMG_DEVICE_TIMEOUT = 9
 LBMG_FP64 = 0
 LBMG_MIXED = 1
 LBMG_GS_COLOURED = 0
@@ -45,7 +46,8 @@ class LbmgError(RuntimeError):
 
 class Options(C.Structure):
     _fields_ = [("min_depth", C.c_int), ("coarse_max", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int),
-                ("smoother", C.c_int), ("jacobi_omega", C.c_double), ("split", C.c_int), ("threads", C.c_int)]
+                ("smoother", C.c_int), ("jacobi_omega", C.c_double), ("split", C.c_int), ("threads", C.c_int),
+                ("persistent", C.c_int), ("narrow_max", C.c_int), ("barrier_phantoms", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -204,7 +206,7 @@ def lbmg_solve(h, rhs, x, tol, max_cycles, precision, stream=None, raise_not_con
     st = Stats()
     code = load_library().lbmg_solve(h, _ptr(rhs), _ptr(x), _nrhs(rhs), float(tol), int(max_cycles), int(precision),
                                      C.byref(st), _stream(stream))
-    _check(code, "lbmg_solve", allow=() if raise_not_converged else (LBMG_NOT_CONVERGED,))
+    _check(code, "lbmg_solve", allow=() if raise_not_converged else (LBMG_NOT_CONVERGED, LBMG_DEVICE_TIMEOUT))
     return code, st
 
 

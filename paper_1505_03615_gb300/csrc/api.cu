@@ -89,6 +89,7 @@ struct lbmg_ctx {
         for (void *p : allocs) cudaFree(p);
         if (c.h_norm) cudaFreeHost(c.h_norm);
         if (h_flag) cudaFreeHost(h_flag);
+        if (c.h_state) cudaFreeHost(c.h_state);
         if (c.capture_stream) cudaStreamDestroy(c.capture_stream);
         if (c.ev0) cudaEventDestroy(c.ev0);
         if (c.ev1) cudaEventDestroy(c.ev1);
@@ -311,6 +312,14 @@ int upload_hierarchy(lbmg_handle h) {
     LBMG_CK(cudaEventCreate(&c.ev0));
     LBMG_CK(cudaEventCreate(&c.ev1));
     for (int q = 0; q < 4; q++) LBMG_CK(cudaEventCreate(&c.ev_smooth[q]));
+    c.persist_view_bytes = persist_view_bytes();
+    LBMG_TRY(h->alloc((char **)&c.persist_views, c.persist_view_bytes));
+    LBMG_TRY(h->alloc(&c.persist_part, 8 * 1024));
+    LBMG_TRY(h->alloc(&c.persist_norm, 16));
+    LBMG_TRY(h->alloc((char **)&c.persist_state, 64));
+    LBMG_CK(cudaMallocHost(&c.h_state, 64 + 16 * sizeof(double)));
+    c.persist_ok = persist_setup(c) == 0 && c.persist_blocks <= 1024;
+    cudaGetLastError();
     return LBMG_OK;
 }
 
@@ -329,6 +338,7 @@ const char *lbmg_status_string(int code) {
         case LBMG_COARSE_FACTOR: return "coarse factorisation failed";
         case LBMG_CUDA_ERROR: return "CUDA error";
         case LBMG_DIVERGED: return "diverged";
+        case LBMG_DEVICE_TIMEOUT: return "device wait timed out";
         default: return "unknown status";
     }
 }
@@ -345,6 +355,9 @@ void lbmg_default_options(lbmg_options *o) {
     o->jacobi_omega = 0.6;
     o->split = 1;
     o->threads = 0;
+    o->persistent = 1;
+    o->narrow_max = 2048;
+    o->barrier_phantoms = 0;
 }
 
 int lbmg_build_hierarchy(const double *V, int nv, const int *F, int nt, int depth, const lbmg_options *opt,
@@ -356,6 +369,7 @@ int lbmg_build_hierarchy(const double *V, int nv, const int *F, int nt, int dept
     if (opt) o = *opt;
     if (o.nu1 < 0 || o.nu2 < 0 || o.coarse_max < 1 || o.coarse_max > kMaxCoarse) return LBMG_INVALID_ARG;
     if (o.smoother != LBMG_GS_COLOURED && o.smoother != LBMG_JACOBI) return LBMG_INVALID_ARG;
+    if (o.narrow_max < 0 || o.barrier_phantoms < 0 || o.barrier_phantoms > 1024) return LBMG_INVALID_ARG;
     lbmg_ctx *h = new (std::nothrow) lbmg_ctx();
     if (!h) return LBMG_OUT_OF_MEMORY;
     std::string err;
@@ -372,6 +386,9 @@ int lbmg_build_hierarchy(const double *V, int nv, const int *F, int nt, int dept
     h->c.nu2 = o.nu2;
     h->c.smoother = o.smoother;
     h->c.omega = o.jacobi_omega;
+    h->c.persistent = o.persistent;
+    h->c.persist_narrow = o.narrow_max;
+    h->c.barrier_phantoms = o.barrier_phantoms;
     st = upload_hierarchy(h);
     if (st != 0) { delete h; return st; }
     *out = h;
@@ -463,6 +480,53 @@ static int solve_impl(lbmg_handle h, const double *rhs, double *x, int nrhs, dou
     LBMG_TRY(input_ptr(h, rhs, cnt, 0, s, &rd));
     LBMG_TRY(input_ptr(h, x, cnt, 1, s, &xin));
     LBMG_TRY(output_ptr(h, x, cnt, 1, &xout, &host_out));
+    if (c.persistent && c.persist_ok && c.smoother == LBMG_GS_COLOURED) {
+        LBMG_CK(cudaEventRecord(c.ev0, s));
+        launch_pack(rd, Fl.n, nrhs, R, c.bs, s);
+        launch_pack(xin, Fl.n, nrhs, R, c.xs, s);
+        const int e = persist_solve(c, precision, R, nrhs, check ? tol : 0.0, max_cycles, s);
+        if (e) {
+            g_cuda_err = std::string("cooperative launch: ") + cudaGetErrorString((cudaError_t)e);
+            cudaGetLastError();
+            return LBMG_CUDA_ERROR;
+        }
+        unsigned char *hs = reinterpret_cast<unsigned char *>(c.h_state);
+        LBMG_CK(cudaMemcpyAsync(hs, c.persist_state, 64, cudaMemcpyDeviceToHost, s));
+        LBMG_CK(cudaMemcpyAsync(hs + 64, c.persist_norm, 16 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        launch_unpack(c.xs, Fl.n, nrhs, R, xout, s);
+        LBMG_CK(cudaEventRecord(c.ev1, s));
+        LBMG_TRY(finish_output(x, xout, cnt, host_out, s));
+        LBMG_CK(cudaEventSynchronize(c.ev1));
+        int dstat, dcyc;
+        unsigned long long sns;
+        double nrm[16];
+        std::memcpy(&dstat, hs + 16, sizeof(int));
+        std::memcpy(&dcyc, hs + 20, sizeof(int));
+        std::memcpy(&sns, hs + 24, sizeof(sns));
+        std::memcpy(nrm, hs + 64, sizeof nrm);
+        bool conv = true;
+        for (int r = 0; r < nrhs; r++) {
+            const double rel = nrm[4 + r] > 0 ? std::sqrt(nrm[r] / nrm[4 + r]) : 0.0;
+            if (!(rel <= tol)) conv = false;
+        }
+        int status = LBMG_OK;
+        if (dstat == 1) status = LBMG_DEVICE_TIMEOUT;
+        else if (dstat == 2) status = LBMG_DIVERGED;
+        else if (check && !conv) status = LBMG_NOT_CONVERGED;
+        if (stats) {
+            stats->cycles = dcyc;
+            stats->converged = (check && conv && dstat == 0) ? 1 : 0;
+            for (int r = 0; r < 4; r++) {
+                stats->rel_residual[r] = (r < nrhs && nrm[4 + r] > 0) ? std::sqrt(nrm[r] / nrm[4 + r]) : 0.0;
+                stats->initial_residual[r] = (r < nrhs && nrm[4 + r] > 0) ? std::sqrt(nrm[8 + r] / nrm[4 + r]) : 0.0;
+            }
+            float ms = 0;
+            cudaEventElapsedTime(&ms, c.ev0, c.ev1);
+            stats->ms_total = ms;
+            stats->ms_fine_smooth = (float)(sns * 1e-6);
+        }
+        return status;
+    }
     cudaGraphExec_t exec;
     LBMG_TRY(get_graph(h, R, precision, &exec));
     LBMG_CK(cudaEventRecord(c.ev0, s));

@@ -75,7 +75,23 @@ struct Ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     cudaEvent_t ev_smooth[4] = {nullptr, nullptr, nullptr, nullptr};   // around finest-level smoothing in the cycle graph
     GraphCache graph;
+    // persistent cooperative solve
+    int persistent = 1;           // use the one-launch solve when the device allows it
+    int persist_ok = 0;
+    int persist_blocks = 0, persist_dn = 0, persist_narrow = 2048;
+    int barrier_phantoms = 0;        // fault injection: extra arrivals a grid barrier waits for
+    void *persist_views = nullptr;
+    size_t persist_view_bytes = 0;
+    double *persist_part = nullptr;   // [blocks][8]
+    double *persist_norm = nullptr;   // [16]
+    void *persist_state = nullptr;    // 64 bytes: barrier, status, cycles, timer
+    void *h_state = nullptr;          // pinned mirror: 64 bytes state + 16 doubles norms
 };
+
+// ----- persistent solve (persist.cu) -----
+int persist_setup(Ctx &c);
+int persist_solve(Ctx &c, int precision, int R, int nrhs, double tol, int max_cycles, cudaStream_t s);
+size_t persist_view_bytes();
 
 // ----- kernels (assemble.cu) -----
 void launch_fragment_moments(const Ctx &c, cudaStream_t s);

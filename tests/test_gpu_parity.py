@@ -297,3 +297,52 @@ def test_weighted_jacobi_smoother_converges():
         assert _mnorm_err(Mo, x.cpu().numpy(), xd) <= 1e-5
     finally:
         c.close()
+
+
+def test_persistent_and_per_cycle_graph_paths_agree(case):
+    """The one-launch cooperative solve and the per-cycle graph launch run the same
+    arithmetic in the same order: a fixed number of cycles gives the same iterate."""
+    h2 = L.lbmg_build_hierarchy(case.V, case.F, case.D, min_depth=case.d0, persistent=0)
+    try:
+        L.lbmg_assemble(h2, case.t)
+        n = case.n(case.D)
+        rhs = torch.zeros((n, 3), dtype=torch.float64, device=DEV)
+        L.lbmg_project_rhs(case.h, _dev(case.V), rhs)
+        for prec in (L.LBMG_MIXED, L.LBMG_FP64):
+            xa = torch.zeros_like(rhs)
+            xb = torch.zeros_like(rhs)
+            L.lbmg_vcycles(case.h, rhs, xa, 5, prec)
+            L.lbmg_vcycles(h2, rhs, xb, 5, prec)
+            assert _rel(xa.cpu().numpy(), xb.cpu().numpy()) <= 1e-12
+        xa = torch.zeros_like(rhs)
+        xb = torch.zeros_like(rhs)
+        ca, sa = L.lbmg_solve(case.h, rhs, xa, 1e-6, 3000, L.LBMG_MIXED)
+        cb, sb = L.lbmg_solve(h2, rhs, xb, 1e-6, 3000, L.LBMG_MIXED)
+        assert ca == cb == L.LBMG_OK
+        assert abs(sa.cycles - sb.cycles) <= 1
+    finally:
+        L.lbmg_destroy(h2)
+
+
+def test_bounded_barrier_wait_reports_timeout_and_context_stays_usable():
+    """Fault injected on the host: the grid barrier is told to wait for one extra
+    arrival that never comes.  Its bounded wait (about a second) expires, every
+    block returns, the solve reports LBMG_DEVICE_TIMEOUT, and the device keeps working."""
+    V, F = meshgen.icosphere(2, 1.0, 1e-3, 1)
+    bad = L.lbmg_build_hierarchy(V, F, 4, barrier_phantoms=1)
+    good = L.lbmg_build_hierarchy(V, F, 4)
+    try:
+        for h in (bad, good):
+            L.lbmg_assemble(h, 1e-2)
+        n = L.lbmg_level_info(good, 4)[0]
+        rhs = torch.zeros((n, 1), dtype=torch.float64, device=DEV)
+        L.lbmg_project_rhs(good, _dev(V[:, :1]), rhs)
+        x = torch.zeros_like(rhs)
+        code, st = L.lbmg_solve(bad, rhs, x, 1e-6, 100, L.LBMG_MIXED)
+        assert code == L.LBMG_DEVICE_TIMEOUT
+        x = torch.zeros_like(rhs)
+        code, st = L.lbmg_solve(good, rhs, x, 1e-6, 1000, L.LBMG_MIXED)
+        assert code == L.LBMG_OK and st.converged
+    finally:
+        L.lbmg_destroy(bad)
+        L.lbmg_destroy(good)
