@@ -51,13 +51,13 @@ def test_unit_weights_give_the_plain_coloured_sweep(system):
     assert np.abs(r8 - (b - A @ x)).max() < 1e-12 * np.abs(b).max()
 
 
-def test_zero_network_is_the_plain_sweep():
+def test_zero_network_gives_the_midpoint_weight():
     p = LS.init_params(0)
     for k in p:
         p[k] = np.zeros_like(p[k])
     X = np.random.default_rng(1).normal(size=(5, LS.N_FEATURES))
     _, _, y = LS.mlp_forward(p, X)
-    assert np.all(LS.omega_of(y) == 1.0)
+    assert np.all(LS.omega_of(y) == 1.45)
 
 
 def test_gradients_match_finite_differences(system):
@@ -85,4 +85,59 @@ def test_gradients_match_finite_differences(system):
 def test_weights_stay_in_convergent_range():
     y = np.linspace(-1e6, 1e6, 1001)
     om = LS.omega_of(y)
-    assert om.min() > 0.1 - 1e-12 and om.max() < 1.9 + 1e-12
+    assert om.min() > 1.0 - 1e-12 and om.max() < 1.9 + 1e-12
+
+
+@pytest.fixture(scope="module")
+def levels():
+    V, F = meshgen.icosphere(2, 1.0, 1e-3, 1)
+    h = oracle.Hierarchy(V, F, 4, min_depth=2)
+    A, col, P = {}, {}, {}
+    for d in h.levels():
+        M, L = h.matrices(d)
+        A[d] = (M + 1e-2 * L).tocsr()
+        c, _ = h.dofs(d)
+        col[d] = LS.colours(c)
+        if d > h.min_depth:
+            P[d] = h.prolongation(d).tocsr()
+    corner, _ = h.dofs(4)
+    return LS.Levels(A, col, P, h.min_depth, 4), corner
+
+
+def test_coarse_vcycle_is_symmetric(levels):
+    lv, _ = levels
+    rng = np.random.default_rng(4)
+    n = lv.A[3].shape[0]
+    u, v = rng.normal(size=(n, 1)), rng.normal(size=(n, 1))
+    a, b = (u.T @ lv.vcycle(3, v)).item(), (lv.vcycle(3, u).T @ v).item()
+    assert abs(a - b) <= 1e-12 * abs(a)
+
+
+def test_cycle_loss_with_unit_weights_is_the_plain_vcycle(levels):
+    lv, _ = levels
+    rng = np.random.default_rng(6)
+    A = lv.A[4]
+    R0 = rng.normal(size=(A.shape[0], 2))
+    L, _ = LS.cycle_loss_grad_omega(lv, np.ones(A.shape[0]), R0)
+    r = R0 - A @ lv.vcycle(4, R0)
+    expect = np.mean((r ** 2).sum(0) / (R0 ** 2).sum(0))
+    assert L == pytest.approx(expect, rel=1e-10)
+
+
+def test_cycle_gradients_match_finite_differences(levels):
+    lv, corner = levels
+    A = lv.A[4]
+    X = LS.stencil_features(A, corner)
+    rng = np.random.default_rng(8)
+    R0 = rng.normal(size=(A.shape[0], 2))
+    p = LS.init_params(9, scale=0.3)
+    L, g = LS.cycle_loss_and_grads(p, X, lv, R0)
+    eps = 1e-6
+    for key, ix in (("W1", (0, 1)), ("W1", (13, 7)), ("b1", (5,)), ("w2", (2,)), ("b2", (0,))):
+        q = {k: v.copy() for k, v in p.items()}
+        q[key][ix] += eps
+        Lp, _ = LS.cycle_loss_grad_omega(lv, LS.omega_of(LS.mlp_forward(q, X)[2]), R0)
+        q[key][ix] -= 2 * eps
+        Lm, _ = LS.cycle_loss_grad_omega(lv, LS.omega_of(LS.mlp_forward(q, X)[2]), R0)
+        fd = (Lp - Lm) / (2 * eps)
+        assert abs(fd - g[key][ix]) <= 1e-5 * max(1e-4, abs(fd)), (key, ix, fd, g[key][ix])
