@@ -104,6 +104,28 @@ int lbmg_build_hierarchy(const double *V, int nv, const int *F, int nt, int dept
                          const lbmg_options *opt, lbmg_handle *out);
 void lbmg_destroy(lbmg_handle h);
 
+/*
+ * Build one hierarchy for a batch of meshes solved together (many meshes of
+ * uneven size, each with its own embedding and depth).  V[i], F[i], nv[i],
+ * nt[i], depth[i] describe mesh i as for lbmg_build_hierarchy.  Levels are
+ * aligned at the finest: batch depth d holds level depth[i] - (D - d) of every
+ * mesh, where D = (largest level count) - 1 and the coarsest batch depth is 0.
+ * The finest-level vectors of a batch are the meshes' own finest vectors
+ * concatenated in mesh order (see lbmg_instance_info); vertex arrays likewise.
+ * A batch always uses the persistent solve; it stops when every mesh meets tol.
+ */
+int lbmg_build_batch(const double *const *V, const int *nv, const int *const *F, const int *nt, const int *depth,
+                     int ninst, const lbmg_options *opt, lbmg_handle *out);
+/* number of meshes in the hierarchy (1 for lbmg_build_hierarchy) */
+int lbmg_instances(lbmg_handle h, int *ninst);
+/* mesh `inst`: its finest and coarsest depth, finest function count, and the offsets of its rows in
+   finest-level vectors and of its vertices in vertex arrays */
+int lbmg_instance_info(lbmg_handle h, int inst, int *depth, int *min_depth, long *nfine, long *row_offset,
+                       long *vertex_offset);
+/* relative residual ||rhs - A x|| / ||rhs|| of every mesh and right-hand side after the last
+   persistent solve, rel[ninst][nrhs] (host) */
+int lbmg_instance_residuals(lbmg_handle h, int nrhs, double *rel);
+
 /* min_depth and depth of the hierarchy. */
 int lbmg_levels(lbmg_handle h, int *min_depth, int *depth);
 /* functions (dofs), stored non-zeros and, for the finest level, fragments of level d */
@@ -148,7 +170,8 @@ int lbmg_solve(lbmg_handle h, const double *rhs, double *x, int nrhs, double tol
 
 /* Number of kernels each call launches: lbmg_assemble, lbmg_project_rhs, one
    V-cycle step of lbmg_solve/lbmg_vcycles in `precision` (cycle + FP64 residual
-   + norms), and the fixed part of lbmg_solve around its cycles.  Host only. */
+   + norms; 0 for the persistent solve, whose cycles run inside its one launch),
+   and the fixed part of lbmg_solve around its cycles.  Host only. */
 int lbmg_launch_counts(lbmg_handle h, int precision, int *assemble, int *project_rhs, int *per_cycle,
                        int *solve_fixed);
 

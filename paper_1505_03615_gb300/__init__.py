@@ -20,7 +20,8 @@ __all__ = [
     "lbmg_build_hierarchy", "lbmg_destroy", "lbmg_levels", "lbmg_level_info", "lbmg_embedding",
     "lbmg_assemble", "lbmg_project_rhs", "lbmg_solve", "lbmg_vcycles", "lbmg_residual", "lbmg_smooth",
     "lbmg_restrict", "lbmg_prolong_add", "lbmg_eval_vertices", "lbmg_get_dofs", "lbmg_get_matrix",
-    "lbmg_get_prolongation", "lbmg_launch_counts", "lbmg_status_string", "lbmg_last_cuda_error", "lbmg_default_options",
+    "lbmg_get_prolongation", "lbmg_launch_counts", "lbmg_build_batch", "lbmg_instances", "lbmg_instance_info",
+    "lbmg_instance_residuals", "lbmg_status_string", "lbmg_last_cuda_error", "lbmg_default_options",
 ]
 
 LBMG_OK = 0
@@ -86,6 +87,10 @@ def load_library():
         "lbmg_launch_counts": (i, [P, i, P, P, P, P]),
         "lbmg_get_matrix": (i, [P, i, P, P, P, P]),
         "lbmg_get_prolongation": (i, [P, i, P, P]),
+        "lbmg_build_batch": (i, [P, P, P, P, P, i, P, P]),
+        "lbmg_instances": (i, [P, P]),
+        "lbmg_instance_info": (i, [P, i, P, P, P, P, P]),
+        "lbmg_instance_residuals": (i, [P, i, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -167,6 +172,47 @@ def lbmg_build_hierarchy(V, F, depth, **opts):
     _check(lib.lbmg_build_hierarchy(_ptr(V), V.shape[0], _ptr(F), F.shape[0], int(depth), C.byref(o), C.byref(h)),
            "lbmg_build_hierarchy")
     return h
+
+
+def lbmg_build_batch(meshes, **opts):
+    """Build one hierarchy for a list of (V, F, depth) meshes solved together.  Returns the handle."""
+    lib = load_library()
+    Vs = [np.ascontiguousarray(V, dtype=np.float64) for V, _, _ in meshes]
+    Fs = [np.ascontiguousarray(F, dtype=np.int32) for _, F, _ in meshes]
+    n = len(meshes)
+    Vp = (C.c_void_p * n)(*[V.ctypes.data for V in Vs])
+    Fp = (C.c_void_p * n)(*[F.ctypes.data for F in Fs])
+    nv = (C.c_int * n)(*[V.shape[0] for V in Vs])
+    nt = (C.c_int * n)(*[F.shape[0] for F in Fs])
+    dp = (C.c_int * n)(*[int(d) for _, _, d in meshes])
+    o = lbmg_default_options()
+    for k, v in opts.items():
+        setattr(o, k, v)
+    h = C.c_void_p()
+    _check(lib.lbmg_build_batch(Vp, nv, Fp, nt, dp, n, C.byref(o), C.byref(h)), "lbmg_build_batch")
+    return h
+
+
+def lbmg_instances(h):
+    n = C.c_int()
+    _check(load_library().lbmg_instances(h, C.byref(n)), "lbmg_instances")
+    return n.value
+
+
+def lbmg_instance_info(h, inst):
+    """(depth, min_depth, finest functions, row offset in finest vectors, vertex offset)."""
+    d, d0 = C.c_int(), C.c_int()
+    nf, ro, vo = C.c_long(), C.c_long(), C.c_long()
+    _check(load_library().lbmg_instance_info(h, int(inst), C.byref(d), C.byref(d0), C.byref(nf), C.byref(ro),
+                                             C.byref(vo)), "lbmg_instance_info")
+    return d.value, d0.value, nf.value, ro.value, vo.value
+
+
+def lbmg_instance_residuals(h, nrhs):
+    n = lbmg_instances(h)
+    out = np.zeros((n, nrhs))
+    _check(load_library().lbmg_instance_residuals(h, int(nrhs), _ptr(out)), "lbmg_instance_residuals")
+    return out
 
 
 def lbmg_destroy(h):

@@ -14,7 +14,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblbmg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU = ["assemble.cu", "relax.cu", "persist.cu", "api.cu"]
-CPP = ["hier.cpp"]
+CPP = ["hier.cpp", "batch.cpp"]
 
 
 def _nvcc():

@@ -62,6 +62,9 @@ __global__ void to_double_kernel(const float *__restrict__ a, double *__restrict
 struct lbmg_ctx {
     Ctx c;
     std::vector<void *> allocs;
+    const int **lev_rp = nullptr, **lev_ci = nullptr;   // device arrays of per-level pointers
+    const double **lev_A = nullptr;
+    std::vector<double> inst_norm_host;                 // last solve: [ninst][12]
     size_t io_cap = 0;   // doubles per io slot
     int *h_flag = nullptr;
 
@@ -148,7 +151,7 @@ template <class T>
 void enqueue_smooth(Ctx &c, DevLevel &L, int R, int sweeps, bool forward, cudaStream_t s) {
     for (int sw = 0; sw < sweeps; sw++) {
         if (c.smoother == LBMG_JACOBI) {
-            launch_residual<T>(L, P<T>::A(L), P<T>::b(L), P<T>::x(L), P<T>::r(L), R, s);
+            launch_residual<T>(L, P<T>::A(L), P<T>::b(L), P<T>::x(L), P<T>::r(L), R, s, L.ns);
             launch_jacobi_update<T>(L, P<T>::dinv(L), P<T>::r(L), P<T>::x(L), (T)c.omega, R, s);
         } else {
             for (int q = 0; q < 8; q++) {
@@ -164,15 +167,16 @@ template <class T>
 void enqueue_vcycle(Ctx &c, int R, cudaStream_t s, bool timed) {
     for (int d = c.D; d > c.d0; d--) {
         DevLevel &L = c.lev[d], &Lc = c.lev[d - 1];
+        launch_coarse_apply<T>(c, L, P<T>::inv(c), P<T>::b(L), P<T>::x(L), R, s);
         if (timed && d == c.D) cudaEventRecordWithFlags(c.ev_smooth[0], s, cudaEventRecordExternal);
         enqueue_smooth<T>(c, L, R, c.nu1, true, s);
         if (timed && d == c.D) cudaEventRecordWithFlags(c.ev_smooth[1], s, cudaEventRecordExternal);
-        launch_residual<T>(L, P<T>::A(L), P<T>::b(L), P<T>::x(L), P<T>::r(L), R, s);
+        launch_residual<T>(L, P<T>::A(L), P<T>::b(L), P<T>::x(L), P<T>::r(L), R, s, L.ns);
         launch_restrict<T>(Lc, P<T>::r(L), P<T>::b(Lc), R, s);
         if (d - 1 > c.d0) cudaMemsetAsync(P<T>::x(Lc), 0, (size_t)Lc.n * R * sizeof(T), s);
     }
     DevLevel &L0 = c.lev[c.d0];
-    launch_coarse_apply<T>(L0.n, P<T>::inv(c), P<T>::b(L0), P<T>::x(L0), R, s);
+    launch_coarse_apply<T>(c, L0, P<T>::inv(c), P<T>::b(L0), P<T>::x(L0), R, s);
     for (int d = c.d0 + 1; d <= c.D; d++) {
         DevLevel &L = c.lev[d];
         launch_prolong_add<T>(L, P<T>::x(c.lev[d - 1]), P<T>::x(L), R, s);
@@ -242,12 +246,33 @@ int upload_hierarchy(lbmg_handle h) {
     Ctx &c = h->c;
     HostHierarchy &H = c.host;
     c.D = H.D; c.d0 = H.d0; c.nv = H.nv; c.nt = H.nt; c.nfrag = H.nfrag;
-    if (H.lev[H.d0].ndof > kMaxCoarse) return LBMG_INVALID_ARG;
+    c.ninst = H.ninst;
+    c.nu = (int)H.fperm.size();
+    // coarsest blocks, sorted by level
+    c.cblk_host.clear();
+    c.n0max = 0;
+    int64_t inv_total = 0;
+    for (int d = c.d0; d <= c.D; d++) {
+        HostLevel &hl = H.lev[d];
+        c.lev[d].cb0 = (int)(c.cblk_host.size() / 5);
+        c.lev[d].ncb = (int)(hl.coarse.size() / 3);
+        for (size_t q = 0; q < hl.coarse.size(); q += 3) {
+            const int n0 = hl.coarse[q + 2];
+            if (n0 > kMaxCoarse) return LBMG_INVALID_ARG;
+            c.cblk_host.insert(c.cblk_host.end(), {d, hl.coarse[q], hl.coarse[q + 1], n0, (int)inv_total});
+            inv_total += (int64_t)n0 * n0;
+            c.n0max = std::max(c.n0max, n0);
+            if (inv_total > INT32_MAX) return LBMG_INVALID_ARG;
+        }
+    }
+    c.ncblk = (int)(c.cblk_host.size() / 5);
+    LBMG_TRY(h->upload(&c.cblk, c.cblk_host));
     for (int d = c.d0; d <= c.D; d++) {
         HostLevel &hl = H.lev[d];
         DevLevel &L = c.lev[d];
         L.d = d;
         L.n = hl.ndof;
+        L.ns = hl.ns;
         L.nnz = hl.rp.empty() ? 0 : hl.rp[hl.ndof];
         for (int q = 0; q < 9; q++) L.cs[q] = hl.colour_start[q];
         LBMG_TRY(h->upload(&L.rp, hl.rp));
@@ -258,7 +283,7 @@ int upload_hierarchy(lbmg_handle h) {
         LBMG_TRY(h->alloc(&L.A32, L.nnz));
         LBMG_TRY(h->alloc(&L.dinv64, L.n));
         LBMG_TRY(h->alloc(&L.dinv32, L.n));
-        if (d > c.d0) {
+        if (!hl.par.empty()) {
             LBMG_TRY(h->upload(&L.par, hl.par));
             LBMG_TRY(h->upload(&L.npl2, hl.npar_log2));
         }
@@ -288,15 +313,41 @@ int upload_hierarchy(lbmg_handle h) {
     LBMG_TRY(h->upload(&c.aidx, H.aidx));
     LBMG_TRY(h->upload(&c.rrp, H.rrp));
     LBMG_TRY(h->upload(&c.ridx, H.ridx));
-    LBMG_TRY(h->upload(&c.vdof, H.vdof));
+    LBMG_TRY(h->upload(&c.frag_scale, H.frag_scale));
+    LBMG_TRY(h->upload(&c.fperm, H.fperm));
+    {
+        std::vector<int32_t> inv(H.fperm.size()), vdu(H.vdof.size());
+        for (size_t u = 0; u < H.fperm.size(); u++) inv[H.fperm[u]] = (int32_t)u;
+        for (size_t q = 0; q < H.vdof.size(); q++) vdu[q] = H.vdof[q] >= 0 ? inv[H.vdof[q]] : -1;
+        LBMG_TRY(h->upload(&c.fiperm, inv));
+        LBMG_TRY(h->upload(&c.vdof, vdu));   // vertex evaluation reads user-ordered vectors
+    }
     LBMG_TRY(h->upload(&c.vw, H.vw));
+    // finest-level norm work items: chunks of each (colour, mesh) segment
+    c.nitem_host.clear();
+    for (int m = 0; m < c.ninst; m++)
+        for (int q = 0; q < 8; q++) {
+            const int s0 = H.seg[2 * (8 * m + q)], s1 = H.seg[2 * (8 * m + q) + 1];
+            for (int r = s0; r < s1; r += 2048) c.nitem_host.insert(c.nitem_host.end(), {m, r, std::min(s1, r + 2048)});
+        }
+    c.nnitem = (int)(c.nitem_host.size() / 3);
+    LBMG_TRY(h->upload(&c.nitem, c.nitem_host));
+    LBMG_TRY(h->alloc(&c.item_part, 8 * (size_t)std::max(c.nnitem, 1)));
+    LBMG_TRY(h->alloc(&c.inst_norm, 12 * (size_t)c.ninst));
+    {
+        std::vector<const int *> rps(kMaxDepth + 1, nullptr), cis(kMaxDepth + 1, nullptr);
+        std::vector<const double *> As(kMaxDepth + 1, nullptr);
+        for (int d = c.d0; d <= c.D; d++) { rps[d] = c.lev[d].rp; cis[d] = c.lev[d].ci; As[d] = c.lev[d].A64; }
+        LBMG_TRY(h->upload(&h->lev_rp, rps));
+        LBMG_TRY(h->upload(&h->lev_ci, cis));
+        LBMG_TRY(h->upload(&h->lev_A, As));
+    }
     LBMG_TRY(h->alloc(&c.moments, 27 * (size_t)c.nfrag));
     LBMG_TRY(h->alloc(&c.stage, 72 * (size_t)c.nfrag));
     LBMG_TRY(h->alloc(&c.stage_rhs, 32 * (size_t)c.nfrag));
-    const int n0 = c.lev[c.d0].n;
-    LBMG_TRY(h->alloc(&c.cdense, (size_t)n0 * n0));
-    LBMG_TRY(h->alloc(&c.cinv64, (size_t)n0 * n0));
-    LBMG_TRY(h->alloc(&c.cinv32, (size_t)n0 * n0));
+    LBMG_TRY(h->alloc(&c.cdense, (size_t)std::max<int64_t>(inv_total, 1)));
+    LBMG_TRY(h->alloc(&c.cinv64, (size_t)std::max<int64_t>(inv_total, 1)));
+    LBMG_TRY(h->alloc(&c.cinv32, (size_t)std::max<int64_t>(inv_total, 1)));
     LBMG_TRY(h->alloc(&c.flag, 1));
     const size_t nD = (size_t)c.lev[c.D].n;
     LBMG_TRY(h->alloc(&c.xs, 4 * nD));
@@ -304,7 +355,7 @@ int upload_hierarchy(lbmg_handle h) {
     LBMG_TRY(h->alloc(&c.rs, 4 * nD));
     LBMG_TRY(h->alloc(&c.norm_part, 4 * (size_t)kNormBlocks));
     LBMG_TRY(h->alloc(&c.norm_out, 8));
-    h->io_cap = 4 * std::max(nD, (size_t)c.nv);
+    h->io_cap = 4 * std::max(std::max(nD, (size_t)c.nv), (size_t)c.nu);
     LBMG_TRY(h->alloc(&c.dev_io, 2 * h->io_cap));
     LBMG_CK(cudaMallocHost((void **)&c.h_norm, 8 * sizeof(double)));
     LBMG_CK(cudaMallocHost((void **)&h->h_flag, sizeof(int)));
@@ -314,8 +365,6 @@ int upload_hierarchy(lbmg_handle h) {
     for (int q = 0; q < 4; q++) LBMG_CK(cudaEventCreate(&c.ev_smooth[q]));
     c.persist_view_bytes = persist_view_bytes();
     LBMG_TRY(h->alloc((char **)&c.persist_views, c.persist_view_bytes));
-    LBMG_TRY(h->alloc(&c.persist_part, 8 * 1024));
-    LBMG_TRY(h->alloc(&c.persist_norm, 16));
     LBMG_TRY(h->alloc((char **)&c.persist_state, 64));
     LBMG_CK(cudaMallocHost(&c.h_state, 64 + 16 * sizeof(double)));
     c.persist_ok = persist_setup(c) == 0 && c.persist_blocks <= 1024;
@@ -375,7 +424,9 @@ int lbmg_build_hierarchy(const double *V, int nv, const int *F, int nt, int dept
     std::string err;
     int st;
     try {
-        st = build_host_hierarchy(V, nv, F, nt, depth, o.min_depth, o.coarse_max, o.split, o.threads, h->c.host, err);
+        std::vector<HostHierarchy> parts(1);
+        st = build_host_hierarchy(V, nv, F, nt, depth, o.min_depth, o.coarse_max, o.split, o.threads, parts[0], err);
+        if (st == 0) st = combine_batch(parts, h->c.host, err);
     } catch (const std::bad_alloc &) {
         st = LBMG_OUT_OF_MEMORY;
     } catch (...) {
@@ -392,6 +443,71 @@ int lbmg_build_hierarchy(const double *V, int nv, const int *F, int nt, int dept
     st = upload_hierarchy(h);
     if (st != 0) { delete h; return st; }
     *out = h;
+    return LBMG_OK;
+}
+
+int lbmg_build_batch(const double *const *V, const int *nv, const int *const *F, const int *nt, const int *depth,
+                     int ninst, const lbmg_options *opt, lbmg_handle *out) {
+    if (!out || !V || !nv || !F || !nt || !depth || ninst < 1) return LBMG_INVALID_ARG;
+    *out = nullptr;
+    lbmg_options o;
+    lbmg_default_options(&o);
+    if (opt) o = *opt;
+    if (o.nu1 < 0 || o.nu2 < 0 || o.coarse_max < 1 || o.coarse_max > kMaxCoarse) return LBMG_INVALID_ARG;
+    if (o.smoother != LBMG_GS_COLOURED || o.narrow_max < 0 || o.barrier_phantoms < 0) return LBMG_INVALID_ARG;
+    lbmg_ctx *h = new (std::nothrow) lbmg_ctx();
+    if (!h) return LBMG_OUT_OF_MEMORY;
+    std::string err;
+    int st = 0;
+    try {
+        std::vector<HostHierarchy> parts(ninst);
+        for (int i = 0; i < ninst && st == 0; i++) {
+            if (!V[i] || !F[i]) { st = LBMG_INVALID_ARG; break; }
+            st = build_host_hierarchy(V[i], nv[i], F[i], nt[i], depth[i], o.min_depth, o.coarse_max, o.split,
+                                      o.threads, parts[i], err);
+        }
+        if (st == 0) st = combine_batch(parts, h->c.host, err);
+    } catch (const std::bad_alloc &) {
+        st = LBMG_OUT_OF_MEMORY;
+    } catch (...) {
+        st = LBMG_INVALID_ARG;
+    }
+    if (st != 0) { delete h; return st; }
+    h->c.nu1 = o.nu1; h->c.nu2 = o.nu2; h->c.smoother = o.smoother; h->c.omega = o.jacobi_omega;
+    h->c.persistent = 1; h->c.persist_narrow = o.narrow_max; h->c.barrier_phantoms = o.barrier_phantoms;
+    st = upload_hierarchy(h);
+    if (st != 0) { delete h; return st; }
+    if (!h->c.persist_ok) { delete h; return LBMG_CUDA_ERROR; }
+    *out = h;
+    return LBMG_OK;
+}
+
+int lbmg_instances(lbmg_handle h, int *ninst) {
+    if (!h || !ninst) return LBMG_INVALID_ARG;
+    *ninst = h->c.ninst;
+    return LBMG_OK;
+}
+
+int lbmg_instance_info(lbmg_handle h, int inst, int *depth, int *min_depth, long *nfine, long *row_offset,
+                       long *vertex_offset) {
+    if (!h || inst < 0 || inst >= h->c.ninst) return LBMG_INVALID_ARG;
+    const HostHierarchy &H = h->c.host;
+    if (depth) *depth = H.inst_D[inst];
+    if (min_depth) *min_depth = H.inst_d0[inst];
+    if (nfine) *nfine = H.inst_nfine[inst];
+    if (row_offset) *row_offset = H.inst_uoff[inst];
+    if (vertex_offset) *vertex_offset = H.inst_voff[inst];
+    return LBMG_OK;
+}
+
+int lbmg_instance_residuals(lbmg_handle h, int nrhs, double *rel) {
+    if (!h || !rel || nrhs < 1 || nrhs > 4) return LBMG_INVALID_ARG;
+    if (h->inst_norm_host.size() != 12 * (size_t)h->c.ninst) return LBMG_NOT_ASSEMBLED;
+    for (int m = 0; m < h->c.ninst; m++)
+        for (int r = 0; r < nrhs; r++) {
+            const double *nm = &h->inst_norm_host[12 * (size_t)m];
+            rel[(size_t)m * nrhs + r] = nm[4 + r] > 0 ? std::sqrt(nm[r] / nm[4 + r]) : 0.0;
+        }
     return LBMG_OK;
 }
 
@@ -427,7 +543,7 @@ int lbmg_assemble(lbmg_handle h, double t, void *stream) {
     launch_fine_gather(c, t, s);
     for (int d = c.D - 1; d >= c.d0; d--) launch_galerkin(c, d, t, s);
     for (int d = c.d0; d <= c.D; d++) launch_inverse_diag(c.lev[d], s);
-    launch_coarse_factor(c, s);
+    launch_coarse_factor(c, h->lev_rp, h->lev_ci, h->lev_A, s);
     LBMG_TRY(check_launch());
     LBMG_CK(cudaMemcpyAsync(h->h_flag, c.flag, sizeof(int), cudaMemcpyDeviceToHost, s));
     LBMG_CK(cudaStreamSynchronize(s));
@@ -482,8 +598,8 @@ static int solve_impl(lbmg_handle h, const double *rhs, double *x, int nrhs, dou
     LBMG_TRY(output_ptr(h, x, cnt, 1, &xout, &host_out));
     if (c.persistent && c.persist_ok && c.smoother == LBMG_GS_COLOURED) {
         LBMG_CK(cudaEventRecord(c.ev0, s));
-        launch_pack(rd, Fl.n, nrhs, R, c.bs, s);
-        launch_pack(xin, Fl.n, nrhs, R, c.xs, s);
+        launch_pack(rd, Fl.n, nrhs, R, c.bs, s, c.fperm);
+        launch_pack(xin, Fl.n, nrhs, R, c.xs, s, c.fperm);
         const int e = persist_solve(c, precision, R, nrhs, check ? tol : 0.0, max_cycles, s);
         if (e) {
             g_cuda_err = std::string("cooperative launch: ") + cudaGetErrorString((cudaError_t)e);
@@ -492,23 +608,28 @@ static int solve_impl(lbmg_handle h, const double *rhs, double *x, int nrhs, dou
         }
         unsigned char *hs = reinterpret_cast<unsigned char *>(c.h_state);
         LBMG_CK(cudaMemcpyAsync(hs, c.persist_state, 64, cudaMemcpyDeviceToHost, s));
-        LBMG_CK(cudaMemcpyAsync(hs + 64, c.persist_norm, 16 * sizeof(double), cudaMemcpyDeviceToHost, s));
-        launch_unpack(c.xs, Fl.n, nrhs, R, xout, s);
+        launch_unpack(c.xs, Fl.n, nrhs, R, xout, s, c.fperm);
         LBMG_CK(cudaEventRecord(c.ev1, s));
         LBMG_TRY(finish_output(x, xout, cnt, host_out, s));
         LBMG_CK(cudaEventSynchronize(c.ev1));
+        h->inst_norm_host.assign(12 * (size_t)c.ninst, 0.0);
+        LBMG_CK(cudaMemcpy(h->inst_norm_host.data(), c.inst_norm, 12 * sizeof(double) * c.ninst, cudaMemcpyDeviceToHost));
         int dstat, dcyc;
         unsigned long long sns;
-        double nrm[16];
         std::memcpy(&dstat, hs + 16, sizeof(int));
         std::memcpy(&dcyc, hs + 20, sizeof(int));
         std::memcpy(&sns, hs + 24, sizeof(sns));
-        std::memcpy(nrm, hs + 64, sizeof nrm);
         bool conv = true;
-        for (int r = 0; r < nrhs; r++) {
-            const double rel = nrm[4 + r] > 0 ? std::sqrt(nrm[r] / nrm[4 + r]) : 0.0;
-            if (!(rel <= tol)) conv = false;
-        }
+        double worst[4] = {0, 0, 0, 0}, worst0[4] = {0, 0, 0, 0};
+        for (int m = 0; m < c.ninst; m++)
+            for (int r = 0; r < nrhs; r++) {
+                const double *nm = &h->inst_norm_host[12 * (size_t)m];
+                const double rel = nm[4 + r] > 0 ? std::sqrt(nm[r] / nm[4 + r]) : 0.0;
+                const double rel0 = nm[4 + r] > 0 ? std::sqrt(nm[8 + r] / nm[4 + r]) : 0.0;
+                if (!(rel <= tol)) conv = false;
+                worst[r] = std::max(worst[r], rel);
+                worst0[r] = std::max(worst0[r], rel0);
+            }
         int status = LBMG_OK;
         if (dstat == 1) status = LBMG_DEVICE_TIMEOUT;
         else if (dstat == 2) status = LBMG_DIVERGED;
@@ -517,8 +638,8 @@ static int solve_impl(lbmg_handle h, const double *rhs, double *x, int nrhs, dou
             stats->cycles = dcyc;
             stats->converged = (check && conv && dstat == 0) ? 1 : 0;
             for (int r = 0; r < 4; r++) {
-                stats->rel_residual[r] = (r < nrhs && nrm[4 + r] > 0) ? std::sqrt(nrm[r] / nrm[4 + r]) : 0.0;
-                stats->initial_residual[r] = (r < nrhs && nrm[4 + r] > 0) ? std::sqrt(nrm[8 + r] / nrm[4 + r]) : 0.0;
+                stats->rel_residual[r] = r < nrhs ? worst[r] : 0.0;
+                stats->initial_residual[r] = r < nrhs ? worst0[r] : 0.0;
             }
             float ms = 0;
             cudaEventElapsedTime(&ms, c.ev0, c.ev1);
@@ -527,11 +648,12 @@ static int solve_impl(lbmg_handle h, const double *rhs, double *x, int nrhs, dou
         }
         return status;
     }
+    if (c.ninst > 1) return LBMG_INVALID_ARG;   // batches need the persistent solve (per-mesh norms)
     cudaGraphExec_t exec;
     LBMG_TRY(get_graph(h, R, precision, &exec));
     LBMG_CK(cudaEventRecord(c.ev0, s));
-    launch_pack(rd, Fl.n, nrhs, R, c.bs, s);
-    launch_pack(xin, Fl.n, nrhs, R, c.xs, s);
+    launch_pack(rd, Fl.n, nrhs, R, c.bs, s, c.fperm);
+    launch_pack(xin, Fl.n, nrhs, R, c.xs, s, c.fperm);
     launch_residual<double>(Fl, Fl.A64, c.bs, c.xs, c.rs, R, s);
     double nb[4] = {0, 0, 0, 0}, nr[4] = {0, 0, 0, 0}, r0[4] = {0, 0, 0, 0};
     int cycles = 0, status = LBMG_OK;
@@ -580,7 +702,7 @@ static int solve_impl(lbmg_handle h, const double *rhs, double *x, int nrhs, dou
         for (int k = 0; k < max_cycles; k++) LBMG_CK(cudaGraphLaunch(exec, s));
         cycles = max_cycles;
     }
-    launch_unpack(c.xs, Fl.n, nrhs, R, xout, s);
+    launch_unpack(c.xs, Fl.n, nrhs, R, xout, s, c.fperm);
     LBMG_CK(cudaEventRecord(c.ev1, s));
     LBMG_TRY(finish_output(x, xout, cnt, host_out, s));
     if (stats) {
@@ -708,8 +830,10 @@ int lbmg_launch_counts(lbmg_handle h, int precision, int *assemble, int *project
         cyc += (c.nu1 + c.nu2) * per_sweep + 3;   // sweeps, residual, restriction, prolongation
     }
     cyc += (precision == LBMG_MIXED ? 2 : 1) + 1 + 2;   // conversion/update, FP64 residual, norms
-    if (per_cycle) *per_cycle = cyc;
-    if (solve_fixed) *solve_fixed = 2 + 1 + 2 + 2 + 1;  // packs, residual, two norms, unpack
+    const bool persistent = c.persistent && c.persist_ok && c.smoother == LBMG_GS_COLOURED;
+    // the persistent solve runs every cycle inside one launch: two packs, the solve, one unpack
+    if (per_cycle) *per_cycle = persistent ? 0 : cyc;
+    if (solve_fixed) *solve_fixed = persistent ? 4 : 2 + 1 + 2 + 2 + 1;
     return LBMG_OK;
 }
 

@@ -57,8 +57,8 @@ constexpr int kWarpsPerBlock = 8;
 // One warp per fragment.  Writes the 27 moments and the 36 (M, L) local pair entries.
 __global__ void __launch_bounds__(32 * kWarpsPerBlock)
 fragment_moments_kernel(int nfrag, const double *__restrict__ poly, const int *__restrict__ pstart,
-                        const int *__restrict__ ftri, const double *__restrict__ tnormal, double area_scale,
-                        double *__restrict__ moments, double *__restrict__ stage) {
+                        const int *__restrict__ ftri, const double *__restrict__ tnormal,
+                        const double *__restrict__ fscale, double *__restrict__ moments, double *__restrict__ stage) {
     __shared__ double sh[kWarpsPerBlock][27 + 54 + 108 + 216];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int f = blockIdx.x * kWarpsPerBlock + warp;
@@ -161,7 +161,7 @@ fragment_moments_kernel(int nfrag, const double *__restrict__ poly, const int *_
                 }
                 Lab = fma(Q * sgn, G[gidx(t[0], t[1], t[2])], Lab);
             }
-        stage[2 * (36 * (size_t)f + p)] = Mab * area_scale;
+        stage[2 * (36 * (size_t)f + p)] = Mab * fscale[f];
         stage[2 * (36 * (size_t)f + p) + 1] = Lab;
     }
 }
@@ -170,7 +170,7 @@ void launch_fragment_moments(const Ctx &c, cudaStream_t s) {
     ensure_gl();
     const int blocks = (c.nfrag + kWarpsPerBlock - 1) / kWarpsPerBlock;
     fragment_moments_kernel<<<blocks, 32 * kWarpsPerBlock, 0, s>>>(
-        c.nfrag, c.poly, c.pstart, c.ftri, c.tnormal, c.host.sigma * c.host.sigma, c.moments, c.stage);
+        c.nfrag, c.poly, c.pstart, c.ftri, c.tnormal, c.frag_scale, c.moments, c.stage);
 }
 
 // finest level: sum the local-pair contributions of every stored entry
@@ -248,7 +248,8 @@ void launch_inverse_diag(const DevLevel &L, cudaStream_t s) {
 __global__ void fragment_rhs_kernel(int nfrag, int nrhs, const double *__restrict__ moments,
                                     const int *__restrict__ ftri, const int *__restrict__ fvox,
                                     const int *__restrict__ F, const double *__restrict__ Vg,
-                                    const double *__restrict__ fv, double area_scale, double *__restrict__ out) {
+                                    const double *__restrict__ fv, const double *__restrict__ fscale,
+                                    double *__restrict__ out) {
     const int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= nfrag) return;
     const int t = ftri[f];
@@ -296,13 +297,14 @@ __global__ void fragment_rhs_kernel(int nfrag, int nrhs, const double *__restric
         const double beta0 = fa + g[0] * lo[0] + g[1] * lo[1] + g[2] * lo[2];
         for (int a = 0; a < 8; a++) {
             const double v = beta0 * Ib[a] + g[0] * Iu[a][0] + g[1] * Iu[a][1] + g[2] * Iu[a][2];
-            out[(8 * (size_t)f + a) * 4 + r] = v * area_scale;
+            out[(8 * (size_t)f + a) * 4 + r] = v * fscale[f];
         }
     }
 }
 
 __global__ void rhs_gather_kernel(int n, int nrhs, const int64_t *__restrict__ rrp, const uint32_t *__restrict__ ridx,
-                                  const double *__restrict__ stage, double *__restrict__ rhs) {
+                                  const double *__restrict__ stage, const int *__restrict__ fiperm,
+                                  double *__restrict__ rhs) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double acc[4] = {0, 0, 0, 0};
@@ -310,14 +312,15 @@ __global__ void rhs_gather_kernel(int n, int nrhs, const int64_t *__restrict__ r
         const double *v = stage + 4 * (size_t)ridx[k];
         for (int r = 0; r < 4; r++) acc[r] += v[r];
     }
-    for (int r = 0; r < nrhs; r++) rhs[(size_t)i * nrhs + r] = acc[r];
+    const size_t u = (size_t)fiperm[i];
+    for (int r = 0; r < nrhs; r++) rhs[u * nrhs + r] = acc[r];
 }
 
 void launch_project_rhs(const Ctx &c, const double *fv, int nrhs, double *rhs_out, cudaStream_t s) {
     fragment_rhs_kernel<<<(c.nfrag + 127) / 128, 128, 0, s>>>(c.nfrag, nrhs, c.moments, c.ftri, c.fvox, c.F, c.Vg, fv,
-                                                               c.host.sigma * c.host.sigma, c.stage_rhs);
+                                                               c.frag_scale, c.stage_rhs);
     const int n = c.lev[c.D].n;
-    rhs_gather_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, nrhs, c.rrp, c.ridx, c.stage_rhs, rhs_out);
+    rhs_gather_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, nrhs, c.rrp, c.ridx, c.stage_rhs, c.fiperm, rhs_out);
 }
 
 __global__ void eval_vertices_kernel(int nv, int nrhs, const int *__restrict__ vdof, const double *__restrict__ vw,

@@ -15,7 +15,10 @@ constexpr uint32_t kPackMask = (1u << kPackShift) - 1u;
 struct HostLevel {
     int d = 0;
     int ndof = 0;
-    int colour_start[9] = {0};          // dofs sorted by corner parity colour 0..7
+    int ns = 0;                         // rows [0, ns) are smoothed; [ns, ndof) are coarsest-level rows
+    int colour_start[9] = {0};          // smoothed rows sorted by corner parity colour 0..7
+    std::vector<int32_t> coarse;        // coarsest-level blocks: (instance, first row, rows) triples
+    std::vector<int32_t> inst;          // [ndof] instance of each row
     std::vector<int32_t> corner;        // [ndof*3] grid corner index at depth d
     std::vector<int32_t> mintri;        // [ndof] smallest triangle of the component
     // (corner Morton key, triangle) -> dof, sorted by key then triangle
@@ -37,6 +40,14 @@ struct HostLevel {
 
 struct HostHierarchy {
     int D = 0, d0 = 0, nv = 0, nt = 0, split = 1;
+    int ninst = 1;                                    // meshes in this hierarchy (a batch when > 1)
+    // per instance: finest depth, coarsest depth, vertex/triangle/user-row offsets and counts,
+    // physical length per finest grid unit, cube side and centre
+    std::vector<int32_t> inst_D, inst_d0, inst_voff, inst_toff, inst_uoff, inst_nfine;
+    std::vector<double> inst_sigma, inst_S, inst_center;
+    std::vector<double> frag_scale;                   // [nfrag] physical area per finest-unit area
+    std::vector<int32_t> fperm;                       // user finest index -> row of the finest level
+    std::vector<int32_t> seg;                         // finest rows of (colour, instance): [8*ninst][2]
     double S = 0, center[3] = {0, 0, 0}, sigma = 0;   // cube side, centre, physical length per finest unit
     std::vector<double> Vg;                           // vertices in finest-grid units
     std::vector<int32_t> F;
@@ -64,6 +75,12 @@ inline int pair_index(int a, int b) {
     if (a > b) { int t = a; a = b; b = t; }
     return a * 8 - a * (a - 1) / 2 + (b - a);
 }
+
+// Concatenate separately built hierarchies into one batch: level depth D - k of
+// the batch holds level inst_D - k of every instance that has it.  Smoothed rows
+// are ordered by (colour, instance, own order); rows of instances whose coarsest
+// level this is follow, instance by instance.  A batch of one keeps the layout.
+int combine_batch(std::vector<HostHierarchy> &parts, HostHierarchy &B, std::string &err);
 
 // Returns 0 on success, else an lbmg status code with a message in err.
 int build_host_hierarchy(const double *V, int nv, const int *F, int nt, int depth, int min_depth,

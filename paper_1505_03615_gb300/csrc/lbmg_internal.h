@@ -14,6 +14,8 @@ constexpr int kNormBlocks = 256;  // partial sums of the two-pass norm reduction
 
 struct DevLevel {
     int d = 0, n = 0;
+    int ns = 0;                            // rows [0, ns) are smoothed; [ns, n) belong to coarsest blocks
+    int cb0 = 0, ncb = 0;                  // this level's coarsest blocks in Ctx::cblk
     int64_t nnz = 0;
     int cs[9] = {0};                       // colour ranges
     int *rp = nullptr, *ci = nullptr;
@@ -40,6 +42,20 @@ struct GraphCache {
 struct Ctx {
     HostHierarchy host;
     int D = 0, d0 = 0, nv = 0, nt = 0, nfrag = 0;
+    int ninst = 1, nu = 0;                 // meshes; rows of a user finest vector
+    double *frag_scale = nullptr;          // [nfrag] physical area per finest-unit area
+    int *fperm = nullptr;                  // [nu] user finest index -> finest row
+    int *fiperm = nullptr;                 // [n_D] finest row -> user index
+    // coarsest blocks, one per mesh: (level, mesh, first row, rows, inverse offset), sorted by level
+    std::vector<int> cblk_host;
+    int *cblk = nullptr;
+    int ncblk = 0, n0max = 0;
+    // finest-level norm work items: (mesh, first row, end row), chunks of (colour, mesh) segments
+    std::vector<int> nitem_host;
+    int *nitem = nullptr;
+    int nnitem = 0;
+    double *item_part = nullptr;           // [nnitem][8]
+    double *inst_norm = nullptr;           // [ninst][12]: ||r||^2, ||b||^2, initial ||r||^2 per rhs
     int nu1 = 2, nu2 = 2, smoother = 0;
     double omega = 0.6;
     DevLevel lev[kMaxDepth + 1];
@@ -106,16 +122,19 @@ void launch_eval_vertices(const Ctx &c, const double *x, int nrhs, double *u, cu
 template <class T> void launch_smooth_colour(const DevLevel &L, int colour, const T *A, const T *dinv,
                                              const T *b, T *x, int R, cudaStream_t s);
 template <class T> void launch_residual(const DevLevel &L, const T *A, const T *b, const T *x, T *r, int R,
-                                        cudaStream_t s);
+                                        cudaStream_t s, int nrows = -1);
 template <class T> void launch_jacobi_update(const DevLevel &L, const T *dinv, const T *r, T *x, T omega, int R,
                                              cudaStream_t s);
 template <class T> void launch_restrict(const DevLevel &Lc, const T *rf, T *bc, int R, cudaStream_t s);
 template <class T> void launch_prolong_add(const DevLevel &Lf, const T *xc, T *xf, int R, cudaStream_t s);
-template <class T> void launch_coarse_apply(int n, const T *inv, const T *b, T *x, int R, cudaStream_t s);
-void launch_coarse_factor(const Ctx &c, cudaStream_t s);
+struct Ctx;
+template <class T> void launch_coarse_apply(const Ctx &c, const DevLevel &L, const T *inv, const T *b, T *x, int R,
+                                            cudaStream_t s);
+void launch_coarse_factor(const Ctx &c, const int *const *rps, const int *const *cis, const double *const *As,
+                          cudaStream_t s);
 void launch_norms(const double *v, int n, int R, double *part, double *out, cudaStream_t s);
-void launch_pack(const double *user, int n, int nrhs, int R, double *v, cudaStream_t s);
-void launch_unpack(const double *v, int n, int nrhs, int R, double *user, cudaStream_t s);
+void launch_pack(const double *user, int n, int nrhs, int R, double *v, cudaStream_t s, const int *perm = nullptr);
+void launch_unpack(const double *v, int n, int nrhs, int R, double *user, cudaStream_t s, const int *perm = nullptr);
 void launch_to_float(const double *a, float *b, int64_t n, cudaStream_t s);
 void launch_add_float(double *x, const float *e, int64_t n, cudaStream_t s);
 void launch_add_double(double *x, const double *e, int64_t n, cudaStream_t s);

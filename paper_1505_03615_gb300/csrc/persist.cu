@@ -98,8 +98,9 @@ __device__ bool grid_sync(unsigned *bar, int *status, unsigned expected) {
 
 template <class T, int R>
 struct Lv {
-    int n;
+    int n, ns, ncb;
     int cs[9];
+    const int *cb;                  // this level's coarsest blocks: (level, mesh, first row, rows, inverse offset)
     const int *rp, *ci;
     const T *A, *dinv;
     const int *par;
@@ -162,7 +163,7 @@ __device__ void gs_colour(const Lv<T, R> &L, int c, Team tm) {
 
 template <class T, int R>
 __device__ void residual(const Lv<T, R> &L, Team tm) {
-    for_rows<T, R>(0, L.n, tm, [&](int row, bool active, int lane) {
+    for_rows<T, R>(0, L.ns, tm, [&](int row, bool active, int lane) {
         T acc[R];
         row_dot<T, R>(L, row, active, lane, L.x, acc);
         if (active && lane == 0) {
@@ -197,7 +198,7 @@ __device__ void restrict_to(const Lv<T, R> &Lc, const T *rf, Team tm) {
 // x_f += P x_c
 template <class T, int R>
 __device__ void prolong_from(const Lv<T, R> &Lf, const T *xc, Team tm) {
-    for (int i = tm.tid; i < Lf.n; i += tm.nthr) {
+    for (int i = tm.tid; i < Lf.ns; i += tm.nthr) {
         const int np = 1 << __ldg(Lf.npl2 + i);
         T acc[R], v[R], xv[R];
 #pragma unroll
@@ -214,27 +215,33 @@ __device__ void prolong_from(const Lv<T, R> &Lf, const T *xc, Team tm) {
     }
 }
 
+// x = inv b on each coarsest block of a level; a team takes blocks first..first+count-1 by stride
 template <class T, int R>
-__device__ void coarse_apply(const Lv<T, R> &L0, const T *inv, Team tm) {
+__device__ void coarse_apply(const Lv<T, R> &L, const T *inv, int first, int stride, Team tm) {
     const int warp = tm.tid >> 5, lane = tm.tid & 31, nw = tm.nthr >> 5;
-    for (int row = warp; row < L0.n; row += nw) {
-        T acc[R];
+    for (int k = first; k < L.ncb; k += stride) {
+        const int *cb = L.cb + 5 * k;
+        const int row0 = cb[2], n = cb[3];
+        const T *M = inv + cb[4];
+        for (int row = warp; row < n; row += nw) {
+            T acc[R];
 #pragma unroll
-        for (int q = 0; q < R; q++) acc[q] = T(0);
-        for (int j = lane; j < L0.n; j += 32) {
-            const T a = __ldg(inv + (size_t)row * L0.n + j);
-            T v[R];
-            ldcg_vec<T, R>(L0.b + (size_t)j * R, v);
+            for (int q = 0; q < R; q++) acc[q] = T(0);
+            for (int j = lane; j < n; j += 32) {
+                const T a = __ldg(M + (size_t)row * n + j);
+                T v[R];
+                ldcg_vec<T, R>(L.b + (size_t)(row0 + j) * R, v);
 #pragma unroll
-            for (int q = 0; q < R; q++) acc[q] = fma(a, v[q], acc[q]);
+                for (int q = 0; q < R; q++) acc[q] = fma(a, v[q], acc[q]);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                for (int q = 0; q < R; q++) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+            if (lane == 0)
+#pragma unroll
+                for (int q = 0; q < R; q++) L.x[(size_t)(row0 + row) * R + q] = acc[q];
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-            for (int q = 0; q < R; q++) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
-        if (lane == 0)
-#pragma unroll
-            for (int q = 0; q < R; q++) L0.x[(size_t)row * R + q] = acc[q];
     }
 }
 
@@ -249,8 +256,10 @@ struct PersistParams {
     const int *rpF, *ciF;
     const double *A64F, *bs;
     double *xs, *rs;
-    double *part;             // [gridDim][8]
-    double *norm;             // [8]: ||r||^2 [0..3], ||b||^2 [4..7]
+    const int *items;         // norm work items (mesh, first row, end row)
+    int nitems, ninst;
+    double *part;             // [nitems][8]
+    double *norm;             // [ninst][12]: ||r||^2 [0..3], ||b||^2 [4..7], initial ||r||^2 [8..11]
     unsigned *bar;
     unsigned expected;        // arrivals that complete a barrier
     int *status;
@@ -267,39 +276,43 @@ __global__ void __launch_bounds__(1024, 1) solve_persistent_kernel(PersistParams
     __shared__ double red[32][8];
     unsigned long long t_smooth = 0;
 
-    // norms of the FP64 residual rs (and, first time, of bs), per right-hand side
+    // per-mesh norms of the FP64 residual rs (and, the first time, of bs): one warp per
+    // work item (a chunk of the rows of one mesh and colour), then block 0 adds the
+    // items of each mesh in order, so the sums do not depend on timing
     auto norms = [&](bool with_b) -> bool {
-        double acc[8];
+        const int warp = grid.tid >> 5, lane = grid.tid & 31, nw = grid.nthr >> 5;
+        for (int it = warp; it < p.nitems; it += nw) {
+            const int r0 = __ldg(p.items + 3 * it + 1), r1 = __ldg(p.items + 3 * it + 2);
+            double acc[8];
 #pragma unroll
-        for (int q = 0; q < 8; q++) acc[q] = 0.0;
-        const int nF = lev[p.D].n;
-        for (int i = grid.tid; i < nF; i += grid.nthr)
+            for (int q = 0; q < 8; q++) acc[q] = 0.0;
+            for (int i = r0 + lane; i < r1; i += 32)
 #pragma unroll
-            for (int q = 0; q < R; q++) {
-                const double rv = __ldcg(p.rs + (size_t)i * R + q);
-                acc[q] = fma(rv, rv, acc[q]);
-                if (with_b) { const double bv = p.bs[(size_t)i * R + q]; acc[4 + q] = fma(bv, bv, acc[4 + q]); }
+                for (int q = 0; q < R; q++) {
+                    const double rv = __ldcg(p.rs + (size_t)i * R + q);
+                    acc[q] = fma(rv, rv, acc[q]);
+                    if (with_b) { const double bv = p.bs[(size_t)i * R + q]; acc[4 + q] = fma(bv, bv, acc[4 + q]); }
+                }
+#pragma unroll
+            for (int q = 0; q < 8; q++)
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+            if (lane < 8) {
+                double v = 0.0;
+#pragma unroll
+                for (int q = 0; q < 8; q++) if (q == lane) v = acc[q];
+                p.part[8 * (size_t)it + lane] = v;
             }
-#pragma unroll
-        for (int q = 0; q < 8; q++)
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
-        if ((threadIdx.x & 31) == 0)
-#pragma unroll
-            for (int q = 0; q < 8; q++) red[threadIdx.x >> 5][q] = acc[q];
-        __syncthreads();
-        if (threadIdx.x < 8) {
-            double s = 0.0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += red[w][threadIdx.x];
-            p.part[blockIdx.x * 8 + threadIdx.x] = s;
         }
         if (!grid_sync(p.bar, p.status, p.expected)) return false;
-        if (b0 && threadIdx.x < 8) {
-            const int q = threadIdx.x;
-            if (q < 4 || with_b) {
+        if (b0) {
+            for (int k = threadIdx.x; k < p.ninst * 8; k += blockDim.x) {
+                const int m = k >> 3, q = k & 7;
+                if (q >= 4 && !with_b) continue;
                 double s = 0.0;
-                for (int g = 0; g < (int)gridDim.x; g++) s += __ldcg(p.part + g * 8 + q);
-                p.norm[q] = s;
+                for (int it = 0; it < p.nitems; it++)
+                    if (__ldg(p.items + 3 * it) == m) s += __ldcg(p.part + 8 * (size_t)it + q);
+                p.norm[12 * m + q] = s;
             }
         }
         return grid_sync(p.bar, p.status, p.expected);
@@ -335,17 +348,20 @@ __global__ void __launch_bounds__(1024, 1) solve_persistent_kernel(PersistParams
     fine_residual();
     if (!grid_sync(p.bar, p.status, p.expected)) return;
     if (!norms(true)) return;
-    if (b0 && threadIdx.x < 4) p.norm[8 + threadIdx.x] = __ldcg(p.norm + threadIdx.x);
+    if (b0)
+        for (int k = threadIdx.x; k < p.ninst * 4; k += blockDim.x)
+            p.norm[12 * (k >> 2) + 8 + (k & 3)] = __ldcg(p.norm + 12 * (k >> 2) + (k & 3));
     if (!grid_sync(p.bar, p.status, p.expected)) return;
 
     int cyc = 0;
     for (;; cyc++) {
         bool done = true, bad = false;
-        for (int q = 0; q < p.nrhs; q++) {
-            const double r2 = __ldcg(p.norm + q), b2 = __ldcg(p.norm + 4 + q);
-            if (!(r2 <= p.tol2 * b2)) done = false;
-            if (!(r2 <= 1e300) || r2 > 1e12 * __ldcg(p.norm + 8 + q) + 1e-300) bad = true;   // NaN, inf or growth by 1e6
-        }
+        for (int m = 0; m < p.ninst; m++)
+            for (int q = 0; q < p.nrhs; q++) {
+                const double r2 = __ldcg(p.norm + 12 * m + q), b2 = __ldcg(p.norm + 12 * m + 4 + q);
+                if (!(r2 <= p.tol2 * b2)) done = false;
+                if (!(r2 <= 1e300) || r2 > 1e12 * __ldcg(p.norm + 12 * m + 8 + q) + 1e-300) bad = true;   // NaN, inf or growth by 1e6
+            }
         if (bad) { if (b0 && threadIdx.x == 0) atomicExch(p.status, 2); break; }
         if (done || cyc >= p.max_cycles) break;
         // b_D = T(r), x_D = 0
@@ -354,9 +370,15 @@ __global__ void __launch_bounds__(1024, 1) solve_persistent_kernel(PersistParams
             for (int q = grid.tid; q < F.n * R; q += grid.nthr) { F.b[q] = (T)__ldcg(p.rs + q); F.x[q] = T(0); }
         }
         if (!grid_sync(p.bar, p.status, p.expected)) return;
-        // down the wide levels
-        for (int d = p.D; d > p.dn; d--) {
+        // down the wide levels (all blocks); dn < d0 means there are no narrow levels
+        const int dw = p.dn >= p.d0 ? p.dn + 1 : p.d0;
+        for (int d = p.D; d >= dw; d--) {
             const Lv<T, R> &L = lev[d];
+            if (L.ncb > 0) {
+                coarse_apply<T, R>(L, reinterpret_cast<const T *>(p.cinv), blockIdx.x, gridDim.x, blk);
+                if (!grid_sync(p.bar, p.status, p.expected)) return;
+            }
+            if (d == p.d0) break;
             const unsigned long long t0 = (d == p.D && b0 && threadIdx.x == 0) ? globaltimer() : 0;
             for (int s = 0; s < p.nu1; s++)
                 for (int c = 0; c < 8; c++) {
@@ -371,29 +393,31 @@ __global__ void __launch_bounds__(1024, 1) solve_persistent_kernel(PersistParams
             if (!grid_sync(p.bar, p.status, p.expected)) return;
         }
         // the narrow levels, block 0 alone
-        if (b0) {
-            for (int d = p.dn; d > p.d0; d--) {
-                const Lv<T, R> &L = lev[d];
-                for (int s = 0; s < p.nu1; s++)
-                    for (int c = 0; c < 8; c++) { gs_colour<T, R>(L, c, blk); __syncthreads(); }
-                residual<T, R>(L, blk);
-                __syncthreads();
-                restrict_to<T, R>(lev[d - 1], L.r, blk);
-                __syncthreads();
+        if (p.dn >= p.d0) {
+            if (b0) {
+                for (int d = p.dn; d >= p.d0; d--) {
+                    const Lv<T, R> &L = lev[d];
+                    if (L.ncb > 0) { coarse_apply<T, R>(L, reinterpret_cast<const T *>(p.cinv), 0, 1, blk); __syncthreads(); }
+                    if (d == p.d0) break;
+                    for (int s = 0; s < p.nu1; s++)
+                        for (int c = 0; c < 8; c++) { gs_colour<T, R>(L, c, blk); __syncthreads(); }
+                    residual<T, R>(L, blk);
+                    __syncthreads();
+                    restrict_to<T, R>(lev[d - 1], L.r, blk);
+                    __syncthreads();
+                }
+                for (int d = p.d0 + 1; d <= p.dn; d++) {
+                    const Lv<T, R> &L = lev[d];
+                    prolong_from<T, R>(L, lev[d - 1].x, blk);
+                    __syncthreads();
+                    for (int s = 0; s < p.nu2; s++)
+                        for (int c = 7; c >= 0; c--) { gs_colour<T, R>(L, c, blk); __syncthreads(); }
+                }
             }
-            coarse_apply<T, R>(lev[p.d0], reinterpret_cast<const T *>(p.cinv), blk);
-            __syncthreads();
-            for (int d = p.d0 + 1; d <= p.dn; d++) {
-                const Lv<T, R> &L = lev[d];
-                prolong_from<T, R>(L, lev[d - 1].x, blk);
-                __syncthreads();
-                for (int s = 0; s < p.nu2; s++)
-                    for (int c = 7; c >= 0; c--) { gs_colour<T, R>(L, c, blk); __syncthreads(); }
-            }
+            if (!grid_sync(p.bar, p.status, p.expected)) return;
         }
-        if (!grid_sync(p.bar, p.status, p.expected)) return;
         // up the wide levels
-        for (int d = p.dn + 1; d <= p.D; d++) {
+        for (int d = dw > p.d0 ? dw : p.d0 + 1; d <= p.D; d++) {
             const Lv<T, R> &L = lev[d];
             prolong_from<T, R>(L, lev[d - 1].x, grid);
             if (!grid_sync(p.bar, p.status, p.expected)) return;
@@ -451,6 +475,9 @@ static void fill_views(const Ctx &c, std::vector<char> &buf) {
         const DevLevel &L = c.lev[d];
         Lv<T, R> &o = v[d];
         o.n = L.n;
+        o.ns = L.ns;
+        o.ncb = L.ncb;
+        o.cb = c.cblk + 5 * L.cb0;
         for (int q = 0; q < 9; q++) o.cs[q] = L.cs[q];
         o.rp = L.rp; o.ci = L.ci;
         if constexpr (sizeof(T) == 4) {
@@ -476,8 +503,10 @@ int persist_setup(Ctx &c) {
     if (pd < 1) return 1;
     c.persist_blocks = sms;   // one block per SM
     // narrow levels: the bottom range whose every level has at most persist_narrow rows
-    c.persist_dn = c.d0;
-    for (int d = c.d0 + 1; d <= c.D; d++) {
+    // narrow levels: the bottom range whose every level has at most persist_narrow rows
+    // (persist_dn = d0 - 1: none, the bottom level itself is handled by all blocks)
+    c.persist_dn = c.d0 - 1;
+    for (int d = c.d0; d <= c.D; d++) {
         if (c.lev[d].n <= c.persist_narrow) c.persist_dn = d; else break;
     }
     return 0;
@@ -502,8 +531,11 @@ int persist_solve(Ctx &c, int precision, int R, int nrhs, double tol, int max_cy
     prm.cinv = f32 ? (const void *)c.cinv32 : (const void *)c.cinv64;
     prm.rpF = c.lev[c.D].rp; prm.ciF = c.lev[c.D].ci; prm.A64F = c.lev[c.D].A64;
     prm.bs = c.bs; prm.xs = c.xs; prm.rs = c.rs;
-    prm.part = c.persist_part;
-    prm.norm = c.persist_norm;
+    prm.items = c.nitem;
+    prm.nitems = c.nnitem;
+    prm.ninst = c.ninst;
+    prm.part = c.item_part;
+    prm.norm = c.inst_norm;
     unsigned char *st = reinterpret_cast<unsigned char *>(c.persist_state);
     prm.bar = reinterpret_cast<unsigned *>(st);
     prm.expected = (unsigned)(c.persist_blocks + c.barrier_phantoms);

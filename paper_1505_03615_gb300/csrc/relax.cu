@@ -120,13 +120,14 @@ void launch_smooth_colour(const DevLevel &L, int colour, const T *A, const T *di
 }
 
 template <class T>
-void launch_residual(const DevLevel &L, const T *A, const T *b, const T *x, T *r, int R, cudaStream_t s) {
-    if (L.n == 0) return;
+void launch_residual(const DevLevel &L, const T *A, const T *b, const T *x, T *r, int R, cudaStream_t s, int nrows) {
+    const int n = nrows < 0 ? L.n : nrows;
+    if (n == 0) return;
     const int threads = 256;
-    const unsigned blocks = (unsigned)(((int64_t)L.n * kRowGroup + threads - 1) / threads);
-    if (R == 1) residual_kernel<T, 1, kRowGroup><<<blocks, threads, 0, s>>>(L.n, L.rp, L.ci, A, b, x, r);
-    else if (R == 2) residual_kernel<T, 2, kRowGroup><<<blocks, threads, 0, s>>>(L.n, L.rp, L.ci, A, b, x, r);
-    else residual_kernel<T, 4, kRowGroup><<<blocks, threads, 0, s>>>(L.n, L.rp, L.ci, A, b, x, r);
+    const unsigned blocks = (unsigned)(((int64_t)n * kRowGroup + threads - 1) / threads);
+    if (R == 1) residual_kernel<T, 1, kRowGroup><<<blocks, threads, 0, s>>>(n, L.rp, L.ci, A, b, x, r);
+    else if (R == 2) residual_kernel<T, 2, kRowGroup><<<blocks, threads, 0, s>>>(n, L.rp, L.ci, A, b, x, r);
+    else residual_kernel<T, 4, kRowGroup><<<blocks, threads, 0, s>>>(n, L.rp, L.ci, A, b, x, r);
 }
 
 template <class T>
@@ -138,9 +139,9 @@ __global__ void jacobi_update_kernel(int n, int R, const T *__restrict__ dinv, c
 
 template <class T>
 void launch_jacobi_update(const DevLevel &L, const T *dinv, const T *r, T *x, T omega, int R, cudaStream_t s) {
-    const int64_t m = (int64_t)L.n * R;
+    const int64_t m = (int64_t)L.ns * R;
     if (m == 0) return;
-    jacobi_update_kernel<T><<<(unsigned)((m + 255) / 256), 256, 0, s>>>(L.n, R, dinv, r, x, omega);
+    jacobi_update_kernel<T><<<(unsigned)((m + 255) / 256), 256, 0, s>>>(L.ns, R, dinv, r, x, omega);
 }
 
 // b_c[J] = sum over fine children i of J of r_f[i] / #parents(i)
@@ -198,90 +199,112 @@ __global__ void prolong_add_kernel(int nf, const int *__restrict__ par, const in
 
 template <class T>
 void launch_prolong_add(const DevLevel &Lf, const T *xc, T *xf, int R, cudaStream_t s) {
-    if (Lf.n == 0) return;
-    const unsigned blocks = (unsigned)((Lf.n + 255) / 256);
-    if (R == 1) prolong_add_kernel<T, 1><<<blocks, 256, 0, s>>>(Lf.n, Lf.par, Lf.npl2, xc, xf);
-    else if (R == 2) prolong_add_kernel<T, 2><<<blocks, 256, 0, s>>>(Lf.n, Lf.par, Lf.npl2, xc, xf);
-    else prolong_add_kernel<T, 4><<<blocks, 256, 0, s>>>(Lf.n, Lf.par, Lf.npl2, xc, xf);
+    if (Lf.ns == 0) return;   // only smoothed rows have a coarser level
+    const unsigned blocks = (unsigned)((Lf.ns + 255) / 256);
+    if (R == 1) prolong_add_kernel<T, 1><<<blocks, 256, 0, s>>>(Lf.ns, Lf.par, Lf.npl2, xc, xf);
+    else if (R == 2) prolong_add_kernel<T, 2><<<blocks, 256, 0, s>>>(Lf.ns, Lf.par, Lf.npl2, xc, xf);
+    else prolong_add_kernel<T, 4><<<blocks, 256, 0, s>>>(Lf.ns, Lf.par, Lf.npl2, xc, xf);
 }
 
-// x = inv * b at the coarsest level, one warp per row
+// x = inv * b on every coarsest block of a level (one block per mesh), one warp per row
 template <class T, int R>
-__global__ void coarse_apply_kernel(int n, const T *__restrict__ inv, const T *__restrict__ b, T *__restrict__ x) {
-    const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (row >= n) return;
-    T acc[R];
+__global__ void coarse_apply_kernel(const int *__restrict__ cblk, const T *__restrict__ inv, const T *__restrict__ b,
+                                    T *__restrict__ x) {
+    const int *cb = cblk + 5 * blockIdx.x;
+    const int row0 = cb[2], n = cb[3];
+    const T *M = inv + cb[4];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int row = warp; row < n; row += nw) {
+        T acc[R];
 #pragma unroll
-    for (int r = 0; r < R; r++) acc[r] = T(0);
-    for (int j = lane; j < n; j += 32) {
-        const T a = inv[(size_t)row * n + j];
+        for (int r = 0; r < R; r++) acc[r] = T(0);
+        for (int j = lane; j < n; j += 32) {
+            const T a = M[(size_t)row * n + j];
 #pragma unroll
-        for (int r = 0; r < R; r++) acc[r] = fma(a, b[(size_t)j * R + r], acc[r]);
-    }
+            for (int r = 0; r < R; r++) acc[r] = fma(a, b[(size_t)(row0 + j) * R + r], acc[r]);
+        }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
+        for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-        for (int r = 0; r < R; r++) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
-    if (lane == 0) {
+            for (int r = 0; r < R; r++) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+        if (lane == 0) {
 #pragma unroll
-        for (int r = 0; r < R; r++) x[(size_t)row * R + r] = acc[r];
+            for (int r = 0; r < R; r++) x[(size_t)(row0 + row) * R + r] = acc[r];
+        }
     }
 }
 
 template <class T>
-void launch_coarse_apply(int n, const T *inv, const T *b, T *x, int R, cudaStream_t s) {
-    if (n == 0) return;
-    const unsigned blocks = (unsigned)((n * 32 + 255) / 256);
-    if (R == 1) coarse_apply_kernel<T, 1><<<blocks, 256, 0, s>>>(n, inv, b, x);
-    else if (R == 2) coarse_apply_kernel<T, 2><<<blocks, 256, 0, s>>>(n, inv, b, x);
-    else coarse_apply_kernel<T, 4><<<blocks, 256, 0, s>>>(n, inv, b, x);
+void launch_coarse_apply(const Ctx &c, const DevLevel &L, const T *inv, const T *b, T *x, int R, cudaStream_t s) {
+    if (L.ncb == 0) return;
+    const int *cb = c.cblk + 5 * L.cb0;
+    if (R == 1) coarse_apply_kernel<T, 1><<<L.ncb, 256, 0, s>>>(cb, inv, b, x);
+    else if (R == 2) coarse_apply_kernel<T, 2><<<L.ncb, 256, 0, s>>>(cb, inv, b, x);
+    else coarse_apply_kernel<T, 4><<<L.ncb, 256, 0, s>>>(cb, inv, b, x);
 }
 
 // ---- coarsest-level dense FP64 Cholesky of A + eps Id, eps = 1e-12 mean diag ----
-__global__ void dense_from_csr_kernel(int n, const int *__restrict__ rp, const int *__restrict__ ci,
-                                      const double *__restrict__ A, double *__restrict__ D) {
+// dense copy of each coarsest block (rows and columns row0..row0+n-1 of its level)
+__global__ void dense_from_csr_kernel(const int *__restrict__ cblk, const int *const *__restrict__ rps,
+                                      const int *const *__restrict__ cis, const double *const *__restrict__ As,
+                                      double *__restrict__ D) {
+    const int *cb = cblk + 5 * blockIdx.y;
+    const int lev = cb[0], row0 = cb[2], n = cb[3];
+    double *Dk = D + cb[4];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    for (int j = 0; j < n; j++) D[(size_t)i * n + j] = 0.0;
-    for (int k = rp[i]; k < rp[i + 1]; k++) D[(size_t)i * n + ci[k]] = A[k];
+    const int *rp = rps[lev], *ci = cis[lev];
+    const double *A = As[lev];
+    for (int j = 0; j < n; j++) Dk[(size_t)i * n + j] = 0.0;
+    for (int k = rp[row0 + i]; k < rp[row0 + i + 1]; k++) {
+        const int j = ci[k] - row0;
+        if (j >= 0 && j < n) Dk[(size_t)i * n + j] = A[k];
+    }
 }
 
-__global__ void __launch_bounds__(1024) cholesky_kernel(int n, double *D, int *flag) {
+__global__ void __launch_bounds__(1024) cholesky_kernel(const int *__restrict__ cblk, double *D, int *flag) {
     __shared__ double s_val;
+    const int *cb = cblk + 5 * blockIdx.x;
+    const int n = cb[3];
+    double *Dk = D + cb[4];
     const int tid = threadIdx.x, nthr = blockDim.x, warp = tid >> 5, lane = tid & 31, nw = nthr >> 5;
     if (tid == 0) {
         double tr = 0.0;
-        for (int i = 0; i < n; i++) tr += D[(size_t)i * n + i];
+        for (int i = 0; i < n; i++) tr += Dk[(size_t)i * n + i];
         s_val = 1e-12 * tr / (double)(n > 0 ? n : 1);
-        *flag = 0;
     }
     __syncthreads();
     const double eps = s_val;
-    for (int i = tid; i < n; i += nthr) D[(size_t)i * n + i] += eps;
+    for (int i = tid; i < n; i += nthr) Dk[(size_t)i * n + i] += eps;
     for (int j = 0; j < n; j++) {
         __syncthreads();
         if (tid == 0) {
-            double d = D[(size_t)j * n + j];
-            if (!(d > 0.0)) { *flag = 1; d = 1.0; }
+            double d = Dk[(size_t)j * n + j];
+            if (!(d > 0.0)) { atomicExch(flag, 1); d = 1.0; }
             s_val = sqrt(d);
-            D[(size_t)j * n + j] = s_val;
+            Dk[(size_t)j * n + j] = s_val;
         }
         __syncthreads();
         const double piv = s_val;
-        for (int i = j + 1 + tid; i < n; i += nthr) D[(size_t)i * n + j] /= piv;
+        for (int i = j + 1 + tid; i < n; i += nthr) Dk[(size_t)i * n + j] /= piv;
         __syncthreads();
         for (int i = j + 1 + warp; i < n; i += nw) {
-            const double lij = D[(size_t)i * n + j];
-            for (int k = j + 1 + lane; k <= i; k += 32) D[(size_t)i * n + k] -= lij * D[(size_t)k * n + j];
+            const double lij = Dk[(size_t)i * n + j];
+            for (int k = j + 1 + lane; k <= i; k += 32) Dk[(size_t)i * n + k] -= lij * Dk[(size_t)k * n + j];
         }
     }
 }
 
-// column c of (L L^T)^{-1}: forward then backward substitution on e_c
-__global__ void __launch_bounds__(256) cholesky_inverse_kernel(int n, const double *__restrict__ Lf,
+// column c of (L L^T)^{-1} of every block: forward then backward substitution on e_c
+__global__ void __launch_bounds__(256) cholesky_inverse_kernel(const int *__restrict__ cblk, const double *__restrict__ D,
                                                                double *__restrict__ inv64, float *__restrict__ inv32) {
     extern __shared__ double y[];
-    const int c = blockIdx.x, tid = threadIdx.x, nthr = blockDim.x;
+    const int *cb = cblk + 5 * blockIdx.y;
+    const int n = cb[3];
+    const int c = blockIdx.x;
+    if (c >= n) return;
+    const double *Lf = D + cb[4];
+    const int tid = threadIdx.x, nthr = blockDim.x;
     for (int i = tid; i < n; i += nthr) y[i] = (i == c) ? 1.0 : 0.0;
     for (int k = 0; k < n; k++) {
         __syncthreads();
@@ -299,17 +322,18 @@ __global__ void __launch_bounds__(256) cholesky_inverse_kernel(int n, const doub
     }
     __syncthreads();
     for (int i = tid; i < n; i += nthr) {
-        inv64[(size_t)i * n + c] = y[i];
-        inv32[(size_t)i * n + c] = (float)y[i];
+        inv64[cb[4] + (size_t)i * n + c] = y[i];
+        inv32[cb[4] + (size_t)i * n + c] = (float)y[i];
     }
 }
 
-void launch_coarse_factor(const Ctx &c, cudaStream_t s) {
-    const DevLevel &L = c.lev[c.d0];
-    const int n = L.n;
-    dense_from_csr_kernel<<<(n + 127) / 128, 128, 0, s>>>(n, L.rp, L.ci, L.A64, c.cdense);
-    cholesky_kernel<<<1, 1024, 0, s>>>(n, c.cdense, c.flag);
-    cholesky_inverse_kernel<<<n, 256, n * sizeof(double), s>>>(n, c.cdense, c.cinv64, c.cinv32);
+void launch_coarse_factor(const Ctx &c, const int *const *rps, const int *const *cis, const double *const *As,
+                          cudaStream_t s) {
+    if (c.ncblk == 0) return;
+    dense_from_csr_kernel<<<dim3((c.n0max + 127) / 128, c.ncblk), 128, 0, s>>>(c.cblk, rps, cis, As, c.cdense);
+    cholesky_kernel<<<c.ncblk, 1024, 0, s>>>(c.cblk, c.cdense, c.flag);
+    cholesky_inverse_kernel<<<dim3(c.n0max, c.ncblk), 256, c.n0max * sizeof(double), s>>>(c.cblk, c.cdense, c.cinv64,
+                                                                                         c.cinv32);
 }
 
 // ---- per-right-hand-side sums of squares, two passes (deterministic) ----
@@ -357,19 +381,24 @@ void launch_norms(const double *v, int n, int R, double *part, double *out, cuda
 }
 
 // ---- layout and elementwise kernels ----
-__global__ void pack_kernel(const double *__restrict__ u, int n, int nrhs, int R, double *__restrict__ v) {
+// user row u of [n][nrhs] <-> internal row perm[u] of [n][R] (perm = null: identity)
+__global__ void pack_kernel(const double *__restrict__ u, int n, int nrhs, int R, const int *__restrict__ perm,
+                            double *__restrict__ v) {
     const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= (int64_t)n * R) return;
     const int64_t i = q / R;
     const int r = (int)(q % R);
-    v[q] = r < nrhs ? u[i * nrhs + r] : 0.0;
+    const int64_t row = perm ? perm[i] : i;
+    v[row * R + r] = r < nrhs ? u[i * nrhs + r] : 0.0;
 }
-__global__ void unpack_kernel(const double *__restrict__ v, int n, int nrhs, int R, double *__restrict__ u) {
+__global__ void unpack_kernel(const double *__restrict__ v, int n, int nrhs, int R, const int *__restrict__ perm,
+                              double *__restrict__ u) {
     const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (q >= (int64_t)n * nrhs) return;
     const int64_t i = q / nrhs;
     const int r = (int)(q % nrhs);
-    u[q] = v[i * R + r];
+    const int64_t row = perm ? perm[i] : i;
+    u[q] = v[row * R + r];
 }
 __global__ void to_float_kernel(const double *__restrict__ a, float *__restrict__ b, int64_t n) {
     const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -384,13 +413,13 @@ __global__ void add_double_kernel(double *__restrict__ x, const double *__restri
     if (q < n) x[q] += e[q];
 }
 
-void launch_pack(const double *user, int n, int nrhs, int R, double *v, cudaStream_t s) {
+void launch_pack(const double *user, int n, int nrhs, int R, double *v, cudaStream_t s, const int *perm) {
     const int64_t m = (int64_t)n * R;
-    if (m) pack_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(user, n, nrhs, R, v);
+    if (m) pack_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(user, n, nrhs, R, perm, v);
 }
-void launch_unpack(const double *v, int n, int nrhs, int R, double *user, cudaStream_t s) {
+void launch_unpack(const double *v, int n, int nrhs, int R, double *user, cudaStream_t s, const int *perm) {
     const int64_t m = (int64_t)n * nrhs;
-    if (m) unpack_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(v, n, nrhs, R, user);
+    if (m) unpack_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(v, n, nrhs, R, perm, user);
 }
 void launch_to_float(const double *a, float *b, int64_t n, cudaStream_t s) {
     if (n) to_float_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, b, n);
@@ -406,11 +435,11 @@ void launch_add_double(double *x, const double *e, int64_t n, cudaStream_t s) {
 #define LBMG_INST(T)                                                                                           \
     template void launch_smooth_colour<T>(const DevLevel &, int, const T *, const T *, const T *, T *, int,   \
                                           cudaStream_t);                                                       \
-    template void launch_residual<T>(const DevLevel &, const T *, const T *, const T *, T *, int, cudaStream_t); \
+    template void launch_residual<T>(const DevLevel &, const T *, const T *, const T *, T *, int, cudaStream_t, int); \
     template void launch_jacobi_update<T>(const DevLevel &, const T *, const T *, T *, T, int, cudaStream_t);   \
     template void launch_restrict<T>(const DevLevel &, const T *, T *, int, cudaStream_t);                     \
     template void launch_prolong_add<T>(const DevLevel &, const T *, T *, int, cudaStream_t);                  \
-    template void launch_coarse_apply<T>(int, const T *, const T *, T *, int, cudaStream_t);
+    template void launch_coarse_apply<T>(const Ctx &, const DevLevel &, const T *, const T *, T *, int, cudaStream_t);
 LBMG_INST(float)
 LBMG_INST(double)
 
