@@ -77,8 +77,11 @@ typedef struct lbmg_stats {
     double rel_residual[4];  /* final ||rhs - A x||_2 / ||rhs||_2 per right-hand side (FP64) */
     double initial_residual[4];
     float ms_total;          /* device time of the solve, CUDA events */
-    float ms_fine_smooth;    /* device time of the finest-level smoothing sweeps summed over all cycles,
-                                from CUDA events recorded inside the cycle (0 for lbmg_vcycles) */
+    float ms_fine_smooth;    /* device time of the finest-level smoothing sweeps summed over all cycles
+                                (events in the per-cycle graph; %globaltimer in the persistent solve) */
+    int learned;             /* 1 if the finest sweeps started with learned weights (lbmg_learned_enable) */
+    int learned_fallback;    /* 1 if a learned cycle failed to reduce a residual and the solve went on
+                                with plain Gauss-Seidel weights */
 } lbmg_stats;
 
 typedef struct lbmg_ctx *lbmg_handle;
@@ -208,6 +211,43 @@ int lbmg_eval_vertices(lbmg_handle h, const double *x, int nrhs, double *u, void
 int lbmg_get_dofs(lbmg_handle h, int d, int *corner, int *mintri);
 int lbmg_get_matrix(lbmg_handle h, int d, int *rowptr, int *col, double *M, double *L);
 int lbmg_get_prolongation(lbmg_handle h, int d, int *parents, double *weights);
+
+/*
+ * Learned relaxation weights for the finest-level Gauss-Seidel sweeps.  The paper
+ * has no counterpart: its smoother is plain Gauss-Seidel (Sections 4.3, 5.2), which
+ * is also the fallback and the judge here.  A network 28 -> 64 (ReLU) -> 1 maps each
+ * finest node's stencil (coefficients / A_ii summed per neighbour-corner offset,
+ * A_ii / mean diagonal, entry count / 27) to y, and the node's sweep update is
+ * scaled by omega = 1.45 + 0.45 y / (1 + |y|) in (1, 1.9), so the sweep stays
+ * convergent for SPD systems.  Dense layers run on the tensor cores (BF16 inputs,
+ * FP32 accumulation).  Training minimises mean ||r_after||^2 / ||r_before||^2 over
+ * one V-cycle (learned finest sweeps, plain coarse correction), in FP64, by the
+ * exact adjoint of the cycle, with Adam on FP32 master weights.  Single-mesh
+ * hierarchies with at least two levels; needs lbmg_assemble first.
+ *  lbmg_learned_nparams: length P of the flat parameter vector: W1 [32][64]
+ *    row-major (rows 28..31 unused, zero), b1 [64], w2 [64], b2 [1].
+ *  lbmg_learned_params: get (host double[P], may be NULL) and/or set (host
+ *    double[P], may be NULL; resets the Adam moments).
+ *  lbmg_learned_collect: runs plain FP64 V-cycles from x = 0 on each column of
+ *    rhs [n_depth][ns] (user order) and stores the residuals of cycles
+ *    skip..skip+keep-1 as training samples (appended to the bank).
+ *  lbmg_learned_loss_grad: loss and gradient (host double[P], may be NULL) at
+ *    the current parameters for residual samples r0 [n_depth][ns], ns <= 4.
+ *  lbmg_learned_train: `steps` Adam steps; order (host int[steps][batch],
+ *    batch <= 4) lists the bank samples of each step; loss_hist (host
+ *    double[steps], may be NULL) receives each step's loss.
+ *  lbmg_learned_enable: on = 1 evaluates omega for the current matrix and makes
+ *    lbmg_solve use it (persistent solve only); 0 switches back.
+ *  lbmg_learned_omega: omega per finest function in user order (host double[n]).
+ */
+int lbmg_learned_nparams(void);
+int lbmg_learned_params(lbmg_handle h, double *get, const double *set, void *stream);
+int lbmg_learned_collect(lbmg_handle h, const double *rhs, int ns, int skip, int keep, void *stream);
+int lbmg_learned_loss_grad(lbmg_handle h, const double *r0, int ns, double *loss, double *grad, void *stream);
+int lbmg_learned_train(lbmg_handle h, int steps, double lr, const int *order, int batch, double *loss_hist,
+                       void *stream);
+int lbmg_learned_enable(lbmg_handle h, int on, void *stream);
+int lbmg_learned_omega(lbmg_handle h, double *omega);
 
 #ifdef __cplusplus
 }

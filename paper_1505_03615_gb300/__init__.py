@@ -21,7 +21,8 @@ __all__ = [
     "lbmg_assemble", "lbmg_project_rhs", "lbmg_solve", "lbmg_vcycles", "lbmg_residual", "lbmg_smooth",
     "lbmg_restrict", "lbmg_prolong_add", "lbmg_eval_vertices", "lbmg_get_dofs", "lbmg_get_matrix",
     "lbmg_get_prolongation", "lbmg_launch_counts", "lbmg_build_batch", "lbmg_instances", "lbmg_instance_info",
-    "lbmg_instance_residuals", "lbmg_status_string", "lbmg_last_cuda_error", "lbmg_default_options",
+    "lbmg_instance_residuals", "lbmg_learned_nparams", "lbmg_learned_params", "lbmg_learned_collect",
+    "lbmg_learned_loss_grad", "lbmg_learned_train", "lbmg_learned_enable", "lbmg_learned_omega", "lbmg_status_string", "lbmg_last_cuda_error", "lbmg_default_options",
 ]
 
 LBMG_OK = 0
@@ -53,7 +54,8 @@ class Options(C.Structure):
 
 class Stats(C.Structure):
     _fields_ = [("cycles", C.c_int), ("converged", C.c_int), ("rel_residual", C.c_double * 4),
-                ("initial_residual", C.c_double * 4), ("ms_total", C.c_float), ("ms_fine_smooth", C.c_float)]
+                ("initial_residual", C.c_double * 4), ("ms_total", C.c_float), ("ms_fine_smooth", C.c_float),
+                ("learned", C.c_int), ("learned_fallback", C.c_int)]
 
 
 def load_library():
@@ -91,6 +93,13 @@ def load_library():
         "lbmg_instances": (i, [P, P]),
         "lbmg_instance_info": (i, [P, i, P, P, P, P, P]),
         "lbmg_instance_residuals": (i, [P, i, P]),
+        "lbmg_learned_nparams": (i, []),
+        "lbmg_learned_params": (i, [P, P, P, P]),
+        "lbmg_learned_collect": (i, [P, P, i, i, i, P]),
+        "lbmg_learned_loss_grad": (i, [P, P, i, P, P, P]),
+        "lbmg_learned_train": (i, [P, i, d, P, i, P, P]),
+        "lbmg_learned_enable": (i, [P, i, P]),
+        "lbmg_learned_omega": (i, [P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -212,6 +221,55 @@ def lbmg_instance_residuals(h, nrhs):
     n = lbmg_instances(h)
     out = np.zeros((n, nrhs))
     _check(load_library().lbmg_instance_residuals(h, int(nrhs), _ptr(out)), "lbmg_instance_residuals")
+    return out
+
+
+def lbmg_learned_nparams():
+    return load_library().lbmg_learned_nparams()
+
+
+def lbmg_learned_params(h, set_params=None, stream=None):
+    """Set (if given, flat float64) and return the flat parameter vector W1 [32][64], b1, w2, b2."""
+    P = lbmg_learned_nparams()
+    out = np.zeros(P)
+    s = None if set_params is None else np.ascontiguousarray(set_params, dtype=np.float64)
+    if s is not None and s.size != P:
+        raise ValueError(f"expected {P} parameters")
+    _check(load_library().lbmg_learned_params(h, _ptr(out), _ptr(s), _stream(stream)), "lbmg_learned_params")
+    return out
+
+
+def lbmg_learned_collect(h, rhs, skip, keep, stream=None):
+    return _check(load_library().lbmg_learned_collect(h, _ptr(rhs), _nrhs(rhs), int(skip), int(keep), _stream(stream)),
+                  "lbmg_learned_collect")
+
+
+def lbmg_learned_loss_grad(h, r0, stream=None, grad=True):
+    P = lbmg_learned_nparams()
+    loss = C.c_double()
+    g = np.zeros(P) if grad else None
+    _check(load_library().lbmg_learned_loss_grad(h, _ptr(r0), _nrhs(r0), C.byref(loss), _ptr(g), _stream(stream)),
+           "lbmg_learned_loss_grad")
+    return loss.value, g
+
+
+def lbmg_learned_train(h, order, lr, stream=None):
+    order = np.ascontiguousarray(order, dtype=np.int32)
+    steps, batch = order.shape
+    hist = np.zeros(steps)
+    _check(load_library().lbmg_learned_train(h, int(steps), float(lr), _ptr(order), int(batch), _ptr(hist),
+                                             _stream(stream)), "lbmg_learned_train")
+    return hist
+
+
+def lbmg_learned_enable(h, on=True, stream=None):
+    return _check(load_library().lbmg_learned_enable(h, int(bool(on)), _stream(stream)), "lbmg_learned_enable")
+
+
+def lbmg_learned_omega(h):
+    n, _, _ = lbmg_level_info(h, lbmg_levels(h)[1])
+    out = np.zeros(n)
+    _check(load_library().lbmg_learned_omega(h, _ptr(out)), "lbmg_learned_omega")
     return out
 
 

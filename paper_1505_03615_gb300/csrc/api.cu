@@ -96,6 +96,7 @@ struct lbmg_ctx {
         if (c.capture_stream) cudaStreamDestroy(c.capture_stream);
         if (c.ev0) cudaEventDestroy(c.ev0);
         if (c.ev1) cudaEventDestroy(c.ev1);
+        learned_free(c);
         for (int q = 0; q < 4; q++) if (c.ev_smooth[q]) cudaEventDestroy(c.ev_smooth[q]);
     }
 };
@@ -164,25 +165,26 @@ void enqueue_smooth(Ctx &c, DevLevel &L, int R, int sweeps, bool forward, cudaSt
 
 // one V-cycle on A e = b at the finest level; e (finest x) must be zero on entry
 template <class T>
-void enqueue_vcycle(Ctx &c, int R, cudaStream_t s, bool timed) {
-    for (int d = c.D; d > c.d0; d--) {
+void enqueue_vcycle(Ctx &c, int R, cudaStream_t s, bool timed, int top = -1) {
+    if (top < 0) top = c.D;
+    for (int d = top; d > c.d0; d--) {
         DevLevel &L = c.lev[d], &Lc = c.lev[d - 1];
         launch_coarse_apply<T>(c, L, P<T>::inv(c), P<T>::b(L), P<T>::x(L), R, s);
-        if (timed && d == c.D) cudaEventRecordWithFlags(c.ev_smooth[0], s, cudaEventRecordExternal);
+        if (timed && d == top) cudaEventRecordWithFlags(c.ev_smooth[0], s, cudaEventRecordExternal);
         enqueue_smooth<T>(c, L, R, c.nu1, true, s);
-        if (timed && d == c.D) cudaEventRecordWithFlags(c.ev_smooth[1], s, cudaEventRecordExternal);
+        if (timed && d == top) cudaEventRecordWithFlags(c.ev_smooth[1], s, cudaEventRecordExternal);
         launch_residual<T>(L, P<T>::A(L), P<T>::b(L), P<T>::x(L), P<T>::r(L), R, s, L.ns);
         launch_restrict<T>(Lc, P<T>::r(L), P<T>::b(Lc), R, s);
         if (d - 1 > c.d0) cudaMemsetAsync(P<T>::x(Lc), 0, (size_t)Lc.n * R * sizeof(T), s);
     }
     DevLevel &L0 = c.lev[c.d0];
     launch_coarse_apply<T>(c, L0, P<T>::inv(c), P<T>::b(L0), P<T>::x(L0), R, s);
-    for (int d = c.d0 + 1; d <= c.D; d++) {
+    for (int d = c.d0 + 1; d <= top; d++) {
         DevLevel &L = c.lev[d];
         launch_prolong_add<T>(L, P<T>::x(c.lev[d - 1]), P<T>::x(L), R, s);
-        if (timed && d == c.D) cudaEventRecordWithFlags(c.ev_smooth[2], s, cudaEventRecordExternal);
+        if (timed && d == top) cudaEventRecordWithFlags(c.ev_smooth[2], s, cudaEventRecordExternal);
         enqueue_smooth<T>(c, L, R, c.nu2, false, s);
-        if (timed && d == c.D) cudaEventRecordWithFlags(c.ev_smooth[3], s, cudaEventRecordExternal);
+        if (timed && d == top) cudaEventRecordWithFlags(c.ev_smooth[3], s, cudaEventRecordExternal);
     }
 }
 
@@ -333,7 +335,7 @@ int upload_hierarchy(lbmg_handle h) {
     c.nnitem = (int)(c.nitem_host.size() / 3);
     LBMG_TRY(h->upload(&c.nitem, c.nitem_host));
     LBMG_TRY(h->alloc(&c.item_part, 8 * (size_t)std::max(c.nnitem, 1)));
-    LBMG_TRY(h->alloc(&c.inst_norm, 12 * (size_t)c.ninst));
+    LBMG_TRY(h->alloc(&c.inst_norm, 16 * (size_t)c.ninst));
     {
         std::vector<const int *> rps(kMaxDepth + 1, nullptr), cis(kMaxDepth + 1, nullptr);
         std::vector<const double *> As(kMaxDepth + 1, nullptr);
@@ -373,6 +375,10 @@ int upload_hierarchy(lbmg_handle h) {
 }
 
 }  // namespace
+
+namespace lbmg {
+void enqueue_vcycle64_from(Ctx &c, int top, int R, cudaStream_t s) { enqueue_vcycle<double>(c, R, s, false, top); }
+}  // namespace lbmg
 
 extern "C" {
 
@@ -502,10 +508,10 @@ int lbmg_instance_info(lbmg_handle h, int inst, int *depth, int *min_depth, long
 
 int lbmg_instance_residuals(lbmg_handle h, int nrhs, double *rel) {
     if (!h || !rel || nrhs < 1 || nrhs > 4) return LBMG_INVALID_ARG;
-    if (h->inst_norm_host.size() != 12 * (size_t)h->c.ninst) return LBMG_NOT_ASSEMBLED;
+    if (h->inst_norm_host.size() != 16 * (size_t)h->c.ninst) return LBMG_NOT_ASSEMBLED;
     for (int m = 0; m < h->c.ninst; m++)
         for (int r = 0; r < nrhs; r++) {
-            const double *nm = &h->inst_norm_host[12 * (size_t)m];
+            const double *nm = &h->inst_norm_host[16 * (size_t)m];
             rel[(size_t)m * nrhs + r] = nm[4 + r] > 0 ? std::sqrt(nm[r] / nm[4 + r]) : 0.0;
         }
     return LBMG_OK;
@@ -550,6 +556,7 @@ int lbmg_assemble(lbmg_handle h, double t, void *stream) {
     c.assembled = true;
     c.t = t;
     if (*h->h_flag != 0) return LBMG_COARSE_FACTOR;
+    if (c.learned_on && learned_enable(c, 1, s) != 0) return LBMG_CUDA_ERROR;   // weights of the new matrix
     return LBMG_OK;
 }
 
@@ -612,9 +619,10 @@ static int solve_impl(lbmg_handle h, const double *rhs, double *x, int nrhs, dou
         LBMG_CK(cudaEventRecord(c.ev1, s));
         LBMG_TRY(finish_output(x, xout, cnt, host_out, s));
         LBMG_CK(cudaEventSynchronize(c.ev1));
-        h->inst_norm_host.assign(12 * (size_t)c.ninst, 0.0);
-        LBMG_CK(cudaMemcpy(h->inst_norm_host.data(), c.inst_norm, 12 * sizeof(double) * c.ninst, cudaMemcpyDeviceToHost));
-        int dstat, dcyc;
+        h->inst_norm_host.assign(16 * (size_t)c.ninst, 0.0);
+        LBMG_CK(cudaMemcpy(h->inst_norm_host.data(), c.inst_norm, 16 * sizeof(double) * c.ninst, cudaMemcpyDeviceToHost));
+        int dstat, dcyc, dfall;
+        std::memcpy(&dfall, hs + 32, sizeof(int));
         unsigned long long sns;
         std::memcpy(&dstat, hs + 16, sizeof(int));
         std::memcpy(&dcyc, hs + 20, sizeof(int));
@@ -623,7 +631,7 @@ static int solve_impl(lbmg_handle h, const double *rhs, double *x, int nrhs, dou
         double worst[4] = {0, 0, 0, 0}, worst0[4] = {0, 0, 0, 0};
         for (int m = 0; m < c.ninst; m++)
             for (int r = 0; r < nrhs; r++) {
-                const double *nm = &h->inst_norm_host[12 * (size_t)m];
+                const double *nm = &h->inst_norm_host[16 * (size_t)m];
                 const double rel = nm[4 + r] > 0 ? std::sqrt(nm[r] / nm[4 + r]) : 0.0;
                 const double rel0 = nm[4 + r] > 0 ? std::sqrt(nm[8 + r] / nm[4 + r]) : 0.0;
                 if (!(rel <= tol)) conv = false;
@@ -645,6 +653,8 @@ static int solve_impl(lbmg_handle h, const double *rhs, double *x, int nrhs, dou
             cudaEventElapsedTime(&ms, c.ev0, c.ev1);
             stats->ms_total = ms;
             stats->ms_fine_smooth = (float)(sns * 1e-6);
+            stats->learned = c.learned_on;
+            stats->learned_fallback = c.learned_on ? dfall : 0;
         }
         return status;
     }
@@ -835,6 +845,65 @@ int lbmg_launch_counts(lbmg_handle h, int precision, int *assemble, int *project
     if (per_cycle) *per_cycle = persistent ? 0 : cyc;
     if (solve_fixed) *solve_fixed = persistent ? 4 : 2 + 1 + 2 + 2 + 1;
     return LBMG_OK;
+}
+
+static int learned_ready(lbmg_handle h, cudaStream_t s) {
+    if (!h) return LBMG_INVALID_ARG;
+    if (!h->c.assembled) return LBMG_NOT_ASSEMBLED;
+    const int st = learned_setup(h->c, s);
+    if (st == 1) return LBMG_INVALID_ARG;
+    if (st) return LBMG_OUT_OF_MEMORY;
+    return LBMG_OK;
+}
+
+int lbmg_learned_nparams(void) { return learned_nparams(); }
+
+int lbmg_learned_params(lbmg_handle h, double *get, const double *set, void *stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    LBMG_TRY(learned_ready(h, s));
+    return learned_params(h->c, get, set, s) ? LBMG_CUDA_ERROR : LBMG_OK;
+}
+
+int lbmg_learned_collect(lbmg_handle h, const double *rhs, int ns, int skip, int keep, void *stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!rhs || ns < 1 || skip < 0 || keep < 1) return LBMG_INVALID_ARG;
+    LBMG_TRY(learned_ready(h, s));
+    const double *rd;
+    const size_t cnt = (size_t)h->c.lev[h->c.D].n * ns;
+    if (!on_device(rhs)) {
+        if (cnt > h->io_cap) return LBMG_INVALID_ARG;
+    }
+    LBMG_TRY(input_ptr(h, rhs, cnt, 0, s, &rd));
+    return learned_collect(h->c, rd, ns, skip, keep, s) ? LBMG_CUDA_ERROR : LBMG_OK;
+}
+
+int lbmg_learned_loss_grad(lbmg_handle h, const double *r0, int ns, double *loss, double *grad, void *stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!r0 || !loss || ns < 1 || ns > 4) return LBMG_INVALID_ARG;
+    LBMG_TRY(learned_ready(h, s));
+    const double *rd;
+    LBMG_TRY(input_ptr(h, r0, (size_t)h->c.lev[h->c.D].n * ns, 0, s, &rd));
+    return learned_loss_grad(h->c, rd, ns, loss, grad, s) ? LBMG_CUDA_ERROR : LBMG_OK;
+}
+
+int lbmg_learned_train(lbmg_handle h, int steps, double lr, const int *order, int batch, double *loss_hist,
+                       void *stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    if (steps < 0 || !order || batch < 1 || batch > 4 || !(lr > 0)) return LBMG_INVALID_ARG;
+    LBMG_TRY(learned_ready(h, s));
+    const int st = learned_train(h->c, steps, lr, order, batch, loss_hist, s);
+    return st == 1 ? LBMG_INVALID_ARG : (st ? LBMG_CUDA_ERROR : LBMG_OK);
+}
+
+int lbmg_learned_enable(lbmg_handle h, int on, void *stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    LBMG_TRY(learned_ready(h, s));
+    return learned_enable(h->c, on, s) ? LBMG_CUDA_ERROR : LBMG_OK;
+}
+
+int lbmg_learned_omega(lbmg_handle h, double *omega) {
+    if (!h || !omega || !h->c.learned) return LBMG_INVALID_ARG;
+    return learned_omega(h->c, omega) ? LBMG_CUDA_ERROR : LBMG_OK;
 }
 
 int lbmg_get_dofs(lbmg_handle h, int d, int *corner, int *mintri) {

@@ -34,6 +34,8 @@ struct DevLevel {
     float *x32 = nullptr, *b32 = nullptr, *r32 = nullptr;
 };
 
+struct Learned;
+
 struct GraphCache {
     cudaGraphExec_t exec = nullptr;
     int R = 0, precision = -1, nu1 = -1, nu2 = -1, smoother = -1;
@@ -102,7 +104,23 @@ struct Ctx {
     double *persist_norm = nullptr;   // [16]
     void *persist_state = nullptr;    // 64 bytes: barrier, status, cycles, timer
     void *h_state = nullptr;          // pinned mirror: 64 bytes state + 16 doubles norms
+    // learned relaxation weights at the finest level (learned.cu)
+    Learned *learned = nullptr;
+    int learned_on = 0;
+    double *learned_dinv64 = nullptr;
+    float *learned_dinv32 = nullptr;
 };
+
+// ----- learned relaxation weights (learned.cu) -----
+int learned_setup(Ctx &c, cudaStream_t s);
+void learned_free(Ctx &c);
+int learned_params(Ctx &c, double *get, const double *set, cudaStream_t s);
+int learned_collect(Ctx &c, const double *rhs_user, int ns, int skip, int keep, cudaStream_t s);
+int learned_loss_grad(Ctx &c, const double *r0_user, int ns, double *loss, double *grad, cudaStream_t s);
+int learned_train(Ctx &c, int steps, double lr, const int *order, int batch, double *loss_hist, cudaStream_t s);
+int learned_enable(Ctx &c, int on, cudaStream_t s);
+int learned_omega(Ctx &c, double *omega_user);
+int learned_nparams();
 
 // ----- persistent solve (persist.cu) -----
 int persist_setup(Ctx &c);

@@ -101,6 +101,7 @@ struct Lv {
     int n, ns, ncb;
     int cs[9];
     const int *cb;                  // this level's coarsest blocks: (level, mesh, first row, rows, inverse offset)
+    const T *dinvL;                 // learned omega / a_ii (finest level, when enabled), else null
     const int *rp, *ci;
     const T *A, *dinv;
     const int *par;
@@ -146,12 +147,13 @@ __device__ __forceinline__ void row_dot(const Lv<T, R> &L, int row, bool active,
 }
 
 template <class T, int R>
-__device__ void gs_colour(const Lv<T, R> &L, int c, Team tm) {
+__device__ void gs_colour(const Lv<T, R> &L, int c, Team tm, bool learned = false) {
+    const T *dv = (learned && L.dinvL) ? L.dinvL : L.dinv;
     for_rows<T, R>(L.cs[c], L.cs[c + 1], tm, [&](int row, bool active, int lane) {
         T acc[R];
         row_dot<T, R>(L, row, active, lane, L.x, acc);
         if (active && lane == 0) {
-            const T d = __ldg(L.dinv + row);
+            const T d = __ldg(dv + row);
             T bv[R], xv[R];
             ldcg_vec<T, R>(L.b + (size_t)row * R, bv);
             ldcg_vec<T, R>(L.x + (size_t)row * R, xv);
@@ -259,7 +261,8 @@ struct PersistParams {
     const int *items;         // norm work items (mesh, first row, end row)
     int nitems, ninst;
     double *part;             // [nitems][8]
-    double *norm;             // [ninst][12]: ||r||^2 [0..3], ||b||^2 [4..7], initial ||r||^2 [8..11]
+    double *norm;             // [ninst][16]: ||r||^2, ||b||^2, initial ||r||^2, previous ||r||^2 (4 each)
+    int *fallback;            // set when a learned cycle did not reduce some residual
     unsigned *bar;
     unsigned expected;        // arrivals that complete a barrier
     int *status;
@@ -273,8 +276,8 @@ __global__ void __launch_bounds__(1024, 1) solve_persistent_kernel(PersistParams
     const Team grid{(int)(blockIdx.x * blockDim.x + threadIdx.x), (int)(gridDim.x * blockDim.x)};
     const Team blk{(int)threadIdx.x, (int)blockDim.x};
     const bool b0 = blockIdx.x == 0;
-    __shared__ double red[32][8];
     unsigned long long t_smooth = 0;
+    bool use_learned = lev[p.D].dinvL != nullptr;
 
     // per-mesh norms of the FP64 residual rs (and, the first time, of bs): one warp per
     // work item (a chunk of the rows of one mesh and colour), then block 0 adds the
@@ -312,7 +315,12 @@ __global__ void __launch_bounds__(1024, 1) solve_persistent_kernel(PersistParams
                 double s = 0.0;
                 for (int it = 0; it < p.nitems; it++)
                     if (__ldg(p.items + 3 * it) == m) s += __ldcg(p.part + 8 * (size_t)it + q);
-                p.norm[12 * m + q] = s;
+                if (q < 4) {
+                    const double prev = p.norm[16 * m + q];
+                    p.norm[16 * m + 12 + q] = prev;
+                    if (!with_b && use_learned && q < p.nrhs && !(s < prev)) atomicExch(p.fallback, 1);
+                }
+                p.norm[16 * m + q] = s;
             }
         }
         return grid_sync(p.bar, p.status, p.expected);
@@ -350,7 +358,7 @@ __global__ void __launch_bounds__(1024, 1) solve_persistent_kernel(PersistParams
     if (!norms(true)) return;
     if (b0)
         for (int k = threadIdx.x; k < p.ninst * 4; k += blockDim.x)
-            p.norm[12 * (k >> 2) + 8 + (k & 3)] = __ldcg(p.norm + 12 * (k >> 2) + (k & 3));
+            p.norm[16 * (k >> 2) + 8 + (k & 3)] = __ldcg(p.norm + 16 * (k >> 2) + (k & 3));
     if (!grid_sync(p.bar, p.status, p.expected)) return;
 
     int cyc = 0;
@@ -358,9 +366,9 @@ __global__ void __launch_bounds__(1024, 1) solve_persistent_kernel(PersistParams
         bool done = true, bad = false;
         for (int m = 0; m < p.ninst; m++)
             for (int q = 0; q < p.nrhs; q++) {
-                const double r2 = __ldcg(p.norm + 12 * m + q), b2 = __ldcg(p.norm + 12 * m + 4 + q);
+                const double r2 = __ldcg(p.norm + 16 * m + q), b2 = __ldcg(p.norm + 16 * m + 4 + q);
                 if (!(r2 <= p.tol2 * b2)) done = false;
-                if (!(r2 <= 1e300) || r2 > 1e12 * __ldcg(p.norm + 12 * m + 8 + q) + 1e-300) bad = true;   // NaN, inf or growth by 1e6
+                if (!(r2 <= 1e300) || r2 > 1e12 * __ldcg(p.norm + 16 * m + 8 + q) + 1e-300) bad = true;   // NaN, inf or growth by 1e6
             }
         if (bad) { if (b0 && threadIdx.x == 0) atomicExch(p.status, 2); break; }
         if (done || cyc >= p.max_cycles) break;
@@ -383,7 +391,7 @@ __global__ void __launch_bounds__(1024, 1) solve_persistent_kernel(PersistParams
             for (int s = 0; s < p.nu1; s++)
                 for (int c = 0; c < 8; c++) {
                     if (L.cs[c + 1] == L.cs[c]) continue;
-                    gs_colour<T, R>(L, c, grid);
+                    gs_colour<T, R>(L, c, grid, use_learned && d == p.D);
                     if (!grid_sync(p.bar, p.status, p.expected)) return;
                 }
             if (d == p.D && b0 && threadIdx.x == 0) t_smooth += globaltimer() - t0;
@@ -425,7 +433,7 @@ __global__ void __launch_bounds__(1024, 1) solve_persistent_kernel(PersistParams
             for (int s = 0; s < p.nu2; s++)
                 for (int c = 7; c >= 0; c--) {
                     if (L.cs[c + 1] == L.cs[c]) continue;
-                    gs_colour<T, R>(L, c, grid);
+                    gs_colour<T, R>(L, c, grid, use_learned && d == p.D);
                     if (!grid_sync(p.bar, p.status, p.expected)) return;
                 }
             if (d == p.D && b0 && threadIdx.x == 0) t_smooth += globaltimer() - t0;
@@ -439,11 +447,13 @@ __global__ void __launch_bounds__(1024, 1) solve_persistent_kernel(PersistParams
         fine_residual();
         if (!grid_sync(p.bar, p.status, p.expected)) return;
         if (!norms(false)) return;
+        if (use_learned && *(volatile int *)p.fallback) use_learned = false;   // plain sweeps from now on
     }
     if (b0 && threadIdx.x == 0) {
         *p.cycles = cyc;
         *p.smooth_ns = t_smooth;
     }
+    (void)use_learned;
 }
 
 // host side -------------------------------------------------------------------
@@ -488,6 +498,9 @@ static void fill_views(const Ctx &c, std::vector<char> &buf) {
             o.x = (T *)L.x64; o.b = (T *)L.b64; o.r = (T *)L.r64;
         }
         o.par = L.par; o.npl2 = L.npl2; o.crp = L.crp; o.cch = L.cch;
+        o.dinvL = nullptr;
+        if (d == c.D && c.learned_on)
+            o.dinvL = (sizeof(T) == 4) ? (const T *)(const void *)c.learned_dinv32 : (const T *)(const void *)c.learned_dinv64;
     }
 }
 
@@ -542,6 +555,7 @@ int persist_solve(Ctx &c, int precision, int R, int nrhs, double tol, int max_cy
     prm.status = reinterpret_cast<int *>(st + 16);
     prm.cycles = reinterpret_cast<int *>(st + 20);
     prm.smooth_ns = reinterpret_cast<unsigned long long *>(st + 24);
+    prm.fallback = reinterpret_cast<int *>(st + 32);
     const int B = c.persist_blocks;
     if (f32) {
         if (R == 1) return launch_persist_t<float, 1>(prm, B, s);
