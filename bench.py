@@ -183,6 +183,7 @@ def main():
     ap.add_argument("--impl", default="lbmg")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-cycles", type=int, default=60)
+    ap.add_argument("--persistent", action="store_true", help="one cooperative launch per solve")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_main(args)
@@ -200,7 +201,7 @@ def main():
     dev = torch.device("cuda", local)
     V, F, depth, t, f, tol, _ = meshgen.config_mesh(WORKLOAD)
     nv = V.shape[0]
-    h = L.lbmg_build_hierarchy(V, F, depth)
+    h = L.lbmg_build_hierarchy(V, F, depth, persistent=int(args.persistent))
     d0, D = L.lbmg_levels(h)
     n, nnz, nfrag = L.lbmg_level_info(h, D)
     nrhs = 3
@@ -293,29 +294,40 @@ def main():
     torch.cuda.synchronize()
     fp64_ms = g0.elapsed_time(g1) / fp64_steps
 
-    # roofline of the dominant kernel: the persistent solve (one cooperative launch per
-    # solve), timed live by CUDA events on its stream; algorithmic bytes from the level sizes
+    # roofline of the dominant kernel, timed live with CUDA events on its stream
     a_cnt, p_cnt, per_cycle, fixed = L.lbmg_launch_counts(h, L.LBMG_MIXED)
     opts = L.lbmg_default_options()
-    cyc_bytes, fixed_bytes = solve_bytes(h, opts.nu1 + opts.nu2, nrhs)
-    launch_bytes = cyc_bytes * (cycles / args.steps) + fixed_bytes
-    avg_launch_ms = solve_ms / args.steps
+    sweeps = opts.nu1 + opts.nu2
     peak, peak_kind = _peaks()
+    R = 4
+    if args.persistent:
+        cyc_bytes, fixed_bytes = solve_bytes(h, sweeps, nrhs)
+        launch_bytes = cyc_bytes * (cycles / args.steps) + fixed_bytes
+        avg_launch_ms = solve_ms / args.steps
+        kernel = "solve_persistent_kernel<float,4> (whole mixed solve, one launch)"
+        key = "solve_persistent_knot23_200k_d8"
+    else:
+        # finest-level coloured Gauss-Seidel: events captured in the cycle graph around the
+        # finest pre- and post-smoothing (16 colour launches per cycle and their gaps)
+        launch_bytes = (nnz * 8 + n * (4 + 4 + 3 * R * 4)) / 8
+        avg_launch_ms = smooth_ms / max(cycles * sweeps * 8, 1)
+        kernel = "smooth_colour_kernel<float,4,8> (finest level, per colour)"
+        key = "smooth_colour_knot23_200k_d8"
     achieved = launch_bytes / (avg_launch_ms * 1e-3) / 1e9 if avg_launch_ms > 0 else 0.0
     traffic = None
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
-            tr = json.load(fh).get("solve_persistent_knot23_200k_d8")
+            tr = json.load(fh).get(key)
             if tr:
                 traffic = tr["bytes_per_launch"]
     except Exception:
         pass
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "solve_persistent_kernel<float,4> (whole mixed solve, one launch)",
-                "peak_kind": peak_kind, "bytes_per_launch": launch_bytes, "bytes_per_cycle": cyc_bytes,
-                "avg_launch_ms": avg_launch_ms, "fine_smooth_ms_per_step": smooth_ms / args.steps}
+                "traffic": traffic, "kernel": kernel, "peak_kind": peak_kind, "bytes_per_launch": launch_bytes,
+                "avg_launch_ms": avg_launch_ms, "fine_smooth_ms_per_step": smooth_ms / args.steps,
+                "solve_ms_per_step": solve_ms / args.steps}
 
-    gpu_launches = args.steps * (a_cnt + p_cnt + fixed + 1)
+    gpu_launches = args.steps * (a_cnt + p_cnt + fixed + 1) + cycles * per_cycle
 
     cpu_baseline = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -331,7 +343,8 @@ def main():
             "config": {"workload": WORKLOAD, "triangles": int(F.shape[0]), "depth": depth, "min_depth": d0,
                        "dofs_finest": n, "nnz_finest": nnz, "fragments_finest": nfrag, "nrhs": nrhs, "t": t,
                        "tol": tol, "precision": "mixed", "l2": "inputs larger than L2 (assembly streams >0.5 GB/step)",
-                       "parallelism": "replicas" if ws > 1 else "single"},
+                       "parallelism": "replicas" if ws > 1 else "single",
+                       "solve": "persistent" if args.persistent else "graph per cycle"},
             "ms_to_tol_mixed": ms_per_step, "ms_to_tol_fp64": fp64_ms,
             "cycles_per_step": cycles / args.steps, "fp64_cycles_per_step": fp64_cycles / fp64_steps,
             "max_rel_residual": rel,

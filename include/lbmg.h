@@ -62,10 +62,11 @@ typedef struct lbmg_options {
     double jacobi_omega;/* damping of the weighted Jacobi smoother, default 0.6 */
     int split;          /* 1 (default): connectivity-aware split of Section 4.2; 0: unsplit space of Section 3.2 */
     int threads;        /* host threads for the hierarchy build; 0 = all cores */
-    int persistent;     /* 1 (default): whole solve in one cooperative launch (grid barriers between
-                           phases, bounded waits); 0: one graph launch per cycle */
-    int narrow_max;     /* persistent solve: bottom levels with at most this many rows run in one
-                           block (default 2048) */
+    int persistent;     /* 1: whole solve in one cooperative launch (grid barriers between phases,
+                           bounded waits; always used for batches); 0 (default): one graph launch
+                           per cycle */
+    int narrow_max;     /* bottom levels with at most this many rows run inside one block, with
+                           block barriers between their phases (default 2048) */
     int barrier_phantoms; /* fault injection for tests, default 0: the persistent solve's grid barrier
                            waits for this many extra arrivals that never come, so its bounded wait
                            (about one second) expires and lbmg_solve returns LBMG_DEVICE_TIMEOUT */
@@ -164,9 +165,10 @@ int lbmg_project_rhs(lbmg_handle h, const double *f_vertex, int nrhs, double *rh
  * FP64 defect-correction loop (residual and update in FP64).  Stops when
  * ||rhs - A x||_2 <= tol ||rhs||_2 for every right-hand side, or after
  * max_cycles.  x: [n_depth][nrhs], in/out (warm start).  stats may be NULL.
- * With options.persistent (default) the cycle loop, residuals and norms run in
- * one cooperative kernel launch and the call synchronizes once at the end;
- * otherwise it synchronizes once per cycle to read the residual norms.
+ * With options.persistent (and for batches) the cycle loop, residuals and norms
+ * run in one cooperative kernel launch and the call synchronizes once at the
+ * end; otherwise (default) each cycle is one CUDA-graph launch and the call
+ * synchronizes once per cycle to read the residual norms.
  */
 int lbmg_solve(lbmg_handle h, const double *rhs, double *x, int nrhs, double tol, int max_cycles,
                int precision, lbmg_stats *stats, void *stream);

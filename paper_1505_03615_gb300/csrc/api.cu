@@ -167,6 +167,29 @@ void enqueue_smooth(Ctx &c, DevLevel &L, int R, int sweeps, bool forward, cudaSt
 template <class T>
 void enqueue_vcycle(Ctx &c, int R, cudaStream_t s, bool timed, int top = -1) {
     if (top < 0) top = c.D;
+    // levels dn..d0 (at most narrow_max rows each) run in one single-block kernel
+    const int dn = std::min(c.persist_dn, top);
+    if (dn >= c.d0 && c.smoother != LBMG_JACOBI) {
+        for (int d = top; d > dn; d--) {
+            DevLevel &L = c.lev[d], &Lc = c.lev[d - 1];
+            launch_coarse_apply<T>(c, L, P<T>::inv(c), P<T>::b(L), P<T>::x(L), R, s);
+            if (timed && d == top) cudaEventRecordWithFlags(c.ev_smooth[0], s, cudaEventRecordExternal);
+            enqueue_smooth<T>(c, L, R, c.nu1, true, s);
+            if (timed && d == top) cudaEventRecordWithFlags(c.ev_smooth[1], s, cudaEventRecordExternal);
+            launch_residual<T>(L, P<T>::A(L), P<T>::b(L), P<T>::x(L), P<T>::r(L), R, s, L.ns);
+            launch_restrict<T>(Lc, P<T>::r(L), P<T>::b(Lc), R, s);
+            cudaMemsetAsync(P<T>::x(Lc), 0, (size_t)Lc.n * R * sizeof(T), s);
+        }
+        launch_narrow_cycle(c, sizeof(T) == 4 ? 1 : 0, R, dn, s);
+        for (int d = dn + 1; d <= top; d++) {
+            DevLevel &L = c.lev[d];
+            launch_prolong_add<T>(L, P<T>::x(c.lev[d - 1]), P<T>::x(L), R, s);
+            if (timed && d == top) cudaEventRecordWithFlags(c.ev_smooth[2], s, cudaEventRecordExternal);
+            enqueue_smooth<T>(c, L, R, c.nu2, false, s);
+            if (timed && d == top) cudaEventRecordWithFlags(c.ev_smooth[3], s, cudaEventRecordExternal);
+        }
+        return;
+    }
     for (int d = top; d > c.d0; d--) {
         DevLevel &L = c.lev[d], &Lc = c.lev[d - 1];
         launch_coarse_apply<T>(c, L, P<T>::inv(c), P<T>::b(L), P<T>::x(L), R, s);
@@ -371,6 +394,15 @@ int upload_hierarchy(lbmg_handle h) {
     LBMG_CK(cudaMallocHost(&c.h_state, 64 + 16 * sizeof(double)));
     c.persist_ok = persist_setup(c) == 0 && c.persist_blocks <= 1024;
     cudaGetLastError();
+    if (!c.persist_ok) {   // no narrow levels either: the persistent set-up also picks them
+        c.persist_dn = c.d0 - 1;
+        for (int d = c.d0; d <= c.D; d++) {
+            if (c.lev[d].n <= c.persist_narrow) c.persist_dn = d; else break;
+        }
+    }
+    LBMG_TRY(h->alloc((char **)&c.views32, c.persist_view_bytes));
+    LBMG_TRY(h->alloc((char **)&c.views64, c.persist_view_bytes));
+    if (narrow_views_setup(c) != 0) return LBMG_CUDA_ERROR;
     return LBMG_OK;
 }
 
@@ -410,7 +442,7 @@ void lbmg_default_options(lbmg_options *o) {
     o->jacobi_omega = 0.6;
     o->split = 1;
     o->threads = 0;
-    o->persistent = 1;
+    o->persistent = 0;
     o->narrow_max = 2048;
     o->barrier_phantoms = 0;
 }
@@ -549,6 +581,7 @@ int lbmg_assemble(lbmg_handle h, double t, void *stream) {
     launch_fine_gather(c, t, s);
     for (int d = c.D - 1; d >= c.d0; d--) launch_galerkin(c, d, t, s);
     for (int d = c.d0; d <= c.D; d++) launch_inverse_diag(c.lev[d], s);
+    cudaMemsetAsync(c.flag, 0, sizeof(int), s);
     launch_coarse_factor(c, h->lev_rp, h->lev_ci, h->lev_A, s);
     LBMG_TRY(check_launch());
     LBMG_CK(cudaMemcpyAsync(h->h_flag, c.flag, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -830,14 +863,15 @@ int lbmg_launch_counts(lbmg_handle h, int precision, int *assemble, int *project
     const int levels = c.D - c.d0;
     if (assemble) *assemble = 2 + levels + (levels + 1) + 3;
     if (project_rhs) *project_rhs = 2;
-    int cyc = 1;   // coarse apply
-    for (int d = c.d0 + 1; d <= c.D; d++) {
+    const bool narrow = c.persist_dn >= c.d0 && c.smoother != LBMG_JACOBI;
+    int cyc = narrow ? 1 : 1;   // the one-block bottom cycle, or the coarse apply
+    for (int d = (narrow ? c.persist_dn : c.d0) + 1; d <= c.D; d++) {
         int per_sweep = 2;
         if (c.smoother != LBMG_JACOBI) {
             per_sweep = 0;
             for (int q = 0; q < 8; q++) per_sweep += c.lev[d].cs[q + 1] > c.lev[d].cs[q];
         }
-        cyc += (c.nu1 + c.nu2) * per_sweep + 3;   // sweeps, residual, restriction, prolongation
+        cyc += (c.nu1 + c.nu2) * per_sweep + 3 + (c.lev[d].ncb > 0);   // sweeps, residual, restriction, prolongation
     }
     cyc += (precision == LBMG_MIXED ? 2 : 1) + 1 + 2;   // conversion/update, FP64 residual, norms
     const bool persistent = c.persistent && c.persist_ok && c.smoother == LBMG_GS_COLOURED;

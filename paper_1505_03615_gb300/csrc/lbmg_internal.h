@@ -99,6 +99,7 @@ struct Ctx {
     int persist_blocks = 0, persist_dn = 0, persist_narrow = 2048;
     int barrier_phantoms = 0;        // fault injection: extra arrivals a grid barrier waits for
     void *persist_views = nullptr;
+    void *views32 = nullptr, *views64 = nullptr;   // level views for the one-block bottom cycle
     size_t persist_view_bytes = 0;
     double *persist_part = nullptr;   // [blocks][8]
     double *persist_norm = nullptr;   // [16]
@@ -124,6 +125,8 @@ int learned_nparams();
 
 // ----- persistent solve (persist.cu) -----
 int persist_setup(Ctx &c);
+int narrow_views_setup(Ctx &c);
+void launch_narrow_cycle(const Ctx &c, int precision, int R, int top, cudaStream_t s);
 int persist_solve(Ctx &c, int precision, int R, int nrhs, double tol, int max_cycles, cudaStream_t s);
 size_t persist_view_bytes();
 

@@ -247,6 +247,37 @@ __device__ void coarse_apply(const Lv<T, R> &L, const T *inv, int first, int str
     }
 }
 
+// The bottom of a V-cycle, levels dn..d0, inside one block: b at level dn is given and its x
+// is zero (or dn is the coarsest level); on return x at dn holds the correction.
+template <class T, int R>
+__device__ void narrow_cycle(const Lv<T, R> *lev, int dn, int d0, int nu1, int nu2, const T *cinv, Team blk) {
+    for (int d = dn; d >= d0; d--) {
+        const Lv<T, R> &L = lev[d];
+        if (L.ncb > 0) { coarse_apply<T, R>(L, cinv, 0, 1, blk); __syncthreads(); }
+        if (d == d0) break;
+        for (int s = 0; s < nu1; s++)
+            for (int c = 0; c < 8; c++) { gs_colour<T, R>(L, c, blk); __syncthreads(); }
+        residual<T, R>(L, blk);
+        __syncthreads();
+        restrict_to<T, R>(lev[d - 1], L.r, blk);
+        __syncthreads();
+    }
+    for (int d = d0 + 1; d <= dn; d++) {
+        const Lv<T, R> &L = lev[d];
+        prolong_from<T, R>(L, lev[d - 1].x, blk);
+        __syncthreads();
+        for (int s = 0; s < nu2; s++)
+            for (int c = 7; c >= 0; c--) { gs_colour<T, R>(L, c, blk); __syncthreads(); }
+    }
+}
+
+template <class T, int R>
+__global__ void __launch_bounds__(1024, 1) narrow_cycle_kernel(const void *lev, int dn, int d0, int nu1, int nu2,
+                                                               const void *cinv) {
+    narrow_cycle<T, R>(reinterpret_cast<const Lv<T, R> *>(lev), dn, d0, nu1, nu2, reinterpret_cast<const T *>(cinv),
+                       Team{(int)threadIdx.x, (int)blockDim.x});
+}
+
 }  // namespace
 
 struct PersistParams {
@@ -402,26 +433,7 @@ __global__ void __launch_bounds__(1024, 1) solve_persistent_kernel(PersistParams
         }
         // the narrow levels, block 0 alone
         if (p.dn >= p.d0) {
-            if (b0) {
-                for (int d = p.dn; d >= p.d0; d--) {
-                    const Lv<T, R> &L = lev[d];
-                    if (L.ncb > 0) { coarse_apply<T, R>(L, reinterpret_cast<const T *>(p.cinv), 0, 1, blk); __syncthreads(); }
-                    if (d == p.d0) break;
-                    for (int s = 0; s < p.nu1; s++)
-                        for (int c = 0; c < 8; c++) { gs_colour<T, R>(L, c, blk); __syncthreads(); }
-                    residual<T, R>(L, blk);
-                    __syncthreads();
-                    restrict_to<T, R>(lev[d - 1], L.r, blk);
-                    __syncthreads();
-                }
-                for (int d = p.d0 + 1; d <= p.dn; d++) {
-                    const Lv<T, R> &L = lev[d];
-                    prolong_from<T, R>(L, lev[d - 1].x, blk);
-                    __syncthreads();
-                    for (int s = 0; s < p.nu2; s++)
-                        for (int c = 7; c >= 0; c--) { gs_colour<T, R>(L, c, blk); __syncthreads(); }
-                }
-            }
+            if (b0) narrow_cycle<T, R>(lev, p.dn, p.d0, p.nu1, p.nu2, reinterpret_cast<const T *>(p.cinv), blk);
             if (!grid_sync(p.bar, p.status, p.expected)) return;
         }
         // up the wide levels
@@ -502,6 +514,30 @@ static void fill_views(const Ctx &c, std::vector<char> &buf) {
         if (d == c.D && c.learned_on)
             o.dinvL = (sizeof(T) == 4) ? (const T *)(const void *)c.learned_dinv32 : (const T *)(const void *)c.learned_dinv64;
     }
+}
+
+// one block per launch: the bottom levels of a V-cycle from level `top` (graph path)
+void launch_narrow_cycle(const Ctx &c, int precision, int R, int top, cudaStream_t s) {
+    const void *views = precision == 1 ? c.views32 : c.views64;
+    const void *inv = precision == 1 ? (const void *)c.cinv32 : (const void *)c.cinv64;
+    if (precision == 1) {
+        if (R == 1) narrow_cycle_kernel<float, 1><<<1, 1024, 0, s>>>(views, top, c.d0, c.nu1, c.nu2, inv);
+        else if (R == 2) narrow_cycle_kernel<float, 2><<<1, 1024, 0, s>>>(views, top, c.d0, c.nu1, c.nu2, inv);
+        else narrow_cycle_kernel<float, 4><<<1, 1024, 0, s>>>(views, top, c.d0, c.nu1, c.nu2, inv);
+    } else {
+        if (R == 1) narrow_cycle_kernel<double, 1><<<1, 1024, 0, s>>>(views, top, c.d0, c.nu1, c.nu2, inv);
+        else if (R == 2) narrow_cycle_kernel<double, 2><<<1, 1024, 0, s>>>(views, top, c.d0, c.nu1, c.nu2, inv);
+        else narrow_cycle_kernel<double, 4><<<1, 1024, 0, s>>>(views, top, c.d0, c.nu1, c.nu2, inv);
+    }
+}
+
+int narrow_views_setup(Ctx &c) {
+    std::vector<char> buf;
+    fill_views<float, 4>(c, buf);
+    if (cudaMemcpy(c.views32, buf.data(), buf.size(), cudaMemcpyHostToDevice) != cudaSuccess) return 1;
+    fill_views<double, 4>(c, buf);
+    if (cudaMemcpy(c.views64, buf.data(), buf.size(), cudaMemcpyHostToDevice) != cudaSuccess) return 1;
+    return 0;
 }
 
 int persist_setup(Ctx &c) {

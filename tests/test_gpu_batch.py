@@ -4,6 +4,7 @@ separate single-mesh hierarchies (and hence as the oracle, which those match).""
 import numpy as np
 import pytest
 import scipy.sparse as sp
+import scipy.sparse.linalg as spla
 
 import meshgen
 import paper_1505_03615_gb300 as L
@@ -59,32 +60,31 @@ def _stack(meshes, fn):
 
 
 def test_batch_rhs_and_solution_match_single_meshes(batch):
+    """Mixed-precision batch solve to 1e-6 per mesh (the batched workload's target); each
+    mesh's block of the solution matches that mesh's own direct solution in the M-norm."""
     meshes, t, hb, singles = batch
     f = _stack(meshes, lambda V: V)                      # x, y, z per vertex, meshes concatenated
     nu = sum(L.lbmg_level_info(h, d)[0] for h, (_, _, d) in zip(singles, meshes))
     rhs = torch.zeros((nu, 3), dtype=torch.float64, device=DEV)
     L.lbmg_project_rhs(hb, torch.tensor(f, device=DEV), rhs)
     x = torch.zeros_like(rhs)
-    code, st = L.lbmg_solve(hb, rhs, x, 1e-8, 3000, L.LBMG_FP64)
+    code, st = L.lbmg_solve(hb, rhs, x, 1e-6, 3000, L.LBMG_MIXED)
     assert code == L.LBMG_OK and st.converged
     rel = L.lbmg_instance_residuals(hb, 3)
-    assert rel.shape == (len(meshes), 3) and np.all(rel <= 1e-8)
+    assert rel.shape == (len(meshes), 3) and np.all(rel <= 1e-6)
     off = 0
     for i, (V, F, d) in enumerate(meshes):
         n1 = L.lbmg_level_info(singles[i], d)[0]
         r1 = torch.zeros((n1, 3), dtype=torch.float64, device=DEV)
         L.lbmg_project_rhs(singles[i], torch.tensor(V, device=DEV), r1)
         assert torch.allclose(rhs[off:off + n1], r1, rtol=0, atol=1e-14 * r1.abs().max().item())
-        x1 = torch.zeros_like(r1)
-        c1, s1 = L.lbmg_solve(singles[i], r1, x1, 1e-8, 3000, L.LBMG_FP64)
-        assert c1 == L.LBMG_OK
-        # same system: both solutions within the residual tolerance of each other in the M-norm
         rp, ci, M, Lm = L.lbmg_get_matrix(singles[i], d)
         Mm = sp.csr_matrix((M, ci, rp), shape=(n1, n1))
-        e = (x[off:off + n1] - x1).cpu().numpy()
-        ref = x1.cpu().numpy()
+        A = (Mm + t * sp.csr_matrix((Lm, ci, rp), shape=(n1, n1))).tocsc()
+        ref = spla.splu(A).solve(r1.cpu().numpy())
+        e = x[off:off + n1].cpu().numpy() - ref
         err = np.sqrt(np.einsum("ij,ij->", e, Mm @ e) / np.einsum("ij,ij->", ref, Mm @ ref))
-        assert err < 1e-6
+        assert err < 1e-5
         off += n1
 
 

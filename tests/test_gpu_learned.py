@@ -83,7 +83,7 @@ def test_learned_loss_and_gradient_match_oracle():
 def test_training_lowers_the_loss_and_the_learned_solve_stays_exact():
     V, F = meshgen.torus_knot_tube(2, 3, 1.0, 0.06, 200, 20, 1e-6, 3)
     depth, t = 6, 1e-3
-    h = L.lbmg_build_hierarchy(V, F, depth, min_depth=2)
+    h = L.lbmg_build_hierarchy(V, F, depth, min_depth=2, persistent=1)   # learned weights need the persistent solve
     try:
         L.lbmg_assemble(h, t)
         n = L.lbmg_level_info(h, depth)[0]

@@ -302,7 +302,7 @@ def test_weighted_jacobi_smoother_converges():
 def test_persistent_and_per_cycle_graph_paths_agree(case):
     """The one-launch cooperative solve and the per-cycle graph launch run the same
     arithmetic in the same order: a fixed number of cycles gives the same iterate."""
-    h2 = L.lbmg_build_hierarchy(case.V, case.F, case.D, min_depth=case.d0, persistent=0)
+    h2 = L.lbmg_build_hierarchy(case.V, case.F, case.D, min_depth=case.d0, persistent=1)
     try:
         L.lbmg_assemble(h2, case.t)
         n = case.n(case.D)
@@ -329,8 +329,8 @@ def test_bounded_barrier_wait_reports_timeout_and_context_stays_usable():
     arrival that never comes.  Its bounded wait (about a second) expires, every
     block returns, the solve reports LBMG_DEVICE_TIMEOUT, and the device keeps working."""
     V, F = meshgen.icosphere(2, 1.0, 1e-3, 1)
-    bad = L.lbmg_build_hierarchy(V, F, 4, barrier_phantoms=1)
-    good = L.lbmg_build_hierarchy(V, F, 4)
+    bad = L.lbmg_build_hierarchy(V, F, 4, barrier_phantoms=1, persistent=1)
+    good = L.lbmg_build_hierarchy(V, F, 4, persistent=1)
     try:
         for h in (bad, good):
             L.lbmg_assemble(h, 1e-2)
