@@ -194,6 +194,29 @@ int lbmg_residual(lbmg_handle h, int d, const double *rhs, const double *x, doub
 int lbmg_smooth(lbmg_handle h, int d, const double *rhs, double *x, int nrhs, int sweeps,
                 int precision, void *stream);
 
+/*
+ * ||rhs_q - A_d x_q||_2 for each right-hand side q < nrhs of level d (FP64), the
+ * norms of lbmg_residual's output, computed without allocating anything.  The
+ * paper has no counterpart.  It is for callers that cannot allocate device memory
+ * while they run: a time-critical loop cannot afford cudaMalloc's implicit device
+ * synchronisation or an out-of-memory failure midway, and a plug-in inside an
+ * application that owns the device memory budget may not grow it.  The call's only
+ * scratch, the partial sums of a two-pass reduction, is a file-scope device array
+ * of 512 x 4 doubles (16 KiB) that every GPU loading the library keeps until the
+ * process exits.
+ *  rhs, x: device double[n_d][nrhs] in the library's dof order of level d;
+ *  norms: device double[nrhs]; 1 <= nrhs <= 4.  Host pointers or more than 4
+ *  right-hand sides are rejected with LBMG_INVALID_ARG (lbmg_last_cuda_error
+ *  names the reason).  Needs lbmg_assemble.  Asynchronous on `stream`.
+ *  The first call on each device looks up the array's device address with that
+ *  device current and keeps it; make that first call before any stream capture.
+ *  Each call overwrites the whole array before reading it; calls that overlap on
+ *  the GPU (other streams or host threads) share the array and race, so serialize
+ *  them.
+ */
+int lbmg_residual_norms_noalloc(lbmg_handle h, int d, const double *rhs, const double *x, int nrhs, double *norms,
+                                void *stream);
+
 /* r_c = P^T r_f from level d to d-1 (FP64). r_f: [n_d][nrhs], r_c: [n_{d-1}][nrhs]. */
 int lbmg_restrict(lbmg_handle h, int d, const double *r_fine, double *r_coarse, int nrhs, void *stream);
 /* x_f += P x_c from level d-1 to d (FP64). */

@@ -22,7 +22,8 @@ __all__ = [
     "lbmg_restrict", "lbmg_prolong_add", "lbmg_eval_vertices", "lbmg_get_dofs", "lbmg_get_matrix",
     "lbmg_get_prolongation", "lbmg_launch_counts", "lbmg_build_batch", "lbmg_instances", "lbmg_instance_info",
     "lbmg_instance_residuals", "lbmg_learned_nparams", "lbmg_learned_params", "lbmg_learned_collect",
-    "lbmg_learned_loss_grad", "lbmg_learned_train", "lbmg_learned_enable", "lbmg_learned_omega", "lbmg_status_string", "lbmg_last_cuda_error", "lbmg_default_options",
+    "lbmg_learned_loss_grad", "lbmg_learned_train", "lbmg_learned_enable", "lbmg_learned_omega",
+    "lbmg_residual_norms_noalloc", "lbmg_status_string", "lbmg_last_cuda_error", "lbmg_default_options",
 ]
 
 LBMG_OK = 0
@@ -100,6 +101,7 @@ def load_library():
         "lbmg_learned_train": (i, [P, i, d, P, i, P, P]),
         "lbmg_learned_enable": (i, [P, i, P]),
         "lbmg_learned_omega": (i, [P, P]),
+        "lbmg_residual_norms_noalloc": (i, [P, i, P, P, i, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -322,6 +324,12 @@ def lbmg_vcycles(h, rhs, x, cycles, precision, stream=None):
 def lbmg_residual(h, d, rhs, x, r, stream=None):
     return _check(load_library().lbmg_residual(h, int(d), _ptr(rhs), _ptr(x), _ptr(r), _nrhs(rhs), _stream(stream)),
                   "lbmg_residual")
+
+
+def lbmg_residual_norms_noalloc(h, d, rhs, x, norms, stream=None):
+    """Per-column ||rhs - A_d x||_2 into `norms` (all device tensors); the call allocates nothing."""
+    return _check(load_library().lbmg_residual_norms_noalloc(h, int(d), _ptr(rhs), _ptr(x), _nrhs(rhs), _ptr(norms),
+                                                             _stream(stream)), "lbmg_residual_norms_noalloc")
 
 
 def lbmg_smooth(h, d, rhs, x, sweeps, precision, stream=None):

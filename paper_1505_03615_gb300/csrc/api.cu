@@ -410,6 +410,13 @@ int upload_hierarchy(lbmg_handle h) {
 
 namespace lbmg {
 void enqueue_vcycle64_from(Ctx &c, int top, int R, cudaStream_t s) { enqueue_vcycle<double>(c, R, s, false, top); }
+
+// level d of an assembled handle, for entry points defined in other files
+const DevLevel *noalloc_level(lbmg_handle h, int d) {
+    if (!h || d < h->c.d0 || d > h->c.D || !h->c.assembled) return nullptr;
+    return &h->c.lev[d];
+}
+void noalloc_set_error(const std::string &msg) { g_cuda_err = msg; }
 }  // namespace lbmg
 
 extern "C" {
