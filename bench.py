@@ -184,6 +184,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--oracle-cycles", type=int, default=60)
     ap.add_argument("--persistent", action="store_true", help="one cooperative launch per solve")
+    ap.add_argument("--no-graphs", action="store_true", help="launch each cycle's kernels directly (profilers)")
+    ap.add_argument("--only-timed", action="store_true", help="stop after the timed steps (profiling runs)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_main(args)
@@ -201,7 +203,7 @@ def main():
     dev = torch.device("cuda", local)
     V, F, depth, t, f, tol, _ = meshgen.config_mesh(WORKLOAD)
     nv = V.shape[0]
-    h = L.lbmg_build_hierarchy(V, F, depth, persistent=int(args.persistent))
+    h = L.lbmg_build_hierarchy(V, F, depth, persistent=int(args.persistent), use_graphs=int(not args.no_graphs))
     d0, D = L.lbmg_levels(h)
     n, nnz, nfrag = L.lbmg_level_info(h, D)
     nrhs = 3
@@ -256,6 +258,12 @@ def main():
     ms_max = ms_t[0].item()
     value = n * nrhs * all_cycles / (ms_max / 1e3)
     ms_per_step = ms_max / args.steps
+    if args.only_timed:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "ms_per_step": ms_per_step,
+                              "cycles_per_step": cycles / args.steps, "note": "timed steps only"}), flush=True)
+        L.lbmg_destroy(h)
+        return
 
     # end to end through the C ABI with host buffers (pinned): H2D of the vertex data,
     # D2H of the evaluated vertex positions, inside the timed region

@@ -70,6 +70,8 @@ typedef struct lbmg_options {
     int barrier_phantoms; /* fault injection for tests, default 0: the persistent solve's grid barrier
                            waits for this many extra arrivals that never come, so its bounded wait
                            (about one second) expires and lbmg_solve returns LBMG_DEVICE_TIMEOUT */
+    int use_graphs;     /* per-cycle path: 1 (default) replays a captured CUDA graph per cycle; 0
+                           launches the cycle's kernels directly (same kernels, e.g. for profilers) */
 } lbmg_options;
 
 typedef struct lbmg_stats {

@@ -168,8 +168,9 @@ template <class T>
 void enqueue_vcycle(Ctx &c, int R, cudaStream_t s, bool timed, int top = -1) {
     if (top < 0) top = c.D;
     // levels dn..d0 (at most narrow_max rows each) run in one single-block kernel
+    // (FP32 only: a single SM's FP64 rate makes the one-block bottom slower than per-phase launches)
     const int dn = std::min(c.persist_dn, top);
-    if (dn >= c.d0 && c.smoother != LBMG_JACOBI) {
+    if (dn >= c.d0 && c.smoother != LBMG_JACOBI && sizeof(T) == 4) {
         for (int d = top; d > dn; d--) {
             DevLevel &L = c.lev[d], &Lc = c.lev[d - 1];
             launch_coarse_apply<T>(c, L, P<T>::inv(c), P<T>::b(L), P<T>::x(L), R, s);
@@ -452,6 +453,7 @@ void lbmg_default_options(lbmg_options *o) {
     o->persistent = 0;
     o->narrow_max = 2048;
     o->barrier_phantoms = 0;
+    o->use_graphs = 1;
 }
 
 int lbmg_build_hierarchy(const double *V, int nv, const int *F, int nt, int depth, const lbmg_options *opt,
@@ -483,6 +485,7 @@ int lbmg_build_hierarchy(const double *V, int nv, const int *F, int nt, int dept
     h->c.smoother = o.smoother;
     h->c.omega = o.jacobi_omega;
     h->c.persistent = o.persistent;
+    h->c.use_graphs = o.use_graphs;
     h->c.persist_narrow = o.narrow_max;
     h->c.barrier_phantoms = o.barrier_phantoms;
     st = upload_hierarchy(h);
@@ -699,8 +702,8 @@ static int solve_impl(lbmg_handle h, const double *rhs, double *x, int nrhs, dou
         return status;
     }
     if (c.ninst > 1) return LBMG_INVALID_ARG;   // batches need the persistent solve (per-mesh norms)
-    cudaGraphExec_t exec;
-    LBMG_TRY(get_graph(h, R, precision, &exec));
+    cudaGraphExec_t exec = nullptr;
+    if (c.use_graphs) LBMG_TRY(get_graph(h, R, precision, &exec));
     LBMG_CK(cudaEventRecord(c.ev0, s));
     launch_pack(rd, Fl.n, nrhs, R, c.bs, s, c.fperm);
     launch_pack(xin, Fl.n, nrhs, R, c.xs, s, c.fperm);
@@ -726,7 +729,8 @@ static int solve_impl(lbmg_handle h, const double *rhs, double *x, int nrhs, dou
             }
             if (bad) { status = LBMG_DIVERGED; break; }
             if (conv || cycles >= max_cycles) break;
-            LBMG_CK(cudaGraphLaunch(exec, s));
+            if (exec) LBMG_CK(cudaGraphLaunch(exec, s));
+            else enqueue_iteration(c, R, precision, s);
             LBMG_TRY(read_norms(h, R, s, nr));
             if (c.D > c.d0) {
                 float a0 = 0, a1 = 0;
@@ -749,7 +753,10 @@ static int solve_impl(lbmg_handle h, const double *rhs, double *x, int nrhs, dou
             }
         }
     } else {
-        for (int k = 0; k < max_cycles; k++) LBMG_CK(cudaGraphLaunch(exec, s));
+        for (int k = 0; k < max_cycles; k++) {
+            if (exec) LBMG_CK(cudaGraphLaunch(exec, s));
+            else enqueue_iteration(c, R, precision, s);
+        }
         cycles = max_cycles;
     }
     launch_unpack(c.xs, Fl.n, nrhs, R, xout, s, c.fperm);
@@ -870,7 +877,7 @@ int lbmg_launch_counts(lbmg_handle h, int precision, int *assemble, int *project
     const int levels = c.D - c.d0;
     if (assemble) *assemble = 2 + levels + (levels + 1) + 3;
     if (project_rhs) *project_rhs = 2;
-    const bool narrow = c.persist_dn >= c.d0 && c.smoother != LBMG_JACOBI;
+    const bool narrow = c.persist_dn >= c.d0 && c.smoother != LBMG_JACOBI && precision == LBMG_MIXED;
     int cyc = narrow ? 1 : 1;   // the one-block bottom cycle, or the coarse apply
     for (int d = (narrow ? c.persist_dn : c.d0) + 1; d <= c.D; d++) {
         int per_sweep = 2;

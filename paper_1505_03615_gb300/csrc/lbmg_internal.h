@@ -95,6 +95,7 @@ struct Ctx {
     GraphCache graph;
     // persistent cooperative solve
     int persistent = 1;           // use the one-launch solve when the device allows it
+    int use_graphs = 1;           // per-cycle path: replay a captured graph (1) or launch directly (0)
     int persist_ok = 0;
     int persist_blocks = 0, persist_dn = 0, persist_narrow = 2048;
     int barrier_phantoms = 0;        // fault injection: extra arrivals a grid barrier waits for
