@@ -79,9 +79,8 @@ __device__ bool grid_sync(unsigned *bar, int *status, unsigned expected) {
             const unsigned long long t0 = globaltimer();
             unsigned long long spins = 0;
             while (ld_acquire(bar + 1) == gen) {
-                __nanosleep(64);
                 ++spins;
-                if (((spins & 255) == 0 && globaltimer() - t0 > kWaitNs) || spins > kSpinCap) {
+                if (((spins & 1023) == 0 && globaltimer() - t0 > kWaitNs) || spins > kSpinCap) {
                     atomicExch(status, 1);
                     ok = 0;
                     break;
@@ -89,7 +88,6 @@ __device__ bool grid_sync(unsigned *bar, int *status, unsigned expected) {
             }
         }
         __threadfence();
-        if (ok && *(volatile int *)status != 0) ok = 0;
         s_ok = ok;
     }
     __syncthreads();

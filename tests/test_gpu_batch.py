@@ -18,7 +18,7 @@ def _meshes():
     return [
         (*meshgen.icosphere(2, 1.0, 1e-3, 1), 4),
         (*meshgen.torus_knot_tube(2, 3, 1.0, 0.12, 48, 8, 1e-6, 3), 5),
-        (*meshgen.torus(1.0, 0.3, 24, 10, 1e-6, 5), 5),
+        (*meshgen.torus(1.0, 0.3, 60, 20, 1e-6, 5), 5),
         (*meshgen.ellipsoid((1.0, 0.6, 0.4), 2, 1e-6, 3), 3),
         (*meshgen.double_sheet(8, 0.05, 5, 0.5, 1e-6, 4), 5),
     ]
