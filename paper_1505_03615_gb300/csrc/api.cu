@@ -97,6 +97,7 @@ struct lbmg_ctx {
         if (c.ev0) cudaEventDestroy(c.ev0);
         if (c.ev1) cudaEventDestroy(c.ev1);
         learned_free(c);
+        if (c.narrow.blob) cudaFree(c.narrow.blob);
         for (int q = 0; q < 4; q++) if (c.ev_smooth[q]) cudaEventDestroy(c.ev_smooth[q]);
     }
 };
@@ -169,6 +170,28 @@ void enqueue_vcycle(Ctx &c, int R, cudaStream_t s, bool timed, int top = -1) {
     if (top < 0) top = c.D;
     // levels dn..d0 (at most narrow_max rows each) run in one single-block kernel
     // (FP32 only: a single SM's FP64 rate makes the one-block bottom slower than per-phase launches)
+    if (sizeof(T) == 4 && c.narrow.dn >= c.d0 && c.narrow.dn <= top && c.smoother != LBMG_JACOBI) {
+        // bottom levels from shared memory (one block), the rest one launch per phase
+        const int dn = c.narrow.dn;
+        for (int d = top; d > dn; d--) {
+            DevLevel &L = c.lev[d], &Lc = c.lev[d - 1];
+            launch_coarse_apply<T>(c, L, P<T>::inv(c), P<T>::b(L), P<T>::x(L), R, s);
+            if (timed && d == top) cudaEventRecordWithFlags(c.ev_smooth[0], s, cudaEventRecordExternal);
+            enqueue_smooth<T>(c, L, R, c.nu1, true, s);
+            if (timed && d == top) cudaEventRecordWithFlags(c.ev_smooth[1], s, cudaEventRecordExternal);
+            launch_residual<T>(L, P<T>::A(L), P<T>::b(L), P<T>::x(L), P<T>::r(L), R, s, L.ns);
+            launch_restrict<T>(Lc, P<T>::r(L), P<T>::b(Lc), R, s);
+        }
+        launch_narrow_smem(c, R, s);
+        for (int d = dn + 1; d <= top; d++) {
+            DevLevel &L = c.lev[d];
+            launch_prolong_add<T>(L, P<T>::x(c.lev[d - 1]), P<T>::x(L), R, s);
+            if (timed && d == top) cudaEventRecordWithFlags(c.ev_smooth[2], s, cudaEventRecordExternal);
+            enqueue_smooth<T>(c, L, R, c.nu2, false, s);
+            if (timed && d == top) cudaEventRecordWithFlags(c.ev_smooth[3], s, cudaEventRecordExternal);
+        }
+        return;
+    }
     const int dn = std::min(c.persist_dn, top);
     if (dn >= c.d0 && c.smoother != LBMG_JACOBI && sizeof(T) == 4) {
         for (int d = top; d > dn; d--) {
@@ -404,6 +427,10 @@ int upload_hierarchy(lbmg_handle h) {
     LBMG_TRY(h->alloc((char **)&c.views32, c.persist_view_bytes));
     LBMG_TRY(h->alloc((char **)&c.views64, c.persist_view_bytes));
     if (narrow_views_setup(c) != 0) return LBMG_CUDA_ERROR;
+    if (c.ninst == 1 && narrow_smem_setup(c, 200 * 1024) != 0) {
+        cudaGetLastError();
+        c.narrow.dn = c.d0 - 1;   // the bottom then runs from global memory
+    }
     return LBMG_OK;
 }
 
@@ -593,6 +620,7 @@ int lbmg_assemble(lbmg_handle h, double t, void *stream) {
     for (int d = c.d0; d <= c.D; d++) launch_inverse_diag(c.lev[d], s);
     cudaMemsetAsync(c.flag, 0, sizeof(int), s);
     launch_coarse_factor(c, h->lev_rp, h->lev_ci, h->lev_A, s);
+    narrow_smem_refresh(c, s);
     LBMG_TRY(check_launch());
     LBMG_CK(cudaMemcpyAsync(h->h_flag, c.flag, sizeof(int), cudaMemcpyDeviceToHost, s));
     LBMG_CK(cudaStreamSynchronize(s));
@@ -878,8 +906,10 @@ int lbmg_launch_counts(lbmg_handle h, int precision, int *assemble, int *project
     if (assemble) *assemble = 2 + levels + (levels + 1) + 3;
     if (project_rhs) *project_rhs = 2;
     const bool narrow = c.persist_dn >= c.d0 && c.smoother != LBMG_JACOBI && precision == LBMG_MIXED;
-    int cyc = narrow ? 1 : 1;   // the one-block bottom cycle, or the coarse apply
-    for (int d = (narrow ? c.persist_dn : c.d0) + 1; d <= c.D; d++) {
+    const bool smem = c.narrow.dn >= c.d0 && c.smoother != LBMG_JACOBI && precision == LBMG_MIXED;
+    const int bottom = smem ? c.narrow.dn : (narrow ? c.persist_dn : c.d0);
+    int cyc = 1;   // the one-block bottom cycle, or the coarse apply
+    for (int d = bottom + 1; d <= c.D; d++) {
         int per_sweep = 2;
         if (c.smoother != LBMG_JACOBI) {
             per_sweep = 0;

@@ -36,6 +36,25 @@ struct DevLevel {
 
 struct Learned;
 
+constexpr int kMaxNarrow = 6;     // bottom levels that can live in shared memory
+struct NarrowLevel {
+    int n = 0, ns = 0, nnz = 0, cb0 = 0, ncb = 0;
+    int cs[9] = {0};
+    // byte offsets in shared memory (blob part, then vectors); -1 = absent
+    int o_rp = -1, o_ci = -1, o_A = -1, o_dinv = -1, o_par = -1, o_npl2 = -1, o_crp = -1, o_cch = -1;
+    int o_x = -1, o_b = -1, o_r = -1;
+};
+struct NarrowParams {
+    int d0 = 0, dn = -1, nu1 = 2, nu2 = 2;
+    NarrowLevel lev[kMaxNarrow];
+};
+struct NarrowState {
+    int dn = -1;                      // top level held in shared memory (< d0: none)
+    NarrowParams p;
+    unsigned char *blob = nullptr;    // packed static data (device)
+    int blob_bytes = 0, vec_bytes = 0;
+};
+
 struct GraphCache {
     cudaGraphExec_t exec = nullptr;
     int R = 0, precision = -1, nu1 = -1, nu2 = -1, smoother = -1;
@@ -106,12 +125,18 @@ struct Ctx {
     double *persist_norm = nullptr;   // [16]
     void *persist_state = nullptr;    // 64 bytes: barrier, status, cycles, timer
     void *h_state = nullptr;          // pinned mirror: 64 bytes state + 16 doubles norms
+    NarrowState narrow;               // shared-memory bottom of the V-cycle (narrow.cu)
     // learned relaxation weights at the finest level (learned.cu)
     Learned *learned = nullptr;
     int learned_on = 0;
     double *learned_dinv64 = nullptr;
     float *learned_dinv32 = nullptr;
 };
+
+// ----- shared-memory bottom cycle (narrow.cu) -----
+int narrow_smem_setup(Ctx &c, size_t smem_budget);
+void narrow_smem_refresh(const Ctx &c, cudaStream_t s);
+void launch_narrow_smem(const Ctx &c, int R, cudaStream_t s);
 
 // ----- learned relaxation weights (learned.cu) -----
 int learned_setup(Ctx &c, cudaStream_t s);

@@ -1,0 +1,334 @@
+// narrow.cu -- the bottom of the V-cycle (Chuang & Kazhdan, Section 4.3) inside
+// one block, out of shared memory.
+//
+// The coarsest levels are tiny, so each of their ~35 phases per cycle (eight
+// colours per Gauss-Seidel sweep, residual, restriction, prolongation) is pure
+// latency: as separate launches each costs a launch gap, and even inside one
+// block each phase waits on three dependent global-memory loads.  Here the
+// static data of those levels (16-bit row pointers, column indices, parents and
+// children, FP32 values and inverse diagonals) are packed once into a compact
+// blob; every cycle one block copies the blob into shared memory with 16-byte
+// loads, runs the bottom V-cycle there with block barriers between phases, and
+// writes the correction of its top level back.  Only the dense coarse inverse
+// and the top level's right-hand side and correction touch global memory.
+#include <cstring>
+#include <vector>
+
+#include "lbmg_internal.h"
+
+namespace lbmg {
+
+namespace {
+
+constexpr int kGN = 8;   // threads per matrix row
+
+template <int R>
+__device__ __forceinline__ void sld(const float *p, float (&v)[R]) {
+#pragma unroll
+    for (int q = 0; q < R; q++) v[q] = p[q];
+}
+template <>
+__device__ __forceinline__ void sld<4>(const float *p, float (&v)[4]) {
+    const float4 q = *reinterpret_cast<const float4 *>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+
+struct SLev {
+    const uint16_t *rp, *ci, *par, *crp, *cch;
+    const float *A, *dinv;
+    const uint8_t *npl2;
+    float *x, *b, *r;
+};
+
+__device__ SLev slev(const NarrowLevel &h, unsigned char *sm) {
+    SLev s;
+    s.rp = reinterpret_cast<const uint16_t *>(sm + h.o_rp);
+    s.ci = reinterpret_cast<const uint16_t *>(sm + h.o_ci);
+    s.A = reinterpret_cast<const float *>(sm + h.o_A);
+    s.dinv = reinterpret_cast<const float *>(sm + h.o_dinv);
+    s.par = h.o_par >= 0 ? reinterpret_cast<const uint16_t *>(sm + h.o_par) : nullptr;
+    s.npl2 = h.o_npl2 >= 0 ? reinterpret_cast<const uint8_t *>(sm + h.o_npl2) : nullptr;
+    s.crp = h.o_crp >= 0 ? reinterpret_cast<const uint16_t *>(sm + h.o_crp) : nullptr;
+    s.cch = h.o_cch >= 0 ? reinterpret_cast<const uint16_t *>(sm + h.o_cch) : nullptr;
+    s.x = reinterpret_cast<float *>(sm + h.o_x);
+    s.b = reinterpret_cast<float *>(sm + h.o_b);
+    s.r = reinterpret_cast<float *>(sm + h.o_r);
+    return s;
+}
+
+// row loop with 8-thread groups; every warp runs the same number of iterations
+template <int R, class F>
+__device__ __forceinline__ void rows8(int r0, int r1, F &&body) {
+    const int tid = threadIdx.x, g = tid / kGN, lane = tid % kGN, ng = blockDim.x / kGN;
+    const int warp_first = (tid / 32) * (32 / kGN);
+    for (int base = r0 + warp_first; base < r1; base += ng) {
+        const int row = base + (g - warp_first);
+        body(row, row < r1, lane);
+    }
+}
+
+template <int R>
+__device__ __forceinline__ void sdot(const SLev &L, int row, bool active, int lane, float (&acc)[R]) {
+#pragma unroll
+    for (int q = 0; q < R; q++) acc[q] = 0.f;
+    if (active) {
+        const int k1 = L.rp[row + 1];
+        for (int k = L.rp[row] + lane; k < k1; k += kGN) {
+            const float a = L.A[k];
+            float v[R];
+            sld<R>(L.x + (size_t)L.ci[k] * R, v);
+#pragma unroll
+            for (int q = 0; q < R; q++) acc[q] = fmaf(a, v[q], acc[q]);
+        }
+    }
+#pragma unroll
+    for (int o = kGN / 2; o > 0; o >>= 1)
+#pragma unroll
+        for (int q = 0; q < R; q++) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o, kGN);
+}
+
+template <int R>
+__global__ void __launch_bounds__(1024, 1) narrow_smem_kernel(const unsigned char *__restrict__ blob, int blob_bytes,
+                                                              int vec_bytes, NarrowParams p,
+                                                              const float *__restrict__ cinv, const int *__restrict__ cblk,
+                                                              const float *__restrict__ b_top, float *__restrict__ x_top) {
+    extern __shared__ __align__(16) unsigned char sm[];
+    // static part of the blob, then zeroed vectors
+    for (int q = threadIdx.x; q < blob_bytes / 16; q += blockDim.x)
+        reinterpret_cast<uint4 *>(sm)[q] = __ldg(reinterpret_cast<const uint4 *>(blob) + q);
+    for (int q = threadIdx.x; q < vec_bytes / 16; q += blockDim.x)
+        reinterpret_cast<uint4 *>(sm + blob_bytes)[q] = make_uint4(0, 0, 0, 0);
+    __syncthreads();
+    const NarrowLevel &T = p.lev[p.dn - p.d0];
+    {
+        float *b = reinterpret_cast<float *>(sm + T.o_b);
+        for (int q = threadIdx.x; q < T.n * R; q += blockDim.x) b[q] = b_top[q];
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, wl = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int d = p.dn; d >= p.d0; d--) {
+        const NarrowLevel &H = p.lev[d - p.d0];
+        const SLev L = slev(H, sm);
+        // dense coarse blocks of this level: x = inv b
+        for (int k = 0; k < H.ncb; k++) {
+            const int *cb = cblk + 5 * (H.cb0 + k);
+            const int row0 = cb[2], n = cb[3];
+            const float *M = cinv + cb[4];
+            for (int row = warp; row < n; row += nw) {
+                float acc[R];
+#pragma unroll
+                for (int q = 0; q < R; q++) acc[q] = 0.f;
+                for (int j = wl; j < n; j += 32) {
+                    const float a = __ldg(M + (size_t)row * n + j);
+                    float v[R];
+                    sld<R>(L.b + (size_t)(row0 + j) * R, v);
+#pragma unroll
+                    for (int q = 0; q < R; q++) acc[q] = fmaf(a, v[q], acc[q]);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                    for (int q = 0; q < R; q++) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+                if (wl == 0)
+#pragma unroll
+                    for (int q = 0; q < R; q++) L.x[(size_t)(row0 + row) * R + q] = acc[q];
+            }
+        }
+        __syncthreads();
+        if (d == p.d0) break;
+        for (int s = 0; s < p.nu1; s++)
+            for (int c = 0; c < 8; c++) {
+                rows8<R>(H.cs[c], H.cs[c + 1], [&](int row, bool active, int lane) {
+                    float acc[R];
+                    sdot<R>(L, row, active, lane, acc);
+                    if (active && lane == 0) {
+                        const float dv = L.dinv[row];
+#pragma unroll
+                        for (int q = 0; q < R; q++)
+                            L.x[(size_t)row * R + q] += (L.b[(size_t)row * R + q] - acc[q]) * dv;
+                    }
+                });
+                __syncthreads();
+            }
+        rows8<R>(0, H.ns, [&](int row, bool active, int lane) {
+            float acc[R];
+            sdot<R>(L, row, active, lane, acc);
+            if (active && lane == 0)
+#pragma unroll
+                for (int q = 0; q < R; q++) L.r[(size_t)row * R + q] = L.b[(size_t)row * R + q] - acc[q];
+        });
+        __syncthreads();
+        const NarrowLevel &HC = p.lev[d - 1 - p.d0];
+        const SLev C = slev(HC, sm);
+        for (int J = threadIdx.x; J < HC.n; J += blockDim.x) {
+            float acc[R];
+#pragma unroll
+            for (int q = 0; q < R; q++) acc[q] = 0.f;
+            for (int k = C.crp[J]; k < C.crp[J + 1]; k++) {
+                const uint16_t e = C.cch[k];
+                const float w = 1.f / (float)(1u << (e >> 14));
+                float v[R];
+                sld<R>(L.r + (size_t)(e & 0x3fff) * R, v);
+#pragma unroll
+                for (int q = 0; q < R; q++) acc[q] = fmaf(w, v[q], acc[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < R; q++) { C.b[(size_t)J * R + q] = acc[q]; C.x[(size_t)J * R + q] = 0.f; }
+        }
+        __syncthreads();
+    }
+    for (int d = p.d0 + 1; d <= p.dn; d++) {
+        const NarrowLevel &H = p.lev[d - p.d0];
+        const SLev L = slev(H, sm), C = slev(p.lev[d - 1 - p.d0], sm);
+        for (int i = threadIdx.x; i < H.ns; i += blockDim.x) {
+            const int np = 1 << L.npl2[i];
+            float acc[R], v[R];
+#pragma unroll
+            for (int q = 0; q < R; q++) acc[q] = 0.f;
+            for (int q2 = 0; q2 < np; q2++) {
+                sld<R>(C.x + (size_t)L.par[8 * i + q2] * R, v);
+#pragma unroll
+                for (int q = 0; q < R; q++) acc[q] += v[q];
+            }
+            const float w = 1.f / (float)np;
+#pragma unroll
+            for (int q = 0; q < R; q++) L.x[(size_t)i * R + q] += w * acc[q];
+        }
+        __syncthreads();
+        for (int s = 0; s < p.nu2; s++)
+            for (int c = 7; c >= 0; c--) {
+                rows8<R>(H.cs[c], H.cs[c + 1], [&](int row, bool active, int lane) {
+                    float acc[R];
+                    sdot<R>(L, row, active, lane, acc);
+                    if (active && lane == 0) {
+                        const float dv = L.dinv[row];
+#pragma unroll
+                        for (int q = 0; q < R; q++)
+                            L.x[(size_t)row * R + q] += (L.b[(size_t)row * R + q] - acc[q]) * dv;
+                    }
+                });
+                __syncthreads();
+            }
+    }
+    {
+        const float *x = reinterpret_cast<const float *>(sm + T.o_x);
+        for (int q = threadIdx.x; q < T.n * R; q += blockDim.x) x_top[q] = x[q];
+    }
+}
+
+}  // namespace
+
+// Pick the bottom levels that fit in shared memory and pack their static data.
+// Returns 0 and leaves c.narrow.dn = d0 - 1 when no level fits.
+int narrow_smem_setup(Ctx &c, size_t smem_budget) {
+    NarrowParams &p = c.narrow.p;
+    c.narrow.dn = c.d0 - 1;
+    const HostHierarchy &H = c.host;
+    auto align16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
+    size_t best_blob = 0, best_vec = 0;
+    int best_dn = c.d0 - 1;
+    for (int dn = c.d0; dn <= c.D && dn - c.d0 < kMaxNarrow; dn++) {
+        size_t blob = 0, vec = 0;
+        bool ok = true;
+        for (int d = c.d0; d <= dn && ok; d++) {
+            const HostLevel &L = H.lev[d];
+            const size_t nnz = L.rp.empty() ? 0 : (size_t)L.rp[L.ndof];
+            if (nnz >= 65535 || L.ndof >= 16384) { ok = false; break; }
+            blob += align16(2 * (L.ndof + 1)) + align16(2 * nnz) + align16(4 * nnz) + align16(4 * (size_t)L.ndof);
+            if (d > c.d0) blob += align16(16 * (size_t)L.ndof) + align16(L.ndof);
+            if (d < dn) blob += align16(2 * (L.ndof + 1)) + align16(2 * L.cch.size());
+            if (d < dn && L.cch.size() >= 65535) ok = false;
+            vec += 3 * align16(16 * (size_t)L.ndof);   // x, b, r with room for 4 lanes
+        }
+        if (!ok || blob + vec > smem_budget) break;
+        best_dn = dn; best_blob = blob; best_vec = vec;
+    }
+    if (best_dn < c.d0) return 0;
+    // pack
+    std::vector<unsigned char> buf(best_blob, 0);
+    size_t off = 0, voff = best_blob;
+    auto put = [&](const void *src, size_t bytes) {
+        const size_t o = off;
+        if (bytes) std::memcpy(buf.data() + o, src, bytes);
+        off += align16(bytes);
+        return (int)o;
+    };
+    p.d0 = c.d0; p.dn = best_dn; p.nu1 = c.nu1; p.nu2 = c.nu2;
+    for (int d = c.d0; d <= best_dn; d++) {
+        const HostLevel &L = H.lev[d];
+        NarrowLevel &o = p.lev[d - c.d0];
+        o = NarrowLevel();
+        o.n = L.ndof; o.ns = L.ns;
+        for (int q = 0; q < 9; q++) o.cs[q] = L.colour_start[q];
+        o.cb0 = c.lev[d].cb0; o.ncb = c.lev[d].ncb;
+        const size_t nnz = (size_t)L.rp[L.ndof];
+        std::vector<uint16_t> rp16(L.ndof + 1), ci16(nnz);
+        for (int i = 0; i <= L.ndof; i++) rp16[i] = (uint16_t)L.rp[i];
+        for (size_t k = 0; k < nnz; k++) ci16[k] = (uint16_t)L.ci[k];
+        o.o_rp = put(rp16.data(), 2 * rp16.size());
+        o.o_ci = put(ci16.data(), 2 * nnz);
+        o.o_A = (int)off; off += align16(4 * nnz);            // values: refreshed after every assembly
+        o.o_dinv = (int)off; off += align16(4 * (size_t)L.ndof);
+        o.nnz = (int)nnz;
+        o.o_par = o.o_npl2 = o.o_crp = o.o_cch = -1;
+        if (d > c.d0) {
+            std::vector<uint16_t> par16(8 * (size_t)L.ndof, 0);
+            std::vector<uint8_t> npl(L.ndof, 0);
+            for (int i = 0; i < L.ndof; i++) {
+                npl[i] = (uint8_t)L.npar_log2[i];
+                for (int q = 0; q < 8; q++) par16[8 * (size_t)i + q] = L.par[8 * (size_t)i + q] < 0 ? 0 : (uint16_t)L.par[8 * (size_t)i + q];
+            }
+            o.o_par = put(par16.data(), 2 * par16.size());
+            o.o_npl2 = put(npl.data(), npl.size());
+        }
+        if (d < best_dn) {
+            std::vector<uint16_t> crp16(L.ndof + 1), cch16(L.cch.size());
+            for (int i = 0; i <= L.ndof; i++) crp16[i] = (uint16_t)L.crp[i];
+            for (size_t k = 0; k < L.cch.size(); k++) {
+                const uint32_t e = L.cch[k];
+                cch16[k] = (uint16_t)((e & kPackMask) | ((e >> kPackShift) << 14));
+            }
+            o.o_crp = put(crp16.data(), 2 * crp16.size());
+            o.o_cch = put(cch16.data(), 2 * cch16.size());
+        }
+        o.o_x = (int)voff; voff += align16(16 * (size_t)L.ndof);
+        o.o_b = (int)voff; voff += align16(16 * (size_t)L.ndof);
+        o.o_r = (int)voff; voff += align16(16 * (size_t)L.ndof);
+    }
+    if (off != best_blob) return 1;
+    if (cudaMalloc((void **)&c.narrow.blob, best_blob) != cudaSuccess) { cudaGetLastError(); c.narrow.blob = nullptr; return 1; }
+    if (cudaMemcpy(c.narrow.blob, buf.data(), best_blob, cudaMemcpyHostToDevice) != cudaSuccess) return 1;
+    c.narrow.blob_bytes = (int)best_blob;
+    c.narrow.vec_bytes = (int)best_vec;
+    for (auto *k : {(const void *)narrow_smem_kernel<1>, (const void *)narrow_smem_kernel<2>, (const void *)narrow_smem_kernel<4>})
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(best_blob + best_vec)) != cudaSuccess)
+            return 1;
+    c.narrow.dn = best_dn;
+    return 0;
+}
+
+// copy the current FP32 values and inverse diagonals of the narrow levels into the blob
+void narrow_smem_refresh(const Ctx &c, cudaStream_t s) {
+    if (c.narrow.dn < c.d0) return;
+    for (int d = c.d0; d <= c.narrow.dn; d++) {
+        const NarrowLevel &o = c.narrow.p.lev[d - c.d0];
+        cudaMemcpyAsync(c.narrow.blob + o.o_A, c.lev[d].A32, 4 * (size_t)o.nnz, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(c.narrow.blob + o.o_dinv, c.lev[d].dinv32, 4 * (size_t)o.n, cudaMemcpyDeviceToDevice, s);
+    }
+}
+
+void launch_narrow_smem(const Ctx &c, int R, cudaStream_t s) {
+    const DevLevel &T = c.lev[c.narrow.dn];
+    const int smem = c.narrow.blob_bytes + c.narrow.vec_bytes;
+    if (R == 1)
+        narrow_smem_kernel<1><<<1, 1024, smem, s>>>(c.narrow.blob, c.narrow.blob_bytes, c.narrow.vec_bytes, c.narrow.p,
+                                                    c.cinv32, c.cblk, T.b32, T.x32);
+    else if (R == 2)
+        narrow_smem_kernel<2><<<1, 1024, smem, s>>>(c.narrow.blob, c.narrow.blob_bytes, c.narrow.vec_bytes, c.narrow.p,
+                                                    c.cinv32, c.cblk, T.b32, T.x32);
+    else
+        narrow_smem_kernel<4><<<1, 1024, smem, s>>>(c.narrow.blob, c.narrow.blob_bytes, c.narrow.vec_bytes, c.narrow.p,
+                                                    c.cinv32, c.cblk, T.b32, T.x32);
+}
+
+}  // namespace lbmg

@@ -60,34 +60,30 @@ __device__ __forceinline__ unsigned long long globaltimer() {
     return t;
 }
 
-// bounded grid barrier: bar[0] = arrivals, bar[1] = generation.  `expected` is
-// the number of arrivals that complete it (gridDim.x, plus phantom participants
-// when the bounded-wait path is being tested).
+// Bounded grid barrier on a monotonic arrival counter bar[0] (zeroed before the
+// launch): arrival k belongs to barrier k / expected, which completes when the
+// counter reaches the next multiple of `expected` (gridDim.x, plus phantom
+// participants when the bounded-wait path is being tested).  The arrival is a
+// release, the polling an acquire, so the block's writes before the barrier
+// are visible to every block after it.
 __device__ bool grid_sync(unsigned *bar, int *status, unsigned expected) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        const unsigned gen = ld_acquire(bar + 1);
-        __threadfence();
-        const unsigned arrived = atomicAdd(bar, 1u) + 1u;
-        if (arrived == expected) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
-            const unsigned long long t0 = globaltimer();
-            unsigned long long spins = 0;
-            while (ld_acquire(bar + 1) == gen) {
-                ++spins;
-                if (((spins & 1023) == 0 && globaltimer() - t0 > kWaitNs) || spins > kSpinCap) {
-                    atomicExch(status, 1);
-                    ok = 0;
-                    break;
-                }
+        unsigned old;
+        asm volatile("atom.add.release.gpu.global.u32 %0, [%1], 1;" : "=r"(old) : "l"(bar) : "memory");
+        const unsigned target = (old / expected + 1) * expected;
+        const unsigned long long t0 = globaltimer();
+        unsigned long long spins = 0;
+        while ((int)(ld_acquire(bar) - target) < 0) {
+            ++spins;
+            if (((spins & 1023) == 0 && globaltimer() - t0 > kWaitNs) || spins > kSpinCap) {
+                atomicExch(status, 1);
+                ok = 0;
+                break;
             }
         }
-        __threadfence();
         s_ok = ok;
     }
     __syncthreads();
