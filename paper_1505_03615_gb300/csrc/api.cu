@@ -181,6 +181,8 @@ void enqueue_vcycle(Ctx &c, int R, cudaStream_t s, bool timed, int top = -1) {
             if (timed && d == top) cudaEventRecordWithFlags(c.ev_smooth[1], s, cudaEventRecordExternal);
             launch_residual<T>(L, P<T>::A(L), P<T>::b(L), P<T>::x(L), P<T>::r(L), R, s, L.ns);
             launch_restrict<T>(Lc, P<T>::r(L), P<T>::b(Lc), R, s);
+            // the shared-memory kernel starts level dn from zero itself
+            if (d - 1 > dn) cudaMemsetAsync(P<T>::x(Lc), 0, (size_t)Lc.n * R * sizeof(T), s);
         }
         launch_narrow_smem(c, R, s);
         for (int d = dn + 1; d <= top; d++) {
