@@ -186,6 +186,8 @@ def main():
     ap.add_argument("--persistent", action="store_true", help="one cooperative launch per solve")
     ap.add_argument("--no-graphs", action="store_true", help="launch each cycle's kernels directly (profilers)")
     ap.add_argument("--only-timed", action="store_true", help="stop after the timed steps (profiling runs)")
+    ap.add_argument("--no-pdl", action="store_true", help="plain stream order between the cycle's kernels")
+    ap.add_argument("--no-tune", action="store_true", help="default launch shapes (no autotuning at setup)")
     ap.add_argument("--max-cycles", type=int, default=2000,
                     help="cap on V-cycles per solve (profiling runs cap it to keep launch lists short)")
     args = ap.parse_args()
@@ -205,10 +207,17 @@ def main():
     dev = torch.device("cuda", local)
     V, F, depth, t, f, tol, _ = meshgen.config_mesh(WORKLOAD)
     nv = V.shape[0]
-    h = L.lbmg_build_hierarchy(V, F, depth, persistent=int(args.persistent), use_graphs=int(not args.no_graphs))
+    h = L.lbmg_build_hierarchy(V, F, depth, persistent=int(args.persistent), use_graphs=int(not args.no_graphs),
+                               pdl=int(not args.no_pdl))
     d0, D = L.lbmg_levels(h)
     n, nnz, nfrag = L.lbmg_level_info(h, D)
     nrhs = 3
+    # setup, like the hierarchy build: launch shapes tuned once per mesh on its own matrices
+    L.lbmg_assemble(h, t)
+    if not args.no_tune:
+        for prec in (L.LBMG_MIXED, L.LBMG_FP64):
+            L.lbmg_autotune(h, nrhs, prec, reps=4)
+    shapes = {str(d): L.lbmg_launch_shape(h, d, L.LBMG_MIXED) for d in range(d0 + 1, D + 1)}
     f_dev = torch.tensor(f, dtype=torch.float64, device=dev)
     rhs = torch.zeros((n, nrhs), dtype=torch.float64, device=dev)
     x = torch.zeros_like(rhs)
@@ -321,7 +330,8 @@ def main():
         # finest pre- and post-smoothing (16 colour launches per cycle and their gaps)
         launch_bytes = (nnz * 8 + n * (4 + 4 + 3 * R * 4)) / 8
         avg_launch_ms = smooth_ms / max(cycles * sweeps * 8, 1)
-        kernel = "smooth_colour_kernel<float,4,8> (finest level, per colour)"
+        kernel = f"smooth_colour_kernel<float,4,{shapes[str(D)][0][0]}> (finest level, per colour, " \
+                 f"{shapes[str(D)][0][1]} threads/block)"
         key = "smooth_colour_knot23_200k_d8"
     achieved = launch_bytes / (avg_launch_ms * 1e-3) / 1e9 if avg_launch_ms > 0 else 0.0
     traffic = None
@@ -354,7 +364,10 @@ def main():
                        "dofs_finest": n, "nnz_finest": nnz, "fragments_finest": nfrag, "nrhs": nrhs, "t": t,
                        "tol": tol, "precision": "mixed", "l2": "inputs larger than L2 (assembly streams >0.5 GB/step)",
                        "parallelism": "replicas" if ws > 1 else "single",
-                       "solve": "persistent" if args.persistent else "graph per cycle"},
+                       "solve": "persistent" if args.persistent else "graph per cycle",
+                       "dependent_launch": not args.no_pdl and not args.persistent,
+                       "launch_shapes_mixed": {d: {"sweep": list(v[0]), "residual": list(v[1])}
+                                               for d, v in shapes.items()}},
             "ms_to_tol_mixed": ms_per_step, "ms_to_tol_fp64": fp64_ms,
             "cycles_per_step": cycles / args.steps, "fp64_cycles_per_step": fp64_cycles / fp64_steps,
             "max_rel_residual": rel,

@@ -72,6 +72,11 @@ typedef struct lbmg_options {
                            (about one second) expires and lbmg_solve returns LBMG_DEVICE_TIMEOUT */
     int use_graphs;     /* per-cycle path: 1 (default) replays a captured CUDA graph per cycle; 0
                            launches the cycle's kernels directly (same kernels, e.g. for profilers) */
+    int pdl;            /* per-cycle path: 1 (default) chains the cycle's kernels with programmatic
+                           dependent launch, so each kernel loads its static matrix rows while the
+                           previous one finishes; 0 launches them with plain stream order.  Direct
+                           launches (use_graphs = 0) on the legacy or per-thread default stream
+                           always use plain stream order */
 } lbmg_options;
 
 typedef struct lbmg_stats {
@@ -181,6 +186,36 @@ int lbmg_solve(lbmg_handle h, const double *rhs, double *x, int nrhs, double tol
    and the fixed part of lbmg_solve around its cycles.  Host only. */
 int lbmg_launch_counts(lbmg_handle h, int precision, int *assemble, int *project_rhs, int *per_cycle,
                        int *solve_fixed);
+
+/*
+ * Launch-shape autotuner (throughput layer; the paper fixes no launch shapes).
+ * For every level above the coarsest, times the coloured Gauss-Seidel sweep and
+ * the residual kernel of `precision` for nrhs right-hand sides (1..4) with each
+ * of nine launch shapes -- 4, 8 or 16 threads per matrix row x 128, 256 or 512
+ * threads per block -- as a captured graph of `reps` (1..64) sweeps replayed three
+ * times, and keeps the fastest in the handle (the default 8 x 256 unless another
+ * shape is at least 2% faster).  Results are also kept in a process-wide cache
+ * keyed by (device name, precision, kernel, lanes, rows, non-zeros): levels of
+ * any handle that match an entry are not timed again.  The levels' cycle work
+ * vectors are overwritten; they carry no state between calls.  Captured cycle
+ * graphs are rebuilt at the next solve.  Needs lbmg_assemble first
+ * (LBMG_NOT_ASSEMBLED).  Synchronous.  *timed (may be NULL) receives how many
+ * (level, kernel) pairs were timed rather than taken from the cache.
+ */
+int lbmg_autotune(lbmg_handle h, int nrhs, int precision, int reps, int *timed, void *stream);
+/* launch shapes of level d for `precision`: out[4] = Gauss-Seidel sweep (threads per row,
+   threads per block), residual (threads per row, threads per block).  Host only. */
+int lbmg_launch_shape(lbmg_handle h, int d, int precision, int *out);
+/* set a launch shape of level d by hand: kind 0 = Gauss-Seidel sweep, 1 = residual;
+   tpr in {4, 8, 16}; tpb a multiple of 32 in [32, 512] (LBMG_INVALID_ARG otherwise).
+   Results change only by the summation order inside a row.  Host only. */
+int lbmg_set_launch_shape(lbmg_handle h, int d, int precision, int kind, int tpr, int tpb);
+/* write / read the process-wide tuning cache as text, one entry per line:
+   device fp64 kind lanes rows nnz threads_per_row threads_per_block.
+   Load merges valid lines and returns LBMG_INVALID_ARG if the file cannot be
+   opened or a line is malformed (valid lines are still taken). */
+int lbmg_tune_cache_save(const char *path);
+int lbmg_tune_cache_load(const char *path);
 
 /* Exactly `cycles` V-cycles in the same defect-correction form, with no norm
    read-back (used for throughput measurement).  x in/out. */

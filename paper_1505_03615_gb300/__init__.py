@@ -24,6 +24,7 @@ __all__ = [
     "lbmg_instance_residuals", "lbmg_learned_nparams", "lbmg_learned_params", "lbmg_learned_collect",
     "lbmg_learned_loss_grad", "lbmg_learned_train", "lbmg_learned_enable", "lbmg_learned_omega",
     "lbmg_residual_norms_noalloc", "lbmg_status_string", "lbmg_last_cuda_error", "lbmg_default_options",
+    "lbmg_autotune", "lbmg_launch_shape", "lbmg_set_launch_shape", "lbmg_tune_cache_save", "lbmg_tune_cache_load",
 ]
 
 LBMG_OK = 0
@@ -51,7 +52,7 @@ class Options(C.Structure):
     _fields_ = [("min_depth", C.c_int), ("coarse_max", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int),
                 ("smoother", C.c_int), ("jacobi_omega", C.c_double), ("split", C.c_int), ("threads", C.c_int),
                 ("persistent", C.c_int), ("narrow_max", C.c_int), ("barrier_phantoms", C.c_int),
-                ("use_graphs", C.c_int)]
+                ("use_graphs", C.c_int), ("pdl", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -89,6 +90,11 @@ def load_library():
         "lbmg_eval_vertices": (i, [P, P, i, P, P]),
         "lbmg_get_dofs": (i, [P, i, P, P]),
         "lbmg_launch_counts": (i, [P, i, P, P, P, P]),
+        "lbmg_autotune": (i, [P, i, i, i, P, P]),
+        "lbmg_launch_shape": (i, [P, i, i, P]),
+        "lbmg_set_launch_shape": (i, [P, i, i, i, i, i]),
+        "lbmg_tune_cache_save": (i, [C.c_char_p]),
+        "lbmg_tune_cache_load": (i, [C.c_char_p]),
         "lbmg_get_matrix": (i, [P, i, P, P, P, P]),
         "lbmg_get_prolongation": (i, [P, i, P, P]),
         "lbmg_build_batch": (i, [P, P, P, P, P, i, P, P]),
@@ -358,6 +364,34 @@ def lbmg_launch_counts(h, precision):
     v = [C.c_int() for _ in range(4)]
     _check(load_library().lbmg_launch_counts(h, int(precision), *[C.byref(x) for x in v]), "lbmg_launch_counts")
     return tuple(x.value for x in v)
+
+
+def lbmg_autotune(h, nrhs, precision, reps=4, stream=None):
+    """Tune the launch shapes of every level; returns how many (level, kernel) pairs were timed."""
+    n = C.c_int()
+    _check(load_library().lbmg_autotune(h, int(nrhs), int(precision), int(reps), C.byref(n), _stream(stream)),
+           "lbmg_autotune")
+    return n.value
+
+
+def lbmg_launch_shape(h, d, precision):
+    """((sweep threads/row, sweep threads/block), (residual threads/row, residual threads/block)) of level d."""
+    out = (C.c_int * 4)()
+    _check(load_library().lbmg_launch_shape(h, int(d), int(precision), out), "lbmg_launch_shape")
+    return (out[0], out[1]), (out[2], out[3])
+
+
+def lbmg_set_launch_shape(h, d, precision, kind, tpr, tpb):
+    return _check(load_library().lbmg_set_launch_shape(h, int(d), int(precision), int(kind), int(tpr), int(tpb)),
+                  "lbmg_set_launch_shape")
+
+
+def lbmg_tune_cache_save(path):
+    return _check(load_library().lbmg_tune_cache_save(os.fsencode(path)), "lbmg_tune_cache_save")
+
+
+def lbmg_tune_cache_load(path):
+    return _check(load_library().lbmg_tune_cache_load(os.fsencode(path)), "lbmg_tune_cache_load")
 
 
 def lbmg_get_dofs(h, d):

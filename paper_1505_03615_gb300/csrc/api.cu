@@ -150,90 +150,69 @@ template <> struct P<double> {
 };
 
 template <class T>
-void enqueue_smooth(Ctx &c, DevLevel &L, int R, int sweeps, bool forward, cudaStream_t s) {
+void enqueue_smooth(Ctx &c, DevLevel &L, int R, int sweeps, bool forward, cudaStream_t s, Chain *ch) {
     for (int sw = 0; sw < sweeps; sw++) {
         if (c.smoother == LBMG_JACOBI) {
-            launch_residual<T>(L, P<T>::A(L), P<T>::b(L), P<T>::x(L), P<T>::r(L), R, s, L.ns);
+            launch_residual<T>(L, P<T>::A(L), P<T>::b(L), P<T>::x(L), P<T>::r(L), R, s, L.ns, ch);
             launch_jacobi_update<T>(L, P<T>::dinv(L), P<T>::r(L), P<T>::x(L), (T)c.omega, R, s);
+            if (ch) ch->cut();
         } else {
             for (int q = 0; q < 8; q++) {
                 const int colour = forward ? q : 7 - q;
-                launch_smooth_colour<T>(L, colour, P<T>::A(L), P<T>::dinv(L), P<T>::b(L), P<T>::x(L), R, s);
+                launch_smooth_colour<T>(L, colour, P<T>::A(L), P<T>::dinv(L), P<T>::b(L), P<T>::x(L), R, s, ch);
             }
         }
     }
 }
 
-// one V-cycle on A e = b at the finest level; e (finest x) must be zero on entry
+// event record inside the cycle (an external event node when captured into a graph,
+// which a plain record outside capture must not ask for); it ends the chain of
+// dependent launches
+inline void record(cudaEvent_t e, cudaStream_t s, Chain *ch) {
+    if (ch->capturing) cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+    else cudaEventRecord(e, s);
+    ch->cut();
+}
+
+// one V-cycle on A e = b at the finest level; e (finest x) must be zero on entry.
+// Every coarser correction is zeroed by the restriction that fills its right-hand
+// side, so the kernels of the cycle follow one another with no memset between
+// them and run as one chain of dependent launches.
 template <class T>
-void enqueue_vcycle(Ctx &c, int R, cudaStream_t s, bool timed, int top = -1) {
+void enqueue_vcycle(Ctx &c, int R, cudaStream_t s, bool timed, Chain *ch, int top = -1) {
     if (top < 0) top = c.D;
-    // levels dn..d0 (at most narrow_max rows each) run in one single-block kernel
-    // (FP32 only: a single SM's FP64 rate makes the one-block bottom slower than per-phase launches)
-    if (sizeof(T) == 4 && c.narrow.dn >= c.d0 && c.narrow.dn <= top && c.smoother != LBMG_JACOBI) {
-        // bottom levels from shared memory (one block), the rest one launch per phase
-        const int dn = c.narrow.dn;
-        for (int d = top; d > dn; d--) {
-            DevLevel &L = c.lev[d], &Lc = c.lev[d - 1];
-            launch_coarse_apply<T>(c, L, P<T>::inv(c), P<T>::b(L), P<T>::x(L), R, s);
-            if (timed && d == top) cudaEventRecordWithFlags(c.ev_smooth[0], s, cudaEventRecordExternal);
-            enqueue_smooth<T>(c, L, R, c.nu1, true, s);
-            if (timed && d == top) cudaEventRecordWithFlags(c.ev_smooth[1], s, cudaEventRecordExternal);
-            launch_residual<T>(L, P<T>::A(L), P<T>::b(L), P<T>::x(L), P<T>::r(L), R, s, L.ns);
-            launch_restrict<T>(Lc, P<T>::r(L), P<T>::b(Lc), R, s);
-            // the shared-memory kernel starts level dn from zero itself
-            if (d - 1 > dn) cudaMemsetAsync(P<T>::x(Lc), 0, (size_t)Lc.n * R * sizeof(T), s);
-        }
-        launch_narrow_smem(c, R, s);
-        for (int d = dn + 1; d <= top; d++) {
-            DevLevel &L = c.lev[d];
-            launch_prolong_add<T>(L, P<T>::x(c.lev[d - 1]), P<T>::x(L), R, s);
-            if (timed && d == top) cudaEventRecordWithFlags(c.ev_smooth[2], s, cudaEventRecordExternal);
-            enqueue_smooth<T>(c, L, R, c.nu2, false, s);
-            if (timed && d == top) cudaEventRecordWithFlags(c.ev_smooth[3], s, cudaEventRecordExternal);
-        }
-        return;
+    // bottom levels: from shared memory in one block (FP32), from global memory in
+    // one block (levels of at most narrow_max rows), or one launch per phase down to d0
+    // (a single SM's FP64 rate makes the one-block bottom slower than per-phase launches)
+    int dn = c.d0;
+    enum { kPlain, kSmem, kL2 } bottom = kPlain;
+    if (sizeof(T) == 4 && c.smoother != LBMG_JACOBI) {
+        if (c.narrow.dn >= c.d0 && c.narrow.dn <= top) { bottom = kSmem; dn = c.narrow.dn; }
+        else if (std::min(c.persist_dn, top) >= c.d0) { bottom = kL2; dn = std::min(c.persist_dn, top); }
     }
-    const int dn = std::min(c.persist_dn, top);
-    if (dn >= c.d0 && c.smoother != LBMG_JACOBI && sizeof(T) == 4) {
-        for (int d = top; d > dn; d--) {
-            DevLevel &L = c.lev[d], &Lc = c.lev[d - 1];
-            launch_coarse_apply<T>(c, L, P<T>::inv(c), P<T>::b(L), P<T>::x(L), R, s);
-            if (timed && d == top) cudaEventRecordWithFlags(c.ev_smooth[0], s, cudaEventRecordExternal);
-            enqueue_smooth<T>(c, L, R, c.nu1, true, s);
-            if (timed && d == top) cudaEventRecordWithFlags(c.ev_smooth[1], s, cudaEventRecordExternal);
-            launch_residual<T>(L, P<T>::A(L), P<T>::b(L), P<T>::x(L), P<T>::r(L), R, s, L.ns);
-            launch_restrict<T>(Lc, P<T>::r(L), P<T>::b(Lc), R, s);
-            cudaMemsetAsync(P<T>::x(Lc), 0, (size_t)Lc.n * R * sizeof(T), s);
-        }
-        launch_narrow_cycle(c, sizeof(T) == 4 ? 1 : 0, R, dn, s);
-        for (int d = dn + 1; d <= top; d++) {
-            DevLevel &L = c.lev[d];
-            launch_prolong_add<T>(L, P<T>::x(c.lev[d - 1]), P<T>::x(L), R, s);
-            if (timed && d == top) cudaEventRecordWithFlags(c.ev_smooth[2], s, cudaEventRecordExternal);
-            enqueue_smooth<T>(c, L, R, c.nu2, false, s);
-            if (timed && d == top) cudaEventRecordWithFlags(c.ev_smooth[3], s, cudaEventRecordExternal);
-        }
-        return;
-    }
-    for (int d = top; d > c.d0; d--) {
+    for (int d = top; d > dn; d--) {
         DevLevel &L = c.lev[d], &Lc = c.lev[d - 1];
-        launch_coarse_apply<T>(c, L, P<T>::inv(c), P<T>::b(L), P<T>::x(L), R, s);
-        if (timed && d == top) cudaEventRecordWithFlags(c.ev_smooth[0], s, cudaEventRecordExternal);
-        enqueue_smooth<T>(c, L, R, c.nu1, true, s);
-        if (timed && d == top) cudaEventRecordWithFlags(c.ev_smooth[1], s, cudaEventRecordExternal);
-        launch_residual<T>(L, P<T>::A(L), P<T>::b(L), P<T>::x(L), P<T>::r(L), R, s, L.ns);
-        launch_restrict<T>(Lc, P<T>::r(L), P<T>::b(Lc), R, s);
-        if (d - 1 > c.d0) cudaMemsetAsync(P<T>::x(Lc), 0, (size_t)Lc.n * R * sizeof(T), s);
+        launch_coarse_apply<T>(c, L, P<T>::inv(c), P<T>::b(L), P<T>::x(L), R, s, ch);
+        if (timed && d == top) record(c.ev_smooth[0], s, ch);
+        enqueue_smooth<T>(c, L, R, c.nu1, true, s, ch);
+        if (timed && d == top) record(c.ev_smooth[1], s, ch);
+        launch_residual<T>(L, P<T>::A(L), P<T>::b(L), P<T>::x(L), P<T>::r(L), R, s, L.ns, ch);
+        // the shared-memory bottom starts level dn from zero itself; the dense solve overwrites d0
+        const bool zero = bottom == kSmem ? d - 1 > dn : (bottom == kL2 || d - 1 > c.d0);
+        launch_restrict<T>(Lc, P<T>::r(L), P<T>::b(Lc), R, s, zero ? P<T>::x(Lc) : (T *)nullptr, ch);
     }
-    DevLevel &L0 = c.lev[c.d0];
-    launch_coarse_apply<T>(c, L0, P<T>::inv(c), P<T>::b(L0), P<T>::x(L0), R, s);
-    for (int d = c.d0 + 1; d <= top; d++) {
+    if (bottom == kSmem) launch_narrow_smem(c, R, s, ch);
+    else if (bottom == kL2) { launch_narrow_cycle(c, 1, R, dn, s); ch->cut(); }
+    else {
+        DevLevel &L0 = c.lev[c.d0];
+        launch_coarse_apply<T>(c, L0, P<T>::inv(c), P<T>::b(L0), P<T>::x(L0), R, s, ch);
+    }
+    for (int d = dn + 1; d <= top; d++) {
         DevLevel &L = c.lev[d];
-        launch_prolong_add<T>(L, P<T>::x(c.lev[d - 1]), P<T>::x(L), R, s);
-        if (timed && d == top) cudaEventRecordWithFlags(c.ev_smooth[2], s, cudaEventRecordExternal);
-        enqueue_smooth<T>(c, L, R, c.nu2, false, s);
-        if (timed && d == top) cudaEventRecordWithFlags(c.ev_smooth[3], s, cudaEventRecordExternal);
+        launch_prolong_add<T>(L, P<T>::x(c.lev[d - 1]), P<T>::x(L), R, s, ch);
+        if (timed && d == top) record(c.ev_smooth[2], s, ch);
+        enqueue_smooth<T>(c, L, R, c.nu2, false, s, ch);
+        if (timed && d == top) record(c.ev_smooth[3], s, ch);
     }
 }
 
@@ -241,19 +220,24 @@ void enqueue_vcycle(Ctx &c, int R, cudaStream_t s, bool timed, int top = -1) {
 void enqueue_iteration(Ctx &c, int R, int precision, cudaStream_t s) {
     DevLevel &F = c.lev[c.D];
     const int64_t m = (int64_t)F.n * R;
+    Chain ch;
+    // the legacy and per-thread default streams take no programmatic serialization
+    ch.on = c.pdl != 0 && s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    ch.capturing = cudaStreamIsCapturing(s, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusActive;
     if (precision == LBMG_MIXED) {
-        launch_to_float(c.rs, F.b32, m, s);
-        cudaMemsetAsync(F.x32, 0, m * sizeof(float), s);
-        enqueue_vcycle<float>(c, R, s, true);
-        launch_add_float(c.xs, F.x32, m, s);
+        launch_to_float(c.rs, F.b32, m, s, F.x32, &ch);
+        enqueue_vcycle<float>(c, R, s, true, &ch);
+        launch_add_float(c.xs, F.x32, m, s, &ch);
     } else {
         cudaMemcpyAsync(F.b64, c.rs, m * sizeof(double), cudaMemcpyDeviceToDevice, s);
         cudaMemsetAsync(F.x64, 0, m * sizeof(double), s);
-        enqueue_vcycle<double>(c, R, s, true);
+        enqueue_vcycle<double>(c, R, s, true, &ch);
         launch_add_double(c.xs, F.x64, m, s);
+        ch.cut();
     }
-    launch_residual<double>(F, F.A64, c.bs, c.xs, c.rs, R, s);
-    launch_norms(c.rs, F.n, R, c.norm_part, c.norm_out, s);
+    launch_residual<double>(F, F.A64, c.bs, c.xs, c.rs, R, s, -1, &ch);
+    launch_norms(c.rs, F.n, R, c.norm_part, c.norm_out, s, &ch);
 }
 
 int get_graph(lbmg_handle h, int R, int precision, cudaGraphExec_t *out) {
@@ -439,7 +423,10 @@ int upload_hierarchy(lbmg_handle h) {
 }  // namespace
 
 namespace lbmg {
-void enqueue_vcycle64_from(Ctx &c, int top, int R, cudaStream_t s) { enqueue_vcycle<double>(c, R, s, false, top); }
+void enqueue_vcycle64_from(Ctx &c, int top, int R, cudaStream_t s) {
+    Chain ch;   // plain launches
+    enqueue_vcycle<double>(c, R, s, false, &ch, top);
+}
 
 // level d of an assembled handle, for entry points defined in other files
 const DevLevel *noalloc_level(lbmg_handle h, int d) {
@@ -483,6 +470,7 @@ void lbmg_default_options(lbmg_options *o) {
     o->narrow_max = 2048;
     o->barrier_phantoms = 0;
     o->use_graphs = 1;
+    o->pdl = 1;
 }
 
 int lbmg_build_hierarchy(const double *V, int nv, const int *F, int nt, int depth, const lbmg_options *opt,
@@ -515,6 +503,7 @@ int lbmg_build_hierarchy(const double *V, int nv, const int *F, int nt, int dept
     h->c.omega = o.jacobi_omega;
     h->c.persistent = o.persistent;
     h->c.use_graphs = o.use_graphs;
+    h->c.pdl = o.pdl;
     h->c.persist_narrow = o.narrow_max;
     h->c.barrier_phantoms = o.barrier_phantoms;
     st = upload_hierarchy(h);
@@ -852,10 +841,10 @@ int lbmg_smooth(lbmg_handle h, int d, const double *rhs, double *x, int nrhs, in
     if (precision == LBMG_MIXED) {
         launch_to_float(L.b64, L.b32, m, s);
         launch_to_float(L.x64, L.x32, m, s);
-        enqueue_smooth<float>(h->c, L, R, sweeps, true, s);
+        enqueue_smooth<float>(h->c, L, R, sweeps, true, s, nullptr);
         if (m) to_double_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(L.x32, L.x64, m);
     } else {
-        enqueue_smooth<double>(h->c, L, R, sweeps, true, s);
+        enqueue_smooth<double>(h->c, L, R, sweeps, true, s, nullptr);
     }
     double *xo;
     bool host_out;
@@ -925,6 +914,55 @@ int lbmg_launch_counts(lbmg_handle h, int precision, int *assemble, int *project
     if (per_cycle) *per_cycle = persistent ? 0 : cyc;
     if (solve_fixed) *solve_fixed = persistent ? 4 : 2 + 1 + 2 + 2 + 1;
     return LBMG_OK;
+}
+
+int lbmg_autotune(lbmg_handle h, int nrhs, int precision, int reps, int *timed, void *stream) {
+    if (!h || nrhs < 1 || nrhs > 4 || reps < 1 || reps > 64) return LBMG_INVALID_ARG;
+    if (precision != LBMG_FP64 && precision != LBMG_MIXED) return LBMG_INVALID_ARG;
+    if (!h->c.assembled) return LBMG_NOT_ASSEMBLED;
+    Ctx &c = h->c;
+    const cudaError_t e = (cudaError_t)autotune(c, stride_for(nrhs), precision, reps, (cudaStream_t)stream, timed);
+    if (c.graph.exec) { cudaGraphExecDestroy(c.graph.exec); c.graph.exec = nullptr; }
+    if (e != cudaSuccess) {
+        g_cuda_err = std::string("autotune: ") + cudaGetErrorString(e);
+        cudaGetLastError();
+        return LBMG_CUDA_ERROR;
+    }
+    return LBMG_OK;
+}
+
+int lbmg_launch_shape(lbmg_handle h, int d, int precision, int *out) {
+    LBMG_TRY(check_level(h, d));
+    if (!out || (precision != LBMG_FP64 && precision != LBMG_MIXED)) return LBMG_INVALID_ARG;
+    const DevLevel &L = h->c.lev[d];
+    const int p = precision == LBMG_FP64;
+    out[0] = L.shape[p][kShapeSmooth].tpr;
+    out[1] = L.shape[p][kShapeSmooth].tpb;
+    out[2] = L.shape[p][kShapeResidual].tpr;
+    out[3] = L.shape[p][kShapeResidual].tpb;
+    return LBMG_OK;
+}
+
+int lbmg_set_launch_shape(lbmg_handle h, int d, int precision, int kind, int tpr, int tpb) {
+    LBMG_TRY(check_level(h, d));
+    if (precision != LBMG_FP64 && precision != LBMG_MIXED) return LBMG_INVALID_ARG;
+    if (kind != 0 && kind != 1) return LBMG_INVALID_ARG;
+    if ((tpr != 4 && tpr != 8 && tpr != 16) || tpb < 32 || tpb > 512 || tpb % 32 != 0) return LBMG_INVALID_ARG;
+    LaunchShape &sh = h->c.lev[d].shape[precision == LBMG_FP64][kind];
+    sh.tpr = tpr;
+    sh.tpb = tpb;
+    if (h->c.graph.exec) { cudaGraphExecDestroy(h->c.graph.exec); h->c.graph.exec = nullptr; }
+    return LBMG_OK;
+}
+
+int lbmg_tune_cache_save(const char *path) {
+    if (!path) return LBMG_INVALID_ARG;
+    return tune_cache_save(path) == 0 ? LBMG_OK : LBMG_INVALID_ARG;
+}
+
+int lbmg_tune_cache_load(const char *path) {
+    if (!path) return LBMG_INVALID_ARG;
+    return tune_cache_load(path) == 0 ? LBMG_OK : LBMG_INVALID_ARG;
 }
 
 static int learned_ready(lbmg_handle h, cudaStream_t s) {

@@ -12,6 +12,53 @@ constexpr int kNQ = 4;            // Gauss-Legendre points per direction of the 
 constexpr int kMaxCoarse = 2048;  // largest coarsest level factored densely
 constexpr int kNormBlocks = 256;  // partial sums of the two-pass norm reduction
 
+// Launch shape of the row-parallel kernels (Gauss-Seidel colour sweep, residual):
+// tpr threads share one matrix row (4, 8 or 16), tpb threads per block (128-512).
+struct LaunchShape {
+    int tpr = 8, tpb = 256;
+};
+enum { kShapeSmooth = 0, kShapeResidual = 1 };
+
+// Programmatic dependent launch (sm_90 and later).  A kernel launched with
+// programmatic stream serialization may begin while the kernel before it in the
+// stream is still running; it reads only data that no kernel of the chain writes
+// (the matrices, transfer tables) until grid_dep_wait() returns, which happens
+// once the predecessor has finished and its writes are visible.  Each kernel
+// calls grid_dep_launch() right after its own wait, so at most two kernels of a
+// chain are resident at once.  Without the launch attribute both are no-ops.
+#ifdef __CUDACC__
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+#endif
+
+// The kernels of one V-cycle form a chain: a launch gets the programmatic
+// attribute only when the operation just before it in the stream is a kernel of
+// the same chain (an event record, memset or copy in between cuts it).
+struct Chain {
+    bool on = false, prev = false;
+    bool capturing = false;   // the stream is being captured into a graph
+    void cut() { prev = false; }
+};
+
+// cudaLaunchKernelEx with the programmatic attribute when the chain allows it;
+// marks the chain as ending in a kernel.
+template <class... KArgs, class... Args>
+inline void klaunch(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t s, Chain *ch,
+                    Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = (ch && ch->on && ch->prev) ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+    if (ch) ch->prev = true;
+}
+
 struct DevLevel {
     int d = 0, n = 0;
     int ns = 0;                            // rows [0, ns) are smoothed; [ns, n) belong to coarsest blocks
@@ -32,6 +79,7 @@ struct DevLevel {
     // V-cycle work vectors, room for [n][4]
     double *x64 = nullptr, *b64 = nullptr, *r64 = nullptr;
     float *x32 = nullptr, *b32 = nullptr, *r32 = nullptr;
+    LaunchShape shape[2][2];               // [FP64][kShapeSmooth / kShapeResidual], set by the autotuner
 };
 
 struct Learned;
@@ -115,6 +163,7 @@ struct Ctx {
     // persistent cooperative solve
     int persistent = 1;           // use the one-launch solve when the device allows it
     int use_graphs = 1;           // per-cycle path: replay a captured graph (1) or launch directly (0)
+    int pdl = 1;                  // chain the kernels of a cycle with programmatic dependent launch
     int persist_ok = 0;
     int persist_blocks = 0, persist_dn = 0, persist_narrow = 2048;
     int barrier_phantoms = 0;        // fault injection: extra arrivals a grid barrier waits for
@@ -136,7 +185,12 @@ struct Ctx {
 // ----- shared-memory bottom cycle (narrow.cu) -----
 int narrow_smem_setup(Ctx &c, size_t smem_budget);
 void narrow_smem_refresh(const Ctx &c, cudaStream_t s);
-void launch_narrow_smem(const Ctx &c, int R, cudaStream_t s);
+void launch_narrow_smem(const Ctx &c, int R, cudaStream_t s, Chain *ch = nullptr);
+
+// ----- launch-shape autotuner (tune.cu) -----
+int autotune(Ctx &c, int R, int precision, int reps, cudaStream_t s, int *timed);
+int tune_cache_save(const char *path);
+int tune_cache_load(const char *path);
 
 // ----- learned relaxation weights (learned.cu) -----
 int learned_setup(Ctx &c, cudaStream_t s);
@@ -167,23 +221,26 @@ void launch_eval_vertices(const Ctx &c, const double *x, int nrhs, double *u, cu
 // ----- kernels (relax.cu) -----
 // vectors below are [n][R] with stride R in {1, 2, 4} (3 right-hand sides padded to 4)
 template <class T> void launch_smooth_colour(const DevLevel &L, int colour, const T *A, const T *dinv,
-                                             const T *b, T *x, int R, cudaStream_t s);
+                                             const T *b, T *x, int R, cudaStream_t s, Chain *ch = nullptr);
 template <class T> void launch_residual(const DevLevel &L, const T *A, const T *b, const T *x, T *r, int R,
-                                        cudaStream_t s, int nrows = -1);
+                                        cudaStream_t s, int nrows = -1, Chain *ch = nullptr);
 template <class T> void launch_jacobi_update(const DevLevel &L, const T *dinv, const T *r, T *x, T omega, int R,
                                              cudaStream_t s);
-template <class T> void launch_restrict(const DevLevel &Lc, const T *rf, T *bc, int R, cudaStream_t s);
-template <class T> void launch_prolong_add(const DevLevel &Lf, const T *xc, T *xf, int R, cudaStream_t s);
+// bc = P^T rf; when xc is given, the coarse correction xc is zeroed in the same pass
+template <class T> void launch_restrict(const DevLevel &Lc, const T *rf, T *bc, int R, cudaStream_t s,
+                                        T *xc = nullptr, Chain *ch = nullptr);
+template <class T> void launch_prolong_add(const DevLevel &Lf, const T *xc, T *xf, int R, cudaStream_t s,
+                                           Chain *ch = nullptr);
 struct Ctx;
 template <class T> void launch_coarse_apply(const Ctx &c, const DevLevel &L, const T *inv, const T *b, T *x, int R,
-                                            cudaStream_t s);
+                                            cudaStream_t s, Chain *ch = nullptr);
 void launch_coarse_factor(const Ctx &c, const int *const *rps, const int *const *cis, const double *const *As,
                           cudaStream_t s);
-void launch_norms(const double *v, int n, int R, double *part, double *out, cudaStream_t s);
+void launch_norms(const double *v, int n, int R, double *part, double *out, cudaStream_t s, Chain *ch = nullptr);
 void launch_pack(const double *user, int n, int nrhs, int R, double *v, cudaStream_t s, const int *perm = nullptr);
 void launch_unpack(const double *v, int n, int nrhs, int R, double *user, cudaStream_t s, const int *perm = nullptr);
-void launch_to_float(const double *a, float *b, int64_t n, cudaStream_t s);
-void launch_add_float(double *x, const float *e, int64_t n, cudaStream_t s);
+void launch_to_float(const double *a, float *b, int64_t n, cudaStream_t s, float *zero = nullptr, Chain *ch = nullptr);
+void launch_add_float(double *x, const float *e, int64_t n, cudaStream_t s, Chain *ch = nullptr);
 void launch_add_double(double *x, const double *e, int64_t n, cudaStream_t s);
 
 }  // namespace lbmg

@@ -98,6 +98,9 @@ __global__ void __launch_bounds__(1024, 1) narrow_smem_kernel(const unsigned cha
         reinterpret_cast<uint4 *>(sm)[q] = __ldg(reinterpret_cast<const uint4 *>(blob) + q);
     for (int q = threadIdx.x; q < vec_bytes / 16; q += blockDim.x)
         reinterpret_cast<uint4 *>(sm + blob_bytes)[q] = make_uint4(0, 0, 0, 0);
+    // the blob is static during a solve; b_top comes from the kernel before this one
+    grid_dep_wait();
+    grid_dep_launch();
     __syncthreads();
     const NarrowLevel &T = p.lev[p.dn - p.d0];
     {
@@ -317,18 +320,13 @@ void narrow_smem_refresh(const Ctx &c, cudaStream_t s) {
     }
 }
 
-void launch_narrow_smem(const Ctx &c, int R, cudaStream_t s) {
+void launch_narrow_smem(const Ctx &c, int R, cudaStream_t s, Chain *ch) {
     const DevLevel &T = c.lev[c.narrow.dn];
     const int smem = c.narrow.blob_bytes + c.narrow.vec_bytes;
-    if (R == 1)
-        narrow_smem_kernel<1><<<1, 1024, smem, s>>>(c.narrow.blob, c.narrow.blob_bytes, c.narrow.vec_bytes, c.narrow.p,
-                                                    c.cinv32, c.cblk, T.b32, T.x32);
-    else if (R == 2)
-        narrow_smem_kernel<2><<<1, 1024, smem, s>>>(c.narrow.blob, c.narrow.blob_bytes, c.narrow.vec_bytes, c.narrow.p,
-                                                    c.cinv32, c.cblk, T.b32, T.x32);
-    else
-        narrow_smem_kernel<4><<<1, 1024, smem, s>>>(c.narrow.blob, c.narrow.blob_bytes, c.narrow.vec_bytes, c.narrow.p,
-                                                    c.cinv32, c.cblk, T.b32, T.x32);
+    auto k = R == 1 ? narrow_smem_kernel<1> : R == 2 ? narrow_smem_kernel<2> : narrow_smem_kernel<4>;
+    klaunch(k, 1u, 1024u, (size_t)smem, s, ch, (const unsigned char *)c.narrow.blob, c.narrow.blob_bytes,
+            c.narrow.vec_bytes, c.narrow.p, (const float *)c.cinv32, (const int *)c.cblk, (const float *)T.b32,
+            T.x32);
 }
 
 }  // namespace lbmg

@@ -42,21 +42,49 @@ __device__ __forceinline__ void load_x(const T *p, T (&v)[R]) {
     for (int r = 0; r < R; r++) v[r] = p[r];
 }
 
-template <class T, int R, int G>
-__device__ __forceinline__ void row_dot(int row, const int *__restrict__ rp, const int *__restrict__ ci,
-                                        const T *__restrict__ A, const T *x, int lane, T (&acc)[R]) {
+// The static part of a matrix row (pattern and values) is loaded before the
+// kernel waits for its predecessor: each of the G threads of a row keeps its first
+// P entries in registers, so after the wait only the x gathers remain.
+template <class T, int G>
+struct RowPrefetch {
+    static constexpr int P = 32 / G;
+    int k = 0, k1 = 0;
+    int j[P];
+    T a[P];
+    __device__ __forceinline__ void load(int row, bool active, int lane, const int *__restrict__ rp,
+                                         const int *__restrict__ ci, const T *__restrict__ A) {
+        if (active) { k = __ldg(rp + row) + lane; k1 = __ldg(rp + row + 1); }
 #pragma unroll
-    for (int r = 0; r < R; r++) acc[r] = T(0);
-    const int k1 = rp[row + 1];
-    for (int k = rp[row] + lane; k < k1; k += G) {
-        const int j = __ldg(ci + k);
-        const T a = __ldg(A + k);
-        T xv[R];
-        load_x<T, R>(x + (size_t)j * R, xv);
-#pragma unroll
-        for (int r = 0; r < R; r++) acc[r] = fma(a, xv[r], acc[r]);
+        for (int q = 0; q < P; q++) {
+            const int kk = k + q * G;
+            if (kk < k1) { j[q] = __ldg(ci + kk); a[q] = __ldg(A + kk); }
+            else { j[q] = -1; a[q] = T(0); }
+        }
     }
-}
+    template <int R>
+    __device__ __forceinline__ void dot(const int *__restrict__ ci, const T *__restrict__ A, const T *x,
+                                        T (&acc)[R]) const {
+#pragma unroll
+        for (int r = 0; r < R; r++) acc[r] = T(0);
+#pragma unroll
+        for (int q = 0; q < P; q++) {
+            if (j[q] >= 0) {
+                T xv[R];
+                load_x<T, R>(x + (size_t)j[q] * R, xv);
+#pragma unroll
+                for (int r = 0; r < R; r++) acc[r] = fma(a[q], xv[r], acc[r]);
+            }
+        }
+        for (int kk = k + P * G; kk < k1; kk += G) {
+            const int jj = __ldg(ci + kk);
+            const T aa = __ldg(A + kk);
+            T xv[R];
+            load_x<T, R>(x + (size_t)jj * R, xv);
+#pragma unroll
+            for (int r = 0; r < R; r++) acc[r] = fma(aa, xv[r], acc[r]);
+        }
+    }
+};
 
 template <class T, int R, int G>
 __device__ __forceinline__ void group_sum(T (&acc)[R]) {
@@ -67,67 +95,92 @@ __device__ __forceinline__ void group_sum(T (&acc)[R]) {
 }
 
 template <class T, int R, int G>
-__global__ void __launch_bounds__(256) smooth_colour_kernel(int r0, int r1, const int *__restrict__ rp,
+__global__ void __launch_bounds__(512) smooth_colour_kernel(int r0, int r1, const int *__restrict__ rp,
                                                             const int *__restrict__ ci, const T *__restrict__ A,
                                                             const T *__restrict__ dinv, const T *__restrict__ b, T *x) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int row = r0 + tid / G, lane = tid % G;
+    const bool active = row < r1;
+    RowPrefetch<T, G> pf;
+    pf.load(row, active, lane, rp, ci, A);
+    const T d = (active && lane == 0) ? __ldg(dinv + row) : T(0);
+    grid_dep_wait();
+    grid_dep_launch();
     T acc[R];
-    if (row < r1) row_dot<T, R, G>(row, rp, ci, A, x, lane, acc);
-    else {
-#pragma unroll
-        for (int r = 0; r < R; r++) acc[r] = T(0);
-    }
+    pf.template dot<R>(ci, A, x, acc);
     group_sum<T, R, G>(acc);
-    if (row < r1 && lane == 0) {
-        const T d = dinv[row];
+    if (active && lane == 0) {
 #pragma unroll
         for (int r = 0; r < R; r++) x[(size_t)row * R + r] += (b[(size_t)row * R + r] - acc[r]) * d;
     }
 }
 
 template <class T, int R, int G>
-__global__ void __launch_bounds__(256) residual_kernel(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+__global__ void __launch_bounds__(512) residual_kernel(int n, const int *__restrict__ rp, const int *__restrict__ ci,
                                                        const T *__restrict__ A, const T *__restrict__ b,
                                                        const T *x, T *__restrict__ r) {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int row = tid / G, lane = tid % G;
+    const bool active = row < n;
+    RowPrefetch<T, G> pf;
+    pf.load(row, active, lane, rp, ci, A);
+    grid_dep_wait();
+    grid_dep_launch();
     T acc[R];
-    if (row < n) row_dot<T, R, G>(row, rp, ci, A, x, lane, acc);
-    else {
-#pragma unroll
-        for (int q = 0; q < R; q++) acc[q] = T(0);
-    }
+    pf.template dot<R>(ci, A, x, acc);
     group_sum<T, R, G>(acc);
-    if (row < n && lane == 0) {
+    if (active && lane == 0) {
 #pragma unroll
         for (int q = 0; q < R; q++) r[(size_t)row * R + q] = b[(size_t)row * R + q] - acc[q];
     }
 }
 
-constexpr int kRowGroup = 8;   // threads per matrix row
-
+// kernel instance for (R, threads per row); nullptr for an unsupported pair
 template <class T>
-void launch_smooth_colour(const DevLevel &L, int colour, const T *A, const T *dinv, const T *b, T *x, int R,
-                          cudaStream_t s) {
-    const int r0 = L.cs[colour], r1 = L.cs[colour + 1];
-    if (r1 <= r0) return;
-    const int threads = 256;
-    const unsigned blocks = (unsigned)(((int64_t)(r1 - r0) * kRowGroup + threads - 1) / threads);
-    if (R == 1) smooth_colour_kernel<T, 1, kRowGroup><<<blocks, threads, 0, s>>>(r0, r1, L.rp, L.ci, A, dinv, b, x);
-    else if (R == 2) smooth_colour_kernel<T, 2, kRowGroup><<<blocks, threads, 0, s>>>(r0, r1, L.rp, L.ci, A, dinv, b, x);
-    else smooth_colour_kernel<T, 4, kRowGroup><<<blocks, threads, 0, s>>>(r0, r1, L.rp, L.ci, A, dinv, b, x);
+using SmoothFn = void (*)(int, int, const int *, const int *, const T *, const T *, const T *, T *);
+template <class T>
+using ResidualFn = void (*)(int, const int *, const int *, const T *, const T *, const T *, T *);
+
+template <class T, int R>
+SmoothFn<T> smooth_fn(int tpr) {
+    switch (tpr) {
+        case 4: return smooth_colour_kernel<T, R, 4>;
+        case 8: return smooth_colour_kernel<T, R, 8>;
+        case 16: return smooth_colour_kernel<T, R, 16>;
+        default: return nullptr;
+    }
+}
+template <class T, int R>
+ResidualFn<T> residual_fn(int tpr) {
+    switch (tpr) {
+        case 4: return residual_kernel<T, R, 4>;
+        case 8: return residual_kernel<T, R, 8>;
+        case 16: return residual_kernel<T, R, 16>;
+        default: return nullptr;
+    }
 }
 
 template <class T>
-void launch_residual(const DevLevel &L, const T *A, const T *b, const T *x, T *r, int R, cudaStream_t s, int nrows) {
+void launch_smooth_colour(const DevLevel &L, int colour, const T *A, const T *dinv, const T *b, T *x, int R,
+                          cudaStream_t s, Chain *ch) {
+    const int r0 = L.cs[colour], r1 = L.cs[colour + 1];
+    if (r1 <= r0) return;
+    const LaunchShape &sh = L.shape[sizeof(T) == 8][kShapeSmooth];
+    const unsigned blocks = (unsigned)(((int64_t)(r1 - r0) * sh.tpr + sh.tpb - 1) / sh.tpb);
+    const SmoothFn<T> k = R == 1 ? smooth_fn<T, 1>(sh.tpr) : R == 2 ? smooth_fn<T, 2>(sh.tpr) : smooth_fn<T, 4>(sh.tpr);
+    klaunch(k, blocks, (unsigned)sh.tpb, 0, s, ch, r0, r1, L.rp, L.ci, A, dinv, b, x);
+}
+
+template <class T>
+void launch_residual(const DevLevel &L, const T *A, const T *b, const T *x, T *r, int R, cudaStream_t s, int nrows,
+                     Chain *ch) {
     const int n = nrows < 0 ? L.n : nrows;
     if (n == 0) return;
-    const int threads = 256;
-    const unsigned blocks = (unsigned)(((int64_t)n * kRowGroup + threads - 1) / threads);
-    if (R == 1) residual_kernel<T, 1, kRowGroup><<<blocks, threads, 0, s>>>(n, L.rp, L.ci, A, b, x, r);
-    else if (R == 2) residual_kernel<T, 2, kRowGroup><<<blocks, threads, 0, s>>>(n, L.rp, L.ci, A, b, x, r);
-    else residual_kernel<T, 4, kRowGroup><<<blocks, threads, 0, s>>>(n, L.rp, L.ci, A, b, x, r);
+    const LaunchShape &sh = L.shape[sizeof(T) == 8][kShapeResidual];
+    const unsigned blocks = (unsigned)(((int64_t)n * sh.tpr + sh.tpb - 1) / sh.tpb);
+    const ResidualFn<T> k =
+        R == 1 ? residual_fn<T, 1>(sh.tpr) : R == 2 ? residual_fn<T, 2>(sh.tpr) : residual_fn<T, 4>(sh.tpr);
+    klaunch(k, blocks, (unsigned)sh.tpb, 0, s, ch, n, L.rp, L.ci, A, b, x, r);
 }
 
 template <class T>
@@ -144,35 +197,43 @@ void launch_jacobi_update(const DevLevel &L, const T *dinv, const T *r, T *x, T 
     jacobi_update_kernel<T><<<(unsigned)((m + 255) / 256), 256, 0, s>>>(L.ns, R, dinv, r, x, omega);
 }
 
-// b_c[J] = sum over fine children i of J of r_f[i] / #parents(i)
+// b_c[J] = sum over fine children i of J of r_f[i] / #parents(i); x_c[J] = 0 when x_c is given
 template <class T, int R>
 __global__ void restrict_kernel(int nc, const int *__restrict__ crp, const uint32_t *__restrict__ cch,
-                                const T *__restrict__ rf, T *__restrict__ bc) {
+                                const T *__restrict__ rf, T *__restrict__ bc, T *__restrict__ xc) {
     const int J = blockIdx.x * blockDim.x + threadIdx.x;
-    if (J >= nc) return;
+    const bool active = J < nc;
+    int k0 = 0, k1 = 0;
+    if (active) { k0 = __ldg(crp + J); k1 = __ldg(crp + J + 1); }
+    grid_dep_wait();
+    grid_dep_launch();
+    if (!active) return;
     T acc[R];
 #pragma unroll
     for (int r = 0; r < R; r++) acc[r] = T(0);
-    for (int k = crp[J]; k < crp[J + 1]; k++) {
+    for (int k = k0; k < k1; k++) {
         const uint32_t e = __ldg(cch + k);
         const uint32_t i = e & kPackMask;
         const T w = T(1) / T(1u << (e >> kPackShift));
         T v[R];
-        load_vec<T, R>(rf + (size_t)i * R, v);
+        load_x<T, R>(rf + (size_t)i * R, v);
 #pragma unroll
         for (int r = 0; r < R; r++) acc[r] = fma(w, v[r], acc[r]);
     }
 #pragma unroll
     for (int r = 0; r < R; r++) bc[(size_t)J * R + r] = acc[r];
+    if (xc) {
+#pragma unroll
+        for (int r = 0; r < R; r++) xc[(size_t)J * R + r] = T(0);
+    }
 }
 
 template <class T>
-void launch_restrict(const DevLevel &Lc, const T *rf, T *bc, int R, cudaStream_t s) {
+void launch_restrict(const DevLevel &Lc, const T *rf, T *bc, int R, cudaStream_t s, T *xc, Chain *ch) {
     if (Lc.n == 0) return;
     const unsigned blocks = (unsigned)((Lc.n + 255) / 256);
-    if (R == 1) restrict_kernel<T, 1><<<blocks, 256, 0, s>>>(Lc.n, Lc.crp, Lc.cch, rf, bc);
-    else if (R == 2) restrict_kernel<T, 2><<<blocks, 256, 0, s>>>(Lc.n, Lc.crp, Lc.cch, rf, bc);
-    else restrict_kernel<T, 4><<<blocks, 256, 0, s>>>(Lc.n, Lc.crp, Lc.cch, rf, bc);
+    auto k = R == 1 ? restrict_kernel<T, 1> : R == 2 ? restrict_kernel<T, 2> : restrict_kernel<T, 4>;
+    klaunch(k, blocks, 256u, 0, s, ch, Lc.n, Lc.crp, Lc.cch, rf, bc, xc);
 }
 
 // x_f[i] += (sum of parent values) / #parents(i)
@@ -180,17 +241,27 @@ template <class T, int R>
 __global__ void prolong_add_kernel(int nf, const int *__restrict__ par, const int8_t *__restrict__ npl2,
                                    const T *__restrict__ xc, T *__restrict__ xf) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nf) return;
-    const int np = 1 << npl2[i];
+    const bool active = i < nf;
+    int np = 0, p[8];
+    if (active) {
+        np = 1 << __ldg(npl2 + i);
+#pragma unroll
+        for (int q = 0; q < 8; q++) p[q] = q < np ? __ldg(par + 8 * (size_t)i + q) : 0;
+    }
+    grid_dep_wait();
+    grid_dep_launch();
+    if (!active) return;
     T acc[R];
 #pragma unroll
     for (int r = 0; r < R; r++) acc[r] = T(0);
-    for (int q = 0; q < np; q++) {
-        const int p = __ldg(par + 8 * (size_t)i + q);
-        T v[R];
-        load_vec<T, R>(xc + (size_t)p * R, v);
 #pragma unroll
-        for (int r = 0; r < R; r++) acc[r] += v[r];
+    for (int q = 0; q < 8; q++) {
+        if (q < np) {
+            T v[R];
+            load_x<T, R>(xc + (size_t)p[q] * R, v);
+#pragma unroll
+            for (int r = 0; r < R; r++) acc[r] += v[r];
+        }
     }
     const T w = T(1) / T(np);
 #pragma unroll
@@ -198,12 +269,11 @@ __global__ void prolong_add_kernel(int nf, const int *__restrict__ par, const in
 }
 
 template <class T>
-void launch_prolong_add(const DevLevel &Lf, const T *xc, T *xf, int R, cudaStream_t s) {
+void launch_prolong_add(const DevLevel &Lf, const T *xc, T *xf, int R, cudaStream_t s, Chain *ch) {
     if (Lf.ns == 0) return;   // only smoothed rows have a coarser level
     const unsigned blocks = (unsigned)((Lf.ns + 255) / 256);
-    if (R == 1) prolong_add_kernel<T, 1><<<blocks, 256, 0, s>>>(Lf.ns, Lf.par, Lf.npl2, xc, xf);
-    else if (R == 2) prolong_add_kernel<T, 2><<<blocks, 256, 0, s>>>(Lf.ns, Lf.par, Lf.npl2, xc, xf);
-    else prolong_add_kernel<T, 4><<<blocks, 256, 0, s>>>(Lf.ns, Lf.par, Lf.npl2, xc, xf);
+    auto k = R == 1 ? prolong_add_kernel<T, 1> : R == 2 ? prolong_add_kernel<T, 2> : prolong_add_kernel<T, 4>;
+    klaunch(k, blocks, 256u, 0, s, ch, Lf.ns, Lf.par, Lf.npl2, xc, xf);
 }
 
 // x = inv * b on every coarsest block of a level (one block per mesh), one warp per row
@@ -214,6 +284,8 @@ __global__ void coarse_apply_kernel(const int *__restrict__ cblk, const T *__res
     const int row0 = cb[2], n = cb[3];
     const T *M = inv + cb[4];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    grid_dep_wait();
+    grid_dep_launch();
     for (int row = warp; row < n; row += nw) {
         T acc[R];
 #pragma unroll
@@ -235,12 +307,12 @@ __global__ void coarse_apply_kernel(const int *__restrict__ cblk, const T *__res
 }
 
 template <class T>
-void launch_coarse_apply(const Ctx &c, const DevLevel &L, const T *inv, const T *b, T *x, int R, cudaStream_t s) {
+void launch_coarse_apply(const Ctx &c, const DevLevel &L, const T *inv, const T *b, T *x, int R, cudaStream_t s,
+                         Chain *ch) {
     if (L.ncb == 0) return;
     const int *cb = c.cblk + 5 * L.cb0;
-    if (R == 1) coarse_apply_kernel<T, 1><<<L.ncb, 256, 0, s>>>(cb, inv, b, x);
-    else if (R == 2) coarse_apply_kernel<T, 2><<<L.ncb, 256, 0, s>>>(cb, inv, b, x);
-    else coarse_apply_kernel<T, 4><<<L.ncb, 256, 0, s>>>(cb, inv, b, x);
+    auto k = R == 1 ? coarse_apply_kernel<T, 1> : R == 2 ? coarse_apply_kernel<T, 2> : coarse_apply_kernel<T, 4>;
+    klaunch(k, (unsigned)L.ncb, 256u, 0, s, ch, cb, inv, b, x);
 }
 
 // ---- coarsest-level dense FP64 Cholesky of A + eps Id, eps = 1e-12 mean diag ----
@@ -340,6 +412,8 @@ void launch_coarse_factor(const Ctx &c, const int *const *rps, const int *const 
 template <int R>
 __global__ void __launch_bounds__(256) norm_partial_kernel(const double *__restrict__ v, int n, double *__restrict__ part) {
     __shared__ double sh[256][R];
+    grid_dep_wait();
+    grid_dep_launch();
     double acc[R];
 #pragma unroll
     for (int r = 0; r < R; r++) acc[r] = 0.0;
@@ -361,6 +435,8 @@ __global__ void __launch_bounds__(256) norm_partial_kernel(const double *__restr
 __global__ void __launch_bounds__(256) norm_final_kernel(const double *__restrict__ part, int nblocks, int R,
                                                          double *__restrict__ out) {
     __shared__ double sh[256][4];
+    grid_dep_wait();
+    grid_dep_launch();
     for (int r = 0; r < 4; r++) sh[threadIdx.x][r] = 0.0;
     for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
         for (int r = 0; r < R; r++) sh[threadIdx.x][r] += part[b * 4 + r];
@@ -373,11 +449,10 @@ __global__ void __launch_bounds__(256) norm_final_kernel(const double *__restric
     if (threadIdx.x < 4) out[threadIdx.x] = threadIdx.x < R ? sh[0][threadIdx.x] : 0.0;
 }
 
-void launch_norms(const double *v, int n, int R, double *part, double *out, cudaStream_t s) {
-    if (R == 1) norm_partial_kernel<1><<<kNormBlocks, 256, 0, s>>>(v, n, part);
-    else if (R == 2) norm_partial_kernel<2><<<kNormBlocks, 256, 0, s>>>(v, n, part);
-    else norm_partial_kernel<4><<<kNormBlocks, 256, 0, s>>>(v, n, part);
-    norm_final_kernel<<<1, 256, 0, s>>>(part, kNormBlocks, R, out);
+void launch_norms(const double *v, int n, int R, double *part, double *out, cudaStream_t s, Chain *ch) {
+    auto k = R == 1 ? norm_partial_kernel<1> : R == 2 ? norm_partial_kernel<2> : norm_partial_kernel<4>;
+    klaunch(k, (unsigned)kNormBlocks, 256u, 0, s, ch, v, n, part);
+    klaunch(norm_final_kernel, 1u, 256u, 0, s, ch, (const double *)part, (int)kNormBlocks, R, out);
 }
 
 // ---- layout and elementwise kernels ----
@@ -400,12 +475,20 @@ __global__ void unpack_kernel(const double *__restrict__ v, int n, int nrhs, int
     const int64_t row = perm ? perm[i] : i;
     u[q] = v[row * R + r];
 }
-__global__ void to_float_kernel(const double *__restrict__ a, float *__restrict__ b, int64_t n) {
+__global__ void to_float_kernel(const double *__restrict__ a, float *__restrict__ b, int64_t n,
+                                float *__restrict__ zero) {
     const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (q < n) b[q] = (float)a[q];
+    grid_dep_wait();
+    grid_dep_launch();
+    if (q < n) {
+        b[q] = (float)a[q];
+        if (zero) zero[q] = 0.f;
+    }
 }
 __global__ void add_float_kernel(double *__restrict__ x, const float *__restrict__ e, int64_t n) {
     const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    grid_dep_wait();
+    grid_dep_launch();
     if (q < n) x[q] += (double)e[q];
 }
 __global__ void add_double_kernel(double *__restrict__ x, const double *__restrict__ e, int64_t n) {
@@ -421,11 +504,11 @@ void launch_unpack(const double *v, int n, int nrhs, int R, double *user, cudaSt
     const int64_t m = (int64_t)n * nrhs;
     if (m) unpack_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(v, n, nrhs, R, perm, user);
 }
-void launch_to_float(const double *a, float *b, int64_t n, cudaStream_t s) {
-    if (n) to_float_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, b, n);
+void launch_to_float(const double *a, float *b, int64_t n, cudaStream_t s, float *zero, Chain *ch) {
+    if (n) klaunch(to_float_kernel, (unsigned)((n + 255) / 256), 256u, 0, s, ch, a, b, n, zero);
 }
-void launch_add_float(double *x, const float *e, int64_t n, cudaStream_t s) {
-    if (n) add_float_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, e, n);
+void launch_add_float(double *x, const float *e, int64_t n, cudaStream_t s, Chain *ch) {
+    if (n) klaunch(add_float_kernel, (unsigned)((n + 255) / 256), 256u, 0, s, ch, x, e, n);
 }
 void launch_add_double(double *x, const double *e, int64_t n, cudaStream_t s) {
     if (n) add_double_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, e, n);
@@ -434,12 +517,14 @@ void launch_add_double(double *x, const double *e, int64_t n, cudaStream_t s) {
 // explicit instantiations
 #define LBMG_INST(T)                                                                                           \
     template void launch_smooth_colour<T>(const DevLevel &, int, const T *, const T *, const T *, T *, int,   \
-                                          cudaStream_t);                                                       \
-    template void launch_residual<T>(const DevLevel &, const T *, const T *, const T *, T *, int, cudaStream_t, int); \
+                                          cudaStream_t, Chain *);                                              \
+    template void launch_residual<T>(const DevLevel &, const T *, const T *, const T *, T *, int, cudaStream_t, int, \
+                                     Chain *);                                                                 \
     template void launch_jacobi_update<T>(const DevLevel &, const T *, const T *, T *, T, int, cudaStream_t);   \
-    template void launch_restrict<T>(const DevLevel &, const T *, T *, int, cudaStream_t);                     \
-    template void launch_prolong_add<T>(const DevLevel &, const T *, T *, int, cudaStream_t);                  \
-    template void launch_coarse_apply<T>(const Ctx &, const DevLevel &, const T *, const T *, T *, int, cudaStream_t);
+    template void launch_restrict<T>(const DevLevel &, const T *, T *, int, cudaStream_t, T *, Chain *);       \
+    template void launch_prolong_add<T>(const DevLevel &, const T *, T *, int, cudaStream_t, Chain *);         \
+    template void launch_coarse_apply<T>(const Ctx &, const DevLevel &, const T *, const T *, T *, int, cudaStream_t, \
+                                         Chain *);
 LBMG_INST(float)
 LBMG_INST(double)
 

@@ -65,3 +65,24 @@ def test_null_handle_rejected():
     assert lib.lbmg_assemble(None, 1.0, None) == 1
     assert lib.lbmg_solve(None, None, None, 1, 1e-6, 10, 0, None, None) == 1
     assert lib.lbmg_levels(None, None, None) == 1
+
+
+def test_tune_cache_file_round_trip_and_bad_lines(tmp_path):
+    """The tuning cache is plain text: valid lines load, malformed ones are reported."""
+    good = tmp_path / "tune.txt"
+    good.write_text("# device fp64 kind lanes rows nnz threads_per_row threads_per_block\n"
+                    "Test_GPU 0 0 4 1000 18000 4 128\n"
+                    "Test_GPU 1 1 1 1000 18000 16 512\n")
+    L.lbmg_tune_cache_load(str(good))
+    out = tmp_path / "saved.txt"
+    L.lbmg_tune_cache_save(str(out))
+    lines = [ln.split() for ln in out.read_text().splitlines() if not ln.startswith("#")]
+    assert ["Test_GPU", "0", "0", "4", "1000", "18000", "4", "128"] in lines
+    assert ["Test_GPU", "1", "1", "1", "1000", "18000", "16", "512"] in lines
+    bad = tmp_path / "bad.txt"
+    bad.write_text("Test_GPU 0 0 4 1000 18000 5 128\nnot a line\n")   # 5 threads per row is not a shape
+    with pytest.raises(L.LbmgError) as e:
+        L.lbmg_tune_cache_load(str(bad))
+    assert e.value.code == 1
+    with pytest.raises(L.LbmgError):
+        L.lbmg_tune_cache_load(str(tmp_path / "missing.txt"))
