@@ -188,6 +188,8 @@ def main():
     ap.add_argument("--only-timed", action="store_true", help="stop after the timed steps (profiling runs)")
     ap.add_argument("--no-pdl", action="store_true", help="plain stream order between the cycle's kernels")
     ap.add_argument("--no-tune", action="store_true", help="default launch shapes (no autotuning at setup)")
+    ap.add_argument("--tune-cache", default=None,
+                    help="tuning cache file: loaded before tuning (matching levels are not timed), saved after")
     ap.add_argument("--max-cycles", type=int, default=2000,
                     help="cap on V-cycles per solve (profiling runs cap it to keep launch lists short)")
     args = ap.parse_args()
@@ -215,8 +217,12 @@ def main():
     # setup, like the hierarchy build: launch shapes tuned once per mesh on its own matrices
     L.lbmg_assemble(h, t)
     if not args.no_tune:
+        if args.tune_cache and os.path.exists(args.tune_cache):
+            L.lbmg_tune_cache_load(args.tune_cache)
         for prec in (L.LBMG_MIXED, L.LBMG_FP64):
             L.lbmg_autotune(h, nrhs, prec, reps=4)
+        if args.tune_cache:
+            L.lbmg_tune_cache_save(args.tune_cache)
     shapes = {str(d): L.lbmg_launch_shape(h, d, L.LBMG_MIXED) for d in range(d0 + 1, D + 1)}
     f_dev = torch.tensor(f, dtype=torch.float64, device=dev)
     rhs = torch.zeros((n, nrhs), dtype=torch.float64, device=dev)
@@ -338,7 +344,10 @@ def main():
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
             tr = json.load(fh).get(key)
-            if tr:
+            # counters apply only to the kernel instance they were taken from
+            same = args.persistent or (tr and [tr.get("threads_per_row"), tr.get("threads_per_block")] ==
+                                       list(shapes[str(D)][0]))
+            if tr and same:
                 traffic = tr["bytes_per_launch"]
     except Exception:
         pass
