@@ -338,6 +338,15 @@ int upload_hierarchy(lbmg_handle h) {
     }
     LBMG_TRY(h->upload(&c.poly, H.frag_poly));
     LBMG_TRY(h->upload(&c.pstart, H.frag_pstart));
+    {
+        // fragments by vertex count, so that the threads of a warp integrate equally many sub-triangles
+        std::vector<int32_t> order(c.nfrag), cnt(64, 0);
+        auto nv = [&](int f) { return std::min(63, (int)(H.frag_pstart[f + 1] - H.frag_pstart[f])); };
+        for (int f = 0; f < c.nfrag; f++) cnt[nv(f)]++;
+        for (int k = 1; k < 64; k++) cnt[k] += cnt[k - 1];
+        for (int f = c.nfrag - 1; f >= 0; f--) order[--cnt[nv(f)]] = f;
+        LBMG_TRY(h->upload(&c.forder, order));
+    }
     LBMG_TRY(h->upload(&c.ftri, H.frag_tri));
     LBMG_TRY(h->upload(&c.fvox, H.frag_vox));
     LBMG_TRY(h->upload(&c.fdof, H.frag_dof));

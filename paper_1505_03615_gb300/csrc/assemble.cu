@@ -1,20 +1,28 @@
 // assemble.cu -- Galerkin matrices and right-hand sides of the split B-spline
 // hierarchy (Chuang & Kazhdan, Eq. 2 and Sections 5.1-5.3).
 //
-// Finest level: one warp per fragment (a triangle piece inside one voxel)
+// Finest level: one thread per fragment (a triangle piece inside one voxel)
 // integrates the 27 moments int u^i v^j w^k dA (i,j,k <= 2, local voxel
 // coordinates) with a collapsed Gauss-Legendre rule on each sub-triangle of the
 // piece's fan (exact to degree 6).  Every product of two trilinear hats, and of
 // their tangential gradients, is a combination of those moments, so the 36 + 36
-// local entries follow from a separable 3-stage contraction.  A second kernel
-// sums each stored entry's contributions through a precomputed list (no
-// atomics).  Coarser levels are the Galerkin products P^T A P of Eq. 4's
-// prolongation, summed the same way.
+// local entries follow from a separable contraction of the moments, one axis at a
+// time, pruned to the 90 integrals the entries use.  GB300 runs FP64 at a small
+// fraction of its FP32 rate, so this kernel is bound by the number of FP64
+// instructions: a thread per fragment needs no cross-lane reduction and no idle
+// lanes, and fragments are taken in order of vertex count so that a warp's
+// threads run the same number of sub-triangles.  A second kernel sums each
+// stored entry's contributions through a precomputed list (no atomics).  Coarser
+// levels are the Galerkin products P^T A P of Eq. 4's prolongation, summed the
+// same way.
 #include "lbmg_internal.h"
 
 namespace lbmg {
 
 __constant__ double c_glx[kNQ], c_glw[kNQ];
+// the collapsed rule on the reference triangle {xi, eta >= 0, xi + eta <= 1}:
+// point q = (xi, eta) and weight, kNQ * kNQ points
+__constant__ double c_qxi[kNQ * kNQ], c_qeta[kNQ * kNQ], c_qw[kNQ * kNQ];
 // per-axis factor types over (1, t, t^2):
 // 0: 1, 1: 1-t, 2: t, 3: (1-t)^2, 4: t(1-t), 5: t^2
 __constant__ double c_type[6][3] = {{1, 0, 0}, {1, -1, 0}, {0, 1, 0}, {1, -2, 1}, {0, 1, -1}, {0, 0, 1}};
@@ -49,128 +57,148 @@ static void ensure_gl() {
     gauss_legendre01(kNQ, x, w);
     cudaMemcpyToSymbol(c_glx, x, sizeof x);
     cudaMemcpyToSymbol(c_glw, w, sizeof w);
+    double qx[kNQ * kNQ], qe[kNQ * kNQ], qw[kNQ * kNQ];
+    for (int a = 0; a < kNQ; a++)
+        for (int b = 0; b < kNQ; b++) {
+            qx[a * kNQ + b] = x[a];
+            qe[a * kNQ + b] = x[b] * (1.0 - x[a]);
+            qw[a * kNQ + b] = w[a] * w[b] * (1.0 - x[a]);
+        }
+    cudaMemcpyToSymbol(c_qxi, qx, sizeof qx);
+    cudaMemcpyToSymbol(c_qeta, qe, sizeof qe);
+    cudaMemcpyToSymbol(c_qw, qw, sizeof qw);
     g_gl_ready = true;
 }
 
-constexpr int kWarpsPerBlock = 8;
+// Integral of the per-axis factor type ty (the table c_type) from the integrals
+// (m0, m1, m2) of 1, t, t^2 along that axis.  ty is a compile-time constant at
+// every call, so only the needed differences are formed, and identical ones are
+// shared between calls.
+__device__ __forceinline__ double ftype(int ty, double m0, double m1, double m2) {
+    switch (ty) {
+        case 0: return m0;                        // 1
+        case 1: return m0 - m1;                   // 1 - t
+        case 2: return m1;                        // t
+        case 3: return fma(-2.0, m1, m0) + m2;    // (1 - t)^2
+        case 4: return m1 - m2;                   // t (1 - t)
+        default: return m2;                       // t^2
+    }
+}
 
-// One warp per fragment.  Writes the 27 moments and the 36 (M, L) local pair entries.
-__global__ void __launch_bounds__(32 * kWarpsPerBlock)
-fragment_moments_kernel(int nfrag, const double *__restrict__ poly, const int *__restrict__ pstart,
-                        const int *__restrict__ ftri, const double *__restrict__ tnormal,
-                        const double *__restrict__ fscale, double *__restrict__ moments, double *__restrict__ stage) {
-    __shared__ double sh[kWarpsPerBlock][27 + 54 + 108 + 216];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int f = blockIdx.x * kWarpsPerBlock + warp;
-    if (f >= nfrag) return;
-    double *sm = sh[warp], *h1 = sm + 27, *h2 = h1 + 54, *G = h2 + 108;
-    const int p0 = pstart[f], np = pstart[f + 1] - p0;
+// G(a, b, c) = integral of type_a(u) type_b(v) type_c(w) from the moments m[i][j][k]
+__device__ __forceinline__ double gz(const double (&m)[27], int i, int j, int c) {
+    return ftype(c, m[i * 9 + j * 3], m[i * 9 + j * 3 + 1], m[i * 9 + j * 3 + 2]);
+}
+__device__ __forceinline__ double gy(const double (&m)[27], int i, int b, int c) {
+    return ftype(b, gz(m, i, 0, c), gz(m, i, 1, c), gz(m, i, 2, c));
+}
+__device__ __forceinline__ double G3(const double (&m)[27], int a, int b, int c) {
+    return ftype(a, gy(m, 0, b, c), gy(m, 1, b, c), gy(m, 2, b, c));
+}
+
+constexpr int kMomThreads = 128;
+
+// One thread per fragment (taken in the order forder).  Writes the 27 moments and
+// the 36 (M, L) local pair entries, pairs (a, b), a <= b, in upper-triangular order.
+__global__ void __launch_bounds__(kMomThreads)
+fragment_moments_kernel(int nfrag, const int *__restrict__ forder, const double *__restrict__ poly,
+                        const int *__restrict__ pstart, const int *__restrict__ ftri,
+                        const double *__restrict__ tnormal, const double *__restrict__ fscale,
+                        double *__restrict__ moments, double *__restrict__ stage) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nfrag) return;
+    const int f = __ldg(forder + t);
+    const int p0 = __ldg(pstart + f), np = __ldg(pstart + f + 1) - p0;
     const double *P = poly + 3 * (size_t)p0;
-    const int npts = (np - 2) * kNQ * kNQ;
+    const double *nrm = tnormal + 3 * (size_t)__ldg(ftri + f);
+    const double n0 = __ldg(nrm), n1 = __ldg(nrm + 1), n2 = __ldg(nrm + 2);
+    const double a0 = __ldg(P), a1 = __ldg(P + 1), a2 = __ldg(P + 2);
     double m[27];
 #pragma unroll
     for (int q = 0; q < 27; q++) m[q] = 0.0;
-    for (int q = lane; q < npts; q += 32) {
-        const int sub = q / (kNQ * kNQ), qa = (q / kNQ) % kNQ, qb = q % kNQ;
-        const double *A = P, *B = P + 3 * (sub + 1), *C = P + 3 * (sub + 2);
-        double e1[3], e2[3];
+    double b0 = __ldg(P + 3), b1 = __ldg(P + 4), b2 = __ldg(P + 5);
+    for (int sub = 2; sub < np; sub++) {
+        const double c0 = __ldg(P + 3 * sub), c1 = __ldg(P + 3 * sub + 1), c2 = __ldg(P + 3 * sub + 2);
+        const double e10 = b0 - a0, e11 = b1 - a1, e12 = b2 - a2;
+        const double e20 = c0 - a0, e21 = c1 - a1, e22 = c2 - a2;
+        // twice the sub-triangle's area: the piece lies in its triangle's plane,
+        // so the edge cross product is parallel to the unit normal
+        const double jac = fabs(fma(fma(e11, e22, -e12 * e21), n0,
+                                    fma(fma(e12, e20, -e10 * e22), n1, fma(e10, e21, -e11 * e20) * n2)));
 #pragma unroll
-        for (int k = 0; k < 3; k++) { e1[k] = B[k] - A[k]; e2[k] = C[k] - A[k]; }
-        double cx = e1[1] * e2[2] - e1[2] * e2[1], cy = e1[2] * e2[0] - e1[0] * e2[2], cz = e1[0] * e2[1] - e1[1] * e2[0];
-        double jac = sqrt(cx * cx + cy * cy + cz * cz);
-        double xa = c_glx[qa];
-        double xi = xa, eta = c_glx[qb] * (1.0 - xa);
-        double w = c_glw[qa] * c_glw[qb] * (1.0 - xa) * jac;
-        double u = A[0] + xi * e1[0] + eta * e2[0];
-        double v = A[1] + xi * e1[1] + eta * e2[1];
-        double z = A[2] + xi * e1[2] + eta * e2[2];
-        double pu[3] = {w, w * u, w * u * u}, pv[3] = {1.0, v, v * v}, pz[3] = {1.0, z, z * z};
+        for (int q = 0; q < kNQ * kNQ; q++) {
+            const double xi = c_qxi[q], eta = c_qeta[q];
+            const double u = fma(eta, e20, fma(xi, e10, a0));
+            const double v = fma(eta, e21, fma(xi, e11, a1));
+            const double z = fma(eta, e22, fma(xi, e12, a2));
+            const double w = c_qw[q] * jac;
+            const double wu = w * u;
+            const double pu[3] = {w, wu, wu * u};
+            const double v2 = v * v, z2 = z * z;
 #pragma unroll
-        for (int i = 0; i < 3; i++)
+            for (int i = 0; i < 3; i++) {
+                const double s[3] = {pu[i], pu[i] * v, pu[i] * v2};
 #pragma unroll
-            for (int j = 0; j < 3; j++) {
-                double uv = pu[i] * pv[j];
-#pragma unroll
-                for (int k = 0; k < 3; k++) m[i * 9 + j * 3 + k] = fma(uv, pz[k], m[i * 9 + j * 3 + k]);
-            }
-    }
-#pragma unroll
-    for (int q = 0; q < 27; q++) {
-        double v = m[q];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        m[q] = v;
-    }
-    if (lane < 27) {
-        double mv = 0;
-#pragma unroll
-        for (int q = 0; q < 27; q++) if (q == lane) mv = m[q];
-        sm[lane] = mv;
-        moments[27 * (size_t)f + lane] = mv;
-    }
-    __syncwarp();
-    // contraction along z: h1[(i*3+j)*6+tz]
-    for (int q = lane; q < 54; q += 32) {
-        const int ij = q / 6, tz = q % 6;
-        h1[q] = c_type[tz][0] * sm[ij * 3] + c_type[tz][1] * sm[ij * 3 + 1] + c_type[tz][2] * sm[ij * 3 + 2];
-    }
-    __syncwarp();
-    // along y: h2[(i*6+ty)*6+tz]
-    for (int q = lane; q < 108; q += 32) {
-        const int i = q / 36, ty = (q / 6) % 6, tz = q % 6;
-        h2[q] = c_type[ty][0] * h1[(i * 3 + 0) * 6 + tz] + c_type[ty][1] * h1[(i * 3 + 1) * 6 + tz] +
-                c_type[ty][2] * h1[(i * 3 + 2) * 6 + tz];
-    }
-    __syncwarp();
-    // along x: G[(tx*6+ty)*6+tz]
-    for (int q = lane; q < 216; q += 32) {
-        const int tx = q / 36, yz = q % 36;
-        G[q] = c_type[tx][0] * h2[0 * 36 + yz] + c_type[tx][1] * h2[1 * 36 + yz] + c_type[tx][2] * h2[2 * 36 + yz];
-    }
-    __syncwarp();
-    const double *n = tnormal + 3 * (size_t)ftri[f];
-    const double nn[3] = {n[0], n[1], n[2]};
-    for (int p = lane; p < 36; p += 32) {
-        // pair (a, b), a <= b, in upper-triangular order
-        int a = 0, rem = p;
-        while (rem >= 8 - a) { rem -= 8 - a; a++; }
-        const int b = a + rem;
-        int ab[3], bb[3];
-#pragma unroll
-        for (int k = 0; k < 3; k++) { ab[k] = (a >> k) & 1; bb[k] = (b >> k) & 1; }
-        auto Pt = [&](int k) { return 3 + ab[k] + bb[k]; };           // phi_a phi_b along axis k
-        auto gidx = [](int tx, int ty, int tz) { return (tx * 6 + ty) * 6 + tz; };
-        const double Mab = G[gidx(Pt(0), Pt(1), Pt(2))];
-        double Lab = 0.0;
-#pragma unroll
-        for (int pp = 0; pp < 3; pp++)
-#pragma unroll
-            for (int qq = 0; qq < 3; qq++) {
-                const double Q = (pp == qq ? 1.0 : 0.0) - nn[pp] * nn[qq];
-                int t[3];
-                double sgn;
-                if (pp == qq) {
-                    sgn = (ab[pp] ? 1.0 : -1.0) * (bb[pp] ? 1.0 : -1.0);
-#pragma unroll
-                    for (int k = 0; k < 3; k++) t[k] = (k == pp) ? 0 : Pt(k);
-                } else {
-                    sgn = (ab[pp] ? 1.0 : -1.0) * (bb[qq] ? 1.0 : -1.0);
-#pragma unroll
-                    for (int k = 0; k < 3; k++)
-                        t[k] = (k == pp) ? 1 + bb[k] : (k == qq) ? 1 + ab[k] : Pt(k);
+                for (int j = 0; j < 3; j++) {
+                    m[i * 9 + j * 3] += s[j];
+                    m[i * 9 + j * 3 + 1] = fma(s[j], z, m[i * 9 + j * 3 + 1]);
+                    m[i * 9 + j * 3 + 2] = fma(s[j], z2, m[i * 9 + j * 3 + 2]);
                 }
-                Lab = fma(Q * sgn, G[gidx(t[0], t[1], t[2])], Lab);
             }
-        stage[2 * (36 * (size_t)f + p)] = Mab * fscale[f];
-        stage[2 * (36 * (size_t)f + p) + 1] = Lab;
+        }
+        b0 = c0; b1 = c1; b2 = c2;
+    }
+    double *mo = moments + 27 * (size_t)f;
+#pragma unroll
+    for (int q = 0; q < 27; q++) mo[q] = m[q];
+    // tangential projector I - n n^T
+    const double nv[3] = {n0, n1, n2};
+    const double fs = __ldg(fscale + f);
+    double2 *st = reinterpret_cast<double2 *>(stage) + 36 * (size_t)f;
+    int p = 0;
+#pragma unroll
+    for (int a = 0; a < 8; a++) {
+#pragma unroll
+        for (int b = a; b < 8; b++) {
+            const int ab[3] = {a & 1, (a >> 1) & 1, (a >> 2) & 1};
+            const int bb[3] = {b & 1, (b >> 1) & 1, (b >> 2) & 1};
+            int pt[3];
+#pragma unroll
+            for (int k = 0; k < 3; k++) pt[k] = 3 + ab[k] + bb[k];     // phi_a phi_b along axis k
+            const double Mab = G3(m, pt[0], pt[1], pt[2]) * fs;
+            double Lab = 0.0;
+#pragma unroll
+            for (int pp = 0; pp < 3; pp++)
+#pragma unroll
+                for (int qq = 0; qq < 3; qq++) {
+                    const double Q = (pp == qq ? 1.0 : 0.0) - nv[pp] * nv[qq];
+                    int ty[3];
+                    double sgn;
+                    if (pp == qq) {
+                        // d_p phi_a d_p phi_b: constant along p, products along the others
+                        sgn = (ab[pp] ? 1.0 : -1.0) * (bb[pp] ? 1.0 : -1.0);
+#pragma unroll
+                        for (int k = 0; k < 3; k++) ty[k] = k == pp ? 0 : pt[k];
+                    } else {
+                        // d_p phi_a d_q phi_b: phi_b along p, phi_a along q
+                        sgn = (ab[pp] ? 1.0 : -1.0) * (bb[qq] ? 1.0 : -1.0);
+#pragma unroll
+                        for (int k = 0; k < 3; k++) ty[k] = k == pp ? 1 + bb[k] : (k == qq ? 1 + ab[k] : pt[k]);
+                    }
+                    Lab = fma(Q * sgn, G3(m, ty[0], ty[1], ty[2]), Lab);
+                }
+            st[p] = make_double2(Mab, Lab);
+            p++;
+        }
     }
 }
 
 void launch_fragment_moments(const Ctx &c, cudaStream_t s) {
     ensure_gl();
-    const int blocks = (c.nfrag + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    fragment_moments_kernel<<<blocks, 32 * kWarpsPerBlock, 0, s>>>(
-        c.nfrag, c.poly, c.pstart, c.ftri, c.tnormal, c.frag_scale, c.moments, c.stage);
+    if (c.nfrag == 0) return;
+    const int blocks = (c.nfrag + kMomThreads - 1) / kMomThreads;
+    fragment_moments_kernel<<<blocks, kMomThreads, 0, s>>>(c.nfrag, c.forder, c.poly, c.pstart, c.ftri, c.tnormal,
+                                                           c.frag_scale, c.moments, c.stage);
 }
 
 // finest level: sum the local-pair contributions of every stored entry
@@ -261,43 +289,30 @@ __global__ void fragment_rhs_kernel(int nfrag, int nrhs, const double *__restric
     const double g12 = e1[0] * e2[0] + e1[1] * e2[1] + e1[2] * e2[2];
     const double g22 = e2[0] * e2[0] + e2[1] * e2[1] + e2[2] * e2[2];
     const double det = g11 * g22 - g12 * g12;
-    const double *m = moments + 27 * (size_t)f;
-    // per corner: int b_a and int u_k b_a
+    double m[27];
+#pragma unroll
+    for (int q = 0; q < 27; q++) m[q] = __ldg(moments + 27 * (size_t)f + q);
+    // per corner a: int b_a and int u_k b_a (types 1 + bit: phi along an axis, 4 + bit: t phi)
     double Ib[8], Iu[8][3];
+#pragma unroll
     for (int a = 0; a < 8; a++) {
-        const int bits[3] = {a & 1, (a >> 1) & 1, (a >> 2) & 1};
-        int ts[3], tu[3];
-        for (int k = 0; k < 3; k++) { ts[k] = 1 + bits[k]; tu[k] = 4 + bits[k]; }   // phi and t*phi
-        for (int which = 0; which < 4; which++) {
-            int ty[3] = {ts[0], ts[1], ts[2]};
-            if (which > 0) ty[which - 1] = tu[which - 1];
-            double acc = 0.0;
-            for (int i = 0; i < 3; i++) {
-                const double ci = c_type[ty[0]][i];
-                if (ci == 0.0) continue;
-                for (int j = 0; j < 3; j++) {
-                    const double cj = c_type[ty[1]][j];
-                    if (cj == 0.0) continue;
-                    for (int k = 0; k < 3; k++) {
-                        const double ck = c_type[ty[2]][k];
-                        if (ck == 0.0) continue;
-                        acc = fma(ci * cj * ck, m[i * 9 + j * 3 + k], acc);
-                    }
-                }
-            }
-            if (which == 0) Ib[a] = acc; else Iu[a][which - 1] = acc;
-        }
+        const int b0 = a & 1, b1 = (a >> 1) & 1, b2 = (a >> 2) & 1;
+        Ib[a] = G3(m, 1 + b0, 1 + b1, 1 + b2);
+        Iu[a][0] = G3(m, 4 + b0, 1 + b1, 1 + b2);
+        Iu[a][1] = G3(m, 1 + b0, 4 + b1, 1 + b2);
+        Iu[a][2] = G3(m, 1 + b0, 1 + b1, 4 + b2);
     }
+    const double idet = 1.0 / det, fs = fscale[f];
     for (int r = 0; r < nrhs; r++) {
         const double fa = fv[(size_t)ia * nrhs + r], fb = fv[(size_t)ib * nrhs + r], fc = fv[(size_t)ic * nrhs + r];
         const double d1 = fb - fa, d2 = fc - fa;
-        const double al = (g22 * d1 - g12 * d2) / det, be = (g11 * d2 - g12 * d1) / det;
+        const double al = (g22 * d1 - g12 * d2) * idet, be = (g11 * d2 - g12 * d1) * idet;
         double g[3];
         for (int k = 0; k < 3; k++) g[k] = al * e1[k] + be * e2[k];     // tangential gradient of f
         const double beta0 = fa + g[0] * lo[0] + g[1] * lo[1] + g[2] * lo[2];
         for (int a = 0; a < 8; a++) {
             const double v = beta0 * Ib[a] + g[0] * Iu[a][0] + g[1] * Iu[a][1] + g[2] * Iu[a][2];
-            out[(8 * (size_t)f + a) * 4 + r] = v * fscale[f];
+            out[(8 * (size_t)f + a) * 4 + r] = v * fs;
         }
     }
 }

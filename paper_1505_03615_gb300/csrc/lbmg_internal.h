@@ -130,6 +130,7 @@ struct Ctx {
     DevLevel lev[kMaxDepth + 1];
     // finest-level geometry
     double *poly = nullptr;
+    int *forder = nullptr;       // [nfrag] fragments by vertex count (moment kernel order)
     int *pstart = nullptr, *ftri = nullptr, *fvox = nullptr, *fdof = nullptr;
     double *tnormal = nullptr, *Vg = nullptr;
     int *F = nullptr;
