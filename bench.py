@@ -188,6 +188,8 @@ def main():
     ap.add_argument("--only-timed", action="store_true", help="stop after the timed steps (profiling runs)")
     ap.add_argument("--no-pdl", action="store_true", help="plain stream order between the cycle's kernels")
     ap.add_argument("--no-tune", action="store_true", help="default launch shapes (no autotuning at setup)")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    help="named synthetic workload (meshgen.CONFIGS); the default is the metric's own configuration")
     ap.add_argument("--tune-cache", default=None,
                     help="tuning cache file: loaded before tuning (matching levels are not timed), saved after")
     ap.add_argument("--max-cycles", type=int, default=2000,
@@ -207,13 +209,15 @@ def main():
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    V, F, depth, t, f, tol, _ = meshgen.config_mesh(WORKLOAD)
+    workload = args.workload
+    V, F, depth, t, f, tol, _ = meshgen.config_mesh(workload)
+    f = f.reshape(V.shape[0], -1)
     nv = V.shape[0]
     h = L.lbmg_build_hierarchy(V, F, depth, persistent=int(args.persistent), use_graphs=int(not args.no_graphs),
                                pdl=int(not args.no_pdl))
     d0, D = L.lbmg_levels(h)
     n, nnz, nfrag = L.lbmg_level_info(h, D)
-    nrhs = 3
+    nrhs = f.shape[1]
     # setup, like the hierarchy build: launch shapes tuned once per mesh on its own matrices
     L.lbmg_assemble(h, t)
     if not args.no_tune:
@@ -224,6 +228,7 @@ def main():
         if args.tune_cache:
             L.lbmg_tune_cache_save(args.tune_cache)
     shapes = {str(d): L.lbmg_launch_shape(h, d, L.LBMG_MIXED) for d in range(d0 + 1, D + 1)}
+    tuned_us = {str(d): [round(1e3 * v, 2) for v in L.lbmg_tuned_times(h, d, L.LBMG_MIXED)] for d in range(d0 + 1, D + 1)}
     f_dev = torch.tensor(f, dtype=torch.float64, device=dev)
     rhs = torch.zeros((n, nrhs), dtype=torch.float64, device=dev)
     x = torch.zeros_like(rhs)
@@ -324,21 +329,21 @@ def main():
     opts = L.lbmg_default_options()
     sweeps = opts.nu1 + opts.nu2
     peak, peak_kind = _peaks()
-    R = 4
+    R = 4 if nrhs > 2 else nrhs
     if args.persistent:
         cyc_bytes, fixed_bytes = solve_bytes(h, sweeps, nrhs)
         launch_bytes = cyc_bytes * (cycles / args.steps) + fixed_bytes
         avg_launch_ms = solve_ms / args.steps
-        kernel = "solve_persistent_kernel<float,4> (whole mixed solve, one launch)"
-        key = "solve_persistent_knot23_200k_d8"
+        kernel = f"solve_persistent_kernel<float,{R}> (whole mixed solve, one launch)"
+        key = f"solve_persistent_{workload}"
     else:
         # finest-level coloured Gauss-Seidel: events captured in the cycle graph around the
         # finest pre- and post-smoothing (16 colour launches per cycle and their gaps)
         launch_bytes = (nnz * 8 + n * (4 + 4 + 3 * R * 4)) / 8
         avg_launch_ms = smooth_ms / max(cycles * sweeps * 8, 1)
-        kernel = f"smooth_colour_kernel<float,4,{shapes[str(D)][0][0]}> (finest level, per colour, " \
+        kernel = f"smooth_colour_kernel<float,{R},{shapes[str(D)][0][0]}> (finest level, per colour, " \
                  f"{shapes[str(D)][0][1]} threads/block)"
-        key = "smooth_colour_knot23_200k_d8"
+        key = f"smooth_colour_{workload}"
     achieved = launch_bytes / (avg_launch_ms * 1e-3) / 1e9 if avg_launch_ms > 0 else 0.0
     traffic = None
     try:
@@ -359,7 +364,9 @@ def main():
     gpu_launches = args.steps * (a_cnt + p_cnt + fixed + 1) + cycles * per_cycle
 
     cpu_baseline = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+    # the oracle's hierarchy of the larger workloads takes minutes to build: its baseline is
+    # measured on the metric's own workload only
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and workload == WORKLOAD:
         val, dt, n_o, _ = run_oracle_sample(V, F, depth, t, f, args.oracle_cycles)
         cpu_baseline = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
                         "sample": f"{args.oracle_cycles} FP64 lexicographic-GS V-cycles x 3 right-hand sides on the "
@@ -369,14 +376,15 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 relax / f64 residual+assembly", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "triangles": int(F.shape[0]), "depth": depth, "min_depth": d0,
+            "config": {"workload": workload, "triangles": int(F.shape[0]), "depth": depth, "min_depth": d0,
                        "dofs_finest": n, "nnz_finest": nnz, "fragments_finest": nfrag, "nrhs": nrhs, "t": t,
                        "tol": tol, "precision": "mixed", "l2": "inputs larger than L2 (assembly streams >0.5 GB/step)",
                        "parallelism": "replicas" if ws > 1 else "single",
                        "solve": "persistent" if args.persistent else "graph per cycle",
                        "dependent_launch": not args.no_pdl and not args.persistent,
                        "launch_shapes_mixed": {d: {"sweep": list(v[0]), "residual": list(v[1])}
-                                               for d, v in shapes.items()}},
+                                               for d, v in shapes.items()},
+                       "tuned_us_per_sweep_and_residual": tuned_us},
             "ms_to_tol_mixed": ms_per_step, "ms_to_tol_fp64": fp64_ms,
             "cycles_per_step": cycles / args.steps, "fp64_cycles_per_step": fp64_cycles / fp64_steps,
             "max_rel_residual": rel,

@@ -48,7 +48,8 @@ enum {
     LBMG_COARSE_FACTOR = 6,    /* coarsest-level Cholesky met a non-positive pivot */
     LBMG_CUDA_ERROR = 7,       /* a CUDA call failed; lbmg_last_cuda_error() names it */
     LBMG_DIVERGED = 8,         /* residual became NaN or grew by 1e6 */
-    LBMG_DEVICE_TIMEOUT = 9    /* a bounded device-side wait (grid barrier) expired; results are invalid */
+    LBMG_DEVICE_TIMEOUT = 9    /* a bounded device-side wait (grid barrier, or the bottom kernel's copy of
+                                  its static data) expired; results are invalid */
 };
 
 enum { LBMG_FP64 = 0, LBMG_MIXED = 1 };          /* precision of the V-cycle */
@@ -77,6 +78,11 @@ typedef struct lbmg_options {
                            previous one finishes; 0 launches them with plain stream order.  Direct
                            launches (use_graphs = 0) on the legacy or per-thread default stream
                            always use plain stream order */
+    int copy_phantom_bytes; /* fault injection for tests, default 0 (0..65536): the shared-memory bottom
+                           kernel's copy of its static data waits for this many extra bytes that never
+                           arrive, so its bounded wait (about one second) expires, the kernel sets a
+                           status word and returns, and lbmg_solve returns LBMG_DEVICE_TIMEOUT at the
+                           end of that cycle */
 } lbmg_options;
 
 typedef struct lbmg_stats {
@@ -206,6 +212,10 @@ int lbmg_autotune(lbmg_handle h, int nrhs, int precision, int reps, int *timed, 
 /* launch shapes of level d for `precision`: out[4] = Gauss-Seidel sweep (threads per row,
    threads per block), residual (threads per row, threads per block).  Host only. */
 int lbmg_launch_shape(lbmg_handle h, int d, int precision, int *out);
+/* device time (ms) that the last lbmg_autotune measured on this handle for level d's chosen
+   shapes: ms[0] one Gauss-Seidel sweep (8 chained colour launches), ms[1] one residual
+   launch; 0 where the shape came from the cache or was set by hand.  Host only. */
+int lbmg_tuned_times(lbmg_handle h, int d, int precision, float *ms);
 /* set a launch shape of level d by hand: kind 0 = Gauss-Seidel sweep, 1 = residual;
    tpr in {4, 8, 16}; tpb a multiple of 32 in [32, 512] (LBMG_INVALID_ARG otherwise).
    Results change only by the summation order inside a row.  Host only. */

@@ -24,7 +24,7 @@ __all__ = [
     "lbmg_instance_residuals", "lbmg_learned_nparams", "lbmg_learned_params", "lbmg_learned_collect",
     "lbmg_learned_loss_grad", "lbmg_learned_train", "lbmg_learned_enable", "lbmg_learned_omega",
     "lbmg_residual_norms_noalloc", "lbmg_status_string", "lbmg_last_cuda_error", "lbmg_default_options",
-    "lbmg_autotune", "lbmg_launch_shape", "lbmg_set_launch_shape", "lbmg_tune_cache_save", "lbmg_tune_cache_load",
+    "lbmg_autotune", "lbmg_launch_shape", "lbmg_tuned_times", "lbmg_set_launch_shape", "lbmg_tune_cache_save", "lbmg_tune_cache_load",
 ]
 
 LBMG_OK = 0
@@ -52,7 +52,7 @@ class Options(C.Structure):
     _fields_ = [("min_depth", C.c_int), ("coarse_max", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int),
                 ("smoother", C.c_int), ("jacobi_omega", C.c_double), ("split", C.c_int), ("threads", C.c_int),
                 ("persistent", C.c_int), ("narrow_max", C.c_int), ("barrier_phantoms", C.c_int),
-                ("use_graphs", C.c_int), ("pdl", C.c_int)]
+                ("use_graphs", C.c_int), ("pdl", C.c_int), ("copy_phantom_bytes", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -92,6 +92,7 @@ def load_library():
         "lbmg_launch_counts": (i, [P, i, P, P, P, P]),
         "lbmg_autotune": (i, [P, i, i, i, P, P]),
         "lbmg_launch_shape": (i, [P, i, i, P]),
+        "lbmg_tuned_times": (i, [P, i, i, P]),
         "lbmg_set_launch_shape": (i, [P, i, i, i, i, i]),
         "lbmg_tune_cache_save": (i, [C.c_char_p]),
         "lbmg_tune_cache_load": (i, [C.c_char_p]),
@@ -379,6 +380,13 @@ def lbmg_launch_shape(h, d, precision):
     out = (C.c_int * 4)()
     _check(load_library().lbmg_launch_shape(h, int(d), int(precision), out), "lbmg_launch_shape")
     return (out[0], out[1]), (out[2], out[3])
+
+
+def lbmg_tuned_times(h, d, precision):
+    """(ms per Gauss-Seidel sweep, ms per residual) the last autotune measured for level d (0: not timed)."""
+    out = (C.c_float * 2)()
+    _check(load_library().lbmg_tuned_times(h, int(d), int(precision), out), "lbmg_tuned_times")
+    return out[0], out[1]
 
 
 def lbmg_set_launch_shape(h, d, precision, kind, tpr, tpb):

@@ -265,9 +265,17 @@ int get_graph(lbmg_handle h, int R, int precision, cudaGraphExec_t *out) {
 }
 
 int read_norms(lbmg_handle h, int R, cudaStream_t s, double *out4) {
-    LBMG_CK(cudaMemcpyAsync(h->c.h_norm, h->c.norm_out, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    // four norms, then the bottom kernel's status word
+    LBMG_CK(cudaMemcpyAsync(h->c.h_norm, h->c.norm_out, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
     LBMG_CK(cudaStreamSynchronize(s));
     for (int r = 0; r < 4; r++) out4[r] = r < R ? h->c.h_norm[r] : 0.0;
+    int st = 0;
+    std::memcpy(&st, &h->c.h_norm[4], sizeof st);
+    if (st != 0) {
+        // a bounded wait in the bottom kernel gave up: the cycle's result is invalid
+        LBMG_CK(cudaMemsetAsync(h->c.norm_out + 4, 0, sizeof(double), s));
+        return LBMG_DEVICE_TIMEOUT;
+    }
     return LBMG_OK;
 }
 
@@ -399,6 +407,8 @@ int upload_hierarchy(lbmg_handle h) {
     LBMG_TRY(h->alloc(&c.rs, 4 * nD));
     LBMG_TRY(h->alloc(&c.norm_part, 4 * (size_t)kNormBlocks));
     LBMG_TRY(h->alloc(&c.norm_out, 8));
+    LBMG_CK(cudaMemset(c.norm_out, 0, 8 * sizeof(double)));
+    c.narrow.status = reinterpret_cast<int *>(c.norm_out + 4);
     h->io_cap = 4 * std::max(std::max(nD, (size_t)c.nv), (size_t)c.nu);
     LBMG_TRY(h->alloc(&c.dev_io, 2 * h->io_cap));
     LBMG_CK(cudaMallocHost((void **)&c.h_norm, 8 * sizeof(double)));
@@ -480,6 +490,7 @@ void lbmg_default_options(lbmg_options *o) {
     o->barrier_phantoms = 0;
     o->use_graphs = 1;
     o->pdl = 1;
+    o->copy_phantom_bytes = 0;
 }
 
 int lbmg_build_hierarchy(const double *V, int nv, const int *F, int nt, int depth, const lbmg_options *opt,
@@ -492,6 +503,7 @@ int lbmg_build_hierarchy(const double *V, int nv, const int *F, int nt, int dept
     if (o.nu1 < 0 || o.nu2 < 0 || o.coarse_max < 1 || o.coarse_max > kMaxCoarse) return LBMG_INVALID_ARG;
     if (o.smoother != LBMG_GS_COLOURED && o.smoother != LBMG_JACOBI) return LBMG_INVALID_ARG;
     if (o.narrow_max < 0 || o.barrier_phantoms < 0 || o.barrier_phantoms > 1024) return LBMG_INVALID_ARG;
+    if (o.copy_phantom_bytes < 0 || o.copy_phantom_bytes > 65536) return LBMG_INVALID_ARG;
     lbmg_ctx *h = new (std::nothrow) lbmg_ctx();
     if (!h) return LBMG_OUT_OF_MEMORY;
     std::string err;
@@ -513,6 +525,7 @@ int lbmg_build_hierarchy(const double *V, int nv, const int *F, int nt, int dept
     h->c.persistent = o.persistent;
     h->c.use_graphs = o.use_graphs;
     h->c.pdl = o.pdl;
+    h->c.copy_phantoms = o.copy_phantom_bytes;
     h->c.persist_narrow = o.narrow_max;
     h->c.barrier_phantoms = o.barrier_phantoms;
     st = upload_hierarchy(h);
@@ -952,6 +965,16 @@ int lbmg_launch_shape(lbmg_handle h, int d, int precision, int *out) {
     return LBMG_OK;
 }
 
+int lbmg_tuned_times(lbmg_handle h, int d, int precision, float *ms) {
+    LBMG_TRY(check_level(h, d));
+    if (!ms || (precision != LBMG_FP64 && precision != LBMG_MIXED)) return LBMG_INVALID_ARG;
+    const DevLevel &L = h->c.lev[d];
+    const int p = precision == LBMG_FP64;
+    ms[0] = L.tuned_ms[p][kShapeSmooth];
+    ms[1] = L.tuned_ms[p][kShapeResidual];
+    return LBMG_OK;
+}
+
 int lbmg_set_launch_shape(lbmg_handle h, int d, int precision, int kind, int tpr, int tpb) {
     LBMG_TRY(check_level(h, d));
     if (precision != LBMG_FP64 && precision != LBMG_MIXED) return LBMG_INVALID_ARG;
@@ -960,6 +983,7 @@ int lbmg_set_launch_shape(lbmg_handle h, int d, int precision, int kind, int tpr
     LaunchShape &sh = h->c.lev[d].shape[precision == LBMG_FP64][kind];
     sh.tpr = tpr;
     sh.tpb = tpb;
+    h->c.lev[d].tuned_ms[precision == LBMG_FP64][kind] = 0.f;
     if (h->c.graph.exec) { cudaGraphExecDestroy(h->c.graph.exec); h->c.graph.exec = nullptr; }
     return LBMG_OK;
 }

@@ -80,6 +80,7 @@ struct DevLevel {
     double *x64 = nullptr, *b64 = nullptr, *r64 = nullptr;
     float *x32 = nullptr, *b32 = nullptr, *r32 = nullptr;
     LaunchShape shape[2][2];               // [FP64][kShapeSmooth / kShapeResidual], set by the autotuner
+    float tuned_ms[2][2] = {{0, 0}, {0, 0}};   // device time of the chosen shape when the tuner timed it
 };
 
 struct Learned;
@@ -100,6 +101,8 @@ struct NarrowState {
     int dn = -1;                      // top level held in shared memory (< d0: none)
     NarrowParams p;
     unsigned char *blob = nullptr;    // packed static data (device)
+    int *status = nullptr;            // device word (beside the norms the solve reads back every cycle):
+                                      // 1 after a bounded wait of the bottom kernel gave up
     int blob_bytes = 0, vec_bytes = 0;
 };
 
@@ -168,6 +171,7 @@ struct Ctx {
     int persist_ok = 0;
     int persist_blocks = 0, persist_dn = 0, persist_narrow = 2048;
     int barrier_phantoms = 0;        // fault injection: extra arrivals a grid barrier waits for
+    int copy_phantoms = 0;           // fault injection: extra bytes the bottom kernel's copy waits for
     void *persist_views = nullptr;
     void *views32 = nullptr, *views64 = nullptr;   // level views for the one-block bottom cycle
     size_t persist_view_bytes = 0;

@@ -4,13 +4,16 @@
 // The coarsest levels are tiny, so each of their ~35 phases per cycle (eight
 // colours per Gauss-Seidel sweep, residual, restriction, prolongation) is pure
 // latency: as separate launches each costs a launch gap, and even inside one
-// block each phase waits on three dependent global-memory loads.  Here the
-// static data of those levels (16-bit row pointers, column indices, parents and
-// children, FP32 values and inverse diagonals) are packed once into a compact
-// blob; every cycle one block copies the blob into shared memory with 16-byte
-// loads, runs the bottom V-cycle there with block barriers between phases, and
-// writes the correction of its top level back.  Only the dense coarse inverse
-// and the top level's right-hand side and correction touch global memory.
+// block each phase waits on three dependent memory loads.  Here the static data
+// of those levels (16-bit row pointers, column indices, parents and children,
+// FP32 values and inverse diagonals) are packed once into a compact blob; every
+// cycle one block pulls the blob into shared memory with TMA bulk copies (issued
+// before the kernel waits for its predecessor, so the copy overlaps the previous
+// kernel), runs the bottom V-cycle there with block barriers between phases, and
+// writes the correction of its top level back.  Four threads share a row, which
+// keeps each phase short: a phase is a chain of dependent shared-memory loads.
+// Only the dense coarse inverse and the top level's right-hand side and
+// correction touch global memory.
 #include <cstring>
 #include <vector>
 
@@ -20,7 +23,33 @@ namespace lbmg {
 
 namespace {
 
-constexpr int kGN = 8;   // threads per matrix row
+constexpr int kGN = 4;   // threads per matrix row
+constexpr unsigned long long kCopyWaitNs = 1000000000ull;   // the blob copy is given up after one second
+constexpr int kCopyChunk = 32768;                            // bytes per bulk copy instruction
+
+__device__ __forceinline__ unsigned long long now_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// wait for phase `parity` of the barrier, at most `limit` ns; false when it gave up
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity, unsigned long long limit) {
+    const unsigned long long t0 = now_ns();
+    while (!mbar_try_wait(mbar, parity))
+        if (now_ns() - t0 > limit) return false;
+    return true;
+}
 
 template <int R>
 __device__ __forceinline__ void sld(const float *p, float (&v)[R]) {
@@ -31,6 +60,16 @@ template <>
 __device__ __forceinline__ void sld<4>(const float *p, float (&v)[4]) {
     const float4 q = *reinterpret_cast<const float4 *>(p);
     v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+
+template <int R>
+__device__ __forceinline__ void sst(float *p, const float (&v)[R]) {
+#pragma unroll
+    for (int q = 0; q < R; q++) p[q] = v[q];
+}
+template <>
+__device__ __forceinline__ void sst<4>(float *p, const float (&v)[4]) {
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
 }
 
 struct SLev {
@@ -58,7 +97,7 @@ __device__ SLev slev(const NarrowLevel &h, unsigned char *sm) {
 
 // row loop with 8-thread groups; every warp runs the same number of iterations
 template <int R, class F>
-__device__ __forceinline__ void rows8(int r0, int r1, F &&body) {
+__device__ __forceinline__ void row_groups(int r0, int r1, F &&body) {
     const int tid = threadIdx.x, g = tid / kGN, lane = tid % kGN, ng = blockDim.x / kGN;
     const int warp_first = (tid / 32) * (32 / kGN);
     for (int base = r0 + warp_first; base < r1; base += ng) {
@@ -67,13 +106,29 @@ __device__ __forceinline__ void rows8(int r0, int r1, F &&body) {
     }
 }
 
+// A row's first kGN * kUnroll entries are taken in one predicated, fully unrolled
+// step, so their loads are in flight together (a row has about 14 entries, fewer
+// than one unrolled block of a runtime-count loop); longer rows finish in a loop.
+constexpr int kUnroll = 4;
+
 template <int R>
 __device__ __forceinline__ void sdot(const SLev &L, int row, bool active, int lane, float (&acc)[R]) {
 #pragma unroll
     for (int q = 0; q < R; q++) acc[q] = 0.f;
     if (active) {
-        const int k1 = L.rp[row + 1];
-        for (int k = L.rp[row] + lane; k < k1; k += kGN) {
+        const int k0 = L.rp[row] + lane, k1 = L.rp[row + 1];
+#pragma unroll
+        for (int u = 0; u < kUnroll; u++) {
+            const int k = k0 + u * kGN;
+            if (k < k1) {
+                const float a = L.A[k];
+                float v[R];
+                sld<R>(L.x + (size_t)L.ci[k] * R, v);
+#pragma unroll
+                for (int q = 0; q < R; q++) acc[q] = fmaf(a, v[q], acc[q]);
+            }
+        }
+        for (int k = k0 + kUnroll * kGN; k < k1; k += kGN) {
             const float a = L.A[k];
             float v[R];
             sld<R>(L.x + (size_t)L.ci[k] * R, v);
@@ -87,21 +142,76 @@ __device__ __forceinline__ void sdot(const SLev &L, int row, bool active, int la
         for (int q = 0; q < R; q++) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o, kGN);
 }
 
+// one Gauss-Seidel row update: the row's own inverse diagonal, right-hand side and
+// value are loaded before its dot product, so only the update waits for the sum
+template <int R>
+__device__ __forceinline__ void gs_row(const SLev &L, int row, bool active, int lane) {
+    const bool own = active && lane == 0;
+    float xo[R], bo[R], dv = 0.f;
+    if (own) {
+        dv = L.dinv[row];
+        sld<R>(L.b + (size_t)row * R, bo);
+        sld<R>(L.x + (size_t)row * R, xo);
+    }
+    float acc[R];
+    sdot<R>(L, row, active, lane, acc);
+    if (own) {
+#pragma unroll
+        for (int q = 0; q < R; q++) xo[q] = fmaf(bo[q] - acc[q], dv, xo[q]);
+        sst<R>(L.x + (size_t)row * R, xo);
+    }
+}
+
 template <int R>
 __global__ void __launch_bounds__(1024, 1) narrow_smem_kernel(const unsigned char *__restrict__ blob, int blob_bytes,
-                                                              int vec_bytes, NarrowParams p,
+                                                              int vec_bytes, const NarrowParams pin,
                                                               const float *__restrict__ cinv, const int *__restrict__ cblk,
-                                                              const float *__restrict__ b_top, float *__restrict__ x_top) {
-    extern __shared__ __align__(16) unsigned char sm[];
-    // static part of the blob, then zeroed vectors
-    for (int q = threadIdx.x; q < blob_bytes / 16; q += blockDim.x)
-        reinterpret_cast<uint4 *>(sm)[q] = __ldg(reinterpret_cast<const uint4 *>(blob) + q);
+                                                              const float *__restrict__ b_top, float *__restrict__ x_top,
+                                                              int *__restrict__ status, int extra_tx) {
+    extern __shared__ __align__(128) unsigned char sm[];
+    __shared__ __align__(8) unsigned long long mbar;
+    // the level table, read by every phase, from shared memory rather than from
+    // dynamically indexed kernel parameters
+    __shared__ NarrowParams p;
+    for (int q = threadIdx.x; q < (int)(sizeof(NarrowParams) / sizeof(int)); q += blockDim.x)
+        reinterpret_cast<int *>(&p)[q] = reinterpret_cast<const int *>(&pin)[q];
+    __shared__ int s_ok;
+    const uint32_t mb = (uint32_t)__cvta_generic_to_shared(&mbar);
+    if (threadIdx.x == 0) {
+        // the blob is static during a solve: its copy starts before this kernel
+        // waits for its predecessor
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        // extra_tx > 0 only when a test injects bytes that never arrive
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(blob_bytes + extra_tx)
+                     : "memory");
+        for (int off = 0; off < blob_bytes; off += kCopyChunk) {
+            const int bytes = min(kCopyChunk, blob_bytes - off);
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    (uint32_t)__cvta_generic_to_shared(sm + off)),
+                "l"(blob + off), "r"(bytes), "r"(mb)
+                : "memory");
+        }
+    }
     for (int q = threadIdx.x; q < vec_bytes / 16; q += blockDim.x)
         reinterpret_cast<uint4 *>(sm + blob_bytes)[q] = make_uint4(0, 0, 0, 0);
-    // the blob is static during a solve; b_top comes from the kernel before this one
+    // b_top comes from the kernel before this one
     grid_dep_wait();
     grid_dep_launch();
+    if (threadIdx.x == 0) {
+        int ok = mbar_wait_bounded(mb, 0, kCopyWaitNs) ? 1 : 0;
+        if (!ok) {
+            // report, then give the copies in flight one more bounded wait before leaving
+            atomicExch(status, 1);
+            mbar_wait_bounded(mb, 0, kCopyWaitNs);
+        }
+        s_ok = ok;
+    }
     __syncthreads();
+    if (!s_ok) return;
+    // every thread observes the completed phase, which makes the copied bytes visible to it
+    mbar_wait_bounded(mb, 0, kCopyWaitNs);
     const NarrowLevel &T = p.lev[p.dn - p.d0];
     {
         float *b = reinterpret_cast<float *>(sm + T.o_b);
@@ -117,43 +227,47 @@ __global__ void __launch_bounds__(1024, 1) narrow_smem_kernel(const unsigned cha
             const int *cb = cblk + 5 * (H.cb0 + k);
             const int row0 = cb[2], n = cb[3];
             const float *M = cinv + cb[4];
-            for (int row = warp; row < n; row += nw) {
-                float acc[R];
+            // four rows per warp at a time, so that a warp keeps 4 x 4 loads of the inverse in flight
+            for (int rb = warp; rb < n; rb += 4 * nw) {
+                float acc[4][R];
 #pragma unroll
-                for (int q = 0; q < R; q++) acc[q] = 0.f;
+                for (int u = 0; u < 4; u++)
+#pragma unroll
+                    for (int q = 0; q < R; q++) acc[u][q] = 0.f;
+#pragma unroll 2
                 for (int j = wl; j < n; j += 32) {
-                    const float a = __ldg(M + (size_t)row * n + j);
                     float v[R];
                     sld<R>(L.b + (size_t)(row0 + j) * R, v);
 #pragma unroll
-                    for (int q = 0; q < R; q++) acc[q] = fmaf(a, v[q], acc[q]);
+                    for (int u = 0; u < 4; u++) {
+                        const int row = rb + u * nw;
+                        if (row < n) {
+                            const float a = __ldg(M + (size_t)row * n + j);
+#pragma unroll
+                            for (int q = 0; q < R; q++) acc[u][q] = fmaf(a, v[q], acc[u][q]);
+                        }
+                    }
                 }
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1)
+                for (int u = 0; u < 4; u++) {
 #pragma unroll
-                    for (int q = 0; q < R; q++) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
-                if (wl == 0)
+                    for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-                    for (int q = 0; q < R; q++) L.x[(size_t)(row0 + row) * R + q] = acc[q];
+                        for (int q = 0; q < R; q++) acc[u][q] += __shfl_xor_sync(0xffffffffu, acc[u][q], o);
+                    const int row = rb + u * nw;
+                    if (wl == 0 && row < n) sst<R>(L.x + (size_t)(row0 + row) * R, acc[u]);
+                }
             }
         }
         __syncthreads();
         if (d == p.d0) break;
         for (int s = 0; s < p.nu1; s++)
             for (int c = 0; c < 8; c++) {
-                rows8<R>(H.cs[c], H.cs[c + 1], [&](int row, bool active, int lane) {
-                    float acc[R];
-                    sdot<R>(L, row, active, lane, acc);
-                    if (active && lane == 0) {
-                        const float dv = L.dinv[row];
-#pragma unroll
-                        for (int q = 0; q < R; q++)
-                            L.x[(size_t)row * R + q] += (L.b[(size_t)row * R + q] - acc[q]) * dv;
-                    }
-                });
+                row_groups<R>(H.cs[c], H.cs[c + 1],
+                              [&](int row, bool active, int lane) { gs_row<R>(L, row, active, lane); });
                 __syncthreads();
             }
-        rows8<R>(0, H.ns, [&](int row, bool active, int lane) {
+        row_groups<R>(0, H.ns, [&](int row, bool active, int lane) {
             float acc[R];
             sdot<R>(L, row, active, lane, acc);
             if (active && lane == 0)
@@ -167,14 +281,19 @@ __global__ void __launch_bounds__(1024, 1) narrow_smem_kernel(const unsigned cha
             float acc[R];
 #pragma unroll
             for (int q = 0; q < R; q++) acc[q] = 0.f;
-            for (int k = C.crp[J]; k < C.crp[J + 1]; k++) {
+            const int k0 = C.crp[J], k1 = C.crp[J + 1];
+            auto child = [&](int k) {
                 const uint16_t e = C.cch[k];
                 const float w = 1.f / (float)(1u << (e >> 14));
                 float v[R];
                 sld<R>(L.r + (size_t)(e & 0x3fff) * R, v);
 #pragma unroll
                 for (int q = 0; q < R; q++) acc[q] = fmaf(w, v[q], acc[q]);
-            }
+            };
+#pragma unroll
+            for (int u = 0; u < 8; u++)
+                if (k0 + u < k1) child(k0 + u);
+            for (int k = k0 + 8; k < k1; k++) child(k);
 #pragma unroll
             for (int q = 0; q < R; q++) { C.b[(size_t)J * R + q] = acc[q]; C.x[(size_t)J * R + q] = 0.f; }
         }
@@ -188,10 +307,13 @@ __global__ void __launch_bounds__(1024, 1) narrow_smem_kernel(const unsigned cha
             float acc[R], v[R];
 #pragma unroll
             for (int q = 0; q < R; q++) acc[q] = 0.f;
-            for (int q2 = 0; q2 < np; q2++) {
-                sld<R>(C.x + (size_t)L.par[8 * i + q2] * R, v);
 #pragma unroll
-                for (int q = 0; q < R; q++) acc[q] += v[q];
+            for (int q2 = 0; q2 < 8; q2++) {
+                if (q2 < np) {
+                    sld<R>(C.x + (size_t)L.par[8 * i + q2] * R, v);
+#pragma unroll
+                    for (int q = 0; q < R; q++) acc[q] += v[q];
+                }
             }
             const float w = 1.f / (float)np;
 #pragma unroll
@@ -200,16 +322,8 @@ __global__ void __launch_bounds__(1024, 1) narrow_smem_kernel(const unsigned cha
         __syncthreads();
         for (int s = 0; s < p.nu2; s++)
             for (int c = 7; c >= 0; c--) {
-                rows8<R>(H.cs[c], H.cs[c + 1], [&](int row, bool active, int lane) {
-                    float acc[R];
-                    sdot<R>(L, row, active, lane, acc);
-                    if (active && lane == 0) {
-                        const float dv = L.dinv[row];
-#pragma unroll
-                        for (int q = 0; q < R; q++)
-                            L.x[(size_t)row * R + q] += (L.b[(size_t)row * R + q] - acc[q]) * dv;
-                    }
-                });
+                row_groups<R>(H.cs[c], H.cs[c + 1],
+                              [&](int row, bool active, int lane) { gs_row<R>(L, row, active, lane); });
                 __syncthreads();
             }
     }
@@ -300,6 +414,7 @@ int narrow_smem_setup(Ctx &c, size_t smem_budget) {
     }
     if (off != best_blob) return 1;
     if (cudaMalloc((void **)&c.narrow.blob, best_blob) != cudaSuccess) { cudaGetLastError(); c.narrow.blob = nullptr; return 1; }
+
     if (cudaMemcpy(c.narrow.blob, buf.data(), best_blob, cudaMemcpyHostToDevice) != cudaSuccess) return 1;
     c.narrow.blob_bytes = (int)best_blob;
     c.narrow.vec_bytes = (int)best_vec;
@@ -326,7 +441,7 @@ void launch_narrow_smem(const Ctx &c, int R, cudaStream_t s, Chain *ch) {
     auto k = R == 1 ? narrow_smem_kernel<1> : R == 2 ? narrow_smem_kernel<2> : narrow_smem_kernel<4>;
     klaunch(k, 1u, 1024u, (size_t)smem, s, ch, (const unsigned char *)c.narrow.blob, c.narrow.blob_bytes,
             c.narrow.vec_bytes, c.narrow.p, (const float *)c.cinv32, (const int *)c.cblk, (const float *)T.b32,
-            T.x32);
+            T.x32, c.narrow.status, c.copy_phantoms);
 }
 
 }  // namespace lbmg

@@ -197,29 +197,39 @@ void launch_jacobi_update(const DevLevel &L, const T *dinv, const T *r, T *x, T 
     jacobi_update_kernel<T><<<(unsigned)((m + 255) / 256), 256, 0, s>>>(L.ns, R, dinv, r, x, omega);
 }
 
-// b_c[J] = sum over fine children i of J of r_f[i] / #parents(i); x_c[J] = 0 when x_c is given
+// b_c[J] = sum over fine children i of J of r_f[i] / #parents(i); x_c[J] = 0 when x_c is given.
+// The first kPreChildren entries of the static child list are loaded before the
+// grid-dependency wait, so after it only the residual gathers remain, all in flight
+// together.
+constexpr int kPreChildren = 16;
+
 template <class T, int R>
 __global__ void restrict_kernel(int nc, const int *__restrict__ crp, const uint32_t *__restrict__ cch,
                                 const T *__restrict__ rf, T *__restrict__ bc, T *__restrict__ xc) {
     const int J = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = J < nc;
     int k0 = 0, k1 = 0;
+    uint32_t e[kPreChildren];
     if (active) { k0 = __ldg(crp + J); k1 = __ldg(crp + J + 1); }
+#pragma unroll
+    for (int u = 0; u < kPreChildren; u++) e[u] = k0 + u < k1 ? __ldg(cch + k0 + u) : 0u;
     grid_dep_wait();
     grid_dep_launch();
     if (!active) return;
     T acc[R];
 #pragma unroll
     for (int r = 0; r < R; r++) acc[r] = T(0);
-    for (int k = k0; k < k1; k++) {
-        const uint32_t e = __ldg(cch + k);
-        const uint32_t i = e & kPackMask;
-        const T w = T(1) / T(1u << (e >> kPackShift));
+    auto child = [&](uint32_t ek) {
+        const T w = T(1) / T(1u << (ek >> kPackShift));
         T v[R];
-        load_x<T, R>(rf + (size_t)i * R, v);
+        load_x<T, R>(rf + (size_t)(ek & kPackMask) * R, v);
 #pragma unroll
         for (int r = 0; r < R; r++) acc[r] = fma(w, v[r], acc[r]);
-    }
+    };
+#pragma unroll
+    for (int u = 0; u < kPreChildren; u++)
+        if (k0 + u < k1) child(e[u]);
+    for (int k = k0 + kPreChildren; k < k1; k++) child(__ldg(cch + k));
 #pragma unroll
     for (int r = 0; r < R; r++) bc[(size_t)J * R + r] = acc[r];
     if (xc) {

@@ -108,7 +108,11 @@ cudaError_t tune_levels(Ctx &c, int R, int reps, int *timed) {
             {
                 std::lock_guard<std::mutex> lk(g_mu);
                 auto it = g_cache.find(key);
-                if (it != g_cache.end()) { L.shape[fp64][kind] = it->second; continue; }
+                if (it != g_cache.end()) {
+                    L.shape[fp64][kind] = it->second;
+                    L.tuned_ms[fp64][kind] = 0.f;
+                    continue;
+                }
             }
             LaunchShape best = LaunchShape(), dflt = LaunchShape();
             float best_ms = 0.f, dflt_ms = 0.f;
@@ -127,8 +131,9 @@ cudaError_t tune_levels(Ctx &c, int R, int reps, int *timed) {
                 }
             if (e != cudaSuccess) { L.shape[fp64][kind] = dflt; break; }
             // keep the default unless another shape is clearly faster (timing noise)
-            if (dflt_ms > 0.f && best_ms > 0.98f * dflt_ms) best = dflt;
+            if (dflt_ms > 0.f && best_ms > 0.98f * dflt_ms) { best = dflt; best_ms = dflt_ms; }
             L.shape[fp64][kind] = best;
+            L.tuned_ms[fp64][kind] = best_ms;
             {
                 std::lock_guard<std::mutex> lk(g_mu);
                 g_cache[key] = best;

@@ -301,7 +301,11 @@ def test_weighted_jacobi_smoother_converges():
 
 def test_persistent_and_per_cycle_graph_paths_agree(case):
     """The one-launch cooperative solve and the per-cycle graph launch run the same
-    arithmetic in the same order: a fixed number of cycles gives the same iterate."""
+    arithmetic: a fixed number of cycles gives the same iterate.  In FP64 the order of
+    every sum is the same too (1e-12).  In mixed precision the per-cycle path's
+    shared-memory bottom sums a row with two threads where the cooperative solve's
+    bottom uses eight, so the FP32 cycles differ by rounding, and after five cycles
+    of FP64 defect correction the iterates agree to 1e-5 (4e-8 observed)."""
     h2 = L.lbmg_build_hierarchy(case.V, case.F, case.D, min_depth=case.d0, persistent=1)
     try:
         L.lbmg_assemble(h2, case.t)
@@ -313,7 +317,7 @@ def test_persistent_and_per_cycle_graph_paths_agree(case):
             xb = torch.zeros_like(rhs)
             L.lbmg_vcycles(case.h, rhs, xa, 5, prec)
             L.lbmg_vcycles(h2, rhs, xb, 5, prec)
-            assert _rel(xa.cpu().numpy(), xb.cpu().numpy()) <= 1e-12
+            assert _rel(xa.cpu().numpy(), xb.cpu().numpy()) <= (1e-12 if prec == L.LBMG_FP64 else 1e-5)
         xa = torch.zeros_like(rhs)
         xb = torch.zeros_like(rhs)
         ca, sa = L.lbmg_solve(case.h, rhs, xa, 1e-6, 3000, L.LBMG_MIXED)
@@ -343,6 +347,33 @@ def test_bounded_barrier_wait_reports_timeout_and_context_stays_usable():
         x = torch.zeros_like(rhs)
         code, st = L.lbmg_solve(good, rhs, x, 1e-6, 1000, L.LBMG_MIXED)
         assert code == L.LBMG_OK and st.converged
+    finally:
+        L.lbmg_destroy(bad)
+        L.lbmg_destroy(good)
+
+
+def test_bounded_copy_wait_reports_timeout_and_context_stays_usable():
+    """Fault injected on the host: the shared-memory bottom kernel's bulk copy is told
+    to wait for 16 bytes that never arrive.  Its bounded wait expires, the kernel sets
+    the status word and returns, the per-cycle solve stops with LBMG_DEVICE_TIMEOUT, and
+    the device keeps working."""
+    V, F = meshgen.icosphere(2, 1.0, 1e-3, 1)
+    bad = L.lbmg_build_hierarchy(V, F, 4, copy_phantom_bytes=16)
+    good = L.lbmg_build_hierarchy(V, F, 4)
+    try:
+        for h in (bad, good):
+            L.lbmg_assemble(h, 1e-2)
+        n = L.lbmg_level_info(good, 4)[0]
+        rhs = torch.zeros((n, 1), dtype=torch.float64, device=DEV)
+        L.lbmg_project_rhs(good, _dev(V[:, :1]), rhs)
+        x = torch.zeros_like(rhs)
+        code, st = L.lbmg_solve(bad, rhs, x, 1e-6, 100, L.LBMG_MIXED)
+        assert code == L.LBMG_DEVICE_TIMEOUT
+        for h in (good, bad):   # the status word was cleared: FP64 cycles do not use that kernel
+            x = torch.zeros_like(rhs)
+            prec = L.LBMG_MIXED if h is good else L.LBMG_FP64
+            code, st = L.lbmg_solve(h, rhs, x, 1e-6, 1000, prec)
+            assert code == L.LBMG_OK and st.converged
     finally:
         L.lbmg_destroy(bad)
         L.lbmg_destroy(good)
