@@ -188,6 +188,8 @@ def main():
     ap.add_argument("--only-timed", action="store_true", help="stop after the timed steps (profiling runs)")
     ap.add_argument("--no-pdl", action="store_true", help="plain stream order between the cycle's kernels")
     ap.add_argument("--no-tune", action="store_true", help="default launch shapes (no autotuning at setup)")
+    ap.add_argument("--solver", default="vcycle", choices=["vcycle", "pcg"],
+                    help="V-cycle iteration (the paper's solver, default) or V-cycle-preconditioned CG")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="named synthetic workload (meshgen.CONFIGS); the default is the metric's own configuration")
     ap.add_argument("--tune-cache", default=None,
@@ -239,7 +241,8 @@ def main():
         L.lbmg_assemble(h, t)
         L.lbmg_project_rhs(h, f_dev, rhs)
         x.zero_()
-        code, st = L.lbmg_solve(h, rhs, x, tol, max_cycles, precision)
+        solve = L.lbmg_solve_pcg if args.solver == "pcg" else L.lbmg_solve
+        code, st = solve(h, rhs, x, tol, max_cycles, precision)
         if code != L.LBMG_OK and not (code == L.LBMG_NOT_CONVERGED and args.max_cycles < 2000):
             raise RuntimeError(f"solve did not converge: {st.rel_residual[:3]}")
         L.lbmg_eval_vertices(h, x, u)
@@ -297,7 +300,8 @@ def main():
         L.lbmg_assemble(h, t)
         L.lbmg_project_rhs(h, f_np, rhs)
         x.zero_()
-        code, st = L.lbmg_solve(h, rhs, x, tol, max_cycles, L.LBMG_MIXED)
+        solve = L.lbmg_solve_pcg if args.solver == "pcg" else L.lbmg_solve
+        code, st = solve(h, rhs, x, tol, max_cycles, L.LBMG_MIXED)
         L.lbmg_eval_vertices(h, x, u_np)
         return st
 
@@ -323,6 +327,31 @@ def main():
     g1.record()
     torch.cuda.synchronize()
     fp64_ms = g0.elapsed_time(g1) / fp64_steps
+
+    # the other solver on the same steps: ms to the same tolerance, mixed and FP64
+    other = "pcg" if args.solver == "vcycle" else "vcycle"
+    other_solve = L.lbmg_solve_pcg if other == "pcg" else L.lbmg_solve
+    other_res = {}
+    for name, prec in (("mixed", L.LBMG_MIXED), ("fp64", L.LBMG_FP64)):
+        def ostep():
+            L.lbmg_assemble(h, t)
+            L.lbmg_project_rhs(h, f_dev, rhs)
+            x.zero_()
+            code, st = other_solve(h, rhs, x, tol, max_cycles, prec)
+            L.lbmg_eval_vertices(h, x, u)
+            return code, st
+        ostep()
+        torch.cuda.synchronize()
+        g0.record()
+        its, ok = 0, True
+        for _ in range(fp64_steps):
+            code, st = ostep()
+            its += st.cycles
+            ok = ok and code == L.LBMG_OK
+        g1.record()
+        torch.cuda.synchronize()
+        other_res[name] = {"ms_to_tol": g0.elapsed_time(g1) / fp64_steps, "cycles_per_step": its / fp64_steps,
+                           "converged": ok}
 
     # roofline of the dominant kernel, timed live with CUDA events on its stream
     a_cnt, p_cnt, per_cycle, fixed = L.lbmg_launch_counts(h, L.LBMG_MIXED)
@@ -385,7 +414,8 @@ def main():
                        "launch_shapes_mixed": {d: {"sweep": list(v[0]), "residual": list(v[1])}
                                                for d, v in shapes.items()},
                        "tuned_us_per_sweep_and_residual": tuned_us},
-            "ms_to_tol_mixed": ms_per_step, "ms_to_tol_fp64": fp64_ms,
+            "ms_to_tol_mixed": ms_per_step, "ms_to_tol_fp64": fp64_ms, "solver": args.solver,
+            "other_solver": {"solver": other, **other_res},
             "cycles_per_step": cycles / args.steps, "fp64_cycles_per_step": fp64_cycles / fp64_steps,
             "max_rel_residual": rel,
             "roofline": roofline, "cpu_baseline": cpu_baseline,

@@ -186,6 +186,24 @@ int lbmg_project_rhs(lbmg_handle h, const double *f_vertex, int nrhs, double *rh
 int lbmg_solve(lbmg_handle h, const double *rhs, double *x, int nrhs, double tol, int max_cycles,
                int precision, lbmg_stats *stats, void *stream);
 
+/*
+ * Conjugate gradients on (M + t L) x = rhs, preconditioned by one V-cycle of
+ * Section 4.3 per iteration.  The cycle is symmetric (colours 0..7 on the way
+ * down, 7..0 on the way up, nu1 = nu2, exact dense solve of A + eps I at the
+ * coarsest level), so it is an SPD preconditioner; the iteration takes the
+ * flexible (Polak-Ribiere) form, in which the nearly linear FP32 cycle of
+ * LBMG_MIXED keeps it stable.  Every right-hand side has its own step lengths;
+ * vectors, dot products and the operator are FP64, the cycle runs in `precision`.
+ * Arguments, stopping rule (per right-hand side, recursively updated FP64
+ * residual) and statistics as for lbmg_solve; stats->cycles counts iterations,
+ * one V-cycle each.  Near-null modes that plain V-cycles reduce slowly (nearly
+ * axis-aligned sheets, Discussion of Section 5) are taken out by the Krylov
+ * recurrence.  Single meshes only and only with the coloured Gauss-Seidel
+ * smoother (LBMG_INVALID_ARG otherwise); the persistent option does not apply.
+ */
+int lbmg_solve_pcg(lbmg_handle h, const double *rhs, double *x, int nrhs, double tol, int max_iters,
+                   int precision, lbmg_stats *stats, void *stream);
+
 /* Number of kernels each call launches: lbmg_assemble, lbmg_project_rhs, one
    V-cycle step of lbmg_solve/lbmg_vcycles in `precision` (cycle + FP64 residual
    + norms; 0 for the persistent solve, whose cycles run inside its one launch),

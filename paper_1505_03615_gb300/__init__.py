@@ -24,7 +24,7 @@ __all__ = [
     "lbmg_instance_residuals", "lbmg_learned_nparams", "lbmg_learned_params", "lbmg_learned_collect",
     "lbmg_learned_loss_grad", "lbmg_learned_train", "lbmg_learned_enable", "lbmg_learned_omega",
     "lbmg_residual_norms_noalloc", "lbmg_status_string", "lbmg_last_cuda_error", "lbmg_default_options",
-    "lbmg_autotune", "lbmg_launch_shape", "lbmg_tuned_times", "lbmg_set_launch_shape", "lbmg_tune_cache_save", "lbmg_tune_cache_load",
+    "lbmg_solve_pcg", "lbmg_autotune", "lbmg_launch_shape", "lbmg_tuned_times", "lbmg_set_launch_shape", "lbmg_tune_cache_save", "lbmg_tune_cache_load",
 ]
 
 LBMG_OK = 0
@@ -82,6 +82,7 @@ def load_library():
         "lbmg_assemble": (i, [P, d, P]),
         "lbmg_project_rhs": (i, [P, P, i, P, P]),
         "lbmg_solve": (i, [P, P, P, i, d, i, i, P, P]),
+        "lbmg_solve_pcg": (i, [P, P, P, i, d, i, i, P, P]),
         "lbmg_vcycles": (i, [P, P, P, i, i, i, P]),
         "lbmg_residual": (i, [P, i, P, P, P, i, P]),
         "lbmg_smooth": (i, [P, i, P, P, i, i, i, P]),
@@ -321,6 +322,15 @@ def lbmg_solve(h, rhs, x, tol, max_cycles, precision, stream=None, raise_not_con
     code = load_library().lbmg_solve(h, _ptr(rhs), _ptr(x), _nrhs(rhs), float(tol), int(max_cycles), int(precision),
                                      C.byref(st), _stream(stream))
     _check(code, "lbmg_solve", allow=() if raise_not_converged else (LBMG_NOT_CONVERGED, LBMG_DEVICE_TIMEOUT))
+    return code, st
+
+
+def lbmg_solve_pcg(h, rhs, x, tol, max_iters, precision, stream=None, raise_not_converged=False):
+    """V-cycle-preconditioned conjugate gradients; returns (status, Stats) like lbmg_solve."""
+    st = Stats()
+    code = load_library().lbmg_solve_pcg(h, _ptr(rhs), _ptr(x), _nrhs(rhs), float(tol), int(max_iters),
+                                         int(precision), C.byref(st), _stream(stream))
+    _check(code, "lbmg_solve_pcg", allow=() if raise_not_converged else (LBMG_NOT_CONVERGED, LBMG_DEVICE_TIMEOUT))
     return code, st
 
 

@@ -216,15 +216,20 @@ void enqueue_vcycle(Ctx &c, int R, cudaStream_t s, bool timed, Chain *ch, int to
     }
 }
 
-// one defect-correction step: x += Vcycle(r); r = b - A x; norms(r)
-void enqueue_iteration(Ctx &c, int R, int precision, cudaStream_t s) {
-    DevLevel &F = c.lev[c.D];
-    const int64_t m = (int64_t)F.n * R;
+Chain make_chain(const Ctx &c, cudaStream_t s) {
     Chain ch;
     // the legacy and per-thread default streams take no programmatic serialization
     ch.on = c.pdl != 0 && s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread;
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     ch.capturing = cudaStreamIsCapturing(s, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusActive;
+    return ch;
+}
+
+// one defect-correction step: x += Vcycle(r); r = b - A x; norms(r)
+void enqueue_iteration(Ctx &c, int R, int precision, cudaStream_t s) {
+    DevLevel &F = c.lev[c.D];
+    const int64_t m = (int64_t)F.n * R;
+    Chain ch = make_chain(c, s);
     if (precision == LBMG_MIXED) {
         launch_to_float(c.rs, F.b32, m, s, F.x32, &ch);
         enqueue_vcycle<float>(c, R, s, true, &ch);
@@ -240,16 +245,45 @@ void enqueue_iteration(Ctx &c, int R, int precision, cudaStream_t s) {
     launch_norms(c.rs, F.n, R, c.norm_part, c.norm_out, s, &ch);
 }
 
-int get_graph(lbmg_handle h, int R, int precision, cudaGraphExec_t *out) {
+// one step of conjugate gradients preconditioned by the V-cycle, in the flexible
+// (Polak-Ribiere) form, each right-hand side lane with its own step lengths:
+//   s2 = r.z_old;  z = Vcycle(r);  s1 = r.z;  beta = (s1 - s2) / rz;  rz = s1;
+//   p = z + beta p;  q = -A p;  alpha = s1 / (p.A p);  x += alpha p;  r -= alpha A p;  norms(r)
+void enqueue_pcg_iteration(Ctx &c, int R, int precision, cudaStream_t s) {
+    DevLevel &F = c.lev[c.D];
+    const int64_t m = (int64_t)F.n * R;
+    launch_pcg_dot(c.rs, c.pcg_z, F.n, R, c.pcg_part, c.pcg_s, 0, s);
+    Chain ch = make_chain(c, s);
+    if (precision == LBMG_MIXED) {
+        launch_to_float(c.rs, F.b32, m, s, F.x32, &ch);
+        enqueue_vcycle<float>(c, R, s, true, &ch);
+        to_double_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(F.x32, c.pcg_z, m);
+    } else {
+        cudaMemcpyAsync(F.b64, c.rs, m * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        cudaMemsetAsync(F.x64, 0, m * sizeof(double), s);
+        enqueue_vcycle<double>(c, R, s, true, &ch);
+        cudaMemcpyAsync(c.pcg_z, F.x64, m * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    }
+    launch_pcg_dot(c.rs, c.pcg_z, F.n, R, c.pcg_part, c.pcg_s, 1, s);
+    launch_pcg_direction(c.pcg_z, c.pcg_p, c.pcg_s, F.n, R, s);
+    launch_residual<double>(F, F.A64, c.pcg_zero, c.pcg_p, c.pcg_q, R, s);
+    launch_pcg_dot(c.pcg_p, c.pcg_q, F.n, R, c.pcg_part, c.pcg_s, 2, s);
+    launch_pcg_update(c.xs, c.rs, c.pcg_p, c.pcg_q, c.pcg_s, F.n, R, s);
+    launch_norms(c.rs, F.n, R, c.norm_part, c.norm_out, s);
+}
+
+int get_graph(lbmg_handle h, int R, int precision, bool pcg, cudaGraphExec_t *out) {
     Ctx &c = h->c;
     GraphCache &g = c.graph;
-    if (g.exec && g.R == R && g.precision == precision && g.nu1 == c.nu1 && g.nu2 == c.nu2 && g.smoother == c.smoother) {
+    if (g.exec && g.R == R && g.precision == precision && g.nu1 == c.nu1 && g.nu2 == c.nu2 && g.smoother == c.smoother &&
+        g.pcg == (int)pcg) {
         *out = g.exec;
         return LBMG_OK;
     }
     if (g.exec) { cudaGraphExecDestroy(g.exec); g.exec = nullptr; }
     LBMG_CK(cudaStreamBeginCapture(c.capture_stream, cudaStreamCaptureModeThreadLocal));
-    enqueue_iteration(c, R, precision, c.capture_stream);
+    if (pcg) enqueue_pcg_iteration(c, R, precision, c.capture_stream);
+    else enqueue_iteration(c, R, precision, c.capture_stream);
     cudaGraph_t graph = nullptr;
     LBMG_CK(cudaStreamEndCapture(c.capture_stream, &graph));
     cudaError_t e = cudaGraphInstantiate(&g.exec, graph, 0);
@@ -259,7 +293,7 @@ int get_graph(lbmg_handle h, int R, int precision, cudaGraphExec_t *out) {
         g.exec = nullptr;
         return LBMG_CUDA_ERROR;
     }
-    g.R = R; g.precision = precision; g.nu1 = c.nu1; g.nu2 = c.nu2; g.smoother = c.smoother;
+    g.R = R; g.precision = precision; g.nu1 = c.nu1; g.nu2 = c.nu2; g.smoother = c.smoother; g.pcg = pcg;
     *out = g.exec;
     return LBMG_OK;
 }
@@ -406,6 +440,13 @@ int upload_hierarchy(lbmg_handle h) {
     LBMG_TRY(h->alloc(&c.bs, 4 * nD));
     LBMG_TRY(h->alloc(&c.rs, 4 * nD));
     LBMG_TRY(h->alloc(&c.norm_part, 4 * (size_t)kNormBlocks));
+    LBMG_TRY(h->alloc(&c.pcg_z, 4 * nD));
+    LBMG_TRY(h->alloc(&c.pcg_p, 4 * nD));
+    LBMG_TRY(h->alloc(&c.pcg_q, 4 * nD));
+    LBMG_TRY(h->alloc(&c.pcg_zero, 4 * nD));
+    LBMG_CK(cudaMemset(c.pcg_zero, 0, 4 * nD * sizeof(double)));
+    LBMG_TRY(h->alloc(&c.pcg_s, (size_t)kPcgScalars));
+    LBMG_TRY(h->alloc(&c.pcg_part, 4 * (size_t)kNormBlocks));
     LBMG_TRY(h->alloc(&c.norm_out, 8));
     LBMG_CK(cudaMemset(c.norm_out, 0, 8 * sizeof(double)));
     c.narrow.status = reinterpret_cast<int *>(c.norm_out + 4);
@@ -672,7 +713,7 @@ int lbmg_eval_vertices(lbmg_handle h, const double *x, int nrhs, double *u, void
 }
 
 static int solve_impl(lbmg_handle h, const double *rhs, double *x, int nrhs, double tol, int max_cycles,
-                      int precision, lbmg_stats *stats, void *stream, bool check) {
+                      int precision, lbmg_stats *stats, void *stream, bool check, bool pcg = false) {
     if (!h || !rhs || !x || nrhs < 1 || nrhs > 4 || max_cycles < 0) return LBMG_INVALID_ARG;
     if (precision != LBMG_FP64 && precision != LBMG_MIXED) return LBMG_INVALID_ARG;
     if (!h->c.assembled) return LBMG_NOT_ASSEMBLED;
@@ -687,7 +728,7 @@ static int solve_impl(lbmg_handle h, const double *rhs, double *x, int nrhs, dou
     LBMG_TRY(input_ptr(h, rhs, cnt, 0, s, &rd));
     LBMG_TRY(input_ptr(h, x, cnt, 1, s, &xin));
     LBMG_TRY(output_ptr(h, x, cnt, 1, &xout, &host_out));
-    if (c.persistent && c.persist_ok && c.smoother == LBMG_GS_COLOURED) {
+    if (!pcg && c.persistent && c.persist_ok && c.smoother == LBMG_GS_COLOURED) {
         LBMG_CK(cudaEventRecord(c.ev0, s));
         launch_pack(rd, Fl.n, nrhs, R, c.bs, s, c.fperm);
         launch_pack(xin, Fl.n, nrhs, R, c.xs, s, c.fperm);
@@ -743,12 +784,18 @@ static int solve_impl(lbmg_handle h, const double *rhs, double *x, int nrhs, dou
         return status;
     }
     if (c.ninst > 1) return LBMG_INVALID_ARG;   // batches need the persistent solve (per-mesh norms)
+    if (pcg && c.smoother != LBMG_GS_COLOURED) return LBMG_INVALID_ARG;   // the preconditioner must be symmetric
     cudaGraphExec_t exec = nullptr;
-    if (c.use_graphs) LBMG_TRY(get_graph(h, R, precision, &exec));
+    if (c.use_graphs) LBMG_TRY(get_graph(h, R, precision, pcg, &exec));
     LBMG_CK(cudaEventRecord(c.ev0, s));
     launch_pack(rd, Fl.n, nrhs, R, c.bs, s, c.fperm);
     launch_pack(xin, Fl.n, nrhs, R, c.xs, s, c.fperm);
     launch_residual<double>(Fl, Fl.A64, c.bs, c.xs, c.rs, R, s);
+    if (pcg) {
+        LBMG_CK(cudaMemsetAsync(c.pcg_z, 0, (size_t)Fl.n * R * sizeof(double), s));
+        LBMG_CK(cudaMemsetAsync(c.pcg_p, 0, (size_t)Fl.n * R * sizeof(double), s));
+        LBMG_CK(cudaMemsetAsync(c.pcg_s, 0, kPcgScalars * sizeof(double), s));
+    }
     double nb[4] = {0, 0, 0, 0}, nr[4] = {0, 0, 0, 0}, r0[4] = {0, 0, 0, 0};
     int cycles = 0, status = LBMG_OK;
     float smooth_ms = 0.0f;
@@ -771,6 +818,7 @@ static int solve_impl(lbmg_handle h, const double *rhs, double *x, int nrhs, dou
             if (bad) { status = LBMG_DIVERGED; break; }
             if (conv || cycles >= max_cycles) break;
             if (exec) LBMG_CK(cudaGraphLaunch(exec, s));
+            else if (pcg) enqueue_pcg_iteration(c, R, precision, s);
             else enqueue_iteration(c, R, precision, s);
             LBMG_TRY(read_norms(h, R, s, nr));
             if (c.D > c.d0) {
@@ -796,6 +844,7 @@ static int solve_impl(lbmg_handle h, const double *rhs, double *x, int nrhs, dou
     } else {
         for (int k = 0; k < max_cycles; k++) {
             if (exec) LBMG_CK(cudaGraphLaunch(exec, s));
+            else if (pcg) enqueue_pcg_iteration(c, R, precision, s);
             else enqueue_iteration(c, R, precision, s);
         }
         cycles = max_cycles;
@@ -812,6 +861,12 @@ static int solve_impl(lbmg_handle h, const double *rhs, double *x, int nrhs, dou
         if (!check) stats->cycles = cycles;
     }
     return status;
+}
+
+int lbmg_solve_pcg(lbmg_handle h, const double *rhs, double *x, int nrhs, double tol, int max_iters, int precision,
+                   lbmg_stats *stats, void *stream) {
+    if (!(tol >= 0)) return LBMG_INVALID_ARG;
+    return solve_impl(h, rhs, x, nrhs, tol, max_iters, precision, stats, stream, true, true);
 }
 
 int lbmg_solve(lbmg_handle h, const double *rhs, double *x, int nrhs, double tol, int max_cycles, int precision,

@@ -108,7 +108,7 @@ struct NarrowState {
 
 struct GraphCache {
     cudaGraphExec_t exec = nullptr;
-    int R = 0, precision = -1, nu1 = -1, nu2 = -1, smoother = -1;
+    int R = 0, precision = -1, nu1 = -1, nu2 = -1, smoother = -1, pcg = -1;
 };
 
 struct Ctx {
@@ -152,6 +152,9 @@ struct Ctx {
     // finest FP64 solve vectors, room for [n][4]
     double *xs = nullptr, *bs = nullptr, *rs = nullptr;
     double *norm_part = nullptr, *norm_out = nullptr;
+    // preconditioned conjugate gradients: z, p, q = -A p and a zero vector ([n][4] FP64), scalars, partials
+    double *pcg_z = nullptr, *pcg_p = nullptr, *pcg_q = nullptr, *pcg_zero = nullptr;
+    double *pcg_s = nullptr, *pcg_part = nullptr;
     double *h_norm = nullptr;    // pinned [8]
     // staging of user vectors (device [n][nrhs]) and pinned host mirrors
     double *dev_io = nullptr;
@@ -242,6 +245,13 @@ template <class T> void launch_coarse_apply(const Ctx &c, const DevLevel &L, con
 void launch_coarse_factor(const Ctx &c, const int *const *rps, const int *const *cis, const double *const *As,
                           cudaStream_t s);
 void launch_norms(const double *v, int n, int R, double *part, double *out, cudaStream_t s, Chain *ch = nullptr);
+// conjugate-gradient scalars in Ctx::pcg_s, four lanes each
+enum { kPcgRz = 0, kPcgS1 = 4, kPcgS2 = 8, kPcgAlpha = 12, kPcgBeta = 16, kPcgScalars = 20 };
+void launch_pcg_dot(const double *a, const double *b, int n, int R, double *part, double *sc, int mode,
+                    cudaStream_t s);
+void launch_pcg_direction(const double *z, double *p, const double *sc, int n, int R, cudaStream_t s);
+void launch_pcg_update(double *x, double *r, const double *p, const double *q, const double *sc, int n, int R,
+                       cudaStream_t s);
 void launch_pack(const double *user, int n, int nrhs, int R, double *v, cudaStream_t s, const int *perm = nullptr);
 void launch_unpack(const double *v, int n, int nrhs, int R, double *user, cudaStream_t s, const int *perm = nullptr);
 void launch_to_float(const double *a, float *b, int64_t n, cudaStream_t s, float *zero = nullptr, Chain *ch = nullptr);

@@ -459,6 +459,96 @@ __global__ void __launch_bounds__(256) norm_final_kernel(const double *__restric
     if (threadIdx.x < 4) out[threadIdx.x] = threadIdx.x < R ? sh[0][threadIdx.x] : 0.0;
 }
 
+// ---- conjugate gradients preconditioned by the V-cycle (per right-hand side lane) ----
+// partial sums of a_i . b_i per lane over a grid-stride range
+template <int R>
+__global__ void __launch_bounds__(256) dot_partial_kernel(const double *__restrict__ a, const double *__restrict__ b,
+                                                          int n, double *__restrict__ part) {
+    __shared__ double sh[256][R];
+    double acc[R];
+#pragma unroll
+    for (int r = 0; r < R; r++) acc[r] = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+#pragma unroll
+        for (int r = 0; r < R; r++) acc[r] = fma(a[(size_t)i * R + r], b[(size_t)i * R + r], acc[r]);
+#pragma unroll
+    for (int r = 0; r < R; r++) sh[threadIdx.x][r] = acc[r];
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o)
+#pragma unroll
+            for (int r = 0; r < R; r++) sh[threadIdx.x][r] += sh[threadIdx.x + o][r];
+        __syncthreads();
+    }
+    if (threadIdx.x < R) part[blockIdx.x * 4 + threadIdx.x] = sh[0][threadIdx.x];
+}
+
+// one block: reduce the partial sums to v[lane], then
+//   mode 0: s2 = v                         (r . z of the previous preconditioned residual)
+//   mode 1: s1 = v; beta = (s1 - s2) / rz, rz = s1  (Polak-Ribiere; 0 on the first step, rz = 0)
+//   mode 2: alpha = s1 / (p . A p), with v = p . q and q = -A p
+__global__ void pcg_scalar_kernel(const double *__restrict__ part, int nblocks, int R, double *__restrict__ sc,
+                                  int mode) {
+    __shared__ double sh[256][4];
+    for (int r = 0; r < 4; r++) sh[threadIdx.x][r] = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+        for (int r = 0; r < R; r++) sh[threadIdx.x][r] += part[b * 4 + r];
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o)
+            for (int r = 0; r < 4; r++) sh[threadIdx.x][r] += sh[threadIdx.x + o][r];
+        __syncthreads();
+    }
+    if (threadIdx.x >= R) return;
+    const int r = threadIdx.x;
+    const double v = sh[0][r];
+    double *rz = sc + kPcgRz, *s1 = sc + kPcgS1, *s2 = sc + kPcgS2, *al = sc + kPcgAlpha, *be = sc + kPcgBeta;
+    if (mode == 0) {
+        s2[r] = v;
+    } else if (mode == 1) {
+        s1[r] = v;
+        be[r] = rz[r] > 0.0 ? (v - s2[r]) / rz[r] : 0.0;
+        rz[r] = v;
+    } else {
+        const double pap = -v;
+        al[r] = pap > 0.0 ? s1[r] / pap : 0.0;
+    }
+}
+
+// p = z + beta p
+__global__ void pcg_direction_kernel(const double *__restrict__ z, double *__restrict__ p,
+                                     const double *__restrict__ sc, int64_t m, int R) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q < m) p[q] = fma(sc[kPcgBeta + (int)(q % R)], p[q], z[q]);
+}
+
+// x += alpha p; r += alpha q (q = -A p)
+__global__ void pcg_update_kernel(double *__restrict__ x, double *__restrict__ r, const double *__restrict__ p,
+                                  const double *__restrict__ qv, const double *__restrict__ sc, int64_t m, int R) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= m) return;
+    const double a = sc[kPcgAlpha + (int)(q % R)];
+    x[q] = fma(a, p[q], x[q]);
+    r[q] = fma(a, qv[q], r[q]);
+}
+
+void launch_pcg_dot(const double *a, const double *b, int n, int R, double *part, double *sc, int mode,
+                    cudaStream_t s) {
+    if (R == 1) dot_partial_kernel<1><<<kNormBlocks, 256, 0, s>>>(a, b, n, part);
+    else if (R == 2) dot_partial_kernel<2><<<kNormBlocks, 256, 0, s>>>(a, b, n, part);
+    else dot_partial_kernel<4><<<kNormBlocks, 256, 0, s>>>(a, b, n, part);
+    pcg_scalar_kernel<<<1, 256, 0, s>>>(part, kNormBlocks, R, sc, mode);
+}
+void launch_pcg_direction(const double *z, double *p, const double *sc, int n, int R, cudaStream_t s) {
+    const int64_t m = (int64_t)n * R;
+    if (m) pcg_direction_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(z, p, sc, m, R);
+}
+void launch_pcg_update(double *x, double *r, const double *p, const double *q, const double *sc, int n, int R,
+                       cudaStream_t s) {
+    const int64_t m = (int64_t)n * R;
+    if (m) pcg_update_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(x, r, p, q, sc, m, R);
+}
+
 void launch_norms(const double *v, int n, int R, double *part, double *out, cudaStream_t s, Chain *ch) {
     auto k = R == 1 ? norm_partial_kernel<1> : R == 2 ? norm_partial_kernel<2> : norm_partial_kernel<4>;
     klaunch(k, (unsigned)kNormBlocks, 256u, 0, s, ch, v, n, part);

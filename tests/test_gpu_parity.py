@@ -377,3 +377,32 @@ def test_bounded_copy_wait_reports_timeout_and_context_stays_usable():
     finally:
         L.lbmg_destroy(bad)
         L.lbmg_destroy(good)
+
+
+@pytest.mark.parametrize("precision,tol,err", [(L.LBMG_FP64, 1e-10, 1e-8), (L.LBMG_MIXED, 1e-6, 1e-5)])
+def test_pcg_matches_direct_solution_in_fewer_iterations(case, precision, tol, err):
+    """Conjugate gradients preconditioned by the symmetric V-cycle reach the oracle's
+    direct solution (same tolerances as the V-cycle solve) in about as many or fewer
+    iterations than plain V-cycles.  On the nearly axis-aligned
+    sheets, where plain V-cycles stall near 1e-10, it reaches 1e-10 in FP64.  Its
+    recursively updated residual agrees with b - A x recomputed on the host."""
+    f = np.asarray(case.V, dtype=np.float64)
+    n = case.n(case.D)
+    rhs = torch.zeros((n, 3), dtype=torch.float64, device=DEV)
+    L.lbmg_project_rhs(case.h, _dev(f), rhs)
+    x = torch.zeros_like(rhs)
+    code, st = L.lbmg_solve_pcg(case.h, rhs, x, tol, 1000, precision)
+    assert code == L.LBMG_OK and st.converged == 1
+    assert max(st.rel_residual[:3]) <= tol
+    xd, Mo = _direct(case, rhs.cpu().numpy())
+    assert _mnorm_err(Mo, x.cpu().numpy(), xd) <= err
+    M, Lm = case.lib_matrices(case.D)
+    b = rhs.cpu().numpy()
+    r = b - (M + case.t * Lm) @ x.cpu().numpy()
+    true_rel = np.linalg.norm(r, axis=0) / np.linalg.norm(b, axis=0)
+    assert np.all(true_rel <= 2 * tol)
+    if case.name != "sheets":
+        # never much worse than plain V-cycles, and far better where they converge slowly
+        xv = torch.zeros_like(rhs)
+        code_v, st_v = L.lbmg_solve(case.h, rhs, xv, tol, 3000, precision)
+        assert code_v == L.LBMG_OK and st.cycles <= st_v.cycles + 2
