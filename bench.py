@@ -175,6 +175,185 @@ def reference_main(args):
     print(json.dumps(line), flush=True)
 
 
+def learned_compare(L, V, F, depth, t, f_dev, tol, nrhs, args, dev):
+    """Learned relaxation weights on this mesh: residual histories of plain V-cycles on four
+    random right-hand sides (--learned-skip cycles skipped, 20 kept each), --learned-steps Adam
+    steps of 4 samples at --learned-lr from a network that starts near the plain sweep (omega
+    about 1.05), then the persistent mixed solve of the workload's own right-hand sides with and
+    without the weights, K steps each."""
+    import torch
+    h = L.lbmg_build_hierarchy(V, F, depth, persistent=1)
+    try:
+        L.lbmg_assemble(h, t)
+        n = L.lbmg_level_info(h, depth)[0]
+        rng = np.random.default_rng(7)
+        samp = torch.zeros((n, 4), dtype=torch.float64, device=dev)
+        L.lbmg_project_rhs(h, torch.tensor(rng.uniform(-1, 1, size=(V.shape[0], 4)), device=dev), samp)
+        L.lbmg_learned_collect(h, samp, args.learned_skip, 20)
+        p = np.zeros(L.lbmg_learned_nparams())
+        W1 = np.zeros((32, 64))
+        W1[:28] = rng.normal(0, 0.05, size=(28, 64))
+        p[:32 * 64] = W1.ravel()
+        p[-1] = -8.0
+        L.lbmg_learned_params(h, p)
+        hist = L.lbmg_learned_train(h, rng.integers(0, 80, size=(args.learned_steps, 4)), args.learned_lr)
+        rhs = torch.zeros((n, nrhs), dtype=torch.float64, device=dev)
+        x = torch.zeros_like(rhs)
+        res = {}
+        for name, on in (("plain", False), ("learned", True)):
+            L.lbmg_learned_enable(h, on)
+
+            def lstep():
+                L.lbmg_assemble(h, t)
+                L.lbmg_project_rhs(h, f_dev, rhs)
+                x.zero_()
+                return L.lbmg_solve(h, rhs, x, tol, args.max_cycles, L.LBMG_MIXED)
+            lstep()
+            torch.cuda.synchronize()
+            g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            g0.record()
+            cyc, ok, fb = 0, True, 0
+            for _ in range(args.steps):
+                code, st = lstep()
+                cyc += st.cycles
+                ok = ok and code == L.LBMG_OK
+                fb = max(fb, st.learned_fallback)
+            g1.record()
+            torch.cuda.synchronize()
+            res[name] = {"ms_to_tol": g0.elapsed_time(g1) / args.steps, "cycles_per_step": cyc / args.steps,
+                         "converged": ok, "fallback": fb}
+        om = L.lbmg_learned_omega(h)
+        return {"solve": "persistent, mixed", "train_steps": len(hist), "lr": args.learned_lr,
+                "history_skip": args.learned_skip, "loss_first": float(hist[0]),
+                "loss_last20_mean": float(np.mean(hist[-20:])), "omega_range": [float(om.min()), float(om.max())],
+                **res}
+    finally:
+        L.lbmg_destroy(h)
+
+
+BATCH = "batch64"
+
+
+def batch_main(args):
+    """64 seeded meshes of uneven size (10k-300k triangles; tori, ellipsoids, torus knots;
+    depth 7-9) in one hierarchy, x/y/z right-hand sides, t = 1e-4, mixed precision to 1e-6
+    per mesh in one persistent launch per solve.  A step is assemble + project + solve +
+    vertex evaluation of the whole batch; the value counts every mesh's unknowns."""
+    import torch
+
+    import meshgen
+    import paper_1505_03615_gb300 as L
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    meshes = meshgen.batch_mix(64)
+    t, tol, nrhs = 1e-4, 1e-6, 3
+    hb = L.lbmg_build_batch(meshes)
+    ninst = L.lbmg_instances(hb)
+    nu = sum(L.lbmg_instance_info(hb, i)[2] for i in range(ninst))
+    f = np.concatenate([V for V, _, _ in meshes], axis=0)
+    nv = f.shape[0]
+    f_dev = torch.tensor(f, dtype=torch.float64, device=dev)
+    rhs = torch.zeros((nu, nrhs), dtype=torch.float64, device=dev)
+    x = torch.zeros_like(rhs)
+    u = torch.zeros((nv, nrhs), dtype=torch.float64, device=dev)
+
+    def step(precision=L.LBMG_MIXED, f_in=f_dev, u_out=u):
+        L.lbmg_assemble(hb, t)
+        L.lbmg_project_rhs(hb, f_in, rhs)
+        x.zero_()
+        code, st = L.lbmg_solve(hb, rhs, x, tol, args.max_cycles, precision)
+        if code not in (L.LBMG_OK, L.LBMG_NOT_CONVERGED):
+            raise RuntimeError(f"batch solve failed with status {code}")
+        L.lbmg_eval_vertices(hb, x, u_out)
+        return st
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.25)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    cycles, rel, solve_ms, nconv = 0, 0.0, 0.0, ninst
+    for _ in range(args.steps):
+        st = step()
+        cycles += st.cycles
+        solve_ms += st.ms_total
+        inst = L.lbmg_instance_residuals(hb, nrhs)
+        rel = max(rel, float(inst.max()))
+        nconv = min(nconv, int((inst.max(axis=1) <= tol).sum()))
+    e1.record()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    if ws > 1:
+        mt = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(mt, op=dist.ReduceOp.MAX)
+        ms = mt.item()
+    value = nu * nrhs * cycles * ws / (ms / 1e3)
+    # end to end with pinned host buffers
+    f_pin = torch.tensor(f, dtype=torch.float64).pin_memory()
+    u_pin = torch.zeros((nv, nrhs), dtype=torch.float64).pin_memory()
+    step(f_in=f_pin.numpy(), u_out=u_pin.numpy())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_cycles = 0
+    for _ in range(args.steps):
+        e2e_cycles += step(f_in=f_pin.numpy(), u_out=u_pin.numpy()).cycles
+    torch.cuda.synchronize()
+    e2e_value = nu * nrhs * e2e_cycles * ws / (time.perf_counter() - t0)
+    # plain FP64 on the same batch
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    step(L.LBMG_FP64)
+    torch.cuda.synchronize()
+    g0.record()
+    fp64_cycles = step(L.LBMG_FP64).cycles
+    g1.record()
+    torch.cuda.synchronize()
+    fp64_ms = g0.elapsed_time(g1)
+    peak, peak_kind = _peaks()
+    opts = L.lbmg_default_options()
+    cyc_bytes, fixed_bytes = solve_bytes(hb, opts.nu1 + opts.nu2, nrhs)
+    launch_bytes = cyc_bytes * (cycles / args.steps) + fixed_bytes
+    avg_ms = solve_ms / args.steps
+    achieved = launch_bytes / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else 0.0
+    a_cnt, p_cnt, per_cycle, fixed = L.lbmg_launch_counts(hb, L.LBMG_MIXED)
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 relax / f64 residual+assembly", "data": "synthetic",
+            "config": {"workload": BATCH, "meshes": ninst, "triangles": int(sum(F.shape[0] for _, F, _ in meshes)),
+                       "depths": sorted({int(d) for _, _, d in meshes}), "dofs_finest_total": nu, "nrhs": nrhs,
+                       "t": t, "tol": tol, "precision": "mixed", "solve": "persistent (one launch per solve)",
+                       "l2": "inputs larger than L2 (assembly streams several GB per step)",
+                       "parallelism": "replicas" if ws > 1 else "single"},
+            "ms_to_tol_mixed": ms / args.steps, "ms_to_tol_fp64": fp64_ms, "cycles_per_step": cycles / args.steps,
+            "fp64_cycles_per_step": fp64_cycles, "max_rel_residual_per_mesh": rel,
+            "meshes_converged": nconv, "max_cycles": args.max_cycles,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "kernel": "solve_persistent_kernel<float,4> (whole mixed batch solve)",
+                         "peak_kind": peak_kind, "bytes_per_launch": launch_bytes, "avg_launch_ms": avg_ms},
+            "cpu_baseline": None,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(nv * nrhs * 8),
+                    "d2h_bytes_per_step": int(nv * nrhs * 8)},
+            "gpu_launches": int(args.steps * (a_cnt + p_cnt + 4 + 1)), "clocks": clk,
+        }), flush=True)
+    L.lbmg_destroy(hb)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -188,6 +367,13 @@ def main():
     ap.add_argument("--only-timed", action="store_true", help="stop after the timed steps (profiling runs)")
     ap.add_argument("--no-pdl", action="store_true", help="plain stream order between the cycle's kernels")
     ap.add_argument("--no-tune", action="store_true", help="default launch shapes (no autotuning at setup)")
+    ap.add_argument("--learned", action="store_true",
+                    help="also train the learned relaxation weights on this mesh (setup, untimed) and time the "
+                         "persistent mixed solve with and without them")
+    ap.add_argument("--learned-steps", type=int, default=150, help="Adam steps of the learned weights")
+    ap.add_argument("--learned-lr", type=float, default=2e-3)
+    ap.add_argument("--learned-skip", type=int, default=3,
+                    help="plain V-cycles skipped before residuals are kept for training")
     ap.add_argument("--solver", default="vcycle", choices=["vcycle", "pcg"],
                     help="V-cycle iteration (the paper's solver, default) or V-cycle-preconditioned CG")
     ap.add_argument("--workload", default=WORKLOAD,
@@ -199,6 +385,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_main(args)
+    if args.workload == BATCH:
+        return batch_main(args)
 
     import torch
 
@@ -353,6 +541,10 @@ def main():
         other_res[name] = {"ms_to_tol": g0.elapsed_time(g1) / fp64_steps, "cycles_per_step": its / fp64_steps,
                            "converged": ok}
 
+    learned = None
+    if args.learned:
+        learned = learned_compare(L, V, F, depth, t, f_dev, tol, nrhs, args, dev)
+
     # roofline of the dominant kernel, timed live with CUDA events on its stream
     a_cnt, p_cnt, per_cycle, fixed = L.lbmg_launch_counts(h, L.LBMG_MIXED)
     opts = L.lbmg_default_options()
@@ -415,7 +607,7 @@ def main():
                                                for d, v in shapes.items()},
                        "tuned_us_per_sweep_and_residual": tuned_us},
             "ms_to_tol_mixed": ms_per_step, "ms_to_tol_fp64": fp64_ms, "solver": args.solver,
-            "other_solver": {"solver": other, **other_res},
+            "other_solver": {"solver": other, **other_res}, "learned": learned,
             "cycles_per_step": cycles / args.steps, "fp64_cycles_per_step": fp64_cycles / fp64_steps,
             "max_rel_residual": rel,
             "roofline": roofline, "cpu_baseline": cpu_baseline,

@@ -101,6 +101,8 @@ typedef struct lbmg_stats {
 typedef struct lbmg_ctx *lbmg_handle;
 
 const char *lbmg_status_string(int code);
+/* message of the last failure on this thread: the CUDA call that failed, or, after a
+   failed lbmg_build_hierarchy / lbmg_build_batch, the host builder's reason */
 const char *lbmg_last_cuda_error(void);
 void lbmg_default_options(lbmg_options *o);
 

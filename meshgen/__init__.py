@@ -186,7 +186,9 @@ def batch_mix(count=64, min_tris=10_000, max_tris=300_000, seed=7):
     """Seeded list of (V, F, depth) of uneven size: tori, ellipsoids, torus knots.
 
     Triangle counts are drawn log-uniformly in [min_tris, max_tris]; depth is
-    7 below 40k triangles, 8 below 120k and 9 above.
+    7 below 100k triangles, 8 below 250k and 9 above, which keeps the 64-mesh
+    batch at about 170M stored entries on its finest level (one deeper level per
+    mesh would quadruple that).
     """
     rng = _rng(seed)
     out = []
@@ -208,7 +210,7 @@ def batch_mix(count=64, min_tris=10_000, max_tris=300_000, seed=7):
                                    n_seg=max(40, nt // (2 * ring)), n_ring=ring,
                                    seed=int(rng.integers(1 << 30)))
         ntr = F.shape[0]
-        depth = 7 if ntr < 40_000 else (8 if ntr < 120_000 else 9)
+        depth = 7 if ntr < 100_000 else (8 if ntr < 250_000 else 9)
         out.append((V, F, depth))
     return out
 

@@ -42,8 +42,10 @@ _lib = None
 class LbmgError(RuntimeError):
     def __init__(self, code, where):
         msg = f"{where}: {_lib.lbmg_status_string(code).decode()} ({code})" if _lib else f"{where}: status {code}"
-        if _lib is not None and code == 7:
-            msg += " -- " + _lib.lbmg_last_cuda_error().decode()
+        if _lib is not None and (code == 7 or where.startswith("lbmg_build")):
+            detail = _lib.lbmg_last_cuda_error().decode()
+            if detail:
+                msg += " -- " + detail
         super().__init__(msg)
         self.code = code
 

@@ -447,6 +447,7 @@ int upload_hierarchy(lbmg_handle h) {
     LBMG_CK(cudaMemset(c.pcg_zero, 0, 4 * nD * sizeof(double)));
     LBMG_TRY(h->alloc(&c.pcg_s, (size_t)kPcgScalars));
     LBMG_TRY(h->alloc(&c.pcg_part, 4 * (size_t)kNormBlocks));
+    LBMG_TRY(h->alloc(&c.diag_part, 256));
     LBMG_TRY(h->alloc(&c.norm_out, 8));
     LBMG_CK(cudaMemset(c.norm_out, 0, 8 * sizeof(double)));
     c.narrow.status = reinterpret_cast<int *>(c.norm_out + 4);
@@ -555,10 +556,18 @@ int lbmg_build_hierarchy(const double *V, int nv, const int *F, int nt, int dept
         if (st == 0) st = combine_batch(parts, h->c.host, err);
     } catch (const std::bad_alloc &) {
         st = LBMG_OUT_OF_MEMORY;
+        err = "host memory exhausted";
+    } catch (const std::exception &e) {
+        st = LBMG_INVALID_ARG;
+        err = e.what();
     } catch (...) {
         st = LBMG_INVALID_ARG;
     }
-    if (st != 0) { delete h; return st; }
+    if (st != 0) {
+        g_cuda_err = "hierarchy build: " + err;
+        delete h;
+        return st;
+    }
     h->c.nu1 = o.nu1;
     h->c.nu2 = o.nu2;
     h->c.smoother = o.smoother;
@@ -598,10 +607,18 @@ int lbmg_build_batch(const double *const *V, const int *nv, const int *const *F,
         if (st == 0) st = combine_batch(parts, h->c.host, err);
     } catch (const std::bad_alloc &) {
         st = LBMG_OUT_OF_MEMORY;
+        err = "host memory exhausted";
+    } catch (const std::exception &e) {
+        st = LBMG_INVALID_ARG;
+        err = e.what();
     } catch (...) {
         st = LBMG_INVALID_ARG;
     }
-    if (st != 0) { delete h; return st; }
+    if (st != 0) {
+        g_cuda_err = "hierarchy build: " + err;
+        delete h;
+        return st;
+    }
     h->c.nu1 = o.nu1; h->c.nu2 = o.nu2; h->c.smoother = o.smoother; h->c.omega = o.jacobi_omega;
     h->c.persistent = 1; h->c.persist_narrow = o.narrow_max; h->c.barrier_phantoms = o.barrier_phantoms;
     st = upload_hierarchy(h);
@@ -671,7 +688,7 @@ int lbmg_assemble(lbmg_handle h, double t, void *stream) {
     launch_fragment_moments(c, s);
     launch_fine_gather(c, t, s);
     for (int d = c.D - 1; d >= c.d0; d--) launch_galerkin(c, d, t, s);
-    for (int d = c.d0; d <= c.D; d++) launch_inverse_diag(c.lev[d], s);
+    for (int d = c.d0; d <= c.D; d++) launch_inverse_diag(c.lev[d], c.diag_part, s);
     cudaMemsetAsync(c.flag, 0, sizeof(int), s);
     launch_coarse_factor(c, h->lev_rp, h->lev_ci, h->lev_A, s);
     narrow_smem_refresh(c, s);

@@ -15,6 +15,8 @@
 // stored entry's contributions through a precomputed list (no atomics).  Coarser
 // levels are the Galerkin products P^T A P of Eq. 4's prolongation, summed the
 // same way.
+#include <algorithm>
+
 #include "lbmg_internal.h"
 
 namespace lbmg {
@@ -237,8 +239,8 @@ __global__ void galerkin_kernel(int64_t nnz, const int64_t *__restrict__ grp, co
     double m = 0.0, l = 0.0;
     for (int64_t k = grp[s]; k < grp[s + 1]; k++) {
         const uint32_t e = gidx[k];
-        const uint32_t idx = e & kPackMask;
-        const double w = ldexp(1.0, -(int)(e >> kPackShift));
+        const uint32_t idx = e & kGalMask;
+        const double w = ldexp(1.0, -(int)(e >> kGalShift));
         m = fma(w, Mf[idx], m);
         l = fma(w, Lf[idx], l);
     }
@@ -256,20 +258,66 @@ void launch_galerkin(const Ctx &c, int dc, double t, cudaStream_t s) {
         Lc.nnz, Lc.grp, Lc.gidx, Lf.M, Lf.L, t, Lc.M, Lc.L, Lc.A64, Lc.A32);
 }
 
-__global__ void inverse_diag_kernel(int n, const int *__restrict__ rp, const int *__restrict__ ci,
-                                    const double *__restrict__ A64, double *__restrict__ d64, float *__restrict__ d32) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int end = rp[i + 1];
-    int lo = rp[i], hi = end;
-    while (lo < hi) { int mid = (lo + hi) >> 1; if (ci[mid] < i) lo = mid + 1; else hi = mid; }
-    const double inv = (lo < end && ci[lo] == i) ? 1.0 / A64[lo] : 0.0;
-    d64[i] = inv;
-    d32[i] = (float)inv;
+// Relaxation skips rows whose diagonal is below this fraction of the level's mean
+// diagonal (or not positive).  Such functions meet the mesh in slivers where the hat
+// and its tangential gradient nearly vanish: their diagonals, down to 1e-40 of the mean,
+// lie below the rounding error of the moment contraction that produced them (so they can
+// even come out negative), below FP32's range (1/a_ii overflows), and they carry no
+// measurable mass or stiffness.  Their coefficients stay at zero correction; the residual
+// still includes their rows.
+constexpr double kDiagFloor = 1e-20;
+constexpr int kDiagBlocks = 256;
+
+// per-block partial sums of the diagonal A_ii
+__global__ void __launch_bounds__(256) diag_sum_kernel(int n, const int *__restrict__ rp, const int *__restrict__ ci,
+                                                       const double *__restrict__ A64, double *__restrict__ part) {
+    __shared__ double sh[256];
+    double sum = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int end = rp[i + 1];
+        int lo = rp[i], hi = end;
+        while (lo < hi) { int mid = (lo + hi) >> 1; if (ci[mid] < i) lo = mid + 1; else hi = mid; }
+        sum += (lo < end && ci[lo] == i) ? A64[lo] : 0.0;
+    }
+    sh[threadIdx.x] = sum;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
 }
 
-void launch_inverse_diag(const DevLevel &L, cudaStream_t s) {
-    inverse_diag_kernel<<<(L.n + 255) / 256, 256, 0, s>>>(L.n, L.rp, L.ci, L.A64, L.dinv64, L.dinv32);
+// FP64 and FP32 inverse diagonals, 0 for rows below the floor
+__global__ void __launch_bounds__(256) inverse_diag_kernel(int n, const int *__restrict__ rp,
+                                                           const int *__restrict__ ci, const double *__restrict__ A64,
+                                                           const double *__restrict__ part, int nparts,
+                                                           double *__restrict__ d64, float *__restrict__ d32) {
+    __shared__ double s_thr;
+    if (threadIdx.x == 0) {
+        double sum = 0.0;
+        for (int b = 0; b < nparts; b++) sum += part[b];
+        s_thr = kDiagFloor * (sum / (double)n);
+    }
+    __syncthreads();
+    const double thr = s_thr;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int end = rp[i + 1];
+        int lo = rp[i], hi = end;
+        while (lo < hi) { int mid = (lo + hi) >> 1; if (ci[mid] < i) lo = mid + 1; else hi = mid; }
+        const double a = (lo < end && ci[lo] == i) ? A64[lo] : 0.0;
+        const double inv = (a > 0.0 && a >= thr) ? 1.0 / a : 0.0;
+        d64[i] = inv;
+        d32[i] = (float)inv;
+    }
+}
+
+void launch_inverse_diag(const DevLevel &L, double *part, cudaStream_t s) {
+    if (L.n == 0) return;
+    const int blocks = std::min(kDiagBlocks, (L.n + 255) / 256);
+    diag_sum_kernel<<<blocks, 256, 0, s>>>(L.n, L.rp, L.ci, L.A64, part);
+    inverse_diag_kernel<<<std::min(1024, (L.n + 255) / 256), 256, 0, s>>>(L.n, L.rp, L.ci, L.A64, part, blocks,
+                                                                         L.dinv64, L.dinv32);
 }
 
 // right-hand side: int f b_a over each fragment from its moments, f affine on the triangle

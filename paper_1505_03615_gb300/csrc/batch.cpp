@@ -219,9 +219,9 @@ int combine_batch(std::vector<HostHierarchy> &parts, HostHierarchy &B, std::stri
                     int64_t o = L.grp[nmap[i][k]];
                     for (int64_t q = P.grp[k]; q < P.grp[k + 1]; q++) {
                         const uint32_t e = P.gidx[q];
-                        const int32_t idx = nmapF[i][e & kPackMask];
-                        if ((uint32_t)idx > kPackMask) { err = "batch level too large for packed lists"; return 1; }
-                        L.gidx[o++] = (uint32_t)idx | (e & ~kPackMask);
+                        const int32_t idx = nmapF[i][e & kGalMask];
+                        if ((uint32_t)idx > kGalMask) { err = "batch level too large for packed Galerkin lists"; return 1; }
+                        L.gidx[o++] = (uint32_t)idx | (e & ~kGalMask);
                     }
                 }
             }

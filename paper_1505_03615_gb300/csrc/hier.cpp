@@ -586,11 +586,11 @@ int build_host_hierarchy(const double *V, int nv, const int *F, int nt, int dept
                         for (int b = 0; b < (1 << Lf.npar_log2[l]); b++) {
                             row[q] = Lf.par[8 * (size_t)i + a];
                             col[q] = Lf.par[8 * (size_t)l + b];
-                            val[q] = (uint32_t)k | (e << kPackShift);
+                            val[q] = (uint32_t)k | (e << kGalShift);
                             q++;
                         }
                 }
-            if (nnzf > (int64_t)kPackMask) { err = "level too large for packed contribution lists"; return 1; }
+            if (nnzf > (int64_t)kGalMask) { err = "level too large for packed Galerkin lists"; return 1; }
             pattern_from_pairs(Lc.ndof, row, col, Lc);
             std::vector<int32_t> slot(tot);
 #pragma omp parallel for schedule(static)

@@ -11,6 +11,10 @@ constexpr int kMaxDepth = 12;
 constexpr double kFragTau = 1e-12;   // pieces of at most this area (finest voxel faces) are ignored
 constexpr int kPackShift = 28;       // packed list entry: index | (log2 weight denominator << 28)
 constexpr uint32_t kPackMask = (1u << kPackShift) - 1u;
+// Galerkin list entry: fine stored-entry index | (log2 weight denominator << 29); the
+// exponent is at most 6 (three bits), so the index may reach 2^29 - 1
+constexpr int kGalShift = 29;
+constexpr uint32_t kGalMask = (1u << kGalShift) - 1u;
 
 struct HostLevel {
     int d = 0;

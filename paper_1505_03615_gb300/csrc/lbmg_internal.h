@@ -152,6 +152,7 @@ struct Ctx {
     // finest FP64 solve vectors, room for [n][4]
     double *xs = nullptr, *bs = nullptr, *rs = nullptr;
     double *norm_part = nullptr, *norm_out = nullptr;
+    double *diag_part = nullptr;   // [256] per-block sums of a level's diagonal
     // preconditioned conjugate gradients: z, p, q = -A p and a zero vector ([n][4] FP64), scalars, partials
     double *pcg_z = nullptr, *pcg_p = nullptr, *pcg_q = nullptr, *pcg_zero = nullptr;
     double *pcg_s = nullptr, *pcg_part = nullptr;
@@ -222,7 +223,9 @@ size_t persist_view_bytes();
 void launch_fragment_moments(const Ctx &c, cudaStream_t s);
 void launch_fine_gather(const Ctx &c, double t, cudaStream_t s);
 void launch_galerkin(const Ctx &c, int dc, double t, cudaStream_t s);
-void launch_inverse_diag(const DevLevel &L, cudaStream_t s);
+// FP64 and FP32 inverse diagonals, 0 for rows below 1e-20 of the level's mean diagonal;
+// part: 256 doubles of scratch (per-block sums of the diagonal)
+void launch_inverse_diag(const DevLevel &L, double *part, cudaStream_t s);
 void launch_project_rhs(const Ctx &c, const double *fv, int nrhs, double *rhs_out, cudaStream_t s);
 void launch_eval_vertices(const Ctx &c, const double *x, int nrhs, double *u, cudaStream_t s);
 

@@ -150,14 +150,16 @@ __global__ void __launch_bounds__(256) mlp_forward_kernel(int n, const __nv_bflo
 
 // omega = 1.45 + 0.45 y / (1 + |y|); learned inverse diagonals omega / a_ii
 __global__ void omega_kernel(int n, const float *__restrict__ y, const double *__restrict__ dinv64,
-                             double *__restrict__ omega, double *__restrict__ dl64, float *__restrict__ dl32) {
+                             const float *__restrict__ dinv32, double *__restrict__ omega, double *__restrict__ dl64,
+                             float *__restrict__ dl32) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double yy = (double)y[i];
     const double om = 1.45 + 0.45 * yy / (1.0 + fabs(yy));
     omega[i] = om;
     if (dl64) dl64[i] = om * dinv64[i];
-    if (dl32) dl32[i] = (float)(om * dinv64[i]);
+    // rows that relaxation skips (inverse diagonal 0) stay skipped
+    if (dl32) dl32[i] = dinv32[i] != 0.f ? (float)(om * dinv64[i]) : 0.f;
 }
 
 // ---------------------------------------------------------------- V-cycle adjoint pieces
@@ -467,7 +469,7 @@ static int learned_loss_grad_dev(Ctx &c, int ns, bool need_grad, double *loss, c
     const int64_t m4 = (int64_t)n * 4;
     const unsigned g4 = (unsigned)((m4 + 255) / 256);
     learned_forward(c, need_grad, s);
-    omega_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, L->y, F.dinv64, L->omega, nullptr, nullptr);
+    omega_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, L->y, F.dinv64, F.dinv32, L->omega, nullptr, nullptr);
     // forward through the cycle
     int sidx = 0;
     auto snap = [&](int k) { return L->snap + (size_t)k * m4; };
@@ -606,7 +608,7 @@ int learned_enable(Ctx &c, int on, cudaStream_t s) {
     DevLevel &F = c.lev[c.D];
     learned_features(c, s);
     learned_forward(c, false, s);
-    omega_kernel<<<(F.n + 255) / 256, 256, 0, s>>>(F.n, L->y, F.dinv64, L->omega, L->dl64, L->dl32);
+    omega_kernel<<<(F.n + 255) / 256, 256, 0, s>>>(F.n, L->y, F.dinv64, F.dinv32, L->omega, L->dl64, L->dl32);
     c.learned_dinv64 = L->dl64;
     c.learned_dinv32 = L->dl32;
     c.learned_on = 1;

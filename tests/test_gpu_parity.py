@@ -148,11 +148,20 @@ def test_restriction_and_prolongation_match_oracle(case):
         assert _rel(out.cpu().numpy(), xf + P @ xc) <= 1e-13
 
 
-def _coloured_gs_reference(A, corner, b, x, sweeps):
-    """Gauss-Seidel by corner-parity colour (rows of one colour updated together)."""
+# relaxation leaves rows whose diagonal is below 1e-20 of the level's mean diagonal (or not
+# positive) unrelaxed: sliver functions whose diagonals lie below the assembly's rounding
+# error and FP32's range
+DIAG_FLOOR = 1e-20
+
+
+def _coloured_gs_reference(A, corner, b, x, sweeps, floor=DIAG_FLOOR):
+    """Gauss-Seidel by corner-parity colour (rows of one colour updated together); rows
+    whose diagonal is not positive or below floor * mean diagonal are not relaxed."""
     x = x.copy()
     colour = (corner[:, 0] & 1) | ((corner[:, 1] & 1) << 1) | ((corner[:, 2] & 1) << 2)
-    dinv = 1.0 / A.diagonal()
+    dg = A.diagonal()
+    keep = (dg > 0) & (dg >= floor * dg.mean())
+    dinv = np.where(keep, 1.0 / np.where(keep, dg, 1.0), 0.0)
     for _ in range(sweeps):
         for c in range(8):
             rows = np.where(colour == c)[0]
@@ -406,3 +415,35 @@ def test_pcg_matches_direct_solution_in_fewer_iterations(case, precision, tol, e
         xv = torch.zeros_like(rhs)
         code_v, st_v = L.lbmg_solve(case.h, rhs, xv, tol, 3000, precision)
         assert code_v == L.LBMG_OK and st.cycles <= st_v.cycles + 2
+
+
+def test_mixed_precision_skips_sliver_functions_below_fp32_range():
+    """A torus of the seeded 64-mesh batch (34k triangles, depth 7) has split functions whose
+    supports meet it in slivers where the hat and its tangential gradient nearly vanish: their
+    diagonals reach 1e-40 of the level's mean, below the assembly's rounding error and FP32's
+    range.  Relaxation leaves such rows (diagonal under 1e-20 of the mean, or not positive)
+    alone instead of dividing by them; the mixed solve, V-cycles or CG, then reaches 1e-6,
+    checked by the residual recomputed on the host."""
+    V, F, depth = meshgen.batch_mix(39)[38]
+    t = 1e-4
+    h = L.lbmg_build_hierarchy(V, F, depth)
+    try:
+        L.lbmg_assemble(h, t)
+        rp, ci, M, Lm = L.lbmg_get_matrix(h, depth)
+        n = len(rp) - 1
+        A = sp.csr_matrix((M, ci, rp), shape=(n, n)) + t * sp.csr_matrix((Lm, ci, rp), shape=(n, n))
+        dg = A.diagonal()
+        assert dg.min() < 1e-30 * dg.mean()          # the case this test is about
+        rhs = torch.zeros((n, 3), dtype=torch.float64, device=DEV)
+        L.lbmg_project_rhs(h, _dev(V), rhs)
+        b = rhs.cpu().numpy()
+        for solve in (L.lbmg_solve, L.lbmg_solve_pcg):
+            x = torch.zeros_like(rhs)
+            code, st = solve(h, rhs, x, 1e-6, 3000, L.LBMG_MIXED)
+            assert code == L.LBMG_OK and st.converged
+            xx = x.cpu().numpy()
+            assert np.isfinite(xx).all()
+            rel = np.linalg.norm(b - A @ xx, axis=0) / np.linalg.norm(b, axis=0)
+            assert np.all(rel <= 2e-6)
+    finally:
+        L.lbmg_destroy(h)

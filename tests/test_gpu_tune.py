@@ -39,10 +39,14 @@ def _system(h, d, t):
     return Mm, (Mm + t * sp.csr_matrix((Lm, ci, rp), shape=(n, n))).tocsr()
 
 
-def _colour_sweeps(A, corner, b, x, sweeps):
+def _colour_sweeps(A, corner, b, x, sweeps, floor=1e-20):
+    """Colour-by-colour Gauss-Seidel; rows whose diagonal is not positive or below
+    floor * mean diagonal are not relaxed (the library's rule for sliver functions)."""
     x = x.copy()
     colour = (corner[:, 0] & 1) | ((corner[:, 1] & 1) << 1) | ((corner[:, 2] & 1) << 2)
-    dinv = 1.0 / A.diagonal()
+    dg = A.diagonal()
+    keep = (dg > 0) & (dg >= floor * dg.mean())
+    dinv = np.where(keep, 1.0 / np.where(keep, dg, 1.0), 0.0)
     for _ in range(sweeps):
         for c in range(8):
             rows = np.where(colour == c)[0]
