@@ -266,7 +266,8 @@ def batch_main(args):
         L.lbmg_assemble(hb, t)
         L.lbmg_project_rhs(hb, f_in, rhs)
         x.zero_()
-        code, st = L.lbmg_solve(hb, rhs, x, tol, args.max_cycles, precision)
+        solve = L.lbmg_solve_pcg if args.solver == "pcg" else L.lbmg_solve
+        code, st = solve(hb, rhs, x, tol, args.max_cycles, precision)
         if code not in (L.LBMG_OK, L.LBMG_NOT_CONVERGED):
             raise RuntimeError(f"batch solve failed with status {code}")
         L.lbmg_eval_vertices(hb, x, u_out)
@@ -335,14 +336,18 @@ def batch_main(args):
             "vs_baseline": None, "dtype": "f32 relax / f64 residual+assembly", "data": "synthetic",
             "config": {"workload": BATCH, "meshes": ninst, "triangles": int(sum(F.shape[0] for _, F, _ in meshes)),
                        "depths": sorted({int(d) for _, _, d in meshes}), "dofs_finest_total": nu, "nrhs": nrhs,
-                       "t": t, "tol": tol, "precision": "mixed", "solve": "persistent (one launch per solve)",
+                       "t": t, "tol": tol, "precision": "mixed",
+                       "solve": ("V-cycle-preconditioned CG, per-mesh step lengths, graph per iteration"
+                                 if args.solver == "pcg" else "V-cycles, persistent (one launch per solve)"),
                        "l2": "inputs larger than L2 (assembly streams several GB per step)",
                        "parallelism": "replicas" if ws > 1 else "single"},
             "ms_to_tol_mixed": ms / args.steps, "ms_to_tol_fp64": fp64_ms, "cycles_per_step": cycles / args.steps,
             "fp64_cycles_per_step": fp64_cycles, "max_rel_residual_per_mesh": rel,
             "meshes_converged": nconv, "max_cycles": args.max_cycles,
+            "solver": args.solver,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": None, "kernel": "solve_persistent_kernel<float,4> (whole mixed batch solve)",
+                         "traffic": None, "kernel": ("whole mixed batch solve, algorithmic bytes of its V-cycles "
+                                                     "and FP64 steps over its device time"),
                          "peak_kind": peak_kind, "bytes_per_launch": launch_bytes, "avg_launch_ms": avg_ms},
             "cpu_baseline": None,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(nv * nrhs * 8),

@@ -200,8 +200,11 @@ int lbmg_solve(lbmg_handle h, const double *rhs, double *x, int nrhs, double tol
  * residual) and statistics as for lbmg_solve; stats->cycles counts iterations,
  * one V-cycle each.  Near-null modes that plain V-cycles reduce slowly (nearly
  * axis-aligned sheets, Discussion of Section 5) are taken out by the Krylov
- * recurrence.  Single meshes only and only with the coloured Gauss-Seidel
- * smoother (LBMG_INVALID_ARG otherwise); the persistent option does not apply.
+ * recurrence.  Only with the coloured Gauss-Seidel smoother (LBMG_INVALID_ARG
+ * otherwise); the persistent option does not apply.  On a batch every mesh has its
+ * own step lengths (per-mesh dot products), the solve stops when every mesh and
+ * right-hand side meets tol, stats->rel_residual holds the worst mesh per right-hand
+ * side, and lbmg_instance_residuals reports each mesh afterwards.
  */
 int lbmg_solve_pcg(lbmg_handle h, const double *rhs, double *x, int nrhs, double tol, int max_iters,
                    int precision, lbmg_stats *stats, void *stream);

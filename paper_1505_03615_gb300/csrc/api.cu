@@ -67,6 +67,7 @@ struct lbmg_ctx {
     std::vector<double> inst_norm_host;                 // last solve: [ninst][12]
     size_t io_cap = 0;   // doubles per io slot
     int *h_flag = nullptr;
+    double pcg_tol_host = 0.0;   // source of the tolerance copy of a running batch solve
 
     template <class T>
     int alloc(T **p, size_t count) {
@@ -272,6 +273,35 @@ void enqueue_pcg_iteration(Ctx &c, int R, int precision, cudaStream_t s) {
     launch_norms(c.rs, F.n, R, c.norm_part, c.norm_out, s);
 }
 
+// the same step for a batch: every mesh has its own step lengths (per-mesh dot products
+// over the finest-level work items), and the per-mesh norms of r and b end the step
+void enqueue_pcg_batch_iteration(Ctx &c, int R, int precision, cudaStream_t s) {
+    DevLevel &F = c.lev[c.D];
+    const int64_t m = (int64_t)F.n * R;
+    launch_item_dot2(c.nitem, c.nnitem, c.rs, c.pcg_z, nullptr, nullptr, R, c.item_part, s);
+    launch_inst_pcg_scalar(c.item_start, c.ninst, R, c.item_part, c.pcg_si, 0, c.inst_norm, c.pcg_tol, s);
+    Chain ch = make_chain(c, s);
+    if (precision == LBMG_MIXED) {
+        launch_to_float(c.rs, F.b32, m, s, F.x32, &ch);
+        enqueue_vcycle<float>(c, R, s, false, &ch);
+        to_double_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(F.x32, c.pcg_z, m);
+    } else {
+        cudaMemcpyAsync(F.b64, c.rs, m * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        cudaMemsetAsync(F.x64, 0, m * sizeof(double), s);
+        enqueue_vcycle<double>(c, R, s, false, &ch);
+        cudaMemcpyAsync(c.pcg_z, F.x64, m * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    }
+    launch_item_dot2(c.nitem, c.nnitem, c.rs, c.pcg_z, nullptr, nullptr, R, c.item_part, s);
+    launch_inst_pcg_scalar(c.item_start, c.ninst, R, c.item_part, c.pcg_si, 1, c.inst_norm, c.pcg_tol, s);
+    launch_inst_pcg_direction(c.pcg_z, c.pcg_p, c.pcg_si, c.row_inst, F.n, R, s);
+    launch_residual<double>(F, F.A64, c.pcg_zero, c.pcg_p, c.pcg_q, R, s);
+    launch_item_dot2(c.nitem, c.nnitem, c.pcg_p, c.pcg_q, nullptr, nullptr, R, c.item_part, s);
+    launch_inst_pcg_scalar(c.item_start, c.ninst, R, c.item_part, c.pcg_si, 2, c.inst_norm, c.pcg_tol, s);
+    launch_inst_pcg_update(c.xs, c.rs, c.pcg_p, c.pcg_q, c.pcg_si, c.row_inst, F.n, R, s);
+    launch_item_dot2(c.nitem, c.nnitem, c.rs, c.rs, c.bs, c.bs, R, c.item_part, s);
+    launch_inst_sum(c.item_start, c.ninst, c.item_part, c.inst_norm, 16, s);
+}
+
 int get_graph(lbmg_handle h, int R, int precision, bool pcg, cudaGraphExec_t *out) {
     Ctx &c = h->c;
     GraphCache &g = c.graph;
@@ -282,7 +312,8 @@ int get_graph(lbmg_handle h, int R, int precision, bool pcg, cudaGraphExec_t *ou
     }
     if (g.exec) { cudaGraphExecDestroy(g.exec); g.exec = nullptr; }
     LBMG_CK(cudaStreamBeginCapture(c.capture_stream, cudaStreamCaptureModeThreadLocal));
-    if (pcg) enqueue_pcg_iteration(c, R, precision, c.capture_stream);
+    if (pcg && c.ninst > 1) enqueue_pcg_batch_iteration(c, R, precision, c.capture_stream);
+    else if (pcg) enqueue_pcg_iteration(c, R, precision, c.capture_stream);
     else enqueue_iteration(c, R, precision, c.capture_stream);
     cudaGraph_t graph = nullptr;
     LBMG_CK(cudaStreamEndCapture(c.capture_stream, &graph));
@@ -418,6 +449,16 @@ int upload_hierarchy(lbmg_handle h) {
         }
     c.nnitem = (int)(c.nitem_host.size() / 3);
     LBMG_TRY(h->upload(&c.nitem, c.nitem_host));
+    {
+        // the items are generated mesh by mesh: mesh m owns items [start[m], start[m + 1])
+        std::vector<int32_t> start(c.ninst + 1, 0);
+        for (int it = 0; it < c.nnitem; it++) start[c.nitem_host[3 * it] + 1]++;
+        for (int m = 0; m < c.ninst; m++) start[m + 1] += start[m];
+        LBMG_TRY(h->upload(&c.item_start, start));
+        LBMG_TRY(h->upload(&c.row_inst, H.lev[H.D].inst));
+        LBMG_TRY(h->alloc(&c.pcg_si, (size_t)kPcgScalars * c.ninst));
+        LBMG_TRY(h->alloc(&c.pcg_tol, 1));
+    }
     LBMG_TRY(h->alloc(&c.item_part, 8 * (size_t)std::max(c.nnitem, 1)));
     LBMG_TRY(h->alloc(&c.inst_norm, 16 * (size_t)c.ninst));
     {
@@ -729,6 +770,85 @@ int lbmg_eval_vertices(lbmg_handle h, const double *x, int nrhs, double *u, void
     return finish_output(u, ud, (size_t)h->c.nv * nrhs, host_out, s);
 }
 
+// V-cycle-preconditioned conjugate gradients on a batch: per-mesh step lengths and norms;
+// stops when every mesh meets tol (or after max_iters iterations)
+static int solve_pcg_batch(lbmg_handle h, const double *rd, const double *xin, double *xout, bool host_out,
+                           double *x, size_t cnt, int nrhs, int R, double tol, int max_iters, int precision,
+                           lbmg_stats *stats, cudaStream_t s) {
+    Ctx &c = h->c;
+    DevLevel &Fl = c.lev[c.D];
+    cudaGraphExec_t exec = nullptr;
+    if (c.use_graphs) LBMG_TRY(get_graph(h, R, precision, true, &exec));
+    LBMG_CK(cudaEventRecord(c.ev0, s));
+    launch_pack(rd, Fl.n, nrhs, R, c.bs, s, c.fperm);
+    launch_pack(xin, Fl.n, nrhs, R, c.xs, s, c.fperm);
+    launch_residual<double>(Fl, Fl.A64, c.bs, c.xs, c.rs, R, s);
+    const size_t m = (size_t)Fl.n * R;
+    LBMG_CK(cudaMemsetAsync(c.pcg_z, 0, m * sizeof(double), s));
+    LBMG_CK(cudaMemsetAsync(c.pcg_p, 0, m * sizeof(double), s));
+    LBMG_CK(cudaMemsetAsync(c.pcg_si, 0, sizeof(double) * kPcgScalars * c.ninst, s));
+    h->pcg_tol_host = tol;
+    LBMG_CK(cudaMemcpyAsync(c.pcg_tol, &h->pcg_tol_host, sizeof(double), cudaMemcpyHostToDevice, s));
+    launch_item_dot2(c.nitem, c.nnitem, c.rs, c.rs, c.bs, c.bs, R, c.item_part, s);
+    launch_inst_sum(c.item_start, c.ninst, c.item_part, c.inst_norm, 16, s);
+    std::vector<double> &nh = h->inst_norm_host;
+    nh.assign(16 * (size_t)c.ninst, 0.0);
+    auto read = [&]() -> int {
+        LBMG_CK(cudaMemcpyAsync(nh.data(), c.inst_norm, nh.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+        LBMG_CK(cudaStreamSynchronize(s));
+        return check_launch();
+    };
+    auto worst = [&](const std::vector<double> &v, double *w) {
+        for (int r = 0; r < 4; r++) w[r] = 0.0;
+        for (int mm = 0; mm < c.ninst; mm++)
+            for (int r = 0; r < nrhs; r++) {
+                const double *nm = &v[16 * (size_t)mm];
+                const double rel = nm[4 + r] > 0 ? std::sqrt(nm[r] / nm[4 + r]) : 0.0;
+                w[r] = std::isfinite(rel) ? std::max(w[r], rel) : INFINITY;
+            }
+    };
+    LBMG_TRY(read());
+    double w0[4], w[4];
+    worst(nh, w0);
+    int it = 0, status = LBMG_OK;
+    bool conv = false;
+    for (;;) {
+        worst(nh, w);
+        conv = true;
+        bool bad = false;
+        for (int r = 0; r < nrhs; r++) {
+            if (!(w[r] <= tol)) conv = false;
+            if (!std::isfinite(w[r]) || w[r] > 1e6 * std::max(w0[r], 1e-300)) bad = true;
+        }
+        if (bad) { status = LBMG_DIVERGED; break; }
+        if (conv || it >= max_iters) break;
+        if (exec) LBMG_CK(cudaGraphLaunch(exec, s));
+        else enqueue_pcg_batch_iteration(c, R, precision, s);
+        LBMG_TRY(read());
+        it++;
+    }
+    if (!conv && status == LBMG_OK) status = LBMG_NOT_CONVERGED;
+    launch_unpack(c.xs, Fl.n, nrhs, R, xout, s, c.fperm);
+    LBMG_CK(cudaEventRecord(c.ev1, s));
+    LBMG_TRY(finish_output(x, xout, cnt, host_out, s));
+    if (stats) {
+        LBMG_CK(cudaEventSynchronize(c.ev1));
+        float ms = 0;
+        cudaEventElapsedTime(&ms, c.ev0, c.ev1);
+        stats->cycles = it;
+        stats->converged = conv ? 1 : 0;
+        for (int r = 0; r < 4; r++) {
+            stats->rel_residual[r] = r < nrhs ? w[r] : 0.0;
+            stats->initial_residual[r] = r < nrhs ? w0[r] : 0.0;
+        }
+        stats->ms_total = ms;
+        stats->ms_fine_smooth = 0.f;
+        stats->learned = 0;
+        stats->learned_fallback = 0;
+    }
+    return status;
+}
+
 static int solve_impl(lbmg_handle h, const double *rhs, double *x, int nrhs, double tol, int max_cycles,
                       int precision, lbmg_stats *stats, void *stream, bool check, bool pcg = false) {
     if (!h || !rhs || !x || nrhs < 1 || nrhs > 4 || max_cycles < 0) return LBMG_INVALID_ARG;
@@ -800,8 +920,10 @@ static int solve_impl(lbmg_handle h, const double *rhs, double *x, int nrhs, dou
         }
         return status;
     }
-    if (c.ninst > 1) return LBMG_INVALID_ARG;   // batches need the persistent solve (per-mesh norms)
     if (pcg && c.smoother != LBMG_GS_COLOURED) return LBMG_INVALID_ARG;   // the preconditioner must be symmetric
+    if (pcg && c.ninst > 1)
+        return solve_pcg_batch(h, rd, xin, xout, host_out, x, cnt, nrhs, R, tol, max_cycles, precision, stats, s);
+    if (c.ninst > 1) return LBMG_INVALID_ARG;   // batches need the persistent solve (per-mesh norms)
     cudaGraphExec_t exec = nullptr;
     if (c.use_graphs) LBMG_TRY(get_graph(h, R, precision, pcg, &exec));
     LBMG_CK(cudaEventRecord(c.ev0, s));

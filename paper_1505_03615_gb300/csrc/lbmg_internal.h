@@ -156,6 +156,10 @@ struct Ctx {
     // preconditioned conjugate gradients: z, p, q = -A p and a zero vector ([n][4] FP64), scalars, partials
     double *pcg_z = nullptr, *pcg_p = nullptr, *pcg_q = nullptr, *pcg_zero = nullptr;
     double *pcg_s = nullptr, *pcg_part = nullptr;
+    // batches: per-mesh scalars [ninst][kPcgScalars], the first work item of each mesh, finest row -> mesh
+    double *pcg_si = nullptr;
+    double *pcg_tol = nullptr;     // [1] tolerance of the running batch solve
+    int *item_start = nullptr, *row_inst = nullptr;
     double *h_norm = nullptr;    // pinned [8]
     // staging of user vectors (device [n][nrhs]) and pinned host mirrors
     double *dev_io = nullptr;
@@ -249,12 +253,25 @@ void launch_coarse_factor(const Ctx &c, const int *const *rps, const int *const 
                           cudaStream_t s);
 void launch_norms(const double *v, int n, int R, double *part, double *out, cudaStream_t s, Chain *ch = nullptr);
 // conjugate-gradient scalars in Ctx::pcg_s, four lanes each
-enum { kPcgRz = 0, kPcgS1 = 4, kPcgS2 = 8, kPcgAlpha = 12, kPcgBeta = 16, kPcgScalars = 20 };
+enum { kPcgRz = 0, kPcgS1 = 4, kPcgS2 = 8, kPcgAlpha = 12, kPcgBeta = 16, kPcgRz0 = 20, kPcgScalars = 24 };
+// a lane whose r.z has fallen below this fraction of its first value is converged to
+// rounding level (residual about 1e-14 of the start): its step lengths stay 0
+constexpr double kPcgStop = 1e-28;
 void launch_pcg_dot(const double *a, const double *b, int n, int R, double *part, double *sc, int mode,
                     cudaStream_t s);
 void launch_pcg_direction(const double *z, double *p, const double *sc, int n, int R, cudaStream_t s);
 void launch_pcg_update(double *x, double *r, const double *p, const double *q, const double *sc, int n, int R,
                        cudaStream_t s);
+// batches: per-mesh dot products over the finest-level work items
+void launch_item_dot2(const int *items, int nitems, const double *a, const double *b, const double *c,
+                      const double *d, int R, double *part, cudaStream_t s);
+void launch_inst_sum(const int *istart, int ninst, const double *part, double *out, int ostride, cudaStream_t s);
+void launch_inst_pcg_scalar(const int *istart, int ninst, int R, const double *part, double *sc, int mode,
+                            const double *norms, const double *tol, cudaStream_t s);
+void launch_inst_pcg_direction(const double *z, double *p, const double *sc, const int *row_inst, int n, int R,
+                               cudaStream_t s);
+void launch_inst_pcg_update(double *x, double *r, const double *p, const double *q, const double *sc,
+                            const int *row_inst, int n, int R, cudaStream_t s);
 void launch_pack(const double *user, int n, int nrhs, int R, double *v, cudaStream_t s, const int *perm = nullptr);
 void launch_unpack(const double *v, int n, int nrhs, int R, double *user, cudaStream_t s, const int *perm = nullptr);
 void launch_to_float(const double *a, float *b, int64_t n, cudaStream_t s, float *zero = nullptr, Chain *ch = nullptr);

@@ -483,9 +483,29 @@ __global__ void __launch_bounds__(256) dot_partial_kernel(const double *__restri
     if (threadIdx.x < R) part[blockIdx.x * 4 + threadIdx.x] = sh[0][threadIdx.x];
 }
 
+// one scalar step of lane r on the reduced value v (scalars sc, see pcg_scalar_kernel)
+// (done: the lane already meets its tolerance and takes no further steps)
+__device__ __forceinline__ void pcg_scalar_step(double *sc, int r, double v, int mode, bool done = false) {
+    double *rz = sc + kPcgRz, *s1 = sc + kPcgS1, *s2 = sc + kPcgS2, *al = sc + kPcgAlpha, *be = sc + kPcgBeta,
+           *rz0 = sc + kPcgRz0;
+    if (mode == 0) {
+        s2[r] = v;
+    } else if (mode == 1) {
+        if (rz[r] == 0.0 && rz0[r] == 0.0) rz0[r] = v;   // the first step
+        const bool live = !done && v > kPcgStop * rz0[r];   // false at rounding level, for 0 and NaN
+        s1[r] = live ? v : 0.0;
+        be[r] = (live && rz[r] > 0.0) ? (v - s2[r]) / rz[r] : 0.0;
+        rz[r] = live ? v : 0.0;
+    } else {
+        const double pap = -v;
+        al[r] = (pap > 0.0 && s1[r] > 0.0) ? s1[r] / pap : 0.0;
+    }
+}
+
 // one block: reduce the partial sums to v[lane], then
 //   mode 0: s2 = v                         (r . z of the previous preconditioned residual)
-//   mode 1: s1 = v; beta = (s1 - s2) / rz, rz = s1  (Polak-Ribiere; 0 on the first step, rz = 0)
+//   mode 1: s1 = v; beta = (s1 - s2) / rz, rz = s1  (Polak-Ribiere; 0 on the first step, rz = 0;
+//           a lane at rounding level, v <= kPcgStop * its first v, keeps beta = alpha = 0)
 //   mode 2: alpha = s1 / (p . A p), with v = p . q and q = -A p
 __global__ void pcg_scalar_kernel(const double *__restrict__ part, int nblocks, int R, double *__restrict__ sc,
                                   int mode) {
@@ -502,17 +522,7 @@ __global__ void pcg_scalar_kernel(const double *__restrict__ part, int nblocks, 
     if (threadIdx.x >= R) return;
     const int r = threadIdx.x;
     const double v = sh[0][r];
-    double *rz = sc + kPcgRz, *s1 = sc + kPcgS1, *s2 = sc + kPcgS2, *al = sc + kPcgAlpha, *be = sc + kPcgBeta;
-    if (mode == 0) {
-        s2[r] = v;
-    } else if (mode == 1) {
-        s1[r] = v;
-        be[r] = rz[r] > 0.0 ? (v - s2[r]) / rz[r] : 0.0;
-        rz[r] = v;
-    } else {
-        const double pap = -v;
-        al[r] = pap > 0.0 ? s1[r] / pap : 0.0;
-    }
+    pcg_scalar_step(sc, r, v, mode);
 }
 
 // p = z + beta p
@@ -530,6 +540,116 @@ __global__ void pcg_update_kernel(double *__restrict__ x, double *__restrict__ r
     const double a = sc[kPcgAlpha + (int)(q % R)];
     x[q] = fma(a, p[q], x[q]);
     r[q] = fma(a, qv[q], r[q]);
+}
+
+// ---- the same for a batch: per-mesh dot products over work items (row ranges of one
+// mesh and colour; the items of mesh m are [istart[m], istart[m + 1])) ----
+// per item, per lane: a.b (components 0..3) and, when c is given, c.d (4..7)
+template <int R>
+__global__ void __launch_bounds__(256) item_dot2_kernel(const int *__restrict__ items, int nitems,
+                                                        const double *__restrict__ a, const double *__restrict__ b,
+                                                        const double *__restrict__ cv, const double *__restrict__ dv,
+                                                        double *__restrict__ part) {
+    const int lane = threadIdx.x & 31;
+    const int it = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (it >= nitems) return;
+    const int r0 = items[3 * it + 1], r1 = items[3 * it + 2];
+    double acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; q++) acc[q] = 0.0;
+    for (int i = r0 + lane; i < r1; i += 32)
+#pragma unroll
+        for (int q = 0; q < R; q++) {
+            acc[q] = fma(a[(size_t)i * R + q], b[(size_t)i * R + q], acc[q]);
+            if (cv) acc[4 + q] = fma(cv[(size_t)i * R + q], dv[(size_t)i * R + q], acc[4 + q]);
+        }
+#pragma unroll
+    for (int q = 0; q < 8; q++)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], o);
+    if (lane < 8) {
+        double v = 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; q++) if (q == lane) v = acc[q];
+        part[8 * (size_t)it + lane] = v;
+    }
+}
+
+// per mesh m and component q < 8: out[m * ostride + q] = sum of its items' partials (in item order)
+__global__ void inst_sum_kernel(const int *__restrict__ istart, int ninst, const double *__restrict__ part,
+                                double *__restrict__ out, int ostride) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= ninst * 8) return;
+    const int m = k >> 3, q = k & 7;
+    double s = 0.0;
+    for (int it = istart[m]; it < istart[m + 1]; it++) s += part[8 * (size_t)it + q];
+    out[(size_t)m * ostride + q] = s;
+}
+
+// per mesh m and lane r: the conjugate-gradient scalar step of pcg_scalar_kernel on
+// v = sum of the mesh's item partials (component r); scalars at sc + m * kPcgScalars
+//   norms: [ninst][16] per-mesh squared norms of r (0..3) and b (4..7) after the last step;
+//   tol: the solve's tolerance.  A mesh lane that meets it takes no further steps: the other
+//   meshes keep iterating, and a converged lane's FP32-preconditioned recurrence would
+//   otherwise run on rounding noise.
+__global__ void inst_pcg_scalar_kernel(const int *__restrict__ istart, int ninst, int R,
+                                       const double *__restrict__ part, double *__restrict__ sc, int mode,
+                                       const double *__restrict__ norms, const double *__restrict__ tol) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= ninst * 4) return;
+    const int m = k >> 2, r = k & 3;
+    if (r >= R) return;
+    double v = 0.0;
+    for (int it = istart[m]; it < istart[m + 1]; it++) v += part[8 * (size_t)it + r];
+    const double t = *tol;
+    const bool done = norms[16 * (size_t)m + r] <= t * t * norms[16 * (size_t)m + 4 + r];
+    pcg_scalar_step(sc + (size_t)m * kPcgScalars, r, v, mode, done);
+}
+
+// p = z + beta_mesh p; x += alpha_mesh p, r += alpha_mesh q (q = -A p), the mesh of a row from row_inst
+__global__ void inst_pcg_direction_kernel(const double *__restrict__ z, double *__restrict__ p,
+                                          const double *__restrict__ sc, const int *__restrict__ row_inst,
+                                          int64_t m, int R) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= m) return;
+    const double *s = sc + (size_t)row_inst[q / R] * kPcgScalars;
+    p[q] = fma(s[kPcgBeta + (int)(q % R)], p[q], z[q]);
+}
+__global__ void inst_pcg_update_kernel(double *__restrict__ x, double *__restrict__ r, const double *__restrict__ p,
+                                       const double *__restrict__ qv, const double *__restrict__ sc,
+                                       const int *__restrict__ row_inst, int64_t m, int R) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= m) return;
+    const double a = sc[(size_t)row_inst[q / R] * kPcgScalars + kPcgAlpha + (int)(q % R)];
+    x[q] = fma(a, p[q], x[q]);
+    r[q] = fma(a, qv[q], r[q]);
+}
+
+void launch_item_dot2(const int *items, int nitems, const double *a, const double *b, const double *c,
+                      const double *d, int R, double *part, cudaStream_t s) {
+    if (nitems == 0) return;
+    const unsigned blocks = (unsigned)((nitems + 7) / 8);
+    if (R == 1) item_dot2_kernel<1><<<blocks, 256, 0, s>>>(items, nitems, a, b, c, d, part);
+    else if (R == 2) item_dot2_kernel<2><<<blocks, 256, 0, s>>>(items, nitems, a, b, c, d, part);
+    else item_dot2_kernel<4><<<blocks, 256, 0, s>>>(items, nitems, a, b, c, d, part);
+}
+void launch_inst_sum(const int *istart, int ninst, const double *part, double *out, int ostride, cudaStream_t s) {
+    inst_sum_kernel<<<(unsigned)((ninst * 8 + 255) / 256), 256, 0, s>>>(istart, ninst, part, out, ostride);
+}
+void launch_inst_pcg_scalar(const int *istart, int ninst, int R, const double *part, double *sc, int mode,
+                            const double *norms, const double *tol, cudaStream_t s) {
+    inst_pcg_scalar_kernel<<<(unsigned)((ninst * 4 + 255) / 256), 256, 0, s>>>(istart, ninst, R, part, sc, mode,
+                                                                                norms, tol);
+}
+void launch_inst_pcg_direction(const double *z, double *p, const double *sc, const int *row_inst, int n, int R,
+                               cudaStream_t s) {
+    const int64_t m = (int64_t)n * R;
+    if (m) inst_pcg_direction_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(z, p, sc, row_inst, m, R);
+}
+void launch_inst_pcg_update(double *x, double *r, const double *p, const double *q, const double *sc,
+                            const int *row_inst, int n, int R, cudaStream_t s) {
+    const int64_t m = (int64_t)n * R;
+    if (m) inst_pcg_update_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(x, r, p, q, sc, row_inst, m, R);
 }
 
 void launch_pcg_dot(const double *a, const double *b, int n, int R, double *part, double *sc, int mode,
