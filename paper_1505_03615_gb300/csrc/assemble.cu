@@ -210,8 +210,21 @@ __global__ void fine_gather_kernel(int64_t nnz, const int64_t *__restrict__ arp,
     const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (s >= nnz) return;
     double m = 0.0, l = 0.0;
-    for (int64_t k = arp[s]; k < arp[s + 1]; k++) {
-        const double2 v = stage[aidx[k]];
+    const int64_t k1 = arp[s + 1];
+    int64_t k = arp[s];
+    // eight list entries, then their eight values, in flight together; the sum keeps its order
+    for (; k + 8 <= k1; k += 8) {
+        uint32_t ix[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) ix[u] = __ldg(aidx + k + u);
+        double2 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) v[u] = __ldg(stage + ix[u]);
+#pragma unroll
+        for (int u = 0; u < 8; u++) { m += v[u].x; l += v[u].y; }
+    }
+    for (; k < k1; k++) {
+        const double2 v = __ldg(stage + aidx[k]);
         m += v.x;
         l += v.y;
     }
@@ -237,12 +250,29 @@ __global__ void galerkin_kernel(int64_t nnz, const int64_t *__restrict__ grp, co
     const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (s >= nnz) return;
     double m = 0.0, l = 0.0;
-    for (int64_t k = grp[s]; k < grp[s + 1]; k++) {
-        const uint32_t e = gidx[k];
+    const int64_t k1 = grp[s + 1];
+    int64_t k = grp[s];
+    // eight list entries, then their sixteen values, in flight together; the sum keeps its order
+    for (; k + 8 <= k1; k += 8) {
+        uint32_t e[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) e[u] = __ldg(gidx + k + u);
+        double mv[8], lv[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) { mv[u] = __ldg(Mf + (e[u] & kGalMask)); lv[u] = __ldg(Lf + (e[u] & kGalMask)); }
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            const double w = ldexp(1.0, -(int)(e[u] >> kGalShift));
+            m = fma(w, mv[u], m);
+            l = fma(w, lv[u], l);
+        }
+    }
+    for (; k < k1; k++) {
+        const uint32_t e = __ldg(gidx + k);
         const uint32_t idx = e & kGalMask;
         const double w = ldexp(1.0, -(int)(e >> kGalShift));
-        m = fma(w, Mf[idx], m);
-        l = fma(w, Lf[idx], l);
+        m = fma(w, __ldg(Mf + idx), m);
+        l = fma(w, __ldg(Lf + idx), l);
     }
     M[s] = m;
     L[s] = l;
