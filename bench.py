@@ -93,6 +93,21 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def reduce_over_ranks(ms, units, ws, device):
+    """Replicas on ws ranks: every rank times its own copy of the workload, so the job's time
+    is the slowest rank's and its units are the sum over ranks (weak scaling).  With one rank
+    its own numbers are returned; otherwise a process group must be initialised."""
+    if ws == 1:
+        return float(ms), float(units)
+    import torch
+    import torch.distributed as dist
+    mx = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    sm = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return mx.item(), sm.item()
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -296,12 +311,8 @@ def batch_main(args):
     if ws > 1:
         dist.barrier()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    if ws > 1:
-        mt = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(mt, op=dist.ReduceOp.MAX)
-        ms = mt.item()
-    value = nu * nrhs * cycles * ws / (ms / 1e3)
+    ms, all_cycles = reduce_over_ranks(e0.elapsed_time(e1), cycles, ws, dev)
+    value = nu * nrhs * all_cycles / (ms / 1e3)
     # end to end with pinned host buffers
     f_pin = torch.tensor(f, dtype=torch.float64).pin_memory()
     u_pin = torch.zeros((nv, nrhs), dtype=torch.float64).pin_memory()
@@ -312,7 +323,8 @@ def batch_main(args):
     for _ in range(args.steps):
         e2e_cycles += step(f_in=f_pin.numpy(), u_out=u_pin.numpy()).cycles
     torch.cuda.synchronize()
-    e2e_value = nu * nrhs * e2e_cycles * ws / (time.perf_counter() - t0)
+    e2e_ms, e2e_all = reduce_over_ranks(1e3 * (time.perf_counter() - t0), e2e_cycles, ws, dev)
+    e2e_value = nu * nrhs * e2e_all / (e2e_ms / 1e3)
     # plain FP64 on the same batch
     g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     step(L.LBMG_FP64)
@@ -464,16 +476,7 @@ def main():
     if ws > 1:
         dist.barrier()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    ms_t = torch.tensor([ms, float(cycles)], dtype=torch.float64, device=dev)
-    if ws > 1:
-        tot = torch.tensor([float(cycles)], dtype=torch.float64, device=dev)
-        dist.all_reduce(ms_t[:1], op=dist.ReduceOp.MAX)
-        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
-        all_cycles = tot.item()
-    else:
-        all_cycles = float(cycles)
-    ms_max = ms_t[0].item()
+    ms_max, all_cycles = reduce_over_ranks(e0.elapsed_time(e1), cycles, ws, dev)
     value = n * nrhs * all_cycles / (ms_max / 1e3)
     ms_per_step = ms_max / args.steps
     if args.only_timed:
@@ -506,7 +509,8 @@ def main():
         e2e_cycles += step_e2e().cycles
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    e2e_value = n * nrhs * e2e_cycles / e2e_s * (ws if ws > 1 else 1)
+    e2e_ms, e2e_all = reduce_over_ranks(1e3 * e2e_s, e2e_cycles, ws, dev)
+    e2e_value = n * nrhs * e2e_all / (e2e_ms / 1e3)
 
     # plain FP64 GPU multigrid on the same mesh: ms to the same tolerance
     fp64_steps = max(1, min(3, args.steps))
