@@ -86,3 +86,38 @@ def test_tune_cache_file_round_trip_and_bad_lines(tmp_path):
     assert e.value.code == 1
     with pytest.raises(L.LbmgError):
         L.lbmg_tune_cache_load(str(tmp_path / "missing.txt"))
+
+
+@pytest.mark.parametrize("case,code", [("no_triangles", 1), ("two_vertices", 1), ("zero_extent", 2),
+                                       ("collinear", 2), ("flat_duplicate_corner", 2)])
+def test_empty_and_degenerate_meshes_rejected_on_host(case, code):
+    """A mesh with no triangle piece of positive area spans no basis function
+    (Section 3.2 keeps only pieces of positive area): it is reported, not solved."""
+    V = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], dtype=np.float64)
+    F = np.array([[0, 1, 2], [0, 1, 3]], dtype=np.int32)
+    if case == "no_triangles":
+        F = np.zeros((0, 3), dtype=np.int32)
+    elif case == "two_vertices":
+        V, F = V[:2], np.array([[0, 1, 1]], dtype=np.int32)
+    elif case == "zero_extent":
+        V = np.full((4, 3), 0.25)
+    elif case == "collinear":
+        V = np.array([[0, 0, 0], [1, 1, 1], [2, 2, 2], [3, 3, 3]], dtype=np.float64)
+    elif case == "flat_duplicate_corner":
+        F = np.array([[0, 1, 1], [2, 3, 3]], dtype=np.int32)
+    with pytest.raises(L.LbmgError) as e:
+        L.lbmg_build_hierarchy(V, F, 3)
+    assert e.value.code == code
+
+
+def test_batch_rejects_an_empty_list_and_a_bad_member():
+    V = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], dtype=np.float64)
+    F = np.array([[0, 1, 2], [0, 1, 3]], dtype=np.int32)
+    with pytest.raises(L.LbmgError) as e:
+        L.lbmg_build_batch([])
+    assert e.value.code == 1
+    bad = F.copy()
+    bad[0, 0] = 9
+    with pytest.raises(L.LbmgError) as e:
+        L.lbmg_build_batch([(V, F, 3), (V, bad, 3)])
+    assert e.value.code == 1
