@@ -310,7 +310,7 @@ int lbmg_get_prolongation(lbmg_handle h, int d, int *parents, double *weights);
 /*
  * Learned relaxation weights for the finest-level Gauss-Seidel sweeps.  The paper
  * has no counterpart: its smoother is plain Gauss-Seidel (Sections 4.3, 5.2), which
- * is also the fallback and the judge here.  A network 28 -> 64 (ReLU) -> 1 maps each
+ * is also the fallback here and the yardstick of the learned sweep.  A network 28 -> 64 (ReLU) -> 1 maps each
  * finest node's stencil (coefficients / A_ii summed per neighbour-corner offset,
  * A_ii / mean diagonal, entry count / 27) to y, and the node's sweep update is
  * scaled by omega = 1.45 + 0.45 y / (1 + |y|) in (1, 1.9), so the sweep stays
