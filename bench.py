@@ -168,7 +168,9 @@ def reference_main(args):
     h = oracle.Hierarchy(V, F, depth)
     rhs = h.project_rhs(f)
     n = h.ndof(depth)
-    cyc = 2
+    # each call also forms A and factors the oracle's dense coarsest level: enough cycles
+    # per step that the sample measures the cycles, not that setup
+    cyc = 10
     for _ in range(args.warmup):
         h.vcycles(t, rhs, cycles=1)
     times = []
