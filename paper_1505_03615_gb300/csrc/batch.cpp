@@ -15,9 +15,84 @@
 
 namespace lbmg {
 
+namespace {
+
+// A batch of one mesh has the layout below with identity row and entry maps, so the mesh's
+// own arrays are taken over instead of being remapped entry by entry.
+int adopt_single(HostHierarchy &P, HostHierarchy &B, std::string &err) {
+    if ((int64_t)P.nfrag * 36 > (int64_t)UINT32_MAX) { err = "batch too large"; return 1; }
+    B = HostHierarchy();
+    B.ninst = 1;
+    B.split = P.split;
+    B.D = P.D;
+    B.d0 = P.d0;
+    const int nu = P.lev[P.D].ndof;
+    B.inst_D = {P.D};
+    B.inst_d0 = {P.d0};
+    B.inst_voff = {0};
+    B.inst_toff = {0};
+    B.inst_uoff = {0};
+    B.inst_nfine = {nu};
+    B.inst_sigma = {P.sigma};
+    B.inst_S = {P.S};
+    B.inst_center = {P.center[0], P.center[1], P.center[2]};
+    B.nv = P.nv;
+    B.nt = P.nt;
+    B.nfrag = P.nfrag;
+    B.S = P.S;
+    B.sigma = P.sigma;
+    for (int a = 0; a < 3; a++) B.center[a] = P.center[a];
+    B.Vg = std::move(P.Vg);
+    B.F = std::move(P.F);
+    B.tri_normal = std::move(P.tri_normal);
+    B.frag_tri = std::move(P.frag_tri);
+    B.frag_vox = std::move(P.frag_vox);
+    B.frag_pstart = std::move(P.frag_pstart);
+    B.frag_poly = std::move(P.frag_poly);
+    B.frag_dof = std::move(P.frag_dof);
+    B.arp = std::move(P.arp);
+    B.aidx = std::move(P.aidx);
+    B.rrp = std::move(P.rrp);
+    B.ridx = std::move(P.ridx);
+    B.vdof = std::move(P.vdof);
+    B.vw = std::move(P.vw);
+    B.frag_scale.assign(P.nfrag, P.sigma * P.sigma);
+    B.fperm.resize(nu);
+    std::iota(B.fperm.begin(), B.fperm.end(), 0);
+    B.lev = std::move(P.lev);
+    for (int d = 0; d <= B.D; d++) {
+        HostLevel &L = B.lev[d];
+        // the (corner, triangle) lookup tables serve the build only
+        std::vector<uint64_t>().swap(L.ct_key);
+        std::vector<int32_t>().swap(L.ct_tri);
+        std::vector<int32_t>().swap(L.ct_dof);
+        if (d < B.d0) continue;
+        L.inst.assign(L.ndof, 0);
+        if (d == B.d0) {
+            // the coarsest level is one dense block and is not smoothed
+            for (int c = 0; c <= 8; c++) L.colour_start[c] = 0;
+            L.ns = 0;
+            L.coarse = {0, 0, L.ndof};
+        } else {
+            L.ns = L.ndof;
+        }
+    }
+    B.seg.assign(16, 0);
+    const HostLevel &LF = B.lev[B.D];
+    if (B.D > B.d0) {
+        for (int c = 0; c < 8; c++) { B.seg[2 * c] = LF.colour_start[c]; B.seg[2 * c + 1] = LF.colour_start[c + 1]; }
+    } else {
+        B.seg[1] = LF.ndof;
+    }
+    return 0;
+}
+
+}  // namespace
+
 int combine_batch(std::vector<HostHierarchy> &parts, HostHierarchy &B, std::string &err) {
     const int ni = (int)parts.size();
     if (ni < 1) { err = "empty batch"; return 1; }
+    if (ni == 1) return adopt_single(parts[0], B, err);
     B = HostHierarchy();
     B.ninst = ni;
     B.split = parts[0].split;

@@ -160,23 +160,32 @@ bool point_in_open_box(const double *p, const double *lo, const double *hi) {
 struct KT { uint64_t key; int32_t tri; };
 inline bool kt_less(const KT &a, const KT &b) { return a.key < b.key || (a.key == b.key && a.tri < b.tri); }
 
-// counting sort of (bucket, value) pairs into CSR
+// CSR lists of the positions i of bucket[i], each bucket's positions ascending: a sort of
+// the keys bucket * 2^32 + i (fewer than 2^32 entries)
+void bucket_positions(int64_t nb, const std::vector<int32_t> &bucket, std::vector<int64_t> &ptr,
+                      std::vector<uint32_t> &out) {
+    const size_t m = bucket.size();
+    std::vector<uint64_t> key(m);
+#pragma omp parallel for schedule(static)
+    for (size_t i = 0; i < m; i++) key[i] = (uint64_t)(uint32_t)bucket[i] << 32 | (uint64_t)i;
+    LBMG_SORT(key.begin(), key.end());
+    out.resize(m);
+#pragma omp parallel for schedule(static)
+    for (size_t i = 0; i < m; i++) out[i] = (uint32_t)key[i];
+    ptr.assign(nb + 1, 0);
+    for (size_t i = 0; i < m; i++) ptr[(key[i] >> 32) + 1]++;
+    for (int64_t i = 0; i < nb; i++) ptr[i + 1] += ptr[i];
+}
+
+// (bucket, value) pairs into CSR, the values of one bucket in input order
 template <class V>
 void bucket_csr(int64_t nb, const std::vector<int32_t> &bucket, const std::vector<V> &val,
                 std::vector<int64_t> &ptr, std::vector<V> &out) {
-    ptr.assign(nb + 1, 0);
-    for (int32_t b : bucket) ptr[b + 1]++;
-    for (int64_t i = 0; i < nb; i++) ptr[i + 1] += ptr[i];
-    out.resize(val.size());
-    std::vector<int64_t> fill(ptr.begin(), ptr.end() - 1);
-    for (size_t i = 0; i < val.size(); i++) out[fill[bucket[i]]++] = val[i];
-}
-
-int find_slot(const HostLevel &L, int row, int col) {
-    const int32_t *b = L.ci.data() + L.rp[row], *e = L.ci.data() + L.rp[row + 1];
-    const int32_t *p = std::lower_bound(b, e, col);
-    if (p == e || *p != col) return -1;
-    return (int)(p - L.ci.data());
+    std::vector<uint32_t> pos;
+    bucket_positions(nb, bucket, ptr, pos);
+    out.resize(pos.size());
+#pragma omp parallel for schedule(static)
+    for (size_t i = 0; i < pos.size(); i++) out[i] = val[pos[i]];
 }
 
 int lookup_dof(const HostLevel &L, uint64_t key, int tri) {
@@ -215,23 +224,31 @@ void build_level_basis(HostHierarchy &H, HostLevel &L, const std::vector<KT> &ce
     const int64_t ng = (int64_t)gstart.size() - 1;
     std::vector<int32_t> comp(m);          // component label inside the corner, ordered by min triangle
     std::vector<int32_t> ncomp(ng);
+    // Corners are taken largest first, one at a time: on coarse levels a few corners hold
+    // most of the mesh each, and they must not queue behind one another on one thread.
+    std::vector<int64_t> order(ng);
+    std::iota(order.begin(), order.end(), (int64_t)0);
+    std::sort(order.begin(), order.end(), [&](int64_t x, int64_t y) {
+        const int64_t sx = gstart[x + 1] - gstart[x], sy = gstart[y + 1] - gstart[y];
+        return sx > sy || (sx == sy && x < y);
+    });
 #pragma omp parallel
     {
         std::vector<int32_t> par, lab;
-#pragma omp for schedule(dynamic, 256)
-        for (int64_t g = 0; g < ng; g++) {
+        // position of each triangle within the current corner's list, -1 when absent
+        std::vector<int32_t> slot_of(H.nt, -1);
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t o = 0; o < ng; o++) {
+            const int64_t g = order[o];
             const int64_t b = gstart[g], e = gstart[g + 1];
             const int n = (int)(e - b);
             par.resize(n);
             lab.assign(n, -1);
             std::iota(par.begin(), par.end(), 0);
+            for (int i = 0; i < n; i++) slot_of[ct[b + i].tri] = i;
             auto find = [&](int x) { while (par[x] != x) { par[x] = par[par[x]]; x = par[x]; } return x; };
             auto unite = [&](int x, int y) { x = find(x); y = find(y); if (x != y) { if (x < y) par[y] = x; else par[x] = y; } };
-            auto local = [&](int tri) -> int {
-                int lo = 0, hi = n;
-                while (lo < hi) { int mid = (lo + hi) / 2; if (ct[b + mid].tri < tri) lo = mid + 1; else hi = mid; }
-                return (lo < n && ct[b + lo].tri == tri) ? lo : -1;
-            };
+            auto local = [&](int tri) -> int { return slot_of[tri]; };
             if (H.split) {
                 uint64_t key = ct[b].key;
                 double c[3] = {(double)compact3(key), (double)compact3(key >> 1), (double)compact3(key >> 2)};
@@ -271,6 +288,7 @@ void build_level_basis(HostHierarchy &H, HostLevel &L, const std::vector<KT> &ce
                 comp[b + i] = lab[r];
             }
             ncomp[g] = nc;
+            for (int i = 0; i < n; i++) slot_of[ct[b + i].tri] = -1;
         }
     }
     // dofs: one per (corner, component); order by colour, Morton key, smallest triangle
@@ -311,6 +329,7 @@ void build_level_basis(HostHierarchy &H, HostLevel &L, const std::vector<KT> &ce
     L.ct_key.resize(m);
     L.ct_tri.resize(m);
     L.ct_dof.resize(m);
+#pragma omp parallel for schedule(static)
     for (int64_t g = 0; g < ng; g++)
         for (int64_t i = gstart[g]; i < gstart[g + 1]; i++) {
             L.ct_key[i] = ct[i].key;
@@ -319,24 +338,56 @@ void build_level_basis(HostHierarchy &H, HostLevel &L, const std::vector<KT> &ce
         }
 }
 
-// CSR pattern from lists of (row, col) pairs given per row bucket
-void pattern_from_pairs(int n, const std::vector<int32_t> &row, const std::vector<int32_t> &col, HostLevel &L) {
-    std::vector<int64_t> ptr;
-    std::vector<int32_t> cols;
-    bucket_csr(n, row, col, ptr, cols);
-    L.rp.assign(n + 1, 0);
-    std::vector<int32_t> out;
-    out.reserve(cols.size() / 4 + 16);
+// Sparsity pattern of n rows over ncols columns and the contribution list of every stored
+// entry, built row by row.  emit(i, f) calls f(col, value) for each contribution to row i,
+// in list order; row i stores the distinct cols, sorted, and the list of stored entry
+// (i, col) holds the values of the contributions to it in the order they were emitted.
+// Each thread keeps dense per-column marks, so a contribution costs O(1).
+template <class Emit>
+void rows_with_lists(int n, int ncols, const Emit &emit, HostLevel &L, std::vector<int64_t> &lptr,
+                     std::vector<uint32_t> &lidx) {
     std::vector<int32_t> cnt(n);
-#pragma omp parallel for schedule(dynamic, 1024)
-    for (int i = 0; i < n; i++) {
-        std::sort(cols.begin() + ptr[i], cols.begin() + ptr[i + 1]);
-        cnt[i] = (int32_t)(std::unique(cols.begin() + ptr[i], cols.begin() + ptr[i + 1]) - (cols.begin() + ptr[i]));
+#pragma omp parallel
+    {
+        std::vector<int32_t> seen(ncols, -1);
+#pragma omp for schedule(dynamic, 64)
+        for (int i = 0; i < n; i++) {
+            int32_t m = 0;
+            emit(i, [&](int32_t c, uint32_t) { if (seen[c] != i) { seen[c] = i; m++; } });
+            cnt[i] = m;
+        }
     }
+    L.rp.assign(n + 1, 0);
     for (int i = 0; i < n; i++) L.rp[i + 1] = L.rp[i] + cnt[i];
-    L.ci.resize(L.rp[n]);
-#pragma omp parallel for schedule(static)
-    for (int i = 0; i < n; i++) std::copy(cols.begin() + ptr[i], cols.begin() + ptr[i] + cnt[i], L.ci.begin() + L.rp[i]);
+    const int64_t nnz = L.rp[n];
+    L.ci.resize(nnz);
+    std::vector<int64_t> pos(nnz + 1, 0);   // contributions per stored entry, then list starts
+#pragma omp parallel
+    {
+        std::vector<int32_t> seen(ncols, -1), slot(ncols);
+#pragma omp for schedule(dynamic, 64)
+        for (int i = 0; i < n; i++) {
+            int32_t *row = L.ci.data() + L.rp[i];
+            int m = 0;
+            emit(i, [&](int32_t c, uint32_t) { if (seen[c] != i) { seen[c] = i; row[m++] = c; } });
+            std::sort(row, row + m);
+            for (int q = 0; q < m; q++) slot[row[q]] = L.rp[i] + q;
+            emit(i, [&](int32_t c, uint32_t) { pos[slot[c] + 1]++; });
+        }
+    }
+    for (int64_t k = 0; k < nnz; k++) pos[k + 1] += pos[k];
+    lptr = pos;
+    lidx.resize(pos[nnz]);
+    // each row fills only its own entries' lists
+#pragma omp parallel
+    {
+        std::vector<int32_t> slot(ncols);
+#pragma omp for schedule(dynamic, 64)
+        for (int i = 0; i < n; i++) {
+            for (int32_t k = L.rp[i]; k < L.rp[i + 1]; k++) slot[L.ci[k]] = k;
+            emit(i, [&](int32_t c, uint32_t v) { lidx[pos[slot[c]]++] = v; });
+        }
+    }
 }
 
 }  // namespace
@@ -495,36 +546,19 @@ int build_host_hierarchy(const double *V, int nv, const int *F, int nt, int dept
         }
     if (bad) { err = "internal: fragment corner without a function"; return 1; }
 
-    // finest pattern and assembly contribution lists
-    {
-        std::vector<int32_t> row(64 * (size_t)H.nfrag), col(64 * (size_t)H.nfrag);
-#pragma omp parallel for schedule(static)
-        for (int f = 0; f < H.nfrag; f++)
-            for (int a = 0; a < 8; a++)
-                for (int b = 0; b < 8; b++) {
-                    row[64 * (size_t)f + 8 * a + b] = H.frag_dof[8 * (size_t)f + a];
-                    col[64 * (size_t)f + 8 * a + b] = H.frag_dof[8 * (size_t)f + b];
-                }
-        pattern_from_pairs(LF.ndof, row, col, LF);
-        std::vector<int32_t> slot(64 * (size_t)H.nfrag);
-        std::vector<uint32_t> val(64 * (size_t)H.nfrag);
-#pragma omp parallel for schedule(static)
-        for (int f = 0; f < H.nfrag; f++)
-            for (int a = 0; a < 8; a++)
-                for (int b = 0; b < 8; b++) {
-                    size_t q = 64 * (size_t)f + 8 * a + b;
-                    slot[q] = find_slot(LF, row[q], col[q]);
-                    val[q] = (uint32_t)(36 * (size_t)f + pair_index(a, b));
-                }
-        bucket_csr((int64_t)LF.rp[LF.ndof], slot, val, H.arp, H.aidx);
-    }
-    // finest right-hand-side lists
-    {
-        std::vector<int32_t> dof(8 * (size_t)H.nfrag);
-        std::vector<uint32_t> val(8 * (size_t)H.nfrag);
-        for (size_t q = 0; q < dof.size(); q++) { dof[q] = H.frag_dof[q]; val[q] = (uint32_t)q; }
-        bucket_csr(LF.ndof, dof, val, H.rrp, H.ridx);
-    }
+    // finest right-hand-side lists: per dof, fragment * 8 + corner of its incidences, fragments ascending
+    bucket_positions(LF.ndof, H.frag_dof, H.rrp, H.ridx);
+    // finest pattern and assembly contribution lists: row i couples with every corner dof of
+    // the fragments incident to it; stored entry (i, j) lists 36 f + pair(a, b) for each such
+    // fragment f with corner a at i and corner b at j (the 8 corners of a fragment are 8
+    // different dofs, so each fragment contributes once), fragments ascending
+    rows_with_lists(LF.ndof, LF.ndof, [&](int i, auto &&f) {
+        for (int64_t q = H.rrp[i]; q < H.rrp[i + 1]; q++) {
+            const size_t fr = H.ridx[q] >> 3;
+            const int a = (int)(H.ridx[q] & 7u);
+            for (int b = 0; b < 8; b++) f(H.frag_dof[8 * fr + b], (uint32_t)(36 * fr + pair_index(a, b)));
+        }
+    }, LF, H.arp, H.aidx);
 
     // prolongation, restriction lists and Galerkin contributions, finest to coarsest
     for (int df = depth; df > H.d0; df--) {
@@ -565,38 +599,22 @@ int build_host_hierarchy(const double *V, int nv, const int *F, int nt, int dept
             bucket_csr(Lc.ndof, b, v, ptr, Lc.cch);
             Lc.crp.assign(ptr.begin(), ptr.end());
         }
-        // coarse pattern and Galerkin contributions: (P^T A P)_ab = sum_{i,l} A_il / (np_i np_l)
-        {
-            const int64_t nnzf = Lf.rp[Lf.ndof];
-            std::vector<int64_t> start(nnzf + 1, 0);
-            for (int i = 0; i < Lf.ndof; i++)
-                for (int32_t k = Lf.rp[i]; k < Lf.rp[i + 1]; k++)
-                    start[k + 1] = (int64_t)(1 << Lf.npar_log2[i]) * (1 << Lf.npar_log2[Lf.ci[k]]);
-            for (int64_t k = 0; k < nnzf; k++) start[k + 1] += start[k];
-            const int64_t tot = start[nnzf];
-            std::vector<int32_t> row(tot), col(tot);
-            std::vector<uint32_t> val(tot);
-#pragma omp parallel for schedule(dynamic, 256)
-            for (int i = 0; i < Lf.ndof; i++)
+        // coarse pattern and Galerkin contributions: (P^T A P)_ab = sum_{i,l} A_il / (np_i np_l),
+        // coarse row a from its children i (ascending), their stored entries k = (i, l)
+        // (ascending) and the parents b of l; an (i, k) pair reaches a given (a, b) at most once
+        // since the parents of a function are distinct
+        if ((int64_t)Lf.rp[Lf.ndof] > (int64_t)kGalMask) { err = "level too large for packed Galerkin lists"; return 1; }
+        rows_with_lists(Lc.ndof, Lc.ndof, [&](int a, auto &&f) {
+            for (int32_t q = Lc.crp[a]; q < Lc.crp[a + 1]; q++) {
+                const int i = (int)(Lc.cch[q] & kPackMask);
                 for (int32_t k = Lf.rp[i]; k < Lf.rp[i + 1]; k++) {
                     const int l = Lf.ci[k];
-                    int64_t q = start[k];
                     const uint32_t e = (uint32_t)(Lf.npar_log2[i] + Lf.npar_log2[l]);
-                    for (int a = 0; a < (1 << Lf.npar_log2[i]); a++)
-                        for (int b = 0; b < (1 << Lf.npar_log2[l]); b++) {
-                            row[q] = Lf.par[8 * (size_t)i + a];
-                            col[q] = Lf.par[8 * (size_t)l + b];
-                            val[q] = (uint32_t)k | (e << kGalShift);
-                            q++;
-                        }
+                    for (int pb = 0; pb < (1 << Lf.npar_log2[l]); pb++)
+                        f(Lf.par[8 * (size_t)l + pb], (uint32_t)k | (e << kGalShift));
                 }
-            if (nnzf > (int64_t)kGalMask) { err = "level too large for packed Galerkin lists"; return 1; }
-            pattern_from_pairs(Lc.ndof, row, col, Lc);
-            std::vector<int32_t> slot(tot);
-#pragma omp parallel for schedule(static)
-            for (int64_t q = 0; q < tot; q++) slot[q] = find_slot(Lc, row[q], col[q]);
-            bucket_csr((int64_t)Lc.rp[Lc.ndof], slot, val, Lc.grp, Lc.gidx);
-        }
+            }
+        }, Lc, Lc.grp, Lc.gidx);
     }
 
     // vertex evaluation at the finest level

@@ -32,7 +32,8 @@ def _worker(rank, ws, port, out):
 
 def test_two_rank_replicas_take_the_slowest_time_and_sum_the_units():
     ws = 2
-    with mp.Manager() as mgr:
+    # every helper process is spawned, never forked from this multi-threaded process
+    with mp.get_context("spawn").Manager() as mgr:
         out = mgr.dict()
         mp.spawn(_worker, args=(ws, _free_port(), out), nprocs=ws, join=True)
         for r in range(ws):
