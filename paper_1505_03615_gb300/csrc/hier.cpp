@@ -207,15 +207,37 @@ void build_level_basis(HostHierarchy &H, HostLevel &L, const std::vector<KT> &ce
     const int shift = H.D - L.d;
     const double s = (double)(1 << shift);
     // (corner, triangle) pairs
-    std::vector<KT> ct(cells.size() * 8);
+    std::vector<KT> ct;
+    // a corner of depth d has coordinates up to 2^d, so its Morton key has 3 (d + 1) bits; when
+    // key and triangle fit one 64-bit word, the pairs are sorted as such words (same order)
+    int tbits = 1;
+    while (tbits < 31 && (1LL << tbits) < (int64_t)H.nt) tbits++;
+    if (3 * (L.d + 1) + tbits <= 64) {
+        std::vector<uint64_t> w(cells.size() * 8);
 #pragma omp parallel for schedule(static)
-    for (long i = 0; i < (long)cells.size(); i++) {
-        uint32_t vx = compact3(cells[i].key), vy = compact3(cells[i].key >> 1), vz = compact3(cells[i].key >> 2);
-        for (int a = 0; a < 8; a++)
-            ct[8 * i + a] = KT{morton(vx + (a & 1), vy + ((a >> 1) & 1), vz + ((a >> 2) & 1)), cells[i].tri};
+        for (long i = 0; i < (long)cells.size(); i++) {
+            uint32_t vx = compact3(cells[i].key), vy = compact3(cells[i].key >> 1), vz = compact3(cells[i].key >> 2);
+            for (int a = 0; a < 8; a++)
+                w[8 * i + a] = morton(vx + (a & 1), vy + ((a >> 1) & 1), vz + ((a >> 2) & 1)) << tbits |
+                               (uint64_t)(uint32_t)cells[i].tri;
+        }
+        LBMG_SORT(w.begin(), w.end());
+        w.erase(std::unique(w.begin(), w.end()), w.end());
+        ct.resize(w.size());
+        const uint64_t tmask = (1ULL << tbits) - 1;
+#pragma omp parallel for schedule(static)
+        for (long i = 0; i < (long)w.size(); i++) ct[i] = KT{w[i] >> tbits, (int32_t)(w[i] & tmask)};
+    } else {
+        ct.resize(cells.size() * 8);
+#pragma omp parallel for schedule(static)
+        for (long i = 0; i < (long)cells.size(); i++) {
+            uint32_t vx = compact3(cells[i].key), vy = compact3(cells[i].key >> 1), vz = compact3(cells[i].key >> 2);
+            for (int a = 0; a < 8; a++)
+                ct[8 * i + a] = KT{morton(vx + (a & 1), vy + ((a >> 1) & 1), vz + ((a >> 2) & 1)), cells[i].tri};
+        }
+        LBMG_SORT(ct.begin(), ct.end(), kt_less);
+        ct.erase(std::unique(ct.begin(), ct.end(), [](const KT &a, const KT &b) { return a.key == b.key && a.tri == b.tri; }), ct.end());
     }
-    LBMG_SORT(ct.begin(), ct.end(), kt_less);
-    ct.erase(std::unique(ct.begin(), ct.end(), [](const KT &a, const KT &b) { return a.key == b.key && a.tri == b.tri; }), ct.end());
     const size_t m = ct.size();
     // corner groups
     std::vector<int64_t> gstart;
