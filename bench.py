@@ -269,7 +269,9 @@ def batch_main(args):
     dev = torch.device("cuda", local)
     meshes = meshgen.batch_mix(64)
     t, tol, nrhs = 1e-4, 1e-6, 3
+    t_build = time.perf_counter()
     hb = L.lbmg_build_batch(meshes)
+    t_build = time.perf_counter() - t_build
     ninst = L.lbmg_instances(hb)
     nu = sum(L.lbmg_instance_info(hb, i)[2] for i in range(ninst))
     f = np.concatenate([V for V, _, _ in meshes], axis=0)
@@ -358,6 +360,7 @@ def batch_main(args):
             "ms_to_tol_mixed": ms / args.steps, "ms_to_tol_fp64": fp64_ms, "cycles_per_step": cycles / args.steps,
             "fp64_cycles_per_step": fp64_cycles, "max_rel_residual_per_mesh": rel,
             "meshes_converged": nconv, "max_cycles": args.max_cycles,
+            "setup_s": {"hierarchy_build_and_upload": t_build},
             "solver": args.solver,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": None, "kernel": ("whole mixed batch solve, algorithmic bytes of its V-cycles "
@@ -422,13 +425,17 @@ def main():
     V, F, depth, t, f, tol, _ = meshgen.config_mesh(workload)
     f = f.reshape(V.shape[0], -1)
     nv = V.shape[0]
+    t_build = time.perf_counter()
     h = L.lbmg_build_hierarchy(V, F, depth, persistent=int(args.persistent), use_graphs=int(not args.no_graphs),
                                pdl=int(not args.no_pdl))
+    t_build = time.perf_counter() - t_build
     d0, D = L.lbmg_levels(h)
     n, nnz, nfrag = L.lbmg_level_info(h, D)
     nrhs = f.shape[1]
     # setup, like the hierarchy build: launch shapes tuned once per mesh on its own matrices
     L.lbmg_assemble(h, t)
+    torch.cuda.synchronize()
+    t_tune = time.perf_counter()
     if not args.no_tune:
         if args.tune_cache and os.path.exists(args.tune_cache):
             L.lbmg_tune_cache_load(args.tune_cache)
@@ -436,6 +443,8 @@ def main():
             L.lbmg_autotune(h, nrhs, prec, reps=4)
         if args.tune_cache:
             L.lbmg_tune_cache_save(args.tune_cache)
+    torch.cuda.synchronize()
+    t_tune = time.perf_counter() - t_tune
     shapes = {str(d): L.lbmg_launch_shape(h, d, L.LBMG_MIXED) for d in range(d0 + 1, D + 1)}
     tuned_us = {str(d): [round(1e3 * v, 2) for v in L.lbmg_tuned_times(h, d, L.LBMG_MIXED)] for d in range(d0 + 1, D + 1)}
     f_dev = torch.tensor(f, dtype=torch.float64, device=dev)
@@ -617,6 +626,7 @@ def main():
                        "launch_shapes_mixed": {d: {"sweep": list(v[0]), "residual": list(v[1])}
                                                for d, v in shapes.items()},
                        "tuned_us_per_sweep_and_residual": tuned_us},
+            "setup_s": {"hierarchy_build_and_upload": t_build, "autotune": t_tune},
             "ms_to_tol_mixed": ms_per_step, "ms_to_tol_fp64": fp64_ms, "solver": args.solver,
             "other_solver": {"solver": other, **other_res}, "learned": learned,
             "cycles_per_step": cycles / args.steps, "fp64_cycles_per_step": fp64_cycles / fp64_steps,
