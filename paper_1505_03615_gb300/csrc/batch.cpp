@@ -124,22 +124,25 @@ int combine_batch(std::vector<HostHierarchy> &parts, HostHierarchy &B, std::stri
     B.nv = (int)nv; B.nt = (int)nt; B.nfrag = (int)nf;
     B.S = parts[0].S; B.sigma = parts[0].sigma;
     for (int a = 0; a < 3; a++) B.center[a] = parts[0].center[a];
-    B.Vg.reserve(3 * nv); B.F.reserve(3 * nt); B.tri_normal.reserve(3 * nt);
-    B.frag_tri.reserve(nf); B.frag_vox.reserve(3 * nf); B.frag_pstart.reserve(nf + 1);
-    B.frag_poly.reserve(3 * np); B.frag_scale.reserve(nf);
-    B.frag_pstart.push_back(0);
+    B.Vg.resize(3 * nv); B.F.resize(3 * nt); B.tri_normal.resize(3 * nt);
+    B.frag_tri.resize(nf); B.frag_vox.resize(3 * nf); B.frag_pstart.resize(nf + 1);
+    B.frag_poly.resize(3 * np); B.frag_scale.resize(nf);
+    B.frag_pstart[0] = 0;
     for (int i = 0; i < ni; i++) {
         HostHierarchy &P = parts[i];
-        B.Vg.insert(B.Vg.end(), P.Vg.begin(), P.Vg.end());
-        for (int32_t v : P.F) B.F.push_back(v + B.inst_voff[i]);
-        B.tri_normal.insert(B.tri_normal.end(), P.tri_normal.begin(), P.tri_normal.end());
+        const int64_t vo = B.inst_voff[i], to = B.inst_toff[i], fo = foff[i];
+        std::copy(P.Vg.begin(), P.Vg.end(), B.Vg.begin() + 3 * vo);
+        std::copy(P.tri_normal.begin(), P.tri_normal.end(), B.tri_normal.begin() + 3 * to);
+        std::copy(P.frag_poly.begin(), P.frag_poly.end(), B.frag_poly.begin() + 3 * poff[i]);
+#pragma omp parallel for schedule(static)
+        for (int64_t q = 0; q < 3 * (int64_t)P.nt; q++) B.F[3 * to + q] = P.F[q] + (int32_t)vo;
+#pragma omp parallel for schedule(static)
         for (int f = 0; f < P.nfrag; f++) {
-            B.frag_tri.push_back(P.frag_tri[f] + B.inst_toff[i]);
-            for (int a = 0; a < 3; a++) B.frag_vox.push_back(P.frag_vox[3 * (size_t)f + a]);
-            B.frag_pstart.push_back((int32_t)(poff[i] + P.frag_pstart[f + 1]));
-            B.frag_scale.push_back(P.sigma * P.sigma);
+            B.frag_tri[fo + f] = P.frag_tri[f] + (int32_t)to;
+            for (int a = 0; a < 3; a++) B.frag_vox[3 * (fo + f) + a] = P.frag_vox[3 * (size_t)f + a];
+            B.frag_pstart[fo + f + 1] = (int32_t)(poff[i] + P.frag_pstart[f + 1]);
+            B.frag_scale[fo + f] = P.sigma * P.sigma;
         }
-        B.frag_poly.insert(B.frag_poly.end(), P.frag_poly.begin(), P.frag_poly.end());
     }
 
     B.lev.assign(B.D + 1, HostLevel());
@@ -200,16 +203,20 @@ int combine_batch(std::vector<HostHierarchy> &parts, HostHierarchy &B, std::stri
         L.ci.assign(L.rp[row], 0);
         for (int i = 0; i < ni; i++)
             if (!rmap[i].empty()) nmap[i].assign(parts[i].lev[real(i, dB)].ci.size(), -1);
-        std::vector<std::pair<int32_t, int32_t>> tmp;
-        for (int r = 0; r < row; r++) {
-            const int i = src_i[r], a = src_a[r];
-            const HostLevel &P = parts[i].lev[real(i, dB)];
-            tmp.clear();
-            for (int k = P.rp[a]; k < P.rp[a + 1]; k++) tmp.push_back({rmap[i][P.ci[k]], k});
-            std::sort(tmp.begin(), tmp.end());
-            for (size_t q = 0; q < tmp.size(); q++) {
-                L.ci[L.rp[r] + q] = tmp[q].first;
-                nmap[i][tmp[q].second] = L.rp[r] + (int32_t)q;
+#pragma omp parallel
+        {
+            std::vector<std::pair<int32_t, int32_t>> tmp;
+#pragma omp for schedule(dynamic, 256)
+            for (int r = 0; r < row; r++) {
+                const int i = src_i[r], a = src_a[r];
+                const HostLevel &P = parts[i].lev[real(i, dB)];
+                tmp.clear();
+                for (int k = P.rp[a]; k < P.rp[a + 1]; k++) tmp.push_back({rmap[i][P.ci[k]], k});
+                std::sort(tmp.begin(), tmp.end());
+                for (size_t q = 0; q < tmp.size(); q++) {
+                    L.ci[L.rp[r] + q] = tmp[q].first;
+                    nmap[i][tmp[q].second] = L.rp[r] + (int32_t)q;
+                }
             }
         }
         if (dB == B.D) {
@@ -217,6 +224,7 @@ int combine_batch(std::vector<HostHierarchy> &parts, HostHierarchy &B, std::stri
             B.frag_dof.resize(8 * (size_t)nf);
             for (int i = 0; i < ni; i++) {
                 const HostHierarchy &P = parts[i];
+#pragma omp parallel for schedule(static)
                 for (size_t q = 0; q < P.frag_dof.size(); q++)
                     B.frag_dof[8 * (size_t)foff[i] + q] = rmap[i][P.frag_dof[q]];
             }
@@ -224,15 +232,18 @@ int combine_batch(std::vector<HostHierarchy> &parts, HostHierarchy &B, std::stri
             B.arp.assign(nnz + 1, 0);
             for (int i = 0; i < ni; i++) {
                 const HostHierarchy &P = parts[i];
+#pragma omp parallel for schedule(static)
                 for (size_t k = 0; k < nmap[i].size(); k++) B.arp[nmap[i][k] + 1] = P.arp[k + 1] - P.arp[k];
             }
             for (int64_t s = 0; s < nnz; s++) B.arp[s + 1] += B.arp[s];
             B.aidx.assign(B.arp[nnz], 0);
             for (int i = 0; i < ni; i++) {
                 const HostHierarchy &P = parts[i];
+                const uint32_t fo36 = (uint32_t)(36 * foff[i]);
+#pragma omp parallel for schedule(static)
                 for (size_t k = 0; k < nmap[i].size(); k++) {
                     int64_t o = B.arp[nmap[i][k]];
-                    for (int64_t q = P.arp[k]; q < P.arp[k + 1]; q++) B.aidx[o++] = P.aidx[q] + (uint32_t)(36 * foff[i]);
+                    for (int64_t q = P.arp[k]; q < P.arp[k + 1]; q++) B.aidx[o++] = P.aidx[q] + fo36;
                 }
             }
             B.rrp.assign(row + 1, 0);
@@ -241,6 +252,7 @@ int combine_batch(std::vector<HostHierarchy> &parts, HostHierarchy &B, std::stri
                 B.rrp[r + 1] = B.rrp[r] + (P.rrp[src_a[r] + 1] - P.rrp[src_a[r]]);
             }
             B.ridx.assign(B.rrp[row], 0);
+#pragma omp parallel for schedule(static)
             for (int r = 0; r < row; r++) {
                 const HostHierarchy &P = parts[src_i[r]];
                 int64_t o = B.rrp[r];
@@ -251,6 +263,7 @@ int combine_batch(std::vector<HostHierarchy> &parts, HostHierarchy &B, std::stri
             B.vw.assign(8 * nv, 0.0);
             for (int i = 0; i < ni; i++) {
                 const HostHierarchy &P = parts[i];
+#pragma omp parallel for schedule(static)
                 for (size_t q = 0; q < P.vdof.size(); q++) {
                     const size_t o = 8 * (size_t)B.inst_voff[i] + q;
                     B.vdof[o] = P.vdof[q] >= 0 ? rmap[i][P.vdof[q]] : -1;
@@ -269,6 +282,7 @@ int combine_batch(std::vector<HostHierarchy> &parts, HostHierarchy &B, std::stri
                 L.crp[r + 1] = L.crp[r] + (P.crp[src_a[r] + 1] - P.crp[src_a[r]]);
             }
             L.cch.assign(L.crp[row], 0);
+#pragma omp parallel for schedule(static)
             for (int r = 0; r < row; r++) {
                 const int i = src_i[r];
                 const HostLevel &P = parts[i].lev[real(i, dB)];
@@ -283,29 +297,34 @@ int combine_batch(std::vector<HostHierarchy> &parts, HostHierarchy &B, std::stri
             for (int i = 0; i < ni; i++) {
                 if (rmap[i].empty()) continue;
                 const HostLevel &P = parts[i].lev[real(i, dB)];
+#pragma omp parallel for schedule(static)
                 for (size_t k = 0; k < nmap[i].size(); k++) L.grp[nmap[i][k] + 1] = P.grp[k + 1] - P.grp[k];
             }
             for (int64_t s = 0; s < nnz; s++) L.grp[s + 1] += L.grp[s];
             L.gidx.assign(L.grp[nnz], 0);
+            int too_large = 0;
             for (int i = 0; i < ni; i++) {
                 if (rmap[i].empty()) continue;
                 const HostLevel &P = parts[i].lev[real(i, dB)];
+#pragma omp parallel for schedule(static) reduction(| : too_large)
                 for (size_t k = 0; k < nmap[i].size(); k++) {
                     int64_t o = L.grp[nmap[i][k]];
                     for (int64_t q = P.grp[k]; q < P.grp[k + 1]; q++) {
                         const uint32_t e = P.gidx[q];
                         const int32_t idx = nmapF[i][e & kGalMask];
-                        if ((uint32_t)idx > kGalMask) { err = "batch level too large for packed Galerkin lists"; return 1; }
+                        too_large |= (uint32_t)idx > kGalMask;
                         L.gidx[o++] = (uint32_t)idx | (e & ~kGalMask);
                     }
                 }
             }
+            if (too_large) { err = "batch level too large for packed Galerkin lists"; return 1; }
             Lf.par.assign(8 * (size_t)Lf.ndof, -1);
             Lf.npar_log2.assign(Lf.ndof, 0);
             for (int i = 0; i < ni; i++) {
                 if (rmapF[i].empty() || rmap[i].empty()) continue;
                 const HostLevel &P = parts[i].lev[real(i, dB + 1)];
                 if (P.par.empty()) continue;
+#pragma omp parallel for schedule(static)
                 for (int a = 0; a < P.ndof; a++) {
                     const int r = rmapF[i][a];
                     Lf.npar_log2[r] = P.npar_log2[a];
