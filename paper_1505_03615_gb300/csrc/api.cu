@@ -8,6 +8,10 @@
 #include <string>
 #include <vector>
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
 #include "../../include/lbmg.h"
 #include "lbmg_internal.h"
 
@@ -640,10 +644,34 @@ int lbmg_build_batch(const double *const *V, const int *nv, const int *const *F,
     int st = 0;
     try {
         std::vector<HostHierarchy> parts(ninst);
-        for (int i = 0; i < ninst && st == 0; i++) {
-            if (!V[i] || !F[i]) { st = LBMG_INVALID_ARG; break; }
-            st = build_host_hierarchy(V[i], nv[i], F[i], nt[i], depth[i], o.min_depth, o.coarse_max, o.split,
-                                      o.threads, parts[i], err);
+        for (int i = 0; i < ninst && st == 0; i++)
+            if (!V[i] || !F[i]) { st = LBMG_INVALID_ARG; err = "null mesh pointer"; }
+        if (st == 0) {
+            // Meshes are built concurrently, one per thread; the builder's own parallel loops
+            // then run on that thread alone.  Each mesh's hierarchy is independent of the
+            // schedule.
+            std::vector<int> sti(ninst, 0);
+            std::vector<std::string> erri(ninst);
+#ifdef _OPENMP
+            if (o.threads > 0) omp_set_num_threads(o.threads);
+#endif
+#pragma omp parallel for schedule(dynamic, 1)
+            for (int i = 0; i < ninst; i++) {
+                try {
+                    sti[i] = build_host_hierarchy(V[i], nv[i], F[i], nt[i], depth[i], o.min_depth, o.coarse_max,
+                                                  o.split, 0, parts[i], erri[i]);
+                } catch (const std::bad_alloc &) {
+                    sti[i] = LBMG_OUT_OF_MEMORY;
+                    erri[i] = "host memory exhausted";
+                } catch (const std::exception &e) {
+                    sti[i] = LBMG_INVALID_ARG;
+                    erri[i] = e.what();
+                } catch (...) {
+                    sti[i] = LBMG_INVALID_ARG;
+                }
+            }
+            for (int i = 0; i < ninst && st == 0; i++)
+                if (sti[i] != 0) { st = sti[i]; err = "mesh " + std::to_string(i) + ": " + erri[i]; }
         }
         if (st == 0) st = combine_batch(parts, h->c.host, err);
     } catch (const std::bad_alloc &) {
