@@ -132,6 +132,11 @@ void lbmg_destroy(lbmg_handle h);
  * The finest-level vectors of a batch are the meshes' own finest vectors
  * concatenated in mesh order (see lbmg_instance_info); vertex arrays likewise.
  * A batch always uses the persistent solve; it stops when every mesh meets tol.
+ * The meshes are built concurrently, one per host thread (opt->threads of them,
+ * 0 = all cores), so the host memory held at once grows with the thread count.
+ * Errors: LBMG_INVALID_ARG for a NULL array, ninst < 1 or a bad mesh (the first
+ * failing mesh is named in lbmg_last_cuda_error), LBMG_DEGENERATE_MESH,
+ * LBMG_OUT_OF_MEMORY, LBMG_CUDA_ERROR.
  */
 int lbmg_build_batch(const double *const *V, const int *nv, const int *const *F, const int *nt, const int *depth,
                      int ninst, const lbmg_options *opt, lbmg_handle *out);
