@@ -313,6 +313,29 @@ int lbmg_get_matrix(lbmg_handle h, int d, int *rowptr, int *col, double *M, doub
 int lbmg_get_prolongation(lbmg_handle h, int d, int *parents, double *weights);
 
 /*
+ * Host-only hierarchy: the construction of lbmg_build_hierarchy (Sections 3.2,
+ * 4.1-4.3: voxel pieces, split functions, the Eq. 4 prolongation, the sparsity
+ * pattern of every level) without any device memory or CUDA call, so that the
+ * split space can be built and inspected on a machine without a GPU.  Arguments
+ * and errors of lbmg_host_build are those of lbmg_build_hierarchy (no
+ * LBMG_CUDA_ERROR); the other calls read the result in the same layout and dof
+ * order as the device handle's lbmg_levels, lbmg_level_info, lbmg_get_dofs,
+ * lbmg_get_matrix (pattern only) and lbmg_get_prolongation.  LBMG_INVALID_ARG
+ * for a NULL handle or a level outside [min_depth, depth] (outside
+ * (min_depth, depth] for the prolongation).  The handle is owned by the caller
+ * and released with lbmg_host_destroy; a host handle is not an lbmg_handle.
+ */
+typedef struct lbmg_host_ctx *lbmg_host_handle;
+int lbmg_host_build(const double *V, int nv, const int *F, int nt, int depth, const lbmg_options *opt,
+                    lbmg_host_handle *out);
+void lbmg_host_destroy(lbmg_host_handle h);
+int lbmg_host_levels(lbmg_host_handle h, int *min_depth, int *depth);
+int lbmg_host_level_info(lbmg_host_handle h, int d, long *ndof, long *nnz, long *nfrag);
+int lbmg_host_get_dofs(lbmg_host_handle h, int d, int *corner, int *mintri);
+int lbmg_host_get_pattern(lbmg_host_handle h, int d, int *rowptr, int *col);
+int lbmg_host_get_prolongation(lbmg_host_handle h, int d, int *parents, double *weights);
+
+/*
  * Learned relaxation weights for the finest-level Gauss-Seidel sweeps.  The paper
  * has no counterpart: its smoother is plain Gauss-Seidel (Sections 4.3, 5.2), which
  * is also the fallback here and the yardstick of the learned sweep.  A network 28 -> 64 (ReLU) -> 1 maps each

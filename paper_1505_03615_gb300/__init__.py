@@ -25,6 +25,8 @@ __all__ = [
     "lbmg_learned_loss_grad", "lbmg_learned_train", "lbmg_learned_enable", "lbmg_learned_omega",
     "lbmg_residual_norms_noalloc", "lbmg_status_string", "lbmg_last_cuda_error", "lbmg_default_options",
     "lbmg_solve_pcg", "lbmg_autotune", "lbmg_launch_shape", "lbmg_tuned_times", "lbmg_set_launch_shape", "lbmg_tune_cache_save", "lbmg_tune_cache_load",
+    "lbmg_host_build", "lbmg_host_destroy", "lbmg_host_levels", "lbmg_host_level_info", "lbmg_host_get_dofs",
+    "lbmg_host_get_pattern", "lbmg_host_get_prolongation",
 ]
 
 LBMG_OK = 0
@@ -42,7 +44,7 @@ _lib = None
 class LbmgError(RuntimeError):
     def __init__(self, code, where):
         msg = f"{where}: {_lib.lbmg_status_string(code).decode()} ({code})" if _lib else f"{where}: status {code}"
-        if _lib is not None and (code == 7 or where.startswith("lbmg_build")):
+        if _lib is not None and (code == 7 or where.startswith(("lbmg_build", "lbmg_host_build"))):
             detail = _lib.lbmg_last_cuda_error().decode()
             if detail:
                 msg += " -- " + detail
@@ -113,6 +115,13 @@ def load_library():
         "lbmg_learned_enable": (i, [P, i, P]),
         "lbmg_learned_omega": (i, [P, P]),
         "lbmg_residual_norms_noalloc": (i, [P, i, P, P, i, P, P]),
+        "lbmg_host_build": (i, [P, i, P, i, i, P, P]),
+        "lbmg_host_destroy": (None, [P]),
+        "lbmg_host_levels": (i, [P, P, P]),
+        "lbmg_host_level_info": (i, [P, i, P, P, P]),
+        "lbmg_host_get_dofs": (i, [P, i, P, P]),
+        "lbmg_host_get_pattern": (i, [P, i, P, P]),
+        "lbmg_host_get_prolongation": (i, [P, i, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -437,4 +446,59 @@ def lbmg_get_prolongation(h, d):
     par = np.zeros((n, 8), np.int32)
     w = np.zeros((n, 8))
     _check(load_library().lbmg_get_prolongation(h, int(d), _ptr(par), _ptr(w)), "lbmg_get_prolongation")
+    return par, w
+
+
+def lbmg_host_build(V, F, depth, **opts):
+    """Host-only hierarchy (no GPU needed); V float64 [nv,3], F int32 [nt,3].  Returns the host handle."""
+    lib = load_library()
+    V = np.ascontiguousarray(V, dtype=np.float64)
+    F = np.ascontiguousarray(F, dtype=np.int32)
+    o = lbmg_default_options()
+    for k, v in opts.items():
+        setattr(o, k, v)
+    h = C.c_void_p()
+    _check(lib.lbmg_host_build(_ptr(V), V.shape[0], _ptr(F), F.shape[0], int(depth), C.byref(o), C.byref(h)),
+           "lbmg_host_build")
+    return h
+
+
+def lbmg_host_destroy(h):
+    load_library().lbmg_host_destroy(h)
+
+
+def lbmg_host_levels(h):
+    a, b = C.c_int(), C.c_int()
+    _check(load_library().lbmg_host_levels(h, C.byref(a), C.byref(b)), "lbmg_host_levels")
+    return a.value, b.value
+
+
+def lbmg_host_level_info(h, d):
+    n, z, f = C.c_long(), C.c_long(), C.c_long()
+    _check(load_library().lbmg_host_level_info(h, int(d), C.byref(n), C.byref(z), C.byref(f)),
+           "lbmg_host_level_info")
+    return n.value, z.value, f.value
+
+
+def lbmg_host_get_dofs(h, d):
+    n, _, _ = lbmg_host_level_info(h, d)
+    corner = np.zeros((n, 3), np.int32)
+    mintri = np.zeros(n, np.int32)
+    _check(load_library().lbmg_host_get_dofs(h, int(d), _ptr(corner), _ptr(mintri)), "lbmg_host_get_dofs")
+    return corner, mintri
+
+
+def lbmg_host_get_pattern(h, d):
+    n, nnz, _ = lbmg_host_level_info(h, d)
+    rp = np.zeros(n + 1, np.int32)
+    ci = np.zeros(nnz, np.int32)
+    _check(load_library().lbmg_host_get_pattern(h, int(d), _ptr(rp), _ptr(ci)), "lbmg_host_get_pattern")
+    return rp, ci
+
+
+def lbmg_host_get_prolongation(h, d):
+    n, _, _ = lbmg_host_level_info(h, d)
+    par = np.zeros((n, 8), np.int32)
+    w = np.zeros((n, 8))
+    _check(load_library().lbmg_host_get_prolongation(h, int(d), _ptr(par), _ptr(w)), "lbmg_host_get_prolongation")
     return par, w

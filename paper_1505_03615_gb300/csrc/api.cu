@@ -540,7 +540,64 @@ const DevLevel *noalloc_level(lbmg_handle h, int d) {
     return &h->c.lev[d];
 }
 void noalloc_set_error(const std::string &msg) { g_cuda_err = msg; }
+
+static int check_build_options(const lbmg_options &o) {
+    if (o.nu1 < 0 || o.nu2 < 0 || o.coarse_max < 1 || o.coarse_max > kMaxCoarse) return LBMG_INVALID_ARG;
+    if (o.smoother != LBMG_GS_COLOURED && o.smoother != LBMG_JACOBI) return LBMG_INVALID_ARG;
+    if (o.narrow_max < 0 || o.barrier_phantoms < 0 || o.barrier_phantoms > 1024) return LBMG_INVALID_ARG;
+    if (o.copy_phantom_bytes < 0 || o.copy_phantom_bytes > 65536) return LBMG_INVALID_ARG;
+    return LBMG_OK;
+}
+
+// host hierarchy of one mesh in the layout the device handle uploads; on failure the
+// reason goes to the thread's error string
+static int build_single_host(const double *V, int nv, const int *F, int nt, int depth, const lbmg_options &o,
+                      HostHierarchy &out) {
+    std::string err;
+    int st;
+    try {
+        std::vector<HostHierarchy> parts(1);
+        st = build_host_hierarchy(V, nv, F, nt, depth, o.min_depth, o.coarse_max, o.split, o.threads, parts[0], err);
+        if (st == 0) st = combine_batch(parts, out, err);
+    } catch (const std::bad_alloc &) {
+        st = LBMG_OUT_OF_MEMORY;
+        err = "host memory exhausted";
+    } catch (const std::exception &e) {
+        st = LBMG_INVALID_ARG;
+        err = e.what();
+    } catch (...) {
+        st = LBMG_INVALID_ARG;
+    }
+    if (st != 0) g_cuda_err = "hierarchy build: " + err;
+    return st;
+}
+
+static void copy_dofs(const HostLevel &L, int *corner, int *mintri) {
+    if (corner) std::memcpy(corner, L.corner.data(), L.corner.size() * sizeof(int));
+    if (mintri) std::memcpy(mintri, L.mintri.data(), L.mintri.size() * sizeof(int));
+}
+
+static void copy_pattern(const HostLevel &L, int *rowptr, int *col) {
+    if (rowptr) std::memcpy(rowptr, L.rp.data(), L.rp.size() * sizeof(int));
+    if (col) std::memcpy(col, L.ci.data(), L.ci.size() * sizeof(int));
+}
+
+static void copy_prolongation(const HostLevel &L, int *parents, double *weights) {
+    for (int i = 0; i < L.ndof; i++) {
+        const int np = 1 << L.npar_log2[i];
+        for (int q = 0; q < 8; q++) {
+            if (parents) parents[8 * (size_t)i + q] = q < np ? L.par[8 * (size_t)i + q] : -1;
+            if (weights) weights[8 * (size_t)i + q] = q < np ? 1.0 / np : 0.0;
+        }
+    }
+}
+
 }  // namespace lbmg
+
+// host-only hierarchy (no device memory)
+struct lbmg_host_ctx {
+    lbmg::HostHierarchy H;
+};
 
 extern "C" {
 
@@ -587,29 +644,11 @@ int lbmg_build_hierarchy(const double *V, int nv, const int *F, int nt, int dept
     lbmg_options o;
     lbmg_default_options(&o);
     if (opt) o = *opt;
-    if (o.nu1 < 0 || o.nu2 < 0 || o.coarse_max < 1 || o.coarse_max > kMaxCoarse) return LBMG_INVALID_ARG;
-    if (o.smoother != LBMG_GS_COLOURED && o.smoother != LBMG_JACOBI) return LBMG_INVALID_ARG;
-    if (o.narrow_max < 0 || o.barrier_phantoms < 0 || o.barrier_phantoms > 1024) return LBMG_INVALID_ARG;
-    if (o.copy_phantom_bytes < 0 || o.copy_phantom_bytes > 65536) return LBMG_INVALID_ARG;
+    LBMG_TRY(check_build_options(o));
     lbmg_ctx *h = new (std::nothrow) lbmg_ctx();
     if (!h) return LBMG_OUT_OF_MEMORY;
-    std::string err;
-    int st;
-    try {
-        std::vector<HostHierarchy> parts(1);
-        st = build_host_hierarchy(V, nv, F, nt, depth, o.min_depth, o.coarse_max, o.split, o.threads, parts[0], err);
-        if (st == 0) st = combine_batch(parts, h->c.host, err);
-    } catch (const std::bad_alloc &) {
-        st = LBMG_OUT_OF_MEMORY;
-        err = "host memory exhausted";
-    } catch (const std::exception &e) {
-        st = LBMG_INVALID_ARG;
-        err = e.what();
-    } catch (...) {
-        st = LBMG_INVALID_ARG;
-    }
+    int st = build_single_host(V, nv, F, nt, depth, o, h->c.host);
     if (st != 0) {
-        g_cuda_err = "hierarchy build: " + err;
         delete h;
         return st;
     }
@@ -1281,17 +1320,13 @@ int lbmg_learned_omega(lbmg_handle h, double *omega) {
 
 int lbmg_get_dofs(lbmg_handle h, int d, int *corner, int *mintri) {
     LBMG_TRY(check_level(h, d));
-    const HostLevel &L = h->c.host.lev[d];
-    if (corner) std::memcpy(corner, L.corner.data(), L.corner.size() * sizeof(int));
-    if (mintri) std::memcpy(mintri, L.mintri.data(), L.mintri.size() * sizeof(int));
+    copy_dofs(h->c.host.lev[d], corner, mintri);
     return LBMG_OK;
 }
 
 int lbmg_get_matrix(lbmg_handle h, int d, int *rowptr, int *col, double *M, double *L) {
     LBMG_TRY(check_level(h, d));
-    const HostLevel &hl = h->c.host.lev[d];
-    if (rowptr) std::memcpy(rowptr, hl.rp.data(), hl.rp.size() * sizeof(int));
-    if (col) std::memcpy(col, hl.ci.data(), hl.ci.size() * sizeof(int));
+    copy_pattern(h->c.host.lev[d], rowptr, col);
     if (M || L) {
         if (!h->c.assembled) return LBMG_NOT_ASSEMBLED;
         const DevLevel &dl = h->c.lev[d];
@@ -1304,14 +1339,62 @@ int lbmg_get_matrix(lbmg_handle h, int d, int *rowptr, int *col, double *M, doub
 int lbmg_get_prolongation(lbmg_handle h, int d, int *parents, double *weights) {
     LBMG_TRY(check_level(h, d));
     if (d == h->c.d0) return LBMG_INVALID_ARG;
-    const HostLevel &L = h->c.host.lev[d];
-    for (int i = 0; i < L.ndof; i++) {
-        const int np = 1 << L.npar_log2[i];
-        for (int q = 0; q < 8; q++) {
-            if (parents) parents[8 * (size_t)i + q] = q < np ? L.par[8 * (size_t)i + q] : -1;
-            if (weights) weights[8 * (size_t)i + q] = q < np ? 1.0 / np : 0.0;
-        }
+    copy_prolongation(h->c.host.lev[d], parents, weights);
+    return LBMG_OK;
+}
+
+int lbmg_host_build(const double *V, int nv, const int *F, int nt, int depth, const lbmg_options *opt,
+                    lbmg_host_handle *out) {
+    if (!out || !V || !F) return LBMG_INVALID_ARG;
+    *out = nullptr;
+    lbmg_options o;
+    lbmg_default_options(&o);
+    if (opt) o = *opt;
+    LBMG_TRY(check_build_options(o));
+    lbmg_host_ctx *h = new (std::nothrow) lbmg_host_ctx();
+    if (!h) return LBMG_OUT_OF_MEMORY;
+    const int st = build_single_host(V, nv, F, nt, depth, o, h->H);
+    if (st != 0) {
+        delete h;
+        return st;
     }
+    *out = h;
+    return LBMG_OK;
+}
+
+void lbmg_host_destroy(lbmg_host_handle h) { delete h; }
+
+int lbmg_host_levels(lbmg_host_handle h, int *min_depth, int *depth) {
+    if (!h) return LBMG_INVALID_ARG;
+    if (min_depth) *min_depth = h->H.d0;
+    if (depth) *depth = h->H.D;
+    return LBMG_OK;
+}
+
+int lbmg_host_level_info(lbmg_host_handle h, int d, long *ndof, long *nnz, long *nfrag) {
+    if (!h || d < h->H.d0 || d > h->H.D) return LBMG_INVALID_ARG;
+    const HostLevel &L = h->H.lev[d];
+    if (ndof) *ndof = L.ndof;
+    if (nnz) *nnz = L.rp.empty() ? 0 : (long)L.rp[L.ndof];
+    if (nfrag) *nfrag = d == h->H.D ? h->H.nfrag : 0;
+    return LBMG_OK;
+}
+
+int lbmg_host_get_dofs(lbmg_host_handle h, int d, int *corner, int *mintri) {
+    if (!h || d < h->H.d0 || d > h->H.D) return LBMG_INVALID_ARG;
+    copy_dofs(h->H.lev[d], corner, mintri);
+    return LBMG_OK;
+}
+
+int lbmg_host_get_pattern(lbmg_host_handle h, int d, int *rowptr, int *col) {
+    if (!h || d < h->H.d0 || d > h->H.D) return LBMG_INVALID_ARG;
+    copy_pattern(h->H.lev[d], rowptr, col);
+    return LBMG_OK;
+}
+
+int lbmg_host_get_prolongation(lbmg_host_handle h, int d, int *parents, double *weights) {
+    if (!h || d <= h->H.d0 || d > h->H.D) return LBMG_INVALID_ARG;
+    copy_prolongation(h->H.lev[d], parents, weights);
     return LBMG_OK;
 }
 
