@@ -334,6 +334,18 @@ int lbmg_host_level_info(lbmg_host_handle h, int d, long *ndof, long *nnz, long 
 int lbmg_host_get_dofs(lbmg_host_handle h, int d, int *corner, int *mintri);
 int lbmg_host_get_pattern(lbmg_host_handle h, int d, int *rowptr, int *col);
 int lbmg_host_get_prolongation(lbmg_host_handle h, int d, int *parents, double *weights);
+/*
+ * Host-only batch: the construction of lbmg_build_batch (same arguments and
+ * errors, no LBMG_CUDA_ERROR), read with the calls above.
+ *  lbmg_host_instances: number of meshes and, per mesh (arrays [ninst], may be
+ *    NULL), its finest and coarsest depth.
+ *  lbmg_host_row_instances: inst int[n_d], the mesh of every row of level d.
+ * A single-mesh host handle reports one instance.
+ */
+int lbmg_host_build_batch(const double *const *V, const int *nv, const int *const *F, const int *nt,
+                          const int *depth, int ninst, const lbmg_options *opt, lbmg_host_handle *out);
+int lbmg_host_instances(lbmg_host_handle h, int *ninst, int *depth, int *min_depth);
+int lbmg_host_row_instances(lbmg_host_handle h, int d, int *inst);
 
 /*
  * Learned relaxation weights for the finest-level Gauss-Seidel sweeps.  The paper

@@ -26,7 +26,8 @@ __all__ = [
     "lbmg_residual_norms_noalloc", "lbmg_status_string", "lbmg_last_cuda_error", "lbmg_default_options",
     "lbmg_solve_pcg", "lbmg_autotune", "lbmg_launch_shape", "lbmg_tuned_times", "lbmg_set_launch_shape", "lbmg_tune_cache_save", "lbmg_tune_cache_load",
     "lbmg_host_build", "lbmg_host_destroy", "lbmg_host_levels", "lbmg_host_level_info", "lbmg_host_get_dofs",
-    "lbmg_host_get_pattern", "lbmg_host_get_prolongation",
+    "lbmg_host_get_pattern", "lbmg_host_get_prolongation", "lbmg_host_build_batch", "lbmg_host_instances",
+    "lbmg_host_row_instances",
 ]
 
 LBMG_OK = 0
@@ -122,6 +123,9 @@ def load_library():
         "lbmg_host_get_dofs": (i, [P, i, P, P]),
         "lbmg_host_get_pattern": (i, [P, i, P, P]),
         "lbmg_host_get_prolongation": (i, [P, i, P, P]),
+        "lbmg_host_build_batch": (i, [P, P, P, P, P, i, P, P]),
+        "lbmg_host_instances": (i, [P, P, P, P]),
+        "lbmg_host_row_instances": (i, [P, i, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -461,6 +465,42 @@ def lbmg_host_build(V, F, depth, **opts):
     _check(lib.lbmg_host_build(_ptr(V), V.shape[0], _ptr(F), F.shape[0], int(depth), C.byref(o), C.byref(h)),
            "lbmg_host_build")
     return h
+
+
+def lbmg_host_build_batch(meshes, **opts):
+    """Host-only batch hierarchy (no GPU needed) of a list of (V, F, depth).  Returns the host handle."""
+    lib = load_library()
+    Vs = [np.ascontiguousarray(V, dtype=np.float64) for V, _, _ in meshes]
+    Fs = [np.ascontiguousarray(F, dtype=np.int32) for _, F, _ in meshes]
+    n = len(meshes)
+    Vp = (C.c_void_p * n)(*[V.ctypes.data for V in Vs])
+    Fp = (C.c_void_p * n)(*[F.ctypes.data for F in Fs])
+    nv = (C.c_int * n)(*[V.shape[0] for V in Vs])
+    nt = (C.c_int * n)(*[F.shape[0] for F in Fs])
+    dp = (C.c_int * n)(*[int(d) for _, _, d in meshes])
+    o = lbmg_default_options()
+    for k, v in opts.items():
+        setattr(o, k, v)
+    h = C.c_void_p()
+    _check(lib.lbmg_host_build_batch(Vp, nv, Fp, nt, dp, n, C.byref(o), C.byref(h)), "lbmg_host_build_batch")
+    return h
+
+
+def lbmg_host_instances(h):
+    """(number of meshes, finest depth per mesh, coarsest depth per mesh)."""
+    n = C.c_int()
+    _check(load_library().lbmg_host_instances(h, C.byref(n), None, None), "lbmg_host_instances")
+    D = np.zeros(n.value, np.int32)
+    d0 = np.zeros(n.value, np.int32)
+    _check(load_library().lbmg_host_instances(h, C.byref(n), _ptr(D), _ptr(d0)), "lbmg_host_instances")
+    return n.value, D, d0
+
+
+def lbmg_host_row_instances(h, d):
+    n, _, _ = lbmg_host_level_info(h, d)
+    inst = np.zeros(n, np.int32)
+    _check(load_library().lbmg_host_row_instances(h, int(d), _ptr(inst)), "lbmg_host_row_instances")
+    return inst
 
 
 def lbmg_host_destroy(h):

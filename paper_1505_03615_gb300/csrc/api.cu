@@ -592,6 +592,63 @@ static void copy_prolongation(const HostLevel &L, int *parents, double *weights)
     }
 }
 
+// host hierarchy of a batch in the layout the device handle uploads; on failure the reason
+// goes to the thread's error string
+static int build_batch_host(const double *const *V, const int *nv, const int *const *F, const int *nt,
+                            const int *depth, int ninst, const lbmg_options &o, HostHierarchy &out) {
+    std::string err;
+    int st = 0;
+    try {
+        std::vector<HostHierarchy> parts(ninst);
+        for (int i = 0; i < ninst && st == 0; i++)
+            if (!V[i] || !F[i]) { st = LBMG_INVALID_ARG; err = "null mesh pointer"; }
+        if (st == 0) {
+            // Meshes are built concurrently, one per thread; the builder's own parallel loops
+            // then run on that thread alone.  Each mesh's hierarchy is independent of the
+            // schedule.
+            std::vector<int> sti(ninst, 0);
+            std::vector<std::string> erri(ninst);
+#ifdef _OPENMP
+            if (o.threads > 0) omp_set_num_threads(o.threads);
+#endif
+#pragma omp parallel for schedule(dynamic, 1)
+            for (int i = 0; i < ninst; i++) {
+                try {
+                    sti[i] = build_host_hierarchy(V[i], nv[i], F[i], nt[i], depth[i], o.min_depth, o.coarse_max,
+                                                  o.split, 0, parts[i], erri[i]);
+                } catch (const std::bad_alloc &) {
+                    sti[i] = LBMG_OUT_OF_MEMORY;
+                    erri[i] = "host memory exhausted";
+                } catch (const std::exception &e) {
+                    sti[i] = LBMG_INVALID_ARG;
+                    erri[i] = e.what();
+                } catch (...) {
+                    sti[i] = LBMG_INVALID_ARG;
+                }
+            }
+            for (int i = 0; i < ninst && st == 0; i++)
+                if (sti[i] != 0) { st = sti[i]; err = "mesh " + std::to_string(i) + ": " + erri[i]; }
+        }
+        if (st == 0) st = combine_batch(parts, out, err);
+    } catch (const std::bad_alloc &) {
+        st = LBMG_OUT_OF_MEMORY;
+        err = "host memory exhausted";
+    } catch (const std::exception &e) {
+        st = LBMG_INVALID_ARG;
+        err = e.what();
+    } catch (...) {
+        st = LBMG_INVALID_ARG;
+    }
+    if (st != 0) g_cuda_err = "hierarchy build: " + err;
+    return st;
+}
+
+static int check_batch_options(const lbmg_options &o) {
+    if (o.nu1 < 0 || o.nu2 < 0 || o.coarse_max < 1 || o.coarse_max > kMaxCoarse) return LBMG_INVALID_ARG;
+    if (o.smoother != LBMG_GS_COLOURED || o.narrow_max < 0 || o.barrier_phantoms < 0) return LBMG_INVALID_ARG;
+    return LBMG_OK;
+}
+
 }  // namespace lbmg
 
 // host-only hierarchy (no device memory)
@@ -675,55 +732,11 @@ int lbmg_build_batch(const double *const *V, const int *nv, const int *const *F,
     lbmg_options o;
     lbmg_default_options(&o);
     if (opt) o = *opt;
-    if (o.nu1 < 0 || o.nu2 < 0 || o.coarse_max < 1 || o.coarse_max > kMaxCoarse) return LBMG_INVALID_ARG;
-    if (o.smoother != LBMG_GS_COLOURED || o.narrow_max < 0 || o.barrier_phantoms < 0) return LBMG_INVALID_ARG;
+    LBMG_TRY(check_batch_options(o));
     lbmg_ctx *h = new (std::nothrow) lbmg_ctx();
     if (!h) return LBMG_OUT_OF_MEMORY;
-    std::string err;
-    int st = 0;
-    try {
-        std::vector<HostHierarchy> parts(ninst);
-        for (int i = 0; i < ninst && st == 0; i++)
-            if (!V[i] || !F[i]) { st = LBMG_INVALID_ARG; err = "null mesh pointer"; }
-        if (st == 0) {
-            // Meshes are built concurrently, one per thread; the builder's own parallel loops
-            // then run on that thread alone.  Each mesh's hierarchy is independent of the
-            // schedule.
-            std::vector<int> sti(ninst, 0);
-            std::vector<std::string> erri(ninst);
-#ifdef _OPENMP
-            if (o.threads > 0) omp_set_num_threads(o.threads);
-#endif
-#pragma omp parallel for schedule(dynamic, 1)
-            for (int i = 0; i < ninst; i++) {
-                try {
-                    sti[i] = build_host_hierarchy(V[i], nv[i], F[i], nt[i], depth[i], o.min_depth, o.coarse_max,
-                                                  o.split, 0, parts[i], erri[i]);
-                } catch (const std::bad_alloc &) {
-                    sti[i] = LBMG_OUT_OF_MEMORY;
-                    erri[i] = "host memory exhausted";
-                } catch (const std::exception &e) {
-                    sti[i] = LBMG_INVALID_ARG;
-                    erri[i] = e.what();
-                } catch (...) {
-                    sti[i] = LBMG_INVALID_ARG;
-                }
-            }
-            for (int i = 0; i < ninst && st == 0; i++)
-                if (sti[i] != 0) { st = sti[i]; err = "mesh " + std::to_string(i) + ": " + erri[i]; }
-        }
-        if (st == 0) st = combine_batch(parts, h->c.host, err);
-    } catch (const std::bad_alloc &) {
-        st = LBMG_OUT_OF_MEMORY;
-        err = "host memory exhausted";
-    } catch (const std::exception &e) {
-        st = LBMG_INVALID_ARG;
-        err = e.what();
-    } catch (...) {
-        st = LBMG_INVALID_ARG;
-    }
+    int st = build_batch_host(V, nv, F, nt, depth, ninst, o, h->c.host);
     if (st != 0) {
-        g_cuda_err = "hierarchy build: " + err;
         delete h;
         return st;
     }
@@ -1359,6 +1372,42 @@ int lbmg_host_build(const double *V, int nv, const int *F, int nt, int depth, co
         return st;
     }
     *out = h;
+    return LBMG_OK;
+}
+
+int lbmg_host_build_batch(const double *const *V, const int *nv, const int *const *F, const int *nt,
+                          const int *depth, int ninst, const lbmg_options *opt, lbmg_host_handle *out) {
+    if (!out || !V || !nv || !F || !nt || !depth || ninst < 1) return LBMG_INVALID_ARG;
+    *out = nullptr;
+    lbmg_options o;
+    lbmg_default_options(&o);
+    if (opt) o = *opt;
+    LBMG_TRY(check_batch_options(o));
+    lbmg_host_ctx *h = new (std::nothrow) lbmg_host_ctx();
+    if (!h) return LBMG_OUT_OF_MEMORY;
+    const int st = build_batch_host(V, nv, F, nt, depth, ninst, o, h->H);
+    if (st != 0) {
+        delete h;
+        return st;
+    }
+    *out = h;
+    return LBMG_OK;
+}
+
+int lbmg_host_instances(lbmg_host_handle h, int *ninst, int *depth, int *min_depth) {
+    if (!h) return LBMG_INVALID_ARG;
+    if (ninst) *ninst = h->H.ninst;
+    for (int i = 0; i < h->H.ninst; i++) {
+        if (depth) depth[i] = h->H.inst_D[i];
+        if (min_depth) min_depth[i] = h->H.inst_d0[i];
+    }
+    return LBMG_OK;
+}
+
+int lbmg_host_row_instances(lbmg_host_handle h, int d, int *inst) {
+    if (!h || d < h->H.d0 || d > h->H.D) return LBMG_INVALID_ARG;
+    const HostLevel &L = h->H.lev[d];
+    if (inst) std::memcpy(inst, L.inst.data(), L.inst.size() * sizeof(int));
     return LBMG_OK;
 }
 
