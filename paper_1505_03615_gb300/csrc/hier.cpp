@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstring>
 #include <numeric>
+#include <stdexcept>
 
 #ifdef _OPENMP
 #include <omp.h>
@@ -165,6 +166,7 @@ inline bool kt_less(const KT &a, const KT &b) { return a.key < b.key || (a.key =
 void bucket_positions(int64_t nb, const std::vector<int32_t> &bucket, std::vector<int64_t> &ptr,
                       std::vector<uint32_t> &out) {
     const size_t m = bucket.size();
+    if (m > (size_t)UINT32_MAX) throw std::length_error("list too long for 32-bit positions");
     std::vector<uint64_t> key(m);
 #pragma omp parallel for schedule(static)
     for (size_t i = 0; i < m; i++) key[i] = (uint64_t)(uint32_t)bucket[i] << 32 | (uint64_t)i;
@@ -379,6 +381,9 @@ void rows_with_lists(int n, int ncols, const Emit &emit, HostLevel &L, std::vect
             cnt[i] = m;
         }
     }
+    int64_t total = 0;
+    for (int i = 0; i < n; i++) total += cnt[i];
+    if (total > (int64_t)INT32_MAX) throw std::length_error("level has too many stored entries for 32-bit rows");
     L.rp.assign(n + 1, 0);
     for (int i = 0; i < n; i++) L.rp[i + 1] = L.rp[i] + cnt[i];
     const int64_t nnz = L.rp[n];
