@@ -57,6 +57,7 @@ def _load():
         "orc_corner_tri": (None, [P, i, P, P, P]),
         "orc_fragments": (None, [P, i, P, P, P]),
         "orc_matrices": (None, [P, i, P, P, P, P]),
+        "orc_mass_weighted": (None, [P, i, P, P]),
         "orc_prolongation": (None, [P, i, P, P, P]),
         "orc_check_nesting": (l, [P]),
         "orc_project_rhs": (None, [P, P, i, P]),
@@ -154,6 +155,22 @@ class Hierarchy:
         L = np.zeros(nnz)
         self._lib.orc_matrices(self._h, d, _ptr(rp), _ptr(ci), _ptr(M), _ptr(L))
         return sp.csr_matrix((M, ci, rp), shape=(n, n)), sp.csr_matrix((L, ci, rp), shape=(n, n))
+
+    def mass_weighted(self, d, w_tri):
+        """M_ij = sum_T w_T int_T b_i b_j at level d (one weight per triangle; Section 5.3 M_t),
+        scipy CSR in the pattern of matrices(d)."""
+        import scipy.sparse as sp
+        n = self.ndof(d)
+        nnz = self._lib.orc_nnz(self._h, d)
+        rp = np.zeros(n + 1, np.int32)
+        ci = np.zeros(nnz, np.int32)
+        self._lib.orc_matrices(self._h, d, _ptr(rp), _ptr(ci), None, None)
+        w = np.ascontiguousarray(w_tri, dtype=np.float64)
+        if w.shape != (self._F.shape[0],):
+            raise ValueError("one weight per triangle expected")
+        M = np.zeros(nnz)
+        self._lib.orc_mass_weighted(self._h, d, _ptr(w), _ptr(M))
+        return sp.csr_matrix((M, ci, rp), shape=(n, n))
 
     def prolongation(self, d):
         """P from level d-1 to level d as scipy CSR of shape (n_d, n_{d-1})."""

@@ -471,46 +471,54 @@ static void hat_eval(const double *p, const double *cpos, double s, const int *u
     grad[2] = f[0] * f[1] * df[2];
 }
 
+/* int b_a b_c and int <grad_M b_a, grad_M b_c> over fragment fi of a level, for its 8 voxel
+   corners a, c (finest-grid units) */
+static void fragment_local(const orc_hier *h, const Level *lv, int fi, double Mloc[8][8], double Lloc[8][8]) {
+    const double s = lv->s;
+    const Frag *fr = &lv->frag[fi];
+    const double *n = h->tn + 3 * (size_t)fr->tri;
+    double cpos[8][3];
+    int upper[8][3];
+    for (int a = 0; a < 8; a++) {
+        upper[a][0] = a & 1; upper[a][1] = (a >> 1) & 1; upper[a][2] = (a >> 2) & 1;
+        for (int k = 0; k < 3; k++) cpos[a][k] = (fr->vox[k] + upper[a][k]) * s;
+    }
+    for (int a = 0; a < 8; a++)
+        for (int c = 0; c < 8; c++) { Mloc[a][c] = 0.0; Lloc[a][c] = 0.0; }
+    for (int st = 1; st + 1 < fr->np; st++) {
+        const double *P0 = fr->p[0], *P1 = fr->p[st], *P2 = fr->p[st + 1];
+        double e1[3], e2[3], cr[3];
+        for (int k = 0; k < 3; k++) { e1[k] = P1[k] - P0[k]; e2[k] = P2[k] - P0[k]; }
+        cross3(e1, e2, cr);
+        double jac = sqrt(dot3(cr, cr));    /* twice the sub-triangle area */
+        for (int qa = 0; qa < ORC_NQ; qa++)
+            for (int qb = 0; qb < ORC_NQ; qb++) {
+                double xi = gl_x[qa], eta = gl_x[qb] * (1.0 - gl_x[qa]);
+                double w = gl_w[qa] * gl_w[qb] * (1.0 - gl_x[qa]) * jac;
+                double p[3];
+                for (int k = 0; k < 3; k++) p[k] = P0[k] + xi * e1[k] + eta * e2[k];
+                double b[8], g[8][3];
+                for (int a = 0; a < 8; a++) {
+                    double grad[3];
+                    hat_eval(p, cpos[a], s, upper[a], &b[a], grad);
+                    double gn = dot3(grad, n);
+                    for (int k = 0; k < 3; k++) g[a][k] = grad[k] - gn * n[k];   /* tangential gradient */
+                }
+                for (int a = 0; a < 8; a++)
+                    for (int c = 0; c < 8; c++) {
+                        Mloc[a][c] += w * b[a] * b[c];
+                        Lloc[a][c] += w * dot3(g[a], g[c]);
+                    }
+            }
+    }
+}
+
 static void assemble_level(orc_hier *h, Level *lv) {
     gl_init();
     Row *rows = xcalloc((size_t)lv->ndof, sizeof(Row));
-    const double s = lv->s;
     for (int fi = 0; fi < lv->nfrag; fi++) {
-        const Frag *fr = &lv->frag[fi];
-        const double *n = h->tn + 3 * (size_t)fr->tri;
-        double cpos[8][3];
-        int upper[8][3];
-        for (int a = 0; a < 8; a++) {
-            upper[a][0] = a & 1; upper[a][1] = (a >> 1) & 1; upper[a][2] = (a >> 2) & 1;
-            for (int k = 0; k < 3; k++) cpos[a][k] = (fr->vox[k] + upper[a][k]) * s;
-        }
-        double Mloc[8][8] = {{0}}, Lloc[8][8] = {{0}};
-        for (int st = 1; st + 1 < fr->np; st++) {
-            const double *P0 = fr->p[0], *P1 = fr->p[st], *P2 = fr->p[st + 1];
-            double e1[3], e2[3], cr[3];
-            for (int k = 0; k < 3; k++) { e1[k] = P1[k] - P0[k]; e2[k] = P2[k] - P0[k]; }
-            cross3(e1, e2, cr);
-            double jac = sqrt(dot3(cr, cr));    /* twice the sub-triangle area */
-            for (int qa = 0; qa < ORC_NQ; qa++)
-                for (int qb = 0; qb < ORC_NQ; qb++) {
-                    double xi = gl_x[qa], eta = gl_x[qb] * (1.0 - gl_x[qa]);
-                    double w = gl_w[qa] * gl_w[qb] * (1.0 - gl_x[qa]) * jac;
-                    double p[3];
-                    for (int k = 0; k < 3; k++) p[k] = P0[k] + xi * e1[k] + eta * e2[k];
-                    double b[8], g[8][3];
-                    for (int a = 0; a < 8; a++) {
-                        double grad[3];
-                        hat_eval(p, cpos[a], s, upper[a], &b[a], grad);
-                        double gn = dot3(grad, n);
-                        for (int k = 0; k < 3; k++) g[a][k] = grad[k] - gn * n[k];   /* tangential gradient */
-                    }
-                    for (int a = 0; a < 8; a++)
-                        for (int c = 0; c < 8; c++) {
-                            Mloc[a][c] += w * b[a] * b[c];
-                            Lloc[a][c] += w * dot3(g[a], g[c]);
-                        }
-                }
-        }
+        double Mloc[8][8], Lloc[8][8];
+        fragment_local(h, lv, fi, Mloc, Lloc);
         for (int a = 0; a < 8; a++)
             for (int c = 0; c < 8; c++)
                 row_add(&rows[lv->fdof[8 * fi + a]], lv->fdof[8 * fi + c], Mloc[a][c], Lloc[a][c]);
@@ -735,6 +743,36 @@ void orc_matrices(const orc_hier *h, int d, int *rp, int *ci, double *M, double 
     memcpy(ci, lv->ci, sizeof(int) * (size_t)lv->nnz);
     if (M) memcpy(M, lv->M, sizeof(double) * (size_t)lv->nnz);
     if (L) memcpy(L, lv->L, sizeof(double) * (size_t)lv->nnz);
+}
+
+/* Mass matrix of level d with one weight per triangle, M_ij = sum_T w[T] int_T b_i b_j, in
+   the CSR pattern of orc_matrices.  When the surface moves by an affine map per triangle,
+   as in the time steps of the conformalized mean-curvature flow of Section 5.3, the area
+   element of triangle T is its build-time one times A_t(T) / A_0(T), so with those ratios as
+   w this is the mass matrix M_t of the moved surface on the build-time function space. */
+void orc_mass_weighted(const orc_hier *h, int d, const double *w, double *M) {
+    const Level *lv = &h->lev[d];
+    gl_init();
+    for (long k = 0; k < lv->nnz; k++) M[k] = 0.0;
+    for (int fi = 0; fi < lv->nfrag; fi++) {
+        double Mloc[8][8], Lloc[8][8];
+        fragment_local(h, lv, fi, Mloc, Lloc);
+        const double wt = w[lv->frag[fi].tri];
+        for (int a = 0; a < 8; a++) {
+            const int i = lv->fdof[8 * fi + a];
+            for (int c = 0; c < 8; c++) {
+                const int j = lv->fdof[8 * fi + c];
+                int lo = lv->rp[i], hi = lv->rp[i + 1];
+                while (lo < hi) {      /* column j in row i */
+                    const int mid = (lo + hi) / 2;
+                    if (lv->ci[mid] < j) lo = mid + 1; else hi = mid;
+                }
+                M[lo] += wt * Mloc[a][c];
+            }
+        }
+    }
+    const double area_scale = h->sigma * h->sigma;
+    for (long k = 0; k < lv->nnz; k++) M[k] *= area_scale;
 }
 
 void orc_prolongation(const orc_hier *h, int d, int *rp, int *ci, double *v) {

@@ -481,3 +481,52 @@ def test_vcycle_fixed_point_independent_of_coarsest_level(icosphere):
         xs.append(x[:, 0])
     M, _ = h.matrices(5)
     assert _mnorm(M, xs[0] - xs[1]) < 1e-8 * _mnorm(M, xs[0])
+
+
+def _tri_areas(V, F):
+    e1 = V[F[:, 1]] - V[F[:, 0]]
+    e2 = V[F[:, 2]] - V[F[:, 0]]
+    return 0.5 * np.linalg.norm(np.cross(e1, e2), axis=1)
+
+
+@pytest.mark.parametrize("mesh", ["sphere", "sheets"])
+def test_weighted_mass_partition_of_unity(mesh):
+    """The split functions sum to one on the surface, so for any triangle weights w the
+    entries of the weighted mass matrix sum to sum_T w_T |T|, on every level; one triangle
+    alone gives its own area (Section 5.3's M_t on the build-time space)."""
+    if mesh == "sphere":
+        V, F = meshgen.icosphere(3, 1.0, 1e-3, 1)
+        depth = 5
+    else:
+        V, F = meshgen.double_sheet(12, 0.05, 5, 0.5, 1e-6, 4)
+        depth = 5
+    o = oracle.Hierarchy(V, F, depth)
+    area = _tri_areas(V, F)
+    rng = np.random.default_rng(3)
+    w = rng.uniform(0.2, 3.0, size=F.shape[0])
+    for d in (o.min_depth, depth):
+        Mw = o.mass_weighted(d, w)
+        assert abs(Mw.sum() - (w * area).sum()) <= 1e-12 * (w * area).sum()
+        for T in rng.integers(0, F.shape[0], size=4):
+            e = np.zeros(F.shape[0])
+            e[T] = 1.0
+            assert abs(o.mass_weighted(d, e).sum() - area[T]) <= 1e-11 * area[T]
+
+
+def test_weighted_mass_unit_weights_scaling_and_linearity(icosphere):
+    """Unit weights give the mass matrix itself; weight 4 everywhere is the mass matrix of the
+    surface scaled by 2 (built from scratch: area scales by 4, the grid-unit geometry does not
+    change); the weighted mass is linear in the weights."""
+    V, F = icosphere
+    o = oracle.Hierarchy(V, F, 4)
+    o2 = oracle.Hierarchy(2.0 * V, F, 4)
+    rng = np.random.default_rng(5)
+    w1 = rng.uniform(0, 1, size=F.shape[0])
+    w2 = rng.uniform(0, 1, size=F.shape[0])
+    for d in range(o.min_depth, o.depth + 1):
+        M, _ = o.matrices(d)
+        assert abs(o.mass_weighted(d, np.ones(F.shape[0])) - M).max() == 0
+        M2, _ = o2.matrices(d)
+        assert abs(o.mass_weighted(d, np.full(F.shape[0], 4.0)) - M2).max() <= 1e-14 * abs(M2).max()
+        lin = o.mass_weighted(d, w1 + 2 * w2) - o.mass_weighted(d, w1) - 2 * o.mass_weighted(d, w2)
+        assert abs(lin).max() <= 1e-14 * abs(M).max()
