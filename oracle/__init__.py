@@ -61,6 +61,7 @@ def _load():
         "orc_prolongation": (None, [P, i, P, P, P]),
         "orc_check_nesting": (l, [P]),
         "orc_project_rhs": (None, [P, P, i, P]),
+        "orc_project_rhs_weighted": (None, [P, P, i, P, P]),
         "orc_eval_vertices": (None, [P, P, i, P]),
         "orc_solve": (i, [P, d, P, P, i, d, i, i, i, P]),
         "orc_vcycles": (i, [P, d, P, P, i, i, i, i]),
@@ -195,6 +196,18 @@ class Hierarchy:
             f = f[:, None]
         out = np.zeros((self.ndof(self.depth), f.shape[1]))
         self._lib.orc_project_rhs(self._h, _ptr(f), f.shape[1], _ptr(out))
+        return out
+
+    def project_rhs_weighted(self, f_vertex, w_tri):
+        """int f b_i with triangle T's area element scaled by w_T (the M_t u_t of Section 5.3)."""
+        f = np.ascontiguousarray(f_vertex, dtype=np.float64)
+        if f.ndim == 1:
+            f = f[:, None]
+        w = np.ascontiguousarray(w_tri, dtype=np.float64)
+        if w.shape != (self._F.shape[0],):
+            raise ValueError("one weight per triangle expected")
+        out = np.zeros((self.ndof(self.depth), f.shape[1]))
+        self._lib.orc_project_rhs_weighted(self._h, _ptr(f), f.shape[1], _ptr(w), _ptr(out))
         return out
 
     def eval_vertices(self, x):

@@ -815,7 +815,8 @@ long orc_check_nesting(const orc_hier *h) {
 /* right-hand side int f b_i, f linear on each triangle (Section 5.2)         */
 /* ------------------------------------------------------------------------ */
 
-void orc_project_rhs(const orc_hier *h, const double *fv, int nrhs, double *rhs) {
+/* rhs_i = sum_T wt[T] int_T f b_i, f linear on each triangle; wt = NULL: all weights 1 */
+static void project_rhs(const orc_hier *h, const double *fv, int nrhs, const double *wt, double *rhs) {
     gl_init();
     const Level *lv = &h->lev[h->D];
     const double s = lv->s;
@@ -843,6 +844,7 @@ void orc_project_rhs(const orc_hier *h, const double *fv, int nrhs, double *rhs)
                 for (int qb = 0; qb < ORC_NQ; qb++) {
                     double xi = gl_x[qa], eta = gl_x[qb] * (1.0 - gl_x[qa]);
                     double w = gl_w[qa] * gl_w[qb] * (1.0 - gl_x[qa]) * jac * h->sigma * h->sigma;
+                    if (wt) w *= wt[t];
                     double p[3], q[3];
                     for (int k = 0; k < 3; k++) { p[k] = P0[k] + xi * e1[k] + eta * e2[k]; q[k] = p[k] - A[k]; }
                     /* barycentric coordinates of p in triangle (A,B,C) */
@@ -862,6 +864,16 @@ void orc_project_rhs(const orc_hier *h, const double *fv, int nrhs, double *rhs)
                 }
         }
     }
+}
+
+void orc_project_rhs(const orc_hier *h, const double *fv, int nrhs, double *rhs) {
+    project_rhs(h, fv, nrhs, NULL, rhs);
+}
+
+/* int f b_i with the area element of triangle T scaled by w[T]: the right-hand side M_t u_t of
+   a cMCF step (Section 5.3) on the build-time space */
+void orc_project_rhs_weighted(const orc_hier *h, const double *fv, int nrhs, const double *w, double *rhs) {
+    project_rhs(h, fv, nrhs, w, rhs);
 }
 
 /* ------------------------------------------------------------------------ */

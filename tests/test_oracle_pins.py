@@ -530,3 +530,23 @@ def test_weighted_mass_unit_weights_scaling_and_linearity(icosphere):
         assert abs(o.mass_weighted(d, np.full(F.shape[0], 4.0)) - M2).max() <= 1e-14 * abs(M2).max()
         lin = o.mass_weighted(d, w1 + 2 * w2) - o.mass_weighted(d, w1) - 2 * o.mass_weighted(d, w2)
         assert abs(lin).max() <= 1e-14 * abs(M).max()
+
+
+def test_weighted_rhs_against_weighted_mass(icosphere):
+    """For f = 1 the weighted projection is the row sums of the weighted mass matrix (the
+    split functions sum to one), two separately written quadratures; unit weights give the
+    plain projection, and the total is sum_T w_T int_T f."""
+    V, F = icosphere
+    o = oracle.Hierarchy(V, F, 4)
+    rng = np.random.default_rng(9)
+    w = rng.uniform(0.2, 3.0, size=F.shape[0])
+    ones = np.ones((V.shape[0], 1))
+    r1 = o.project_rhs_weighted(ones, w)[:, 0]
+    Mw = o.mass_weighted(o.depth, w)
+    assert abs(r1 - np.asarray(Mw.sum(axis=1)).ravel()).max() <= 1e-13 * abs(r1).max()
+    f = rng.uniform(-1, 1, size=(V.shape[0], 2))
+    assert abs(o.project_rhs_weighted(f, np.ones(F.shape[0])) - o.project_rhs(f)).max() == 0
+    # f linear per triangle: int_T f = |T| * mean of its three vertex values
+    area = _tri_areas(V, F)
+    tot = (w[:, None] * area[:, None] * f[F].mean(axis=1)).sum(axis=0)
+    assert np.allclose(o.project_rhs_weighted(f, w).sum(axis=0), tot, rtol=1e-12, atol=1e-14)
