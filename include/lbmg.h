@@ -158,6 +158,23 @@ int lbmg_level_info(lbmg_handle h, int d, long *ndof, long *nnz, long *nfrag);
 int lbmg_embedding(lbmg_handle h, double *cube_side, double *center);
 
 /*
+ * Per-triangle area weights for the mass matrix and the right-hand side
+ * (Section 5.3, conformalized mean-curvature flow).  A cMCF step solves
+ * (M_t + delta L_0) u_{t+1} = M_t u_t on the build-time function space: the
+ * surface has moved by an affine map per triangle, so triangle T's area element
+ * is the build-time one times w[T] = A_t(T) / A_0(T).  After this call,
+ * lbmg_assemble forms A = M_w + t L with M_w,ij = sum_T w[T] int_T b_i b_j and L
+ * unchanged, and lbmg_project_rhs integrates with the same weights.
+ *  w: host double[nt] (the meshes' triangles in order, concatenated for a
+ *     batch), each finite and >= 0; NULL restores the build-time metric (all 1).
+ * Synchronizes `stream` first (the kernels that read the weights must have
+ * finished) and copies synchronously.  Takes effect at the next lbmg_assemble /
+ * lbmg_project_rhs.  Errors: LBMG_INVALID_ARG (NULL handle, a negative or
+ * non-finite weight), LBMG_CUDA_ERROR.
+ */
+int lbmg_set_area_weights(lbmg_handle h, const double *w, void *stream);
+
+/*
  * Assemble A_d = M_d + t L_d for every level (Eq. 2, Section 5.1; positive
  * stiffness L_ij = int <grad_M b_i, grad_M b_j>).  The finest level is
  * integrated exactly over each fragment (Gauss-Legendre product rule on a fan

@@ -18,7 +18,7 @@ __all__ = [
     "LbmgError", "Options", "Stats", "load_library", "exported_symbols",
     "LBMG_OK", "LBMG_NOT_CONVERGED", "LBMG_DEVICE_TIMEOUT", "LBMG_FP64", "LBMG_MIXED", "LBMG_GS_COLOURED", "LBMG_JACOBI",
     "lbmg_build_hierarchy", "lbmg_destroy", "lbmg_levels", "lbmg_level_info", "lbmg_embedding",
-    "lbmg_assemble", "lbmg_project_rhs", "lbmg_solve", "lbmg_vcycles", "lbmg_residual", "lbmg_smooth",
+    "lbmg_assemble", "lbmg_set_area_weights", "lbmg_project_rhs", "lbmg_solve", "lbmg_vcycles", "lbmg_residual", "lbmg_smooth",
     "lbmg_restrict", "lbmg_prolong_add", "lbmg_eval_vertices", "lbmg_get_dofs", "lbmg_get_matrix",
     "lbmg_get_prolongation", "lbmg_launch_counts", "lbmg_build_batch", "lbmg_instances", "lbmg_instance_info",
     "lbmg_instance_residuals", "lbmg_learned_nparams", "lbmg_learned_params", "lbmg_learned_collect",
@@ -85,6 +85,7 @@ def load_library():
         "lbmg_level_info": (i, [P, i, P, P, P]),
         "lbmg_embedding": (i, [P, P, P]),
         "lbmg_assemble": (i, [P, d, P]),
+        "lbmg_set_area_weights": (i, [P, P, P]),
         "lbmg_project_rhs": (i, [P, P, i, P, P]),
         "lbmg_solve": (i, [P, P, P, i, d, i, i, P, P]),
         "lbmg_solve_pcg": (i, [P, P, P, i, d, i, i, P, P]),
@@ -324,6 +325,13 @@ def lbmg_embedding(h):
 
 def lbmg_assemble(h, t, stream=None):
     return _check(load_library().lbmg_assemble(h, float(t), _stream(stream)), "lbmg_assemble")
+
+
+def lbmg_set_area_weights(h, w_tri=None, stream=None):
+    """Per-triangle area weights of the mass matrix and the right-hand side (host float64 [nt]);
+    None restores the build-time metric."""
+    w = None if w_tri is None else np.ascontiguousarray(w_tri, dtype=np.float64)
+    return _check(load_library().lbmg_set_area_weights(h, _ptr(w), _stream(stream)), "lbmg_set_area_weights")
 
 
 def lbmg_project_rhs(h, f_vertex, rhs, stream=None):

@@ -802,6 +802,22 @@ int lbmg_embedding(lbmg_handle h, double *cube_side, double *center) {
     return LBMG_OK;
 }
 
+int lbmg_set_area_weights(lbmg_handle h, const double *w, void *stream) {
+    if (!h) return LBMG_INVALID_ARG;
+    const HostHierarchy &H = h->c.host;
+    std::vector<double> fs(H.frag_scale);
+    if (w) {
+        for (int t = 0; t < H.nt; t++)
+            if (!(w[t] >= 0.0) || !std::isfinite(w[t])) return LBMG_INVALID_ARG;
+        for (int f = 0; f < H.nfrag; f++) fs[f] *= w[H.frag_tri[f]];
+    }
+    // the assembly and projection kernels read the scales: none may still be running
+    LBMG_CK(cudaStreamSynchronize((cudaStream_t)stream));
+    if (!fs.empty())
+        LBMG_CK(cudaMemcpy(h->c.frag_scale, fs.data(), fs.size() * sizeof(double), cudaMemcpyHostToDevice));
+    return LBMG_OK;
+}
+
 int lbmg_assemble(lbmg_handle h, double t, void *stream) {
     if (!h || !(t >= 0) || !std::isfinite(t)) return LBMG_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;

@@ -65,6 +65,8 @@ def test_null_handle_rejected():
     assert lib.lbmg_assemble(None, 1.0, None) == 1
     assert lib.lbmg_solve(None, None, None, 1, 1e-6, 10, 0, None, None) == 1
     assert lib.lbmg_levels(None, None, None) == 1
+    assert lib.lbmg_set_area_weights(None, None, None) == 1
+    assert lib.lbmg_host_levels(None, None, None) == 1
 
 
 def test_tune_cache_file_round_trip_and_bad_lines(tmp_path):
