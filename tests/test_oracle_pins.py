@@ -550,3 +550,14 @@ def test_weighted_rhs_against_weighted_mass(icosphere):
     area = _tri_areas(V, F)
     tot = (w[:, None] * area[:, None] * f[F].mean(axis=1)).sum(axis=0)
     assert np.allclose(o.project_rhs_weighted(f, w).sum(axis=0), tot, rtol=1e-12, atol=1e-14)
+
+
+def test_weighted_mass_nests(sphere_h, icosphere):
+    """The split spaces nest (Claim, Section 4.1), whatever the metric: with per-triangle area
+    weights the coarse mass matrix is still P^T M_w P of the finer one."""
+    V, F = icosphere
+    w = np.random.default_rng(21).uniform(0.25, 4.0, size=F.shape[0])
+    for d in range(sphere_h.min_depth + 1, sphere_h.depth + 1):
+        P = sphere_h.prolongation(d)
+        Mc = sphere_h.mass_weighted(d - 1, w)
+        assert abs(P.T @ sphere_h.mass_weighted(d, w) @ P - Mc).max() <= 1e-13 * abs(Mc).max()
