@@ -210,6 +210,27 @@ class Hierarchy:
         self._lib.orc_project_rhs_weighted(self._h, _ptr(f), f.shape[1], _ptr(w), _ptr(out))
         return out
 
+    def cmcf_step(self, X, delta):
+        """One step of conformalized mean-curvature flow (Section 5.3) on the build-time space:
+        solve (M_t + delta L_0) x = M_t u_t, where u_t are the current vertex positions X
+        (linear per triangle), M_t weighs each triangle by its current over its build-time
+        area and L_0 is the build-time stiffness; returns the new vertex positions.  The
+        linear system is solved directly (FP64 sparse LU)."""
+        import scipy.sparse.linalg as spla
+        X = np.ascontiguousarray(X, dtype=np.float64)
+
+        def areas(P):
+            e1 = P[self._F[:, 1]] - P[self._F[:, 0]]
+            e2 = P[self._F[:, 2]] - P[self._F[:, 0]]
+            return 0.5 * np.linalg.norm(np.cross(e1, e2), axis=1)
+
+        w = areas(X) / areas(self._V)
+        D = self.depth
+        _, L0 = self.matrices(D)
+        A = (self.mass_weighted(D, w) + delta * L0).tocsc()
+        x = spla.splu(A).solve(self.project_rhs_weighted(X, w))
+        return self.eval_vertices(x)
+
     def eval_vertices(self, x):
         """u(v) = sum_i x_i b_i(v) at every mesh vertex; x is [n_D, nrhs]."""
         x = np.ascontiguousarray(x, dtype=np.float64)
