@@ -63,8 +63,7 @@ int adopt_single(HostHierarchy &P, HostHierarchy &B, std::string &err) {
     for (int d = 0; d <= B.D; d++) {
         HostLevel &L = B.lev[d];
         // the (corner, triangle) lookup tables serve the build only
-        std::vector<uint64_t>().swap(L.ct_key);
-        std::vector<int32_t>().swap(L.ct_tri);
+        std::vector<CornerTri>().swap(L.ct);
         std::vector<int32_t>().swap(L.ct_dof);
         if (d < B.d0) continue;
         L.inst.assign(L.ndof, 0);

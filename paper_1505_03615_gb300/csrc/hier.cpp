@@ -158,7 +158,7 @@ bool point_in_open_box(const double *p, const double *lo, const double *hi) {
     return p[0] > lo[0] && p[0] < hi[0] && p[1] > lo[1] && p[1] < hi[1] && p[2] > lo[2] && p[2] < hi[2];
 }
 
-struct KT { uint64_t key; int32_t tri; };
+using KT = CornerTri;
 inline bool kt_less(const KT &a, const KT &b) { return a.key < b.key || (a.key == b.key && a.tri < b.tri); }
 
 // CSR lists of the positions i of bucket[i], each bucket's positions ascending: a sort of
@@ -191,14 +191,13 @@ void bucket_csr(int64_t nb, const std::vector<int32_t> &bucket, const std::vecto
 }
 
 int lookup_dof(const HostLevel &L, uint64_t key, int tri) {
-    KT probe{key, tri};
-    size_t lo = 0, hi = L.ct_key.size();
+    const KT probe{key, tri};
+    size_t lo = 0, hi = L.ct.size();
     while (lo < hi) {
         size_t mid = (lo + hi) / 2;
-        KT m{L.ct_key[mid], L.ct_tri[mid]};
-        if (kt_less(m, probe)) lo = mid + 1; else hi = mid;
+        if (kt_less(L.ct[mid], probe)) lo = mid + 1; else hi = mid;
     }
-    if (lo < L.ct_key.size() && L.ct_key[lo] == key && L.ct_tri[lo] == tri) return L.ct_dof[lo];
+    if (lo < L.ct.size() && L.ct[lo].key == key && L.ct[lo].tri == tri) return L.ct_dof[lo];
     return -1;
 }
 
@@ -350,16 +349,11 @@ void build_level_basis(HostHierarchy &H, HostLevel &L, const std::vector<KT> &ce
         dof_id[gbase[r.group] + r.comp] = i;
     }
     for (int c = 0; c < 8; c++) L.colour_start[c + 1] += L.colour_start[c];
-    L.ct_key.resize(m);
-    L.ct_tri.resize(m);
     L.ct_dof.resize(m);
 #pragma omp parallel for schedule(static)
     for (int64_t g = 0; g < ng; g++)
-        for (int64_t i = gstart[g]; i < gstart[g + 1]; i++) {
-            L.ct_key[i] = ct[i].key;
-            L.ct_tri[i] = ct[i].tri;
-            L.ct_dof[i] = dof_id[gbase[g] + comp[i]];
-        }
+        for (int64_t i = gstart[g]; i < gstart[g + 1]; i++) L.ct_dof[i] = dof_id[gbase[g] + comp[i]];
+    L.ct = std::move(ct);
 }
 
 // Sparsity pattern of n rows over ncols columns and the contribution list of every stored

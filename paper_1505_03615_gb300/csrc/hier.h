@@ -16,6 +16,11 @@ constexpr uint32_t kPackMask = (1u << kPackShift) - 1u;
 constexpr int kGalShift = 29;
 constexpr uint32_t kGalMask = (1u << kGalShift) - 1u;
 
+struct CornerTri {
+    uint64_t key;   // Morton key of a grid corner
+    int32_t tri;    // a triangle meeting that corner's support
+};
+
 struct HostLevel {
     int d = 0;
     int ndof = 0;
@@ -25,9 +30,9 @@ struct HostLevel {
     std::vector<int32_t> inst;          // [ndof] instance of each row
     std::vector<int32_t> corner;        // [ndof*3] grid corner index at depth d
     std::vector<int32_t> mintri;        // [ndof] smallest triangle of the component
-    // (corner Morton key, triangle) -> dof, sorted by key then triangle
-    std::vector<uint64_t> ct_key;
-    std::vector<int32_t> ct_tri, ct_dof;
+    // (corner Morton key, triangle) pairs, sorted by key then triangle, and the dof of each
+    std::vector<CornerTri> ct;
+    std::vector<int32_t> ct_dof;
     // sparsity pattern of A_d, columns sorted per row
     std::vector<int32_t> rp, ci;
     // prolongation into this level from depth d-1: parents [ndof*8] (-1 pad), log2 #parents
