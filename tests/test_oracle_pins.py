@@ -581,3 +581,21 @@ def test_cmcf_steps_shrink_the_sphere_by_the_closed_form(icosphere):
         assert radii.std() <= 1e-3 * r_new
         assert np.abs(X.mean(axis=0)).max() <= 1e-3 * r_new
         r = r_new
+
+
+def test_spectrum_falls_with_depth_on_nested_spaces(icosphere):
+    """The split spaces nest (Claim, Section 4.1), so by the min-max principle each eigenvalue
+    of L x = lambda M x can only fall as the depth grows; on the unit sphere the error against
+    l(l+1) shrinks with depth (the resolution study of Section 5.1)."""
+    V, F = icosphere
+    exact = np.array([0.0] + [2.0] * 3 + [6.0] * 5 + [12.0] * 7)
+    prev, prev_err = None, None
+    for d in (2, 3, 4):
+        h = oracle.Hierarchy(V, F, d, min_depth=d)
+        M, L = h.matrices(d)
+        w = sla.eigh(L.toarray(), M.toarray(), eigvals_only=True, subset_by_index=[0, 15])
+        err = np.abs(w[1:] - exact[1:]).max()
+        if prev is not None:
+            assert np.all(w <= prev + 1e-8 * np.abs(prev).max())
+            assert err < 0.6 * prev_err
+        prev, prev_err = w, err
