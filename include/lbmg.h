@@ -83,6 +83,9 @@ typedef struct lbmg_options {
                            arrive, so its bounded wait (about one second) expires, the kernel sets a
                            status word and returns, and lbmg_solve returns LBMG_DEVICE_TIMEOUT at the
                            end of that cycle */
+    int host_alloc_fail; /* fault injection for tests, default 0: 1 makes the host hierarchy builder fail
+                           as an exhausted host allocation does, once the triangles are cut into voxel
+                           pieces, so the build returns LBMG_OUT_OF_MEMORY and creates no handle */
 } lbmg_options;
 
 typedef struct lbmg_stats {

@@ -57,7 +57,8 @@ class Options(C.Structure):
     _fields_ = [("min_depth", C.c_int), ("coarse_max", C.c_int), ("nu1", C.c_int), ("nu2", C.c_int),
                 ("smoother", C.c_int), ("jacobi_omega", C.c_double), ("split", C.c_int), ("threads", C.c_int),
                 ("persistent", C.c_int), ("narrow_max", C.c_int), ("barrier_phantoms", C.c_int),
-                ("use_graphs", C.c_int), ("pdl", C.c_int), ("copy_phantom_bytes", C.c_int)]
+                ("use_graphs", C.c_int), ("pdl", C.c_int), ("copy_phantom_bytes", C.c_int),
+                ("host_alloc_fail", C.c_int)]
 
 
 class Stats(C.Structure):

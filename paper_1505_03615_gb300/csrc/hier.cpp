@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <new>
 #include <numeric>
 #include <stdexcept>
 
@@ -414,7 +415,8 @@ void rows_with_lists(int n, int ncols, const Emit &emit, HostLevel &L, std::vect
 }  // namespace
 
 int build_host_hierarchy(const double *V, int nv, const int *F, int nt, int depth, int min_depth,
-                         int coarse_max, int split, int threads, HostHierarchy &H, std::string &err) {
+                         int coarse_max, int split, int threads, HostHierarchy &H, std::string &err,
+                         bool fail_alloc) {
     if (!V || !F || nv < 3 || nt < 1 || depth < 1 || depth > kMaxDepth) { err = "bad mesh size or depth"; return 1; }
     for (int64_t i = 0; i < 3 * (int64_t)nt; i++)
         if (F[i] < 0 || F[i] >= nv) { err = "triangle index out of range"; return 1; }
@@ -514,6 +516,7 @@ int build_host_hierarchy(const double *V, int nv, const int *F, int nt, int dept
         for (auto &p : part) for (auto &f : p) frags.push_back(std::move(f));
     }
     if (frags.empty()) { err = "no triangle piece of positive area"; return 2; }
+    if (fail_alloc) throw std::bad_alloc();
     LBMG_SORT(frags.begin(), frags.end(), [](const FragOut &a, const FragOut &b) {
         return a.key < b.key || (a.key == b.key && a.tri < b.tri);
     });

@@ -92,7 +92,10 @@ inline int pair_index(int a, int b) {
 int combine_batch(std::vector<HostHierarchy> &parts, HostHierarchy &B, std::string &err);
 
 // Returns 0 on success, else an lbmg status code with a message in err.
+// fail_alloc (tests): throw std::bad_alloc once the triangles are cut, as an exhausted host
+// allocation would.
 int build_host_hierarchy(const double *V, int nv, const int *F, int nt, int depth, int min_depth,
-                         int coarse_max, int split, int threads, HostHierarchy &H, std::string &err);
+                         int coarse_max, int split, int threads, HostHierarchy &H, std::string &err,
+                         bool fail_alloc = false);
 
 }  // namespace lbmg

@@ -123,3 +123,28 @@ def test_batch_rejects_an_empty_list_and_a_bad_member():
     with pytest.raises(L.LbmgError) as e:
         L.lbmg_build_batch([(V, F, 3), (V, bad, 3)])
     assert e.value.code == 1
+
+
+def test_host_allocation_failure_is_reported_and_leaves_no_handle():
+    """An exhausted host allocation inside the hierarchy builder (injected for the test) comes
+    back as LBMG_OUT_OF_MEMORY from every build entry point, with the builder's reason, and
+    the library keeps working afterwards."""
+    import meshgen
+    V, F = meshgen.icosphere(2)
+    builds = {
+        "host": lambda **o: L.lbmg_host_build(V, F, 4, **o),
+        "host batch": lambda **o: L.lbmg_host_build_batch([(V, F, 4), (V, F, 3)], **o),
+        "device": lambda **o: L.lbmg_build_hierarchy(V, F, 4, **o),
+        "device batch": lambda **o: L.lbmg_build_batch([(V, F, 4), (V, F, 3)], **o),
+    }
+    for name, build in builds.items():
+        with pytest.raises(L.LbmgError) as e:
+            build(host_alloc_fail=1)
+        assert e.value.code == 3, name
+        assert "host memory exhausted" in str(e.value), name
+    with pytest.raises(L.LbmgError) as e:
+        L.lbmg_host_build(V, F, 4, host_alloc_fail=2)
+    assert e.value.code == 1
+    h = L.lbmg_host_build(V, F, 4)
+    assert L.lbmg_host_levels(h)[1] == 4
+    L.lbmg_host_destroy(h)
