@@ -541,6 +541,14 @@ const DevLevel *noalloc_level(lbmg_handle h, int d) {
 }
 void noalloc_set_error(const std::string &msg) { g_cuda_err = msg; }
 
+// relative residual sqrt(r2 / b2) from squared norms: a non-finite norm (NaN or inf in the
+// right-hand side or the iterate) gives infinity, so it can never pass for convergence; a zero
+// right-hand side gives 0
+static double rel_residual(double r2, double b2) {
+    if (!std::isfinite(r2) || !std::isfinite(b2)) return INFINITY;
+    return b2 > 0 ? std::sqrt(r2 / b2) : 0.0;
+}
+
 static int check_build_options(const lbmg_options &o) {
     if (o.nu1 < 0 || o.nu2 < 0 || o.coarse_max < 1 || o.coarse_max > kMaxCoarse) return LBMG_INVALID_ARG;
     if (o.smoother != LBMG_GS_COLOURED && o.smoother != LBMG_JACOBI) return LBMG_INVALID_ARG;
@@ -777,7 +785,7 @@ int lbmg_instance_residuals(lbmg_handle h, int nrhs, double *rel) {
     for (int m = 0; m < h->c.ninst; m++)
         for (int r = 0; r < nrhs; r++) {
             const double *nm = &h->inst_norm_host[16 * (size_t)m];
-            rel[(size_t)m * nrhs + r] = nm[4 + r] > 0 ? std::sqrt(nm[r] / nm[4 + r]) : 0.0;
+            rel[(size_t)m * nrhs + r] = rel_residual(nm[r], nm[4 + r]);
         }
     return LBMG_OK;
 }
@@ -903,8 +911,7 @@ static int solve_pcg_batch(lbmg_handle h, const double *rd, const double *xin, d
         for (int mm = 0; mm < c.ninst; mm++)
             for (int r = 0; r < nrhs; r++) {
                 const double *nm = &v[16 * (size_t)mm];
-                const double rel = nm[4 + r] > 0 ? std::sqrt(nm[r] / nm[4 + r]) : 0.0;
-                w[r] = std::isfinite(rel) ? std::max(w[r], rel) : INFINITY;
+                w[r] = std::max(w[r], rel_residual(nm[r], nm[4 + r]));
             }
     };
     LBMG_TRY(read());
@@ -994,8 +1001,8 @@ static int solve_impl(lbmg_handle h, const double *rhs, double *x, int nrhs, dou
         for (int m = 0; m < c.ninst; m++)
             for (int r = 0; r < nrhs; r++) {
                 const double *nm = &h->inst_norm_host[16 * (size_t)m];
-                const double rel = nm[4 + r] > 0 ? std::sqrt(nm[r] / nm[4 + r]) : 0.0;
-                const double rel0 = nm[4 + r] > 0 ? std::sqrt(nm[8 + r] / nm[4 + r]) : 0.0;
+                const double rel = rel_residual(nm[r], nm[4 + r]);
+                const double rel0 = rel_residual(nm[8 + r], nm[4 + r]);
                 if (!(rel <= tol)) conv = false;
                 worst[r] = std::max(worst[r], rel);
                 worst0[r] = std::max(worst0[r], rel0);
@@ -1044,7 +1051,7 @@ static int solve_impl(lbmg_handle h, const double *rhs, double *x, int nrhs, dou
         LBMG_TRY(read_norms(h, R, s, nb));
         launch_norms(c.rs, Fl.n, R, c.norm_part, c.norm_out, s);
         LBMG_TRY(read_norms(h, R, s, nr));
-        auto rel = [&](int r) { return nb[r] > 0 ? std::sqrt(nr[r] / nb[r]) : 0.0; };
+        auto rel = [&](int r) { return rel_residual(nr[r], nb[r]); };
         for (int r = 0; r < nrhs; r++) r0[r] = rel(r);
         for (;;) {
             conv = true;

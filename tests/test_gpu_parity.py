@@ -446,6 +446,26 @@ def test_pcg_matches_direct_solution_in_fewer_iterations(case, precision, tol, e
         assert code_v == L.LBMG_OK and st.cycles <= st_v.cycles + 2
 
 
+@pytest.mark.parametrize("path", ["vcycle", "pcg", "persistent"])
+def test_nan_right_hand_side_is_reported_as_divergence(path):
+    """A NaN in the right-hand side fails every comparison with the tolerance: the solve
+    reports LBMG_DIVERGED before the first cycle instead of passing for converged."""
+    V, F = meshgen.icosphere(2, 1.0, 1e-3, 1)
+    h = L.lbmg_build_hierarchy(V, F, 4, persistent=int(path == "persistent"))
+    try:
+        L.lbmg_assemble(h, 1e-2)
+        n = L.lbmg_level_info(h, 4)[0]
+        rhs = torch.ones((n, 2), dtype=torch.float64, device=DEV)
+        rhs[n // 2, 1] = float("nan")
+        x = torch.zeros_like(rhs)
+        solve = L.lbmg_solve_pcg if path == "pcg" else L.lbmg_solve
+        with pytest.raises(L.LbmgError) as e:
+            solve(h, rhs, x, 1e-8, 50, L.LBMG_MIXED)
+        assert e.value.code == 8
+    finally:
+        L.lbmg_destroy(h)
+
+
 def test_mixed_precision_skips_sliver_functions_below_fp32_range():
     """A torus of the seeded 64-mesh batch (34k triangles, depth 7) has split functions whose
     supports meet it in slivers where the hat and its tangential gradient nearly vanish: their
