@@ -402,6 +402,9 @@ def main():
                     help="named synthetic workload (meshgen.CONFIGS); the default is the metric's own configuration")
     ap.add_argument("--tune-cache", default=None,
                     help="tuning cache file: loaded before tuning (matching levels are not timed), saved after")
+    ap.add_argument("--force-shape", default=None,
+                    help="TPR,TPB: after tuning, set the finest level's mixed-precision sweep and residual launch "
+                         "shape (profiling runs)")
     ap.add_argument("--max-cycles", type=int, default=2000,
                     help="cap on V-cycles per solve (profiling runs cap it to keep launch lists short)")
     args = ap.parse_args()
@@ -445,6 +448,10 @@ def main():
             L.lbmg_tune_cache_save(args.tune_cache)
     torch.cuda.synchronize()
     t_tune = time.perf_counter() - t_tune
+    if args.force_shape:
+        tpr, tpb = (int(v) for v in args.force_shape.split(","))
+        for kind in (0, 1):
+            L.lbmg_set_launch_shape(h, D, L.LBMG_MIXED, kind, tpr, tpb)
     shapes = {str(d): L.lbmg_launch_shape(h, d, L.LBMG_MIXED) for d in range(d0 + 1, D + 1)}
     tuned_us = {str(d): [round(1e3 * v, 2) for v in L.lbmg_tuned_times(h, d, L.LBMG_MIXED)] for d in range(d0 + 1, D + 1)}
     f_dev = torch.tensor(f, dtype=torch.float64, device=dev)

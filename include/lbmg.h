@@ -86,6 +86,11 @@ typedef struct lbmg_options {
     int host_alloc_fail; /* fault injection for tests, default 0: 1 makes the host hierarchy builder fail
                            as an exhausted host allocation does, once the triangles are cut into voxel
                            pieces, so the build returns LBMG_OUT_OF_MEMORY and creates no handle */
+    int host_check;     /* graph path: 0 (default) runs a whole solve as one graph launch whose
+                           conditional loop is stopped by a device-side test of the residual norms, and
+                           the host synchronizes once, at the end; 1 launches one graph per iteration
+                           and reads the norms back after each one (the only mode in which
+                           lbmg_stats.ms_fine_smooth is measured) */
 } lbmg_options;
 
 typedef struct lbmg_stats {
@@ -99,6 +104,9 @@ typedef struct lbmg_stats {
     int learned;             /* 1 if the finest sweeps started with learned weights (lbmg_learned_enable) */
     int learned_fallback;    /* 1 if a learned cycle failed to reduce a residual and the solve went on
                                 with plain Gauss-Seidel weights */
+    int host_syncs;          /* times the call waited for the device: 1 for a solve run as one graph
+                                launch or one persistent launch (the final status read); one more per
+                                iteration with host_check = 1 or without graphs */
 } lbmg_stats;
 
 typedef struct lbmg_ctx *lbmg_handle;
@@ -185,8 +193,9 @@ int lbmg_set_area_weights(lbmg_handle h, const double *w, void *stream);
  * product P^T A_{d+1} P, which equals its own quadrature because the spaces nest
  * (Claim of Section 4.1).  Sums use precomputed contribution lists, no atomics.
  * Also factors the coarsest level (FP64 Cholesky of A + eps Id, eps =
- * 1e-12 mean diag, Discussion of Section 5).  Asynchronous on `stream` except
- * for the coarse-factor status, which it reads back (one synchronization).
+ * 1e-12 mean diag, Discussion of Section 5).  Asynchronous on `stream`; a
+ * non-positive pivot of that factorisation is kept in a device flag and reported
+ * by the next solve (LBMG_COARSE_FACTOR).
  */
 int lbmg_assemble(lbmg_handle h, double t, void *stream);
 
@@ -203,12 +212,18 @@ int lbmg_project_rhs(lbmg_handle h, const double *f_vertex, int nrhs, double *rh
  * prolongation x += P e and ν2 sweeps on the way up (Section 4.3).  precision:
  * LBMG_FP64 runs the whole cycle in FP64; LBMG_MIXED runs it in FP32 inside an
  * FP64 defect-correction loop (residual and update in FP64).  Stops when
- * ||rhs - A x||_2 <= tol ||rhs||_2 for every right-hand side, or after
- * max_cycles.  x: [n_depth][nrhs], in/out (warm start).  stats may be NULL.
- * With options.persistent (and for batches) the cycle loop, residuals and norms
- * run in one cooperative kernel launch and the call synchronizes once at the
- * end; otherwise (default) each cycle is one CUDA-graph launch and the call
- * synchronizes once per cycle to read the residual norms.
+ * ||rhs - A x||_2 <= tol ||rhs||_2 for every right-hand side (||rhs - A x||_2 <=
+ * tol when rhs = 0), or after max_cycles.  x: [n_depth][nrhs], in/out (warm
+ * start).  stats may be NULL.
+ * The default path runs the whole solve as one CUDA-graph launch: a conditional
+ * WHILE node whose body is one cycle and a one-thread kernel that tests the norms
+ * on the device and ends the loop; the call synchronizes once, to read the final
+ * status.  With options.persistent (and for batches) the cycle loop runs in one
+ * cooperative kernel launch, also with one synchronization.  With
+ * options.host_check = 1 (lbmg_set_host_check) or use_graphs = 0 each cycle is one
+ * launch and the call reads the norms back after each.  A coarsest-level
+ * factorisation that failed in lbmg_assemble is reported here as
+ * LBMG_COARSE_FACTOR.
  */
 int lbmg_solve(lbmg_handle h, const double *rhs, double *x, int nrhs, double tol, int max_cycles,
                int precision, lbmg_stats *stats, void *stream);
@@ -244,11 +259,14 @@ int lbmg_launch_counts(lbmg_handle h, int precision, int *assemble, int *project
 /*
  * Launch-shape autotuner (throughput layer; the paper fixes no launch shapes).
  * For every level above the coarsest, times the coloured Gauss-Seidel sweep and
- * the residual kernel of `precision` for nrhs right-hand sides (1..4) with each
- * of nine launch shapes -- 4, 8 or 16 threads per matrix row x 128, 256 or 512
- * threads per block -- as a captured graph of `reps` (1..64) sweeps replayed three
- * times, and keeps the fastest in the handle (the default 8 x 256 unless another
- * shape is at least 2% faster).  Results are also kept in a process-wide cache
+ * the residual kernel of `precision` for nrhs right-hand sides (1..4) with each of
+ * nine launch shapes -- 4, 8 or 16 threads per matrix row x 128, 256 or 512 threads
+ * per block -- as a captured graph of `reps` (1..64) sweeps replayed three times, and
+ * keeps the fastest in the handle (the default 4 x 256 unless another shape is at
+ * least 2% faster).  Threads per row 8 and 16 read the matrix in CSR order; 4 reads
+ * a packed copy in which groups of 8 rows of one colour with equal quad counts
+ * ceil(len / 4) store their entries quad-interleaved, so that each warp load is 256
+ * aligned contiguous bytes.  Results are also kept in a process-wide cache
  * keyed by (device name, precision, kernel, lanes, rows, non-zeros): levels of
  * any handle that match an entry are not timed again.  The levels' cycle work
  * vectors are overwritten; they carry no state between calls.  Captured cycle
@@ -265,9 +283,12 @@ int lbmg_launch_shape(lbmg_handle h, int d, int precision, int *out);
    launch; 0 where the shape came from the cache or was set by hand.  Host only. */
 int lbmg_tuned_times(lbmg_handle h, int d, int precision, float *ms);
 /* set a launch shape of level d by hand: kind 0 = Gauss-Seidel sweep, 1 = residual;
-   tpr in {4, 8, 16}; tpb a multiple of 32 in [32, 512] (LBMG_INVALID_ARG otherwise).
-   Results change only by the summation order inside a row.  Host only. */
+   tpr in {4, 8, 16} (see lbmg_autotune); tpb a multiple of 32 in [32, 512]
+   (LBMG_INVALID_ARG otherwise).  Results change only by the summation order inside a
+   row.  Host only. */
 int lbmg_set_launch_shape(lbmg_handle h, int d, int precision, int kind, int tpr, int tpb);
+/* options.host_check of an existing handle (0 or 1; LBMG_INVALID_ARG otherwise).  Host only. */
+int lbmg_set_host_check(lbmg_handle h, int on);
 /* write / read the process-wide tuning cache as text, one entry per line:
    device fp64 kind lanes rows nnz threads_per_row threads_per_block.
    Load merges valid lines and returns LBMG_INVALID_ARG if the file cannot be

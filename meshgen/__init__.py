@@ -244,6 +244,11 @@ CONFIGS = {
                                precision="mixed"),
     "knot35_4m_d10": dict(mesh=lambda: torus_knot_tube(3, 5, 1.0, 0.02, 10000, 200, 1e-7, 6),
                           depth=10, t=1e-4, rhs=coordinate_rhs, tol=1e-6, precision="mixed"),
+    # the same knot surface on the same depth-10 grid with a quarter of the triangles: its
+    # finest level has the same functions and stencils, with a quarter of the voxel pieces
+    # (a case small enough for whole-kernel profiling)
+    "knot35_1m_d10": dict(mesh=lambda: torus_knot_tube(3, 5, 1.0, 0.02, 5000, 100, 1e-7, 6),
+                          depth=10, t=1e-4, rhs=coordinate_rhs, tol=1e-6, precision="mixed"),
 }
 
 

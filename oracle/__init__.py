@@ -43,6 +43,7 @@ def _load():
     i, l, d = C.c_int, C.c_long, C.c_double
     sig = {
         "orc_build": (P, [P, i, P, i, i, i, i, i]),
+        "orc_build_embedded": (P, [P, i, P, i, i, i, i, i, d, P]),
         "orc_free": (None, [P]),
         "orc_depth": (i, [P]),
         "orc_min_depth": (i, [P]),
@@ -84,15 +85,24 @@ class Hierarchy:
     Levels run from ``min_depth`` (coarsest) to ``depth`` (finest).  With
     ``min_depth < 0`` the coarsest level is the first one, going down from the
     finest, with at most ``coarse_max`` functions.  ``split=False`` gives the
-    connectivity-unaware space of Section 3.2 for comparison.
+    connectivity-unaware space of Section 3.2 for comparison.  ``embedding =
+    (S, center)`` fixes the grid cube (side S, centre) instead of fitting it to
+    the bounding box, so that a piece of a mesh lies on the whole mesh's grid.
     """
 
-    def __init__(self, V, F, depth, min_depth=-1, coarse_max=4096, split=True):
+    def __init__(self, V, F, depth, min_depth=-1, coarse_max=4096, split=True, embedding=None):
         lib = _load()
         self._V = np.ascontiguousarray(V, dtype=np.float64)
         self._F = np.ascontiguousarray(F, dtype=np.int32)
-        h = lib.orc_build(_ptr(self._V), self._V.shape[0], _ptr(self._F), self._F.shape[0],
-                          int(depth), int(min_depth), int(coarse_max), int(bool(split)))
+        if embedding is None:
+            h = lib.orc_build(_ptr(self._V), self._V.shape[0], _ptr(self._F), self._F.shape[0],
+                              int(depth), int(min_depth), int(coarse_max), int(bool(split)))
+        else:
+            S, c = embedding
+            c = np.ascontiguousarray(c, dtype=np.float64)
+            h = lib.orc_build_embedded(_ptr(self._V), self._V.shape[0], _ptr(self._F), self._F.shape[0],
+                                       int(depth), int(min_depth), int(coarse_max), int(bool(split)),
+                                       float(S), _ptr(c))
         if not h:
             raise ValueError("oracle: invalid mesh or depth")
         self._h = h

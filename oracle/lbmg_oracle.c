@@ -616,23 +616,36 @@ static void build_level(orc_hier *h, int d) {
     assemble_level(h, lv);
 }
 
-orc_hier *orc_build(const double *V, int nv, const int *F, int nt, int depth, int min_depth,
-                    int coarse_max, int split) {
+/* The embedding (reading of Section 3.2, which leaves it open): by default the
+   bounding box is centred in a cube of side 1.1 x its largest extent.  A caller
+   may instead fix the cube (side S > 0, centre c), e.g. to put a piece of a
+   mesh on exactly the grid of the whole mesh; every vertex must then lie inside
+   the cube. */
+static orc_hier *build_hier(const double *V, int nv, const int *F, int nt, int depth, int min_depth,
+                            int coarse_max, int split, double S_fixed, const double *c_fixed) {
     if (depth < 1 || depth > ORC_MAXD || nv < 3 || nt < 1) return NULL;
     for (int i = 0; i < 3 * nt; i++) if (F[i] < 0 || F[i] >= nv) return NULL;
     for (int i = 0; i < 3 * nv; i++) if (!isfinite(V[i])) return NULL;
     orc_hier *h = xcalloc(1, sizeof(orc_hier));
     h->D = depth; h->nv = nv; h->nt = nt; h->split = split;
-    /* embedding: centre the bounding box in a cube of side 1.1 x largest extent */
-    double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
-    for (int i = 0; i < nv; i++)
-        for (int a = 0; a < 3; a++) {
-            if (V[3 * i + a] < mn[a]) mn[a] = V[3 * i + a];
-            if (V[3 * i + a] > mx[a]) mx[a] = V[3 * i + a];
-        }
-    double ext = 0;
-    for (int a = 0; a < 3; a++) { h->c[a] = 0.5 * (mn[a] + mx[a]); if (mx[a] - mn[a] > ext) ext = mx[a] - mn[a]; }
-    h->S = 1.1 * ext;
+    if (S_fixed > 0) {
+        h->S = S_fixed;
+        for (int a = 0; a < 3; a++) h->c[a] = c_fixed[a];
+        for (int i = 0; i < nv; i++)
+            for (int a = 0; a < 3; a++)
+                if (!(fabs(V[3 * i + a] - h->c[a]) < 0.5 * h->S)) { free(h); return NULL; }
+    } else {
+        /* centre the bounding box in a cube of side 1.1 x largest extent */
+        double mn[3] = {INFINITY, INFINITY, INFINITY}, mx[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int i = 0; i < nv; i++)
+            for (int a = 0; a < 3; a++) {
+                if (V[3 * i + a] < mn[a]) mn[a] = V[3 * i + a];
+                if (V[3 * i + a] > mx[a]) mx[a] = V[3 * i + a];
+            }
+        double ext = 0;
+        for (int a = 0; a < 3; a++) { h->c[a] = 0.5 * (mn[a] + mx[a]); if (mx[a] - mn[a] > ext) ext = mx[a] - mn[a]; }
+        h->S = 1.1 * ext;
+    }
     const double G = (double)(1 << depth);
     h->sigma = h->S / G;
     h->V = xmalloc(sizeof(double) * 3 * (size_t)nv);
@@ -685,6 +698,17 @@ orc_hier *orc_build(const double *V, int nv, const int *F, int nt, int depth, in
     h->d0 = d;
     for (int k = h->d0 + 1; k <= depth; k++) build_prolongation(&h->lev[k], &h->lev[k - 1]);
     return h;
+}
+
+orc_hier *orc_build(const double *V, int nv, const int *F, int nt, int depth, int min_depth,
+                    int coarse_max, int split) {
+    return build_hier(V, nv, F, nt, depth, min_depth, coarse_max, split, 0.0, NULL);
+}
+
+orc_hier *orc_build_embedded(const double *V, int nv, const int *F, int nt, int depth, int min_depth,
+                             int coarse_max, int split, double S, const double *center) {
+    if (!(S > 0) || !isfinite(S) || !center) return NULL;
+    return build_hier(V, nv, F, nt, depth, min_depth, coarse_max, split, S, center);
 }
 
 void orc_free(orc_hier *h) {

@@ -24,7 +24,7 @@ __all__ = [
     "lbmg_instance_residuals", "lbmg_learned_nparams", "lbmg_learned_params", "lbmg_learned_collect",
     "lbmg_learned_loss_grad", "lbmg_learned_train", "lbmg_learned_enable", "lbmg_learned_omega",
     "lbmg_residual_norms_noalloc", "lbmg_status_string", "lbmg_last_cuda_error", "lbmg_default_options",
-    "lbmg_solve_pcg", "lbmg_autotune", "lbmg_launch_shape", "lbmg_tuned_times", "lbmg_set_launch_shape", "lbmg_tune_cache_save", "lbmg_tune_cache_load",
+    "lbmg_solve_pcg", "lbmg_autotune", "lbmg_launch_shape", "lbmg_tuned_times", "lbmg_set_launch_shape", "lbmg_set_host_check", "lbmg_tune_cache_save", "lbmg_tune_cache_load",
     "lbmg_host_build", "lbmg_host_destroy", "lbmg_host_levels", "lbmg_host_level_info", "lbmg_host_get_dofs",
     "lbmg_host_get_pattern", "lbmg_host_get_prolongation", "lbmg_host_build_batch", "lbmg_host_instances",
     "lbmg_host_row_instances",
@@ -58,13 +58,13 @@ class Options(C.Structure):
                 ("smoother", C.c_int), ("jacobi_omega", C.c_double), ("split", C.c_int), ("threads", C.c_int),
                 ("persistent", C.c_int), ("narrow_max", C.c_int), ("barrier_phantoms", C.c_int),
                 ("use_graphs", C.c_int), ("pdl", C.c_int), ("copy_phantom_bytes", C.c_int),
-                ("host_alloc_fail", C.c_int)]
+                ("host_alloc_fail", C.c_int), ("host_check", C.c_int)]
 
 
 class Stats(C.Structure):
     _fields_ = [("cycles", C.c_int), ("converged", C.c_int), ("rel_residual", C.c_double * 4),
                 ("initial_residual", C.c_double * 4), ("ms_total", C.c_float), ("ms_fine_smooth", C.c_float),
-                ("learned", C.c_int), ("learned_fallback", C.c_int)]
+                ("learned", C.c_int), ("learned_fallback", C.c_int), ("host_syncs", C.c_int)]
 
 
 def load_library():
@@ -102,6 +102,7 @@ def load_library():
         "lbmg_launch_shape": (i, [P, i, i, P]),
         "lbmg_tuned_times": (i, [P, i, i, P]),
         "lbmg_set_launch_shape": (i, [P, i, i, i, i, i]),
+        "lbmg_set_host_check": (i, [P, i]),
         "lbmg_tune_cache_save": (i, [C.c_char_p]),
         "lbmg_tune_cache_load": (i, [C.c_char_p]),
         "lbmg_get_matrix": (i, [P, i, P, P, P, P]),
@@ -426,6 +427,10 @@ def lbmg_tuned_times(h, d, precision):
 def lbmg_set_launch_shape(h, d, precision, kind, tpr, tpb):
     return _check(load_library().lbmg_set_launch_shape(h, int(d), int(precision), int(kind), int(tpr), int(tpb)),
                   "lbmg_set_launch_shape")
+
+
+def lbmg_set_host_check(h, on):
+    return _check(load_library().lbmg_set_host_check(h, int(on)), "lbmg_set_host_check")
 
 
 def lbmg_tune_cache_save(path):

@@ -61,6 +61,81 @@ __global__ void to_double_kernel(const float *__restrict__ a, double *__restrict
     if (q < n) b[q] = (double)a[q];
 }
 
+// ---- stopping test of a solve on the device (one graph launch per solve) ----
+// relative residual from squared norms, the rule every solve path uses: non-finite norms
+// give infinity (never convergence); a zero right-hand side is judged by the absolute
+// residual ||r||, so a warm start on b = 0 still iterates towards x = 0
+__device__ __forceinline__ double ctl_rel(double r2, double b2) {
+    if (!isfinite(r2) || !isfinite(b2)) return __longlong_as_double(0x7ff0000000000000ll);
+    return sqrt(r2 / (b2 > 0.0 ? b2 : 1.0));
+}
+
+__global__ void ctl_setup_kernel(SolveCtl *ctl, double tol, int max_cycles, int fixed, int nrhs, double *pcg_tol) {
+    if (threadIdx.x != 0) return;
+    ctl->tol = tol;
+    ctl->max_cycles = max_cycles;
+    ctl->cycles = 0;
+    ctl->status = kCtlRunning;
+    ctl->fixed = fixed;
+    ctl->nrhs = nrhs;
+    if (pcg_tol) *pcg_tol = tol;
+}
+
+// worst relative residual per lane: one mesh (nr: ||r||^2, ctl->nb: ||b||^2) or a batch
+// (inst: per mesh ||r||^2 at [16 m + q] and ||b||^2 at [16 m + 4 + q])
+__device__ void ctl_worst(const SolveCtl &c, const double *nr, const double *inst, int ninst, double (&rel)[4]) {
+    for (int q = 0; q < 4; q++) rel[q] = 0.0;
+    if (inst) {
+        for (int m = 0; m < ninst; m++)
+            for (int q = 0; q < c.nrhs; q++) rel[q] = fmax(rel[q], ctl_rel(inst[16 * m + q], inst[16 * m + 4 + q]));
+    } else {
+        for (int q = 0; q < c.nrhs; q++) rel[q] = ctl_rel(nr[q], c.nb[q]);
+    }
+}
+
+// status after a check: device timeout (a bounded wait gave up), failed coarse factor,
+// divergence (non-finite, or growth by 1e6 over the initial residual), convergence of
+// every lane, or the iteration cap; the loop continues only while running
+__device__ void ctl_decide(SolveCtl &c, const double (&rel)[4], const int *tstat, const int *cflag,
+                           cudaGraphConditionalHandle h) {
+    bool conv = true, bad = false;
+    for (int q = 0; q < c.nrhs; q++) {
+        c.rel[q] = rel[q];
+        if (!(rel[q] <= c.tol)) conv = false;
+        if (!isfinite(rel[q]) || rel[q] > 1e6 * fmax(c.r0[q], 1e-300)) bad = true;
+    }
+    int st = kCtlRunning;
+    if (*tstat != 0) st = kCtlTimeout;
+    else if (*cflag != 0) st = kCtlCoarse;
+    else if (!c.fixed && bad) st = kCtlDiverged;
+    else if (!c.fixed && conv) st = kCtlConverged;
+    else if (c.cycles >= c.max_cycles) st = kCtlMaxCycles;
+    c.status = st;
+    cudaGraphSetConditional(h, st == kCtlRunning ? 1u : 0u);
+}
+
+__global__ void ctl_begin_kernel(SolveCtl *ctl, const double *nb, const double *nr, const double *inst, int ninst,
+                                 const int *tstat, const int *cflag, cudaGraphConditionalHandle h) {
+    if (threadIdx.x != 0) return;
+    SolveCtl &c = *ctl;
+    if (!inst)
+        for (int q = 0; q < 4; q++) c.nb[q] = nb[q];
+    double rel[4];
+    ctl_worst(c, nr, inst, ninst, rel);
+    for (int q = 0; q < 4; q++) c.r0[q] = rel[q];
+    ctl_decide(c, rel, tstat, cflag, h);
+}
+
+__global__ void ctl_step_kernel(SolveCtl *ctl, const double *nr, const double *inst, int ninst, const int *tstat,
+                                const int *cflag, cudaGraphConditionalHandle h) {
+    if (threadIdx.x != 0) return;
+    SolveCtl &c = *ctl;
+    c.cycles++;
+    double rel[4];
+    ctl_worst(c, nr, inst, ninst, rel);
+    ctl_decide(c, rel, tstat, cflag, h);
+}
+
 }  // namespace
 
 struct lbmg_ctx {
@@ -72,6 +147,8 @@ struct lbmg_ctx {
     size_t io_cap = 0;   // doubles per io slot
     int *h_flag = nullptr;
     double pcg_tol_host = 0.0;   // source of the tolerance copy of a running batch solve
+    int syncs = 0;               // host synchronizations of the running solve
+    double *h_inst = nullptr;    // pinned [ninst][16]: per-mesh norms read after a solve
 
     template <class T>
     int alloc(T **p, size_t count) {
@@ -98,6 +175,8 @@ struct lbmg_ctx {
         if (c.h_norm) cudaFreeHost(c.h_norm);
         if (h_flag) cudaFreeHost(h_flag);
         if (c.h_state) cudaFreeHost(c.h_state);
+        if (c.h_ctl) cudaFreeHost(c.h_ctl);
+        if (h_inst) cudaFreeHost(h_inst);
         if (c.capture_stream) cudaStreamDestroy(c.capture_stream);
         if (c.ev0) cudaEventDestroy(c.ev0);
         if (c.ev1) cudaEventDestroy(c.ev1);
@@ -128,10 +207,11 @@ int output_ptr(lbmg_handle h, double *user, size_t count, int slot, double **out
     return LBMG_OK;
 }
 
-int finish_output(double *user, const double *dev, size_t count, bool host, cudaStream_t s) {
+int finish_output(double *user, const double *dev, size_t count, bool host, cudaStream_t s, int *syncs = nullptr) {
     if (host) {
         LBMG_CK(cudaMemcpyAsync(user, dev, count * sizeof(double), cudaMemcpyDeviceToHost, s));
         LBMG_CK(cudaStreamSynchronize(s));
+        if (syncs) (*syncs)++;
     }
     return check_launch();
 }
@@ -231,18 +311,19 @@ Chain make_chain(const Ctx &c, cudaStream_t s) {
 }
 
 // one defect-correction step: x += Vcycle(r); r = b - A x; norms(r)
-void enqueue_iteration(Ctx &c, int R, int precision, cudaStream_t s) {
+// timed: events around the finest smoothing (not inside the body of a conditional node)
+void enqueue_iteration(Ctx &c, int R, int precision, cudaStream_t s, bool timed = true) {
     DevLevel &F = c.lev[c.D];
     const int64_t m = (int64_t)F.n * R;
     Chain ch = make_chain(c, s);
     if (precision == LBMG_MIXED) {
         launch_to_float(c.rs, F.b32, m, s, F.x32, &ch);
-        enqueue_vcycle<float>(c, R, s, true, &ch);
+        enqueue_vcycle<float>(c, R, s, timed, &ch);
         launch_add_float(c.xs, F.x32, m, s, &ch);
     } else {
         cudaMemcpyAsync(F.b64, c.rs, m * sizeof(double), cudaMemcpyDeviceToDevice, s);
         cudaMemsetAsync(F.x64, 0, m * sizeof(double), s);
-        enqueue_vcycle<double>(c, R, s, true, &ch);
+        enqueue_vcycle<double>(c, R, s, timed, &ch);
         launch_add_double(c.xs, F.x64, m, s);
         ch.cut();
     }
@@ -254,19 +335,19 @@ void enqueue_iteration(Ctx &c, int R, int precision, cudaStream_t s) {
 // (Polak-Ribiere) form, each right-hand side lane with its own step lengths:
 //   s2 = r.z_old;  z = Vcycle(r);  s1 = r.z;  beta = (s1 - s2) / rz;  rz = s1;
 //   p = z + beta p;  q = -A p;  alpha = s1 / (p.A p);  x += alpha p;  r -= alpha A p;  norms(r)
-void enqueue_pcg_iteration(Ctx &c, int R, int precision, cudaStream_t s) {
+void enqueue_pcg_iteration(Ctx &c, int R, int precision, cudaStream_t s, bool timed = true) {
     DevLevel &F = c.lev[c.D];
     const int64_t m = (int64_t)F.n * R;
     launch_pcg_dot(c.rs, c.pcg_z, F.n, R, c.pcg_part, c.pcg_s, 0, s);
     Chain ch = make_chain(c, s);
     if (precision == LBMG_MIXED) {
         launch_to_float(c.rs, F.b32, m, s, F.x32, &ch);
-        enqueue_vcycle<float>(c, R, s, true, &ch);
+        enqueue_vcycle<float>(c, R, s, timed, &ch);
         to_double_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(F.x32, c.pcg_z, m);
     } else {
         cudaMemcpyAsync(F.b64, c.rs, m * sizeof(double), cudaMemcpyDeviceToDevice, s);
         cudaMemsetAsync(F.x64, 0, m * sizeof(double), s);
-        enqueue_vcycle<double>(c, R, s, true, &ch);
+        enqueue_vcycle<double>(c, R, s, timed, &ch);
         cudaMemcpyAsync(c.pcg_z, F.x64, m * sizeof(double), cudaMemcpyDeviceToDevice, s);
     }
     launch_pcg_dot(c.rs, c.pcg_z, F.n, R, c.pcg_part, c.pcg_s, 1, s);
@@ -310,7 +391,7 @@ int get_graph(lbmg_handle h, int R, int precision, bool pcg, cudaGraphExec_t *ou
     Ctx &c = h->c;
     GraphCache &g = c.graph;
     if (g.exec && g.R == R && g.precision == precision && g.nu1 == c.nu1 && g.nu2 == c.nu2 && g.smoother == c.smoother &&
-        g.pcg == (int)pcg) {
+        g.pcg == (int)pcg && g.cond == 0) {
         *out = g.exec;
         return LBMG_OK;
     }
@@ -329,6 +410,79 @@ int get_graph(lbmg_handle h, int R, int precision, bool pcg, cudaGraphExec_t *ou
         return LBMG_CUDA_ERROR;
     }
     g.R = R; g.precision = precision; g.nu1 = c.nu1; g.nu2 = c.nu2; g.smoother = c.smoother; g.pcg = pcg;
+    g.cond = 0;
+    *out = g.exec;
+    return LBMG_OK;
+}
+
+// The whole solve as one graph: a check of the initial residual, then a conditional WHILE
+// node whose body is one iteration (V-cycle step, or CG step preconditioned by one V-cycle)
+// and the check kernel that sets the loop condition.  The parameters (tolerance, cycle
+// cap) and the initial norms are written by ordinary launches before each graph launch.
+int build_cond_graph(Ctx &c, int R, int precision, bool pcg, cudaGraphExec_t *out) {
+    cudaStream_t cs = c.capture_stream;
+    const bool batch = c.ninst > 1;
+    cudaGraph_t g = nullptr;
+    LBMG_CK(cudaGraphCreate(&g, 0));
+    struct GraphGuard {
+        cudaGraph_t g;
+        ~GraphGuard() { if (g) cudaGraphDestroy(g); }
+    } guard{g};
+    cudaGraphConditionalHandle hc;
+    LBMG_CK(cudaGraphConditionalHandleCreate(&hc, g, 0, cudaGraphCondAssignDefault));
+    LBMG_CK(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    ctl_begin_kernel<<<1, 32, 0, cs>>>(c.ctl, c.norm_b, c.norm_out, batch ? c.inst_norm : nullptr, c.ninst,
+                                       c.narrow.status, c.flag, hc);
+    cudaGraph_t gc = nullptr;
+    LBMG_CK(cudaStreamEndCapture(cs, &gc));
+    cudaGraphNode_t begin = nullptr;
+    size_t nn = 1;
+    LBMG_CK(cudaGraphGetNodes(g, &begin, &nn));
+    if (nn != 1) return LBMG_CUDA_ERROR;
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = hc;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t loop = nullptr;
+    LBMG_CK(cudaGraphAddNode(&loop, g, &begin, nullptr, 1, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    LBMG_CK(cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    if (pcg && batch) enqueue_pcg_batch_iteration(c, R, precision, cs);
+    else if (pcg) enqueue_pcg_iteration(c, R, precision, cs, false);
+    else enqueue_iteration(c, R, precision, cs, false);
+    ctl_step_kernel<<<1, 32, 0, cs>>>(c.ctl, c.norm_out, batch ? c.inst_norm : nullptr, c.ninst, c.narrow.status,
+                                      c.flag, hc);
+    cudaGraph_t bc = nullptr;
+    LBMG_CK(cudaStreamEndCapture(cs, &bc));
+    LBMG_CK(cudaGraphInstantiate(out, g, 0));
+    return LBMG_OK;
+}
+
+int get_cond_graph(lbmg_handle h, int R, int precision, bool pcg, cudaGraphExec_t *out) {
+    Ctx &c = h->c;
+    GraphCache &g = c.graph;
+    if (g.exec && g.R == R && g.precision == precision && g.nu1 == c.nu1 && g.nu2 == c.nu2 && g.smoother == c.smoother &&
+        g.pcg == (int)pcg && g.cond == 1) {
+        *out = g.exec;
+        return LBMG_OK;
+    }
+    if (g.exec) { cudaGraphExecDestroy(g.exec); g.exec = nullptr; }
+    int e = build_cond_graph(c, R, precision, pcg, &g.exec);
+    if (e != LBMG_OK) {
+        // end a capture the failure may have left open, then report
+        cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(c.capture_stream, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
+            cudaGraph_t junk = nullptr;
+            cudaStreamEndCapture(c.capture_stream, &junk);
+            if (junk) cudaGraphDestroy(junk);
+        }
+        cudaGetLastError();
+        g.exec = nullptr;
+        return e;
+    }
+    g.R = R; g.precision = precision; g.nu1 = c.nu1; g.nu2 = c.nu2; g.smoother = c.smoother; g.pcg = pcg;
+    g.cond = 1;
     *out = g.exec;
     return LBMG_OK;
 }
@@ -337,6 +491,7 @@ int read_norms(lbmg_handle h, int R, cudaStream_t s, double *out4) {
     // four norms, then the bottom kernel's status word
     LBMG_CK(cudaMemcpyAsync(h->c.h_norm, h->c.norm_out, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
     LBMG_CK(cudaStreamSynchronize(s));
+    h->syncs++;
     for (int r = 0; r < 4; r++) out4[r] = r < R ? h->c.h_norm[r] : 0.0;
     int st = 0;
     std::memcpy(&st, &h->c.h_norm[4], sizeof st);
@@ -404,6 +559,20 @@ int upload_hierarchy(lbmg_handle h) {
             LBMG_TRY(h->upload(&L.cch, hl.cch));
             LBMG_TRY(h->upload(&L.grp, hl.grp));
             LBMG_TRY(h->upload(&L.gidx, hl.gidx));
+        }
+        if (d > c.d0 && L.nnz > 0) {
+            // packed copy of A for the smoothing and residual kernels (packed.cu)
+            std::vector<int32_t> gq, rows, map, col;
+            if (packed_layout(hl, gq, rows, map, col, L.pk_gs, &L.pk_total)) {
+                std::vector<int2> gq2(gq.size() / 2);
+                for (size_t g = 0; g < gq2.size(); g++) gq2[g] = make_int2(gq[2 * g], gq[2 * g + 1]);
+                LBMG_TRY(h->upload(&L.pk_gq, gq2));
+                LBMG_TRY(h->upload(&L.pk_rows, rows));
+                LBMG_TRY(h->upload(&L.pk_map, map));
+                LBMG_TRY(h->upload(&L.pk_col, col));
+                LBMG_TRY(h->alloc(&L.pk_e32, (size_t)L.pk_total));
+                LBMG_TRY(h->alloc(&L.pk_v64, (size_t)L.pk_total));
+            }
         }
         const size_t v4 = 4 * (size_t)L.n;
         LBMG_TRY(h->alloc(&L.x64, v4));
@@ -499,6 +668,11 @@ int upload_hierarchy(lbmg_handle h) {
     h->io_cap = 4 * std::max(std::max(nD, (size_t)c.nv), (size_t)c.nu);
     LBMG_TRY(h->alloc(&c.dev_io, 2 * h->io_cap));
     LBMG_CK(cudaMallocHost((void **)&c.h_norm, 8 * sizeof(double)));
+    LBMG_TRY(h->alloc((char **)&c.ctl, sizeof(SolveCtl)));
+    LBMG_CK(cudaMemset(c.ctl, 0, sizeof(SolveCtl)));
+    LBMG_CK(cudaMallocHost((void **)&c.h_ctl, sizeof(SolveCtl)));
+    LBMG_TRY(h->alloc(&c.norm_b, 4));
+    LBMG_CK(cudaMallocHost((void **)&h->h_inst, 16 * sizeof(double) * (size_t)c.ninst));
     LBMG_CK(cudaMallocHost((void **)&h->h_flag, sizeof(int)));
     LBMG_CK(cudaStreamCreateWithFlags(&c.capture_stream, cudaStreamNonBlocking));
     LBMG_CK(cudaEventCreate(&c.ev0));
@@ -543,13 +717,15 @@ void noalloc_set_error(const std::string &msg) { g_cuda_err = msg; }
 
 // relative residual sqrt(r2 / b2) from squared norms: a non-finite norm (NaN or inf in the
 // right-hand side or the iterate) gives infinity, so it can never pass for convergence; a zero
-// right-hand side gives 0
+// right-hand side is judged by the absolute residual sqrt(r2) (the rule of the device-side
+// stopping test and of the persistent solve)
 static double rel_residual(double r2, double b2) {
     if (!std::isfinite(r2) || !std::isfinite(b2)) return INFINITY;
-    return b2 > 0 ? std::sqrt(r2 / b2) : 0.0;
+    return std::sqrt(r2 / (b2 > 0 ? b2 : 1.0));
 }
 
 static int check_build_options(const lbmg_options &o) {
+    if (o.host_check != 0 && o.host_check != 1) return LBMG_INVALID_ARG;
     if (o.nu1 < 0 || o.nu2 < 0 || o.coarse_max < 1 || o.coarse_max > kMaxCoarse) return LBMG_INVALID_ARG;
     if (o.smoother != LBMG_GS_COLOURED && o.smoother != LBMG_JACOBI) return LBMG_INVALID_ARG;
     if (o.narrow_max < 0 || o.barrier_phantoms < 0 || o.barrier_phantoms > 1024) return LBMG_INVALID_ARG;
@@ -704,6 +880,7 @@ void lbmg_default_options(lbmg_options *o) {
     o->pdl = 1;
     o->copy_phantom_bytes = 0;
     o->host_alloc_fail = 0;
+    o->host_check = 0;
 }
 
 int lbmg_build_hierarchy(const double *V, int nv, const int *F, int nt, int depth, const lbmg_options *opt,
@@ -731,6 +908,7 @@ int lbmg_build_hierarchy(const double *V, int nv, const int *F, int nt, int dept
     h->c.copy_phantoms = o.copy_phantom_bytes;
     h->c.persist_narrow = o.narrow_max;
     h->c.barrier_phantoms = o.barrier_phantoms;
+    h->c.host_check = o.host_check;
     st = upload_hierarchy(h);
     if (st != 0) { delete h; return st; }
     *out = h;
@@ -754,6 +932,7 @@ int lbmg_build_batch(const double *const *V, const int *nv, const int *const *F,
     }
     h->c.nu1 = o.nu1; h->c.nu2 = o.nu2; h->c.smoother = o.smoother; h->c.omega = o.jacobi_omega;
     h->c.persistent = 1; h->c.persist_narrow = o.narrow_max; h->c.barrier_phantoms = o.barrier_phantoms;
+    h->c.host_check = o.host_check;
     st = upload_hierarchy(h);
     if (st != 0) { delete h; return st; }
     if (!h->c.persist_ok) { delete h; return LBMG_CUDA_ERROR; }
@@ -838,15 +1017,14 @@ int lbmg_assemble(lbmg_handle h, double t, void *stream) {
     launch_fine_gather(c, t, s);
     for (int d = c.D - 1; d >= c.d0; d--) launch_galerkin(c, d, t, s);
     for (int d = c.d0; d <= c.D; d++) launch_inverse_diag(c.lev[d], c.diag_part, s);
+    for (int d = c.d0 + 1; d <= c.D; d++) launch_packed_fill(c.lev[d], s);
     cudaMemsetAsync(c.flag, 0, sizeof(int), s);
     launch_coarse_factor(c, h->lev_rp, h->lev_ci, h->lev_A, s);
     narrow_smem_refresh(c, s);
     LBMG_TRY(check_launch());
-    LBMG_CK(cudaMemcpyAsync(h->h_flag, c.flag, sizeof(int), cudaMemcpyDeviceToHost, s));
-    LBMG_CK(cudaStreamSynchronize(s));
+    // the coarse-factor flag stays on the device: the next solve reports a failed factor
     c.assembled = true;
     c.t = t;
-    if (*h->h_flag != 0) return LBMG_COARSE_FACTOR;
     if (c.learned_on && learned_enable(c, 1, s) != 0) return LBMG_CUDA_ERROR;   // weights of the new matrix
     return LBMG_OK;
 }
@@ -878,6 +1056,80 @@ int lbmg_eval_vertices(lbmg_handle h, const double *x, int nrhs, double *u, void
     return finish_output(u, ud, (size_t)h->c.nv * nrhs, host_out, s);
 }
 
+// A solve as one graph launch (conditional WHILE node, see build_cond_graph): packing, the
+// initial residual and norms and the graph go out on `stream`, and the host synchronizes once,
+// to read the final status (and the solution, for a host output buffer).
+static int solve_cond(lbmg_handle h, cudaGraphExec_t exec, const double *rd, const double *xin, double *xout,
+                      bool host_out, double *x, size_t cnt, int nrhs, int R, double tol, int max_cycles, bool pcg,
+                      bool check, lbmg_stats *stats, cudaStream_t s) {
+    Ctx &c = h->c;
+    DevLevel &Fl = c.lev[c.D];
+    const bool batch = c.ninst > 1;
+    h->syncs = 0;
+    LBMG_CK(cudaEventRecord(c.ev0, s));
+    launch_pack(rd, Fl.n, nrhs, R, c.bs, s, c.fperm);
+    launch_pack(xin, Fl.n, nrhs, R, c.xs, s, c.fperm);
+    launch_residual<double>(Fl, Fl.A64, c.bs, c.xs, c.rs, R, s);
+    const size_t m = (size_t)Fl.n * R;
+    if (pcg) {
+        LBMG_CK(cudaMemsetAsync(c.pcg_z, 0, m * sizeof(double), s));
+        LBMG_CK(cudaMemsetAsync(c.pcg_p, 0, m * sizeof(double), s));
+        if (batch) LBMG_CK(cudaMemsetAsync(c.pcg_si, 0, sizeof(double) * kPcgScalars * c.ninst, s));
+        else LBMG_CK(cudaMemsetAsync(c.pcg_s, 0, kPcgScalars * sizeof(double), s));
+    }
+    ctl_setup_kernel<<<1, 32, 0, s>>>(c.ctl, check ? tol : 0.0, max_cycles, check ? 0 : 1, nrhs,
+                                      batch ? c.pcg_tol : nullptr);
+    if (batch) {
+        launch_item_dot2(c.nitem, c.nnitem, c.rs, c.rs, c.bs, c.bs, R, c.item_part, s);
+        launch_inst_sum(c.item_start, c.ninst, c.item_part, c.inst_norm, 16, s);
+    } else {
+        launch_norms(c.bs, Fl.n, R, c.norm_part, c.norm_b, s);
+        launch_norms(c.rs, Fl.n, R, c.norm_part, c.norm_out, s);
+    }
+    LBMG_CK(cudaGraphLaunch(exec, s));
+    launch_unpack(c.xs, Fl.n, nrhs, R, xout, s, c.fperm);
+    LBMG_CK(cudaEventRecord(c.ev1, s));
+    LBMG_CK(cudaMemcpyAsync(c.h_ctl, c.ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, s));
+    if (batch)
+        LBMG_CK(cudaMemcpyAsync(h->h_inst, c.inst_norm, 16 * sizeof(double) * c.ninst, cudaMemcpyDeviceToHost, s));
+    LBMG_TRY(finish_output(x, xout, cnt, host_out, s, &h->syncs));
+    if (!host_out) {
+        LBMG_CK(cudaStreamSynchronize(s));
+        h->syncs++;
+    }
+    const SolveCtl &hc = *c.h_ctl;
+    if (batch) h->inst_norm_host.assign(h->h_inst, h->h_inst + 16 * (size_t)c.ninst);
+    int status = LBMG_OK;
+    switch (hc.status) {
+        case kCtlConverged: status = LBMG_OK; break;
+        case kCtlMaxCycles: status = check ? LBMG_NOT_CONVERGED : LBMG_OK; break;
+        case kCtlDiverged: status = LBMG_DIVERGED; break;
+        case kCtlCoarse: status = LBMG_COARSE_FACTOR; break;
+        case kCtlTimeout:
+            // a bounded wait gave up: the results are invalid; clear the word for the next solve
+            status = LBMG_DEVICE_TIMEOUT;
+            LBMG_CK(cudaMemsetAsync(c.norm_out + 4, 0, sizeof(double), s));
+            break;
+        default: g_cuda_err = "solve ended with an unknown control status"; status = LBMG_CUDA_ERROR;
+    }
+    if (stats) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, c.ev0, c.ev1);
+        stats->cycles = hc.cycles;
+        stats->converged = hc.status == kCtlConverged ? 1 : 0;
+        for (int r = 0; r < 4; r++) {
+            stats->rel_residual[r] = r < nrhs ? hc.rel[r] : 0.0;
+            stats->initial_residual[r] = r < nrhs ? hc.r0[r] : 0.0;
+        }
+        stats->ms_total = ms;
+        stats->ms_fine_smooth = 0.f;
+        stats->learned = 0;
+        stats->learned_fallback = 0;
+        stats->host_syncs = h->syncs;
+    }
+    return status;
+}
+
 // V-cycle-preconditioned conjugate gradients on a batch: per-mesh step lengths and norms;
 // stops when every mesh meets tol (or after max_iters iterations)
 static int solve_pcg_batch(lbmg_handle h, const double *rd, const double *xin, double *xout, bool host_out,
@@ -901,9 +1153,11 @@ static int solve_pcg_batch(lbmg_handle h, const double *rd, const double *xin, d
     launch_inst_sum(c.item_start, c.ninst, c.item_part, c.inst_norm, 16, s);
     std::vector<double> &nh = h->inst_norm_host;
     nh.assign(16 * (size_t)c.ninst, 0.0);
+    h->syncs = 0;
     auto read = [&]() -> int {
         LBMG_CK(cudaMemcpyAsync(nh.data(), c.inst_norm, nh.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
         LBMG_CK(cudaStreamSynchronize(s));
+        h->syncs++;
         return check_launch();
     };
     auto worst = [&](const std::vector<double> &v, double *w) {
@@ -937,11 +1191,13 @@ static int solve_pcg_batch(lbmg_handle h, const double *rd, const double *xin, d
     if (!conv && status == LBMG_OK) status = LBMG_NOT_CONVERGED;
     launch_unpack(c.xs, Fl.n, nrhs, R, xout, s, c.fperm);
     LBMG_CK(cudaEventRecord(c.ev1, s));
-    LBMG_TRY(finish_output(x, xout, cnt, host_out, s));
+    LBMG_TRY(finish_output(x, xout, cnt, host_out, s, &h->syncs));
     if (stats) {
         LBMG_CK(cudaEventSynchronize(c.ev1));
+        if (!host_out) h->syncs++;
         float ms = 0;
         cudaEventElapsedTime(&ms, c.ev0, c.ev1);
+        stats->host_syncs = h->syncs;
         stats->cycles = it;
         stats->converged = conv ? 1 : 0;
         for (int r = 0; r < 4; r++) {
@@ -984,12 +1240,15 @@ static int solve_impl(lbmg_handle h, const double *rhs, double *x, int nrhs, dou
         }
         unsigned char *hs = reinterpret_cast<unsigned char *>(c.h_state);
         LBMG_CK(cudaMemcpyAsync(hs, c.persist_state, 64, cudaMemcpyDeviceToHost, s));
+        LBMG_CK(cudaMemcpyAsync(h->h_inst, c.inst_norm, 16 * sizeof(double) * c.ninst, cudaMemcpyDeviceToHost, s));
+        LBMG_CK(cudaMemcpyAsync(h->h_flag, c.flag, sizeof(int), cudaMemcpyDeviceToHost, s));
         launch_unpack(c.xs, Fl.n, nrhs, R, xout, s, c.fperm);
         LBMG_CK(cudaEventRecord(c.ev1, s));
-        LBMG_TRY(finish_output(x, xout, cnt, host_out, s));
+        h->syncs = 0;
+        LBMG_TRY(finish_output(x, xout, cnt, host_out, s, &h->syncs));
         LBMG_CK(cudaEventSynchronize(c.ev1));
-        h->inst_norm_host.assign(16 * (size_t)c.ninst, 0.0);
-        LBMG_CK(cudaMemcpy(h->inst_norm_host.data(), c.inst_norm, 16 * sizeof(double) * c.ninst, cudaMemcpyDeviceToHost));
+        if (!host_out) h->syncs++;
+        h->inst_norm_host.assign(h->h_inst, h->h_inst + 16 * (size_t)c.ninst);
         int dstat, dcyc, dfall;
         std::memcpy(&dfall, hs + 32, sizeof(int));
         unsigned long long sns;
@@ -1009,9 +1268,11 @@ static int solve_impl(lbmg_handle h, const double *rhs, double *x, int nrhs, dou
             }
         int status = LBMG_OK;
         if (dstat == 1) status = LBMG_DEVICE_TIMEOUT;
+        else if (*h->h_flag != 0) status = LBMG_COARSE_FACTOR;
         else if (dstat == 2) status = LBMG_DIVERGED;
         else if (check && !conv) status = LBMG_NOT_CONVERGED;
         if (stats) {
+            stats->host_syncs = h->syncs;
             stats->cycles = dcyc;
             stats->converged = (check && conv && dstat == 0) ? 1 : 0;
             for (int r = 0; r < 4; r++) {
@@ -1028,11 +1289,20 @@ static int solve_impl(lbmg_handle h, const double *rhs, double *x, int nrhs, dou
         return status;
     }
     if (pcg && c.smoother != LBMG_GS_COLOURED) return LBMG_INVALID_ARG;   // the preconditioner must be symmetric
+    if (!pcg && c.ninst > 1) return LBMG_INVALID_ARG;   // batch V-cycles need the persistent solve (per-mesh norms)
+    if (c.use_graphs && !c.host_check && !c.cond_failed) {
+        cudaGraphExec_t cexec = nullptr;
+        if (get_cond_graph(h, R, precision, pcg, &cexec) == LBMG_OK)
+            return solve_cond(h, cexec, rd, xin, xout, host_out, x, cnt, nrhs, R, tol, max_cycles, pcg, check, stats,
+                              s);
+        c.cond_failed = true;   // no conditional graphs here: the host reads the norms each iteration
+    }
     if (pcg && c.ninst > 1)
         return solve_pcg_batch(h, rd, xin, xout, host_out, x, cnt, nrhs, R, tol, max_cycles, precision, stats, s);
-    if (c.ninst > 1) return LBMG_INVALID_ARG;   // batches need the persistent solve (per-mesh norms)
     cudaGraphExec_t exec = nullptr;
     if (c.use_graphs) LBMG_TRY(get_graph(h, R, precision, pcg, &exec));
+    h->syncs = 0;
+    LBMG_CK(cudaMemcpyAsync(h->h_flag, c.flag, sizeof(int), cudaMemcpyDeviceToHost, s));
     LBMG_CK(cudaEventRecord(c.ev0, s));
     launch_pack(rd, Fl.n, nrhs, R, c.bs, s, c.fperm);
     launch_pack(xin, Fl.n, nrhs, R, c.xs, s, c.fperm);
@@ -1051,6 +1321,7 @@ static int solve_impl(lbmg_handle h, const double *rhs, double *x, int nrhs, dou
         LBMG_TRY(read_norms(h, R, s, nb));
         launch_norms(c.rs, Fl.n, R, c.norm_part, c.norm_out, s);
         LBMG_TRY(read_norms(h, R, s, nr));
+        if (*h->h_flag != 0) return LBMG_COARSE_FACTOR;
         auto rel = [&](int r) { return rel_residual(nr[r], nb[r]); };
         for (int r = 0; r < nrhs; r++) r0[r] = rel(r);
         for (;;) {
@@ -1097,13 +1368,17 @@ static int solve_impl(lbmg_handle h, const double *rhs, double *x, int nrhs, dou
     }
     launch_unpack(c.xs, Fl.n, nrhs, R, xout, s, c.fperm);
     LBMG_CK(cudaEventRecord(c.ev1, s));
-    LBMG_TRY(finish_output(x, xout, cnt, host_out, s));
+    LBMG_TRY(finish_output(x, xout, cnt, host_out, s, &h->syncs));
     if (stats) {
         LBMG_CK(cudaEventSynchronize(c.ev1));
+        if (!host_out) h->syncs++;
         float ms = 0;
         cudaEventElapsedTime(&ms, c.ev0, c.ev1);
         stats->ms_total = ms;
         stats->ms_fine_smooth = smooth_ms;
+        stats->host_syncs = h->syncs;
+        stats->learned = 0;
+        stats->learned_fallback = 0;
         if (!check) stats->cycles = cycles;
     }
     return status;
@@ -1286,6 +1561,12 @@ int lbmg_set_launch_shape(lbmg_handle h, int d, int precision, int kind, int tpr
     sh.tpb = tpb;
     h->c.lev[d].tuned_ms[precision == LBMG_FP64][kind] = 0.f;
     if (h->c.graph.exec) { cudaGraphExecDestroy(h->c.graph.exec); h->c.graph.exec = nullptr; }
+    return LBMG_OK;
+}
+
+int lbmg_set_host_check(lbmg_handle h, int on) {
+    if (!h || (on != 0 && on != 1)) return LBMG_INVALID_ARG;
+    h->c.host_check = on;
     return LBMG_OK;
 }
 

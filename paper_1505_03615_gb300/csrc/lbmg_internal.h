@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include "hier.h"
 
@@ -13,9 +14,10 @@ constexpr int kMaxCoarse = 2048;  // largest coarsest level factored densely
 constexpr int kNormBlocks = 256;  // partial sums of the two-pass norm reduction
 
 // Launch shape of the row-parallel kernels (Gauss-Seidel colour sweep, residual):
-// tpr threads share one matrix row (4, 8 or 16), tpb threads per block (128-512).
+// tpr threads share one matrix row (4, 8 or 16), tpb threads per block (128-512).  With
+// 4 threads per row the kernels read the packed copy of the matrix (packed.cu).
 struct LaunchShape {
-    int tpr = 8, tpb = 256;
+    int tpr = 4, tpb = 256;
 };
 enum { kShapeSmooth = 0, kShapeResidual = 1 };
 
@@ -79,6 +81,16 @@ struct DevLevel {
     // V-cycle work vectors, room for [n][4]
     double *x64 = nullptr, *b64 = nullptr, *r64 = nullptr;
     float *x32 = nullptr, *b32 = nullptr, *r32 = nullptr;
+    // packed copy of A for the row kernels (packed.cu): per colour, 8-row groups of rows with
+    // equal quad counts, entries quad-interleaved across the group; null pk_map when not built
+    int2 *pk_gq = nullptr;                 // [ngroups] (base / 32, quads)
+    int *pk_rows = nullptr;                // [ngroups * 8] rows of the slots, -1 none
+    int *pk_map = nullptr;                 // [total] packed position -> CSR position, -1 pad
+    int *pk_col = nullptr;                 // [total] columns in packed order, -1 pad (FP64 kernels)
+    int2 *pk_e32 = nullptr;                // [total] (column, FP32 value bits)
+    double *pk_v64 = nullptr;              // [total] FP64 values
+    int64_t pk_total = 0;
+    int pk_gs[10] = {0};                   // group ranges of colours 0..7, then rows [ns, n)
     LaunchShape shape[2][2];               // [FP64][kShapeSmooth / kShapeResidual], set by the autotuner
     float tuned_ms[2][2] = {{0, 0}, {0, 0}};   // device time of the chosen shape when the tuner timed it
 };
@@ -109,7 +121,19 @@ struct NarrowState {
 struct GraphCache {
     cudaGraphExec_t exec = nullptr;
     int R = 0, precision = -1, nu1 = -1, nu2 = -1, smoother = -1, pcg = -1;
+    int cond = -1;   // 1: the whole solve (conditional WHILE node), 0: one iteration
 };
+
+// Device-side control of a solve that runs as one graph launch: a conditional WHILE node
+// whose body is one iteration followed by a check kernel that decides, from the residual
+// norms the iteration leaves in device memory, whether another iteration follows.
+struct SolveCtl {
+    double tol;
+    int max_cycles, cycles, status, fixed;   // fixed: run exactly max_cycles iterations
+    int nrhs, pad[3];
+    double nb[4], r0[4], rel[4];            // ||b||^2, initial and current relative residual per lane
+};
+enum { kCtlRunning = 0, kCtlConverged = 1, kCtlDiverged = 2, kCtlTimeout = 3, kCtlMaxCycles = 4, kCtlCoarse = 5 };
 
 struct Ctx {
     HostHierarchy host;
@@ -161,6 +185,12 @@ struct Ctx {
     double *pcg_tol = nullptr;     // [1] tolerance of the running batch solve
     int *item_start = nullptr, *row_inst = nullptr;
     double *h_norm = nullptr;    // pinned [8]
+    SolveCtl *ctl = nullptr;     // device control block of the running solve
+    SolveCtl *h_ctl = nullptr;   // pinned copy read after the solve
+    double *norm_b = nullptr;    // [4] ||b||^2 per lane of the running solve
+    int host_check = 0;          // 1: the host reads the norms after every iteration (events time
+                                 // the finest smoothing); 0: one graph launch per solve
+    bool cond_failed = false;    // the conditional graph could not be built: the host loop is used
     // staging of user vectors (device [n][nrhs]) and pinned host mirrors
     double *dev_io = nullptr;
     size_t dev_io_bytes = 0;
@@ -232,6 +262,20 @@ void launch_galerkin(const Ctx &c, int dc, double t, cudaStream_t s);
 void launch_inverse_diag(const DevLevel &L, double *part, cudaStream_t s);
 void launch_project_rhs(const Ctx &c, const double *fv, int nrhs, double *rhs_out, cudaStream_t s);
 void launch_eval_vertices(const Ctx &c, const double *x, int nrhs, double *u, cudaStream_t s);
+
+// ----- packed matrix layout of the row kernels (packed.cu) -----
+// host: groups, slot rows, packed -> CSR position map and columns of one level (rows of
+// colours 0..7, then [ns, n)); false when the packed positions would not fit 32 bits
+bool packed_layout(const HostLevel &hl, std::vector<int32_t> &gq, std::vector<int32_t> &rows,
+                   std::vector<int32_t> &map, std::vector<int32_t> &col, int gs[10], int64_t *total);
+// refresh the packed FP32 and FP64 values from the level's CSR A32 / A64 (after assembly)
+void launch_packed_fill(const DevLevel &L, cudaStream_t s);
+// packed Gauss-Seidel colour / residual over rows [0, nrows); false when the level or the
+// matrix has no packed copy (the caller then uses the CSR kernels)
+template <class T> bool launch_packed_smooth(const DevLevel &L, int colour, const T *A, const T *dinv, const T *b,
+                                             T *x, int R, int tpb, cudaStream_t s, Chain *ch);
+template <class T> bool launch_packed_residual(const DevLevel &L, const T *A, const T *b, const T *x, T *r, int R,
+                                               int nrows, int tpb, cudaStream_t s, Chain *ch);
 
 // ----- kernels (relax.cu) -----
 // vectors below are [n][R] with stride R in {1, 2, 4} (3 right-hand sides padded to 4)

@@ -1,0 +1,273 @@
+// packed.cu -- packed storage of a level's matrix for the row kernels of the V-cycle
+// (coloured Gauss-Seidel colour sweep and residual, Sections 4.3 and 5.2).
+//
+// On large levels these kernels stream the matrix from HBM.  With four threads per
+// row, two things limit plain CSR: a warp's load touches the scattered 16-byte pieces
+// of eight rows, and a warp spends many instructions per non-zero on row bounds.  The
+// packed copy removes both:
+//
+//  - The rows of each colour are grouped by their number of quads Q = ceil(len / 4);
+//    within one Q, rows keep the level's order (Morton order of their corners, which
+//    keeps the x gathers of neighbouring rows close).  Every 8 consecutive rows of one
+//    (colour, Q) class form a group, handled by one warp with four lanes per row.
+//  - A group stores 32 Q entries: quad q of slot s at base + 32 q + 4 s, so lane
+//    4 s + l reads its row's entry 4 q + l at base + 32 q + lane -- one aligned
+//    256-byte load per warp and quad, no index arithmetic.  Entries beyond a row's
+//    length, and the slots of a class's last group that have no row, are pads
+//    (column -1), about 5% of the entries on the seeded meshes.
+//  - Per group: (base, Q) and the 8 rows of its slots (-1 for none).
+//  - FP32 entries are (column, value bits) pairs, one 8-byte load each; FP64 entries
+//    keep columns and values in two arrays with the same order.
+// A row's sum runs over the same entries as in CSR, in another order (four lanes,
+// each in its own order, then a shuffle reduction).
+#include <algorithm>
+
+#include "lbmg_internal.h"
+
+namespace lbmg {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kPkPrefetch = 8;   // quads per lane held in registers before the grid-dependency wait
+
+template <class T> struct PkMat;
+template <> struct PkMat<float> {
+    const int2 *e;
+    __device__ __forceinline__ void get(int64_t k, int &j, float &a) const {
+        const int2 v = __ldg(e + k);
+        j = v.x;
+        a = __int_as_float(v.y);
+    }
+};
+template <> struct PkMat<double> {
+    const int *col;
+    const double *val;
+    __device__ __forceinline__ void get(int64_t k, int &j, double &a) const {
+        j = __ldg(col + k);
+        a = __ldg(val + k);
+    }
+};
+
+template <class T, int R>
+__device__ __forceinline__ void load_row(const T *p, T (&v)[R]) {
+#pragma unroll
+    for (int r = 0; r < R; r++) v[r] = p[r];
+}
+template <>
+__device__ __forceinline__ void load_row<float, 4>(const float *p, float (&v)[4]) {
+    const float4 q = *reinterpret_cast<const float4 *>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+template <>
+__device__ __forceinline__ void load_row<double, 2>(const double *p, double (&v)[2]) {
+    const double2 q = *reinterpret_cast<const double2 *>(p);
+    v[0] = q.x; v[1] = q.y;
+}
+template <>
+__device__ __forceinline__ void load_row<double, 4>(const double *p, double (&v)[4]) {
+    const double2 q0 = reinterpret_cast<const double2 *>(p)[0];
+    const double2 q1 = reinterpret_cast<const double2 *>(p)[1];
+    v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+}
+
+// One warp per group.  kGs: Gauss-Seidel update x += (b - A x) / A_ii (rows of one
+// colour, which never couple); otherwise r = b - A x.  Before the grid-dependency wait
+// a warp loads its group, its entries and (kGs) the inverse diagonal; after it, the
+// row's own b and x and the x gathers go out together.  x is read with plain loads: a
+// colour launch writes x only at rows of its own colour, which it never gathers.
+template <class T, int R, bool kGs>
+__global__ void __launch_bounds__(512) pk_row_kernel(int g0, int g1, const int2 *__restrict__ gq,
+                                                     const int *__restrict__ rows, PkMat<T> m,
+                                                     const T *__restrict__ dinv, const T *__restrict__ b, T *x,
+                                                     T *__restrict__ r) {
+    const int lane = threadIdx.x & 31;
+    const int g = g0 + (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+    if (g >= g1) return;   // whole warps only (blockDim is a multiple of 32)
+    const int2 hd = __ldg(gq + g);
+    const int64_t base = (int64_t)(unsigned)hd.x * 32;
+    const int Q = hd.y;
+    const int row = __ldg(rows + 8 * (size_t)g + (lane >> 2));
+    const bool lead = row >= 0 && (lane & 3) == 0;
+    int j[kPkPrefetch];
+    T a[kPkPrefetch];
+#pragma unroll
+    for (int q = 0; q < kPkPrefetch; q++) {
+        j[q] = -1;
+        a[q] = T(0);
+        if (q < Q) m.get(base + 32 * q + lane, j[q], a[q]);
+    }
+    T d = T(0);
+    if (kGs && lead) d = __ldg(dinv + row);
+    grid_dep_wait();
+    grid_dep_launch();
+    T bv[R], xo[R];
+    if (lead) {
+        load_row<T, R>(b + (size_t)row * R, bv);
+        if (kGs) load_row<T, R>(x + (size_t)row * R, xo);
+    }
+    T acc[R];
+#pragma unroll
+    for (int c = 0; c < R; c++) acc[c] = T(0);
+#pragma unroll
+    for (int q = 0; q < kPkPrefetch; q++) {
+        if (j[q] >= 0) {
+            T xv[R];
+            load_row<T, R>(x + (size_t)j[q] * R, xv);
+#pragma unroll
+            for (int c = 0; c < R; c++) acc[c] = fma(a[q], xv[c], acc[c]);
+        }
+    }
+    for (int q = kPkPrefetch; q < Q; q++) {   // rows of more than 32 entries
+        int jj;
+        T aa;
+        m.get(base + 32 * q + lane, jj, aa);
+        if (jj >= 0) {
+            T xv[R];
+            load_row<T, R>(x + (size_t)jj * R, xv);
+#pragma unroll
+            for (int c = 0; c < R; c++) acc[c] = fma(aa, xv[c], acc[c]);
+        }
+    }
+#pragma unroll
+    for (int o = 2; o > 0; o >>= 1)
+#pragma unroll
+        for (int c = 0; c < R; c++) acc[c] += __shfl_xor_sync(kFull, acc[c], o, 4);
+    if (lead) {
+        if (kGs) {
+#pragma unroll
+            for (int c = 0; c < R; c++) x[(size_t)row * R + c] = xo[c] + (bv[c] - acc[c]) * d;
+        } else {
+#pragma unroll
+            for (int c = 0; c < R; c++) r[(size_t)row * R + c] = bv[c] - acc[c];
+        }
+    }
+}
+
+__global__ void pk_fill_kernel(int64_t total, const int *__restrict__ map, const int *__restrict__ col,
+                               const float *__restrict__ A32, const double *__restrict__ A64, int2 *__restrict__ e32,
+                               double *__restrict__ v64) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= total) return;
+    const int src = __ldg(map + k);
+    e32[k] = make_int2(__ldg(col + k), src >= 0 ? __float_as_int(__ldg(A32 + src)) : 0);
+    v64[k] = src >= 0 ? __ldg(A64 + src) : 0.0;
+}
+
+template <class T> PkMat<T> pk_mat(const DevLevel &L);
+template <> PkMat<float> pk_mat<float>(const DevLevel &L) { return PkMat<float>{L.pk_e32}; }
+template <> PkMat<double> pk_mat<double>(const DevLevel &L) { return PkMat<double>{L.pk_col, L.pk_v64}; }
+template <class T> const T *level_A(const DevLevel &L);
+template <> const float *level_A<float>(const DevLevel &L) { return L.A32; }
+template <> const double *level_A<double>(const DevLevel &L) { return L.A64; }
+
+template <class T, bool kGs>
+void launch_rows(const DevLevel &L, int g0, int g1, const T *dinv, const T *b, T *x, T *r, int R, int tpb,
+                 cudaStream_t s, Chain *ch) {
+    if (g1 <= g0) return;
+    tpb = std::max(32, std::min(512, tpb / 32 * 32));
+    const unsigned blocks = (unsigned)(((int64_t)(g1 - g0) * 32 + tpb - 1) / tpb);
+    auto k = R == 1 ? pk_row_kernel<T, 1, kGs> : R == 2 ? pk_row_kernel<T, 2, kGs> : pk_row_kernel<T, 4, kGs>;
+    klaunch(k, blocks, (unsigned)tpb, 0, s, ch, g0, g1, (const int2 *)L.pk_gq, (const int *)L.pk_rows, pk_mat<T>(L),
+            dinv, b, x, r);
+}
+
+}  // namespace
+
+bool packed_layout(const HostLevel &hl, std::vector<int32_t> &gq, std::vector<int32_t> &rows,
+                   std::vector<int32_t> &map, std::vector<int32_t> &col, int gs[10], int64_t *total) {
+    const int n = hl.ndof;
+    int rs[10];
+    for (int c = 0; c <= 8; c++) rs[c] = hl.colour_start[c];
+    rs[9] = n;
+    auto quads = [&](int i) { return (int)((hl.rp[i + 1] - hl.rp[i] + 3) / 4); };
+    gq.clear();
+    rows.clear();
+    int64_t base = 0;   // in units of 32 entries
+    std::vector<int> order;
+    for (int c = 0; c < 9; c++) {
+        gs[c] = (int)(gq.size() / 2);
+        // rows of the range by quad count, each count in the level's order (a stable counting sort)
+        const int r0 = rs[c], r1 = rs[c + 1];
+        int qmax = 0;
+        for (int i = r0; i < r1; i++) qmax = std::max(qmax, quads(i));
+        std::vector<int> cnt(qmax + 2, 0);
+        for (int i = r0; i < r1; i++) cnt[quads(i) + 1]++;
+        for (int q = 0; q <= qmax; q++) cnt[q + 1] += cnt[q];
+        order.assign(r1 - r0, 0);
+        for (int i = r0; i < r1; i++) order[cnt[quads(i)]++] = i;
+        for (size_t a = 0; a < order.size();) {
+            const int q = quads(order[a]);
+            size_t e = a;
+            while (e < order.size() && e < a + 8 && quads(order[e]) == q) e++;
+            gq.push_back((int32_t)base);
+            gq.push_back(q);
+            for (size_t s = a; s < a + 8; s++) rows.push_back(s < e ? order[s] : -1);
+            base += q;
+            a = e;
+        }
+    }
+    gs[9] = (int)(gq.size() / 2);
+    if (base * 32 >= ((int64_t)1 << 31)) return false;   // 32-bit entry positions in the value map
+    *total = base * 32;
+    map.assign((size_t)*total, -1);
+    col.assign((size_t)*total, -1);
+    const int ng = gs[9];
+#pragma omp parallel for schedule(dynamic, 1024)
+    for (int g = 0; g < ng; g++) {
+        const int64_t b0 = (int64_t)gq[2 * g] * 32;
+        const int q = gq[2 * g + 1];
+        for (int s = 0; s < 8; s++) {
+            const int row = rows[8 * (size_t)g + s];
+            if (row < 0) continue;
+            const int64_t k0 = hl.rp[row], len = hl.rp[row + 1] - k0;
+            for (int qq = 0; qq < q; qq++)
+                for (int l = 0; l < 4; l++) {
+                    const int k = 4 * qq + l;
+                    if (k >= len) continue;
+                    const int64_t pos = b0 + 32 * qq + 4 * s + l;
+                    map[pos] = (int32_t)(k0 + k);
+                    col[pos] = hl.ci[k0 + k];
+                }
+        }
+    }
+    return true;
+}
+
+void launch_packed_fill(const DevLevel &L, cudaStream_t s) {
+    if (!L.pk_map || L.pk_total == 0) return;
+    pk_fill_kernel<<<(unsigned)((L.pk_total + 255) / 256), 256, 0, s>>>(L.pk_total, L.pk_map, L.pk_col, L.A32, L.A64,
+                                                                        L.pk_e32, L.pk_v64);
+}
+
+template <class T>
+bool launch_packed_smooth(const DevLevel &L, int colour, const T *A, const T *dinv, const T *b, T *x, int R, int tpb,
+                          cudaStream_t s, Chain *ch) {
+    if (!L.pk_map || A != level_A<T>(L)) return false;
+    launch_rows<T, true>(L, L.pk_gs[colour], L.pk_gs[colour + 1], dinv, b, x, nullptr, R, tpb, s, ch);
+    return true;
+}
+
+template <class T>
+bool launch_packed_residual(const DevLevel &L, const T *A, const T *b, const T *x, T *r, int R, int nrows, int tpb,
+                            cudaStream_t s, Chain *ch) {
+    if (!L.pk_map || A != level_A<T>(L)) return false;
+    // the group ranges end exactly at the smoothed rows (ns) and at all rows (n)
+    int g1;
+    if (nrows == L.n) g1 = L.pk_gs[9];
+    else if (nrows == L.ns) g1 = L.pk_gs[8];
+    else return false;
+    launch_rows<T, false>(L, 0, g1, (const T *)nullptr, b, const_cast<T *>(x), r, R, tpb, s, ch);
+    return true;
+}
+
+template bool launch_packed_smooth<float>(const DevLevel &, int, const float *, const float *, const float *, float *,
+                                          int, int, cudaStream_t, Chain *);
+template bool launch_packed_smooth<double>(const DevLevel &, int, const double *, const double *, const double *,
+                                           double *, int, int, cudaStream_t, Chain *);
+template bool launch_packed_residual<float>(const DevLevel &, const float *, const float *, const float *, float *,
+                                            int, int, int, cudaStream_t, Chain *);
+template bool launch_packed_residual<double>(const DevLevel &, const double *, const double *, const double *,
+                                             double *, int, int, int, cudaStream_t, Chain *);
+
+}  // namespace lbmg

@@ -392,7 +392,8 @@ __global__ void __launch_bounds__(1024, 1) solve_persistent_kernel(PersistParams
         for (int m = 0; m < p.ninst; m++)
             for (int q = 0; q < p.nrhs; q++) {
                 const double r2 = __ldcg(p.norm + 16 * m + q), b2 = __ldcg(p.norm + 16 * m + 4 + q);
-                if (!(r2 <= p.tol2 * b2)) done = false;
+                // relative to ||b||; a zero right-hand side is judged by the absolute residual
+                if (!(r2 <= p.tol2 * (b2 > 0.0 ? b2 : 1.0))) done = false;
                 if (!(r2 <= 1e300) || r2 > 1e12 * __ldcg(p.norm + 16 * m + 8 + q) + 1e-300) bad = true;   // NaN, inf or growth by 1e6
             }
         if (bad) { if (b0 && threadIdx.x == 0) atomicExch(p.status, 2); break; }

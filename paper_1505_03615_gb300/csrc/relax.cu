@@ -166,6 +166,8 @@ void launch_smooth_colour(const DevLevel &L, int colour, const T *A, const T *di
     const int r0 = L.cs[colour], r1 = L.cs[colour + 1];
     if (r1 <= r0) return;
     const LaunchShape &sh = L.shape[sizeof(T) == 8][kShapeSmooth];
+    // four threads per row: the packed copy of the matrix (one 256-byte load per warp and quad)
+    if (sh.tpr == 4 && launch_packed_smooth<T>(L, colour, A, dinv, b, x, R, sh.tpb, s, ch)) return;
     const unsigned blocks = (unsigned)(((int64_t)(r1 - r0) * sh.tpr + sh.tpb - 1) / sh.tpb);
     const SmoothFn<T> k = R == 1 ? smooth_fn<T, 1>(sh.tpr) : R == 2 ? smooth_fn<T, 2>(sh.tpr) : smooth_fn<T, 4>(sh.tpr);
     klaunch(k, blocks, (unsigned)sh.tpb, 0, s, ch, r0, r1, L.rp, L.ci, A, dinv, b, x);
@@ -177,6 +179,7 @@ void launch_residual(const DevLevel &L, const T *A, const T *b, const T *x, T *r
     const int n = nrows < 0 ? L.n : nrows;
     if (n == 0) return;
     const LaunchShape &sh = L.shape[sizeof(T) == 8][kShapeResidual];
+    if (sh.tpr == 4 && launch_packed_residual<T>(L, A, b, x, r, R, n, sh.tpb, s, ch)) return;
     const unsigned blocks = (unsigned)(((int64_t)n * sh.tpr + sh.tpb - 1) / sh.tpb);
     const ResidualFn<T> k =
         R == 1 ? residual_fn<T, 1>(sh.tpr) : R == 2 ? residual_fn<T, 2>(sh.tpr) : residual_fn<T, 4>(sh.tpr);

@@ -95,7 +95,7 @@ def test_every_launch_shape_matches_reference_sweep_and_residual(knot, tpr, tpb)
         for d in range(d0 + 1, D + 1):
             for prec in (L.LBMG_FP64, L.LBMG_MIXED):
                 for kind in (0, 1):
-                    L.lbmg_set_launch_shape(h, d, prec, kind, 8, 256)
+                    L.lbmg_set_launch_shape(h, d, prec, kind, 4, 256)
 
 
 def test_invalid_launch_shapes_are_rejected(knot):
