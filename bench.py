@@ -5,10 +5,11 @@ level (A = M + t L), project the right-hand sides (vertex x, y, z), solve
 (M + t L) x = rhs with mixed-precision V-cycles to relative residual 1e-6 for
 all three right-hand sides, and evaluate the solution at the mesh vertices
 (one implicit mean-curvature-flow update, Section 5.3).  The hierarchy is built
-once before timing.  Default workload: (2,3) torus-knot tube, 200k triangles,
-depth 8, t = 1e-4.
+once before timing.  Default workload: (3,5) torus-knot tube of radius 0.02,
+4M triangles, depth 10, t = 1e-4.
 
-Prints one JSON line.  `--impl reference` times the FP64 CPU oracle instead.
+Prints one JSON line.  `--impl reference` times the FP64 CPU oracle instead, on a
+bounded stretch of the same mesh placed on the same grid.
 """
 from __future__ import annotations
 
@@ -29,7 +30,7 @@ import numpy as np
 
 METRIC = "unknowns×V-cycles/s; ms to 1e-6 rel. residual, mixed/learned vs plain FP64"
 UNIT = "unknowns*V-cycles/s"
-WORKLOAD = "knot23_200k_d8"
+WORKLOAD = "knot35_4m_d10"
 
 
 def _peaks():
@@ -115,16 +116,72 @@ def _dist():
     return ws, rank, local
 
 
-def run_oracle_sample(V, F, depth, t, f, cycles):
-    """Time `cycles` FP64 V-cycles (3 right-hand sides) of the oracle; returns (unknowns*cycles/s, seconds, n)."""
+# ---- the FP64 CPU oracle on a bounded sample of the workload ----
+# The oracle (plain C, one thread) would take hours to build the hierarchy of the whole
+# 4M-triangle mesh, so it runs on stretches of the same mesh: the first (or the i-th)
+# `ntri` triangles, a contiguous piece of the tube, embedded in the whole mesh's grid cube
+# so that its functions, stencils and levels are those of the workload.  The metric is
+# unknowns x V-cycles / s, which a stretch measures like the whole.
+SAMPLE_TRIS = 80_000
+SAMPLE_CYCLES = 400
+
+
+def oracle_stretch(V, F, ntri, index=0):
+    """Triangles [index * ntri, (index + 1) * ntri) of F with their vertices, renumbered."""
+    Fp = F[index * ntri:(index + 1) * ntri]
+    used = np.unique(Fp)
+    remap = np.full(V.shape[0], -1, dtype=np.int64)
+    remap[used] = np.arange(used.size)
+    return np.ascontiguousarray(V[used]), np.ascontiguousarray(remap[Fp], dtype=np.int32)
+
+
+def _oracle_cycles(job):
+    """One oracle sample: build the stretch's hierarchy, then time `cycles` FP64 V-cycles on
+    the x/y/z right-hand sides.  Runs in this process or in a spawned worker (no CUDA)."""
+    Vp, Fp, depth, min_depth, emb, t, cycles, barrier = job
     import oracle
-    h = oracle.Hierarchy(V, F, depth)
-    rhs = h.project_rhs(f)
+    h = oracle.Hierarchy(Vp, Fp, depth, min_depth=min_depth, embedding=emb)
+    rhs = h.project_rhs(Vp)
+    h.vcycles(t, rhs, cycles=1)
+    if barrier is not None:
+        barrier.wait()
     t0 = time.perf_counter()
     h.vcycles(t, rhs, cycles=cycles)
     dt = time.perf_counter() - t0
-    n = h.ndof(depth)
-    return n * rhs.shape[1] * cycles / dt, dt, n, h
+    return h.ndof(depth), dt
+
+
+_POOL_BARRIER = None
+
+
+def _pool_init(barrier):
+    global _POOL_BARRIER
+    _POOL_BARRIER = barrier
+
+
+def _pool_job(job):
+    return _oracle_cycles(job[:-1] + (_POOL_BARRIER,))
+
+
+def oracle_baseline(V, F, depth, min_depth, t, cores, ntri=SAMPLE_TRIS, cycles=SAMPLE_CYCLES):
+    """Oracle throughput in unknowns x V-cycles / s on `cores` host cores: one stretch per core,
+    each in its own spawned process (the oracle is single-threaded); the cycles of all of them
+    start together behind a barrier, and the job's time is the slowest one's."""
+    import multiprocessing as mp
+    import oracle
+    emb = oracle.embedding_of(V)
+    nstretch = max(1, F.shape[0] // ntri)
+    jobs = [oracle_stretch(V, F, ntri, i % nstretch) + (depth, min_depth, emb, t, cycles, None) for i in range(cores)]
+    if cores == 1:
+        n, dt = _oracle_cycles(jobs[0])
+        return n * 3 * cycles / dt, dt, [n]
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(cores)
+    with ctx.Pool(cores, initializer=_pool_init, initargs=(barrier,)) as pool:
+        res = pool.map(_pool_job, jobs)
+    units = sum(n * 3 * cycles for n, _ in res)
+    wall = max(dt for _, dt in res)
+    return units / wall, wall, [n for n, _ in res]
 
 
 def solve_bytes(h, sweeps, nrhs):
@@ -158,19 +215,19 @@ def solve_bytes(h, sweeps, nrhs):
 
 
 def reference_main(args):
-    """Reference arm: the FP64 CPU oracle as it stands, one core."""
+    """Reference arm: the FP64 CPU oracle as it stands (one core), on a stretch of the same
+    mesh on the same grid; each step is SAMPLE_CYCLES / 4 V-cycles on the x/y/z right-hand sides."""
     ws, rank, _ = _dist()
     if rank != 0:
         return
     import meshgen
     import oracle
-    V, F, depth, t, f, tol, _ = meshgen.config_mesh(WORKLOAD)
-    h = oracle.Hierarchy(V, F, depth)
-    rhs = h.project_rhs(f)
+    V, F, depth, t, f, tol, _ = meshgen.config_mesh(args.workload)
+    Vp, Fp = oracle_stretch(V, F, SAMPLE_TRIS)
+    h = oracle.Hierarchy(Vp, Fp, depth, min_depth=args.oracle_min_depth, embedding=oracle.embedding_of(V))
+    rhs = h.project_rhs(Vp)
     n = h.ndof(depth)
-    # each call also forms A and factors the oracle's dense coarsest level: enough cycles
-    # per step that the sample measures the cycles, not that setup
-    cyc = 10
+    cyc = SAMPLE_CYCLES // 4
     for _ in range(args.warmup):
         h.vcycles(t, rhs, cycles=1)
     times = []
@@ -180,12 +237,14 @@ def reference_main(args):
         times.append(time.perf_counter() - t0)
     total = sum(times)
     value = n * rhs.shape[1] * cyc * args.steps / total
-    sample = f"{cyc} FP64 lexicographic-GS V-cycles x 3 right-hand sides per step on the {WORKLOAD} hierarchy (n={n})"
+    sample = (f"{cyc} FP64 lexicographic-GS V-cycles x 3 right-hand sides per step on the first {Fp.shape[0]} "
+              f"triangles of the {args.workload} mesh, on its grid (depth {depth}, n={n}), one host core")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "unknowns": n * 3, "depth": depth, "t": t},
+        "config": {"workload": args.workload, "triangles": int(Fp.shape[0]), "depth": depth, "t": t,
+                   "sample_of": int(F.shape[0])},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -383,7 +442,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lbmg")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--oracle-cycles", type=int, default=60)
+    ap.add_argument("--oracle-min-depth", type=int, default=1,
+                    help="coarsest depth of the oracle's V-cycle on its sample (the library's on the default workload)")
     ap.add_argument("--persistent", action="store_true", help="one cooperative launch per solve")
     ap.add_argument("--no-graphs", action="store_true", help="launch each cycle's kernels directly (profilers)")
     ap.add_argument("--only-timed", action="store_true", help="stop after the timed steps (profiling runs)")
@@ -572,7 +632,10 @@ def main():
     if args.learned:
         learned = learned_compare(L, V, F, depth, t, f_dev, tol, nrhs, args, dev)
 
-    # roofline of the dominant kernel, timed live with CUDA events on its stream
+    # roofline of the dominant kernel (the finest-level Gauss-Seidel colour), timed live with
+    # CUDA events on its stream: the timed steps run each solve as one graph launch, whose
+    # conditional loop cannot hold event records, so the same step is replayed with the host
+    # stopping test (one graph per cycle, events around the finest pre- and post-smoothing)
     a_cnt, p_cnt, per_cycle, fixed = L.lbmg_launch_counts(h, L.LBMG_MIXED)
     opts = L.lbmg_default_options()
     sweeps = opts.nu1 + opts.nu2
@@ -582,16 +645,24 @@ def main():
         cyc_bytes, fixed_bytes = solve_bytes(h, sweeps, nrhs)
         launch_bytes = cyc_bytes * (cycles / args.steps) + fixed_bytes
         avg_launch_ms = solve_ms / args.steps
+        roof_cycles = cycles / args.steps
         kernel = f"solve_persistent_kernel<float,{R}> (whole mixed solve, one launch)"
         key = f"solve_persistent_{workload}"
     else:
-        # finest-level coloured Gauss-Seidel: events captured in the cycle graph around the
-        # finest pre- and post-smoothing (16 colour launches per cycle and their gaps)
-        launch_bytes = (nnz * 8 + n * (4 + 4 + 3 * R * 4)) / 8
-        avg_launch_ms = smooth_ms / max(cycles * sweeps * 8, 1)
-        kernel = f"smooth_colour_kernel<float,{R},{shapes[str(D)][0][0]}> (finest level, per colour, " \
-                 f"{shapes[str(D)][0][1]} threads/block)"
-        key = f"smooth_colour_{workload}"
+        L.lbmg_set_host_check(h, 1)
+        roof_smooth, roof_cycles = 0.0, 0
+        for _ in range(2):
+            st = step()
+            roof_smooth, roof_cycles = st.ms_fine_smooth, st.cycles
+        L.lbmg_set_host_check(h, 0)
+        # algorithmic bytes per colour launch (one eighth of a sweep): nnz (4 B value + 4 B
+        # column) + n nrhs (4 B right-hand side + 4 B x read + 4 B x write)
+        launch_bytes = (nnz * 8 + n * nrhs * 12) / 8
+        avg_launch_ms = roof_smooth / max(roof_cycles * sweeps * 8, 1)
+        tpr, tpb = shapes[str(D)][0]
+        kname = "pk_row_kernel" if tpr == 4 else "smooth_colour_kernel"
+        kernel = f"{kname}<float,{R},GS> (finest level, one colour, {tpr} threads per row, {tpb} threads/block)"
+        key = f"{kname}_gs_{workload}"
     achieved = launch_bytes / (avg_launch_ms * 1e-3) / 1e9 if avg_launch_ms > 0 else 0.0
     traffic = None
     try:
@@ -606,19 +677,24 @@ def main():
         pass
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": kernel, "peak_kind": peak_kind, "bytes_per_launch": launch_bytes,
-                "avg_launch_ms": avg_launch_ms, "fine_smooth_ms_per_step": smooth_ms / args.steps,
+                "avg_launch_ms": avg_launch_ms,
+                "timing": "CUDA events in the per-cycle graph around the finest smoothing of a replayed step "
+                          f"({roof_cycles} cycles x {sweeps} sweeps x 8 colour launches and their gaps)",
                 "solve_ms_per_step": solve_ms / args.steps}
 
     gpu_launches = args.steps * (a_cnt + p_cnt + fixed + 1) + cycles * per_cycle
 
     cpu_baseline = None
-    # the oracle's hierarchy of the larger workloads takes minutes to build: its baseline is
-    # measured on the metric's own workload only
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline and workload == WORKLOAD:
-        val, dt, n_o, _ = run_oracle_sample(V, F, depth, t, f, args.oracle_cycles)
-        cpu_baseline = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                        "sample": f"{args.oracle_cycles} FP64 lexicographic-GS V-cycles x 3 right-hand sides on the "
-                                  f"same mesh (oracle hierarchy, n={n_o}), {dt:.1f} s on one host core"}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        v1, dt1, n1 = oracle_baseline(V, F, depth, d0, t, 1)
+        vp, dtp, npc = oracle_baseline(V, F, depth, d0, t, cores)
+        cpu_baseline = {"value": vp, "unit": UNIT, "cores": cores, "kind": "oracle",
+                        "sample": f"{SAMPLE_CYCLES} FP64 lexicographic-GS V-cycles x 3 right-hand sides per core, "
+                                  f"each core on its own stretch of {SAMPLE_TRIS} consecutive triangles of the same "
+                                  f"mesh on its grid (depth {depth}, coarsest depth {d0}, about {int(np.mean(npc))} "
+                                  f"finest functions each), spawned processes started together; {dtp:.1f} s",
+                        "single_core": {"value": v1, "cores": 1, "seconds": dt1, "finest_functions": n1[0]}}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -628,7 +704,8 @@ def main():
                        "dofs_finest": n, "nnz_finest": nnz, "fragments_finest": nfrag, "nrhs": nrhs, "t": t,
                        "tol": tol, "precision": "mixed", "l2": "inputs larger than L2 (assembly streams >0.5 GB/step)",
                        "parallelism": "replicas" if ws > 1 else "single",
-                       "solve": "persistent" if args.persistent else "graph per cycle",
+                       "solve": ("persistent (one cooperative launch)" if args.persistent else
+                                 "one graph launch per solve (conditional loop, device stopping test)"),
                        "dependent_launch": not args.no_pdl and not args.persistent,
                        "launch_shapes_mixed": {d: {"sweep": list(v[0]), "residual": list(v[1])}
                                                for d, v in shapes.items()},

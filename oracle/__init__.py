@@ -75,6 +75,14 @@ def _load():
     return lib
 
 
+def embedding_of(V):
+    """The default embedding (reading A5): cube side 1.1 x the largest extent of the bounding
+    box, centred on it; returns (S, centre) for Hierarchy(..., embedding=...)."""
+    V = np.asarray(V, dtype=np.float64)
+    mn, mx = V.min(axis=0), V.max(axis=0)
+    return 1.1 * float((mx - mn).max()), 0.5 * (mn + mx)
+
+
 def _ptr(a):
     return a.ctypes.data_as(C.c_void_p) if a is not None else None
 
