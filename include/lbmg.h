@@ -157,6 +157,9 @@ int lbmg_instances(lbmg_handle h, int *ninst);
    finest-level vectors and of its vertices in vertex arrays */
 int lbmg_instance_info(lbmg_handle h, int inst, int *depth, int *min_depth, long *nfine, long *row_offset,
                        long *vertex_offset);
+/* inst int[n_d]: the mesh of every row of level d, in the device dof order (all 0 for a
+   single mesh).  Host only. */
+int lbmg_row_instances(lbmg_handle h, int d, int *inst);
 /* relative residual ||rhs - A x|| / ||rhs|| of every mesh and right-hand side after the last
    persistent solve, rel[ninst][nrhs] (host) */
 int lbmg_instance_residuals(lbmg_handle h, int nrhs, double *rel);

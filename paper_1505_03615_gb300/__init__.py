@@ -21,7 +21,7 @@ __all__ = [
     "lbmg_assemble", "lbmg_set_area_weights", "lbmg_project_rhs", "lbmg_solve", "lbmg_vcycles", "lbmg_residual", "lbmg_smooth",
     "lbmg_restrict", "lbmg_prolong_add", "lbmg_eval_vertices", "lbmg_get_dofs", "lbmg_get_matrix",
     "lbmg_get_prolongation", "lbmg_launch_counts", "lbmg_build_batch", "lbmg_instances", "lbmg_instance_info",
-    "lbmg_instance_residuals", "lbmg_learned_nparams", "lbmg_learned_params", "lbmg_learned_collect",
+    "lbmg_instance_residuals", "lbmg_row_instances", "lbmg_learned_nparams", "lbmg_learned_params", "lbmg_learned_collect",
     "lbmg_learned_loss_grad", "lbmg_learned_train", "lbmg_learned_enable", "lbmg_learned_omega",
     "lbmg_residual_norms_noalloc", "lbmg_status_string", "lbmg_last_cuda_error", "lbmg_default_options",
     "lbmg_solve_pcg", "lbmg_autotune", "lbmg_launch_shape", "lbmg_tuned_times", "lbmg_set_launch_shape", "lbmg_set_host_check", "lbmg_tune_cache_save", "lbmg_tune_cache_load",
@@ -111,6 +111,7 @@ def load_library():
         "lbmg_instances": (i, [P, P]),
         "lbmg_instance_info": (i, [P, i, P, P, P, P, P]),
         "lbmg_instance_residuals": (i, [P, i, P]),
+        "lbmg_row_instances": (i, [P, i, P]),
         "lbmg_learned_nparams": (i, []),
         "lbmg_learned_params": (i, [P, P, P, P]),
         "lbmg_learned_collect": (i, [P, P, i, i, i, P]),
@@ -251,6 +252,14 @@ def lbmg_instance_residuals(h, nrhs):
     out = np.zeros((n, nrhs))
     _check(load_library().lbmg_instance_residuals(h, int(nrhs), _ptr(out)), "lbmg_instance_residuals")
     return out
+
+
+def lbmg_row_instances(h, d):
+    """The mesh of every row of level d (device dof order)."""
+    n, _, _ = lbmg_level_info(h, d)
+    inst = np.zeros(n, np.int32)
+    _check(load_library().lbmg_row_instances(h, int(d), _ptr(inst)), "lbmg_row_instances")
+    return inst
 
 
 def lbmg_learned_nparams():

@@ -958,6 +958,14 @@ int lbmg_instance_info(lbmg_handle h, int inst, int *depth, int *min_depth, long
     return LBMG_OK;
 }
 
+int lbmg_row_instances(lbmg_handle h, int d, int *inst) {
+    LBMG_TRY(check_level(h, d));
+    if (!inst) return LBMG_INVALID_ARG;
+    const HostLevel &hl = h->c.host.lev[d];
+    for (int i = 0; i < hl.ndof; i++) inst[i] = hl.inst.empty() ? 0 : hl.inst[i];
+    return LBMG_OK;
+}
+
 int lbmg_instance_residuals(lbmg_handle h, int nrhs, double *rel) {
     if (!h || !rel || nrhs < 1 || nrhs > 4) return LBMG_INVALID_ARG;
     if (h->inst_norm_host.size() != 16 * (size_t)h->c.ninst) return LBMG_NOT_ASSEMBLED;
