@@ -22,7 +22,9 @@ __all__ = [
     "torus",
     "torus_knot_tube",
     "double_sheet",
+    "cube_grid",
     "batch_mix",
+    "random_start",
     "sphere_harmonic_rhs",
     "uniform_rhs",
     "coordinate_rhs",
@@ -180,6 +182,59 @@ def double_sheet(n=500, amplitude=0.05, depth=9, offset_voxels=0.5, jitter=1e-6,
     F = np.concatenate([F1, F1 + V1.shape[0]]).astype(np.int32)
     V = _jitter(V, jitter, rng)
     return np.ascontiguousarray(V), np.ascontiguousarray(F)
+
+
+def cube_grid(n=6, size=1.0, gap=1.0, subdiv=4, jitter=1e-6, seed=8):
+    """n x n x n axis-aligned cubes of side `size`, `gap` apart along every axis (the model of
+    equidistantly spaced unit cubes of the convergence experiment, Section 5.2).
+
+    Each cube is a closed surface whose faces are subdiv x subdiv grids of quads, two
+    triangles per quad, oriented outwards (12 subdiv^2 triangles per cube).  Every vertex
+    is then perturbed by U(-jitter, jitter).
+    """
+    s = int(subdiv)
+    idx = {}
+    Vc = []
+    for i in range(s + 1):
+        for j in range(s + 1):
+            for k in range(s + 1):
+                if min(i, j, k) == 0 or max(i, j, k) == s:
+                    idx[(i, j, k)] = len(Vc)
+                    Vc.append((i, j, k))
+    Vc = np.asarray(Vc, dtype=np.float64) * (size / s)
+    Fc = []
+    for axis in range(3):
+        a1, a2 = [a for a in range(3) if a != axis]
+        for side in (0, s):
+            normal = np.zeros(3)
+            normal[axis] = 1.0 if side == s else -1.0
+            for u in range(s):
+                for v in range(s):
+                    def key(du, dv):
+                        c = [0, 0, 0]
+                        c[axis], c[a1], c[a2] = side, u + du, v + dv
+                        return idx[tuple(c)]
+                    q = (key(0, 0), key(1, 0), key(1, 1), key(0, 1))
+                    for tri in ((q[0], q[1], q[2]), (q[0], q[2], q[3])):
+                        A, B, C = Vc[list(tri)]
+                        if np.cross(B - A, C - A) @ normal < 0:
+                            tri = (tri[0], tri[2], tri[1])
+                        Fc.append(tri)
+    Fc = np.asarray(Fc, dtype=np.int64)
+    Vs, Fs = [], []
+    pitch = size + gap
+    for i in range(n):
+        for j in range(n):
+            for k in range(n):
+                Fs.append(Fc + len(Vs) * Vc.shape[0])
+                Vs.append(Vc + pitch * np.array([i, j, k], dtype=np.float64))
+    V = _jitter(np.concatenate(Vs), jitter, _rng(seed))
+    return np.ascontiguousarray(V), np.ascontiguousarray(np.concatenate(Fs), dtype=np.int32)
+
+
+def random_start(n, ncols=1, seed=9):
+    """Initial coefficients drawn from U[0, 1] (the random initial guess of Section 5.2)."""
+    return np.ascontiguousarray(_rng(seed).uniform(0.0, 1.0, size=(n, ncols)))
 
 
 def batch_mix(count=64, min_tris=10_000, max_tris=300_000, seed=7):

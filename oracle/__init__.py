@@ -66,6 +66,7 @@ def _load():
         "orc_eval_vertices": (None, [P, P, i, P]),
         "orc_solve": (i, [P, d, P, P, i, d, i, i, i, P]),
         "orc_vcycles": (i, [P, d, P, P, i, i, i, i]),
+        "orc_cycles": (i, [P, d, P, P, i, i, i, i, i, i, i]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -281,4 +282,21 @@ class Hierarchy:
                                    int(nu1), int(nu2))
         if rc != 0:
             raise RuntimeError("oracle: coarse Cholesky failed")
+        return x
+
+    def cycles(self, t, rhs, x0=None, cycles=1, nu1=2, nu2=2, gamma=1, coloured=False, coarse_smooth=False):
+        """Exactly `cycles` multigrid cycles (Section 4.3) per right-hand side on (M + t L) x = rhs:
+        gamma 1 = V-cycle, 2 = W-cycle; coloured Gauss-Seidel (colours 0..7 down, 7..0 up, the
+        order of the GPU cycle) or lexicographic; the coarsest level solved directly or, with
+        coarse_smooth, relaxed by nu1 + nu2 sweeps (the min-depth experiment of Section 5.2)."""
+        rhs = np.ascontiguousarray(rhs, dtype=np.float64)
+        if rhs.ndim == 1:
+            rhs = rhs[:, None]
+        x = np.zeros_like(rhs) if x0 is None else np.ascontiguousarray(x0, dtype=np.float64).copy()
+        if x.ndim == 1:
+            x = x[:, None]
+        rc = self._lib.orc_cycles(self._h, float(t), _ptr(rhs), _ptr(x), rhs.shape[1], int(cycles), int(nu1),
+                                  int(nu2), int(gamma), int(bool(coloured)), int(bool(coarse_smooth)))
+        if rc != 0:
+            raise RuntimeError("oracle: bad cycle options or coarse Cholesky failed")
         return x

@@ -23,7 +23,11 @@
  *   - the right-hand side int f b_i for f linear on each triangle (Section 5.2);
  *   - a multigrid V-cycle with lexicographic Gauss-Seidel smoothing
  *     (Sections 4.3 and 5.2) and a dense Cholesky solve on the coarsest grid
- *     with the eps*Id regularisation of the Discussion in Section 5.
+ *     with the eps*Id regularisation of the Discussion in Section 5;
+ *   - general cycles (orc_cycles): V or W (two coarse visits per level, the
+ *     cycle of the convergence experiment of Section 5.2), Gauss-Seidel by
+ *     corner-parity colour or lexicographic, the coarsest grid solved or
+ *     relaxed like the others (the minimum-depth sweep of Section 5.2).
  *
  * Readings where the paper is silent or inconsistent (each also listed in
  * the design notes):
@@ -42,7 +46,11 @@
  *     area;
  *   - fragments of area at most 1e-12 finest voxel faces are ignored;
  *   - dof order: lexicographic corner index, then the smallest triangle id of
- *     the component.
+ *     the component;
+ *   - smoothing order (left open by the paper): lexicographic by default; the
+ *     coloured order of orc_cycles (colours 0..7 on the way down, 7..0 on the
+ *     way up) relaxes no row whose diagonal is not above 1e-20 of the level's
+ *     mean diagonal, as the GPU smoother does.
  */
 #define _DEFAULT_SOURCE
 #include <math.h>
@@ -1010,7 +1018,88 @@ typedef struct {
     SysLevel sys[ORC_MAXD + 1];
     double *r[ORC_MAXD + 1], *bc[ORC_MAXD + 1], *xc[ORC_MAXD + 1];
     int nu1, nu2;
+    /* options of orc_cycles: coarse-grid visits per level (1 V-cycle, 2 W-cycle), colour-ordered
+       smoothing, and relaxation instead of the direct solve at the coarsest level */
+    int gamma, coloured, coarse_smooth;
+    int *order[ORC_MAXD + 1];       /* rows by corner-parity colour (coloured smoothing) */
+    double floor_d[ORC_MAXD + 1];   /* diagonals at or below this are not relaxed (coloured smoothing) */
 } MG;
+
+/* Gauss-Seidel over the rows in the order given by `order` (reversed when backward).
+   Rows whose diagonal is not above `floor` are left unchanged. */
+static void gs_sweep_ordered(const SysLevel *A, const int *order, double floor, const double *b, double *x,
+                             int backward) {
+    for (int q = 0; q < A->n; q++) {
+        int i = order[backward ? A->n - 1 - q : q];
+        double s = b[i], diag = 0.0;
+        for (int k = A->rp[i]; k < A->rp[i + 1]; k++) {
+            int j = A->ci[k];
+            if (j == i) diag = A->a[k]; else s -= A->a[k] * x[j];
+        }
+        if (diag > floor) x[i] = s / diag;
+    }
+}
+
+/* the order of coloured smoothing: rows by the parity class (k mod 2)^3 of their corner, colour
+   c = kx%2 + 2 (ky%2) + 4 (kz%2), within a class by index (rows of one class never couple, so
+   any order inside a class gives the same sweep); and the diagonal floor of reading A17 */
+static void colour_order(const orc_hier *h, int d, const SysLevel *A, int **out, double *floor_out) {
+    const Level *lv = &h->lev[d];
+    int *ord = xmalloc(sizeof(int) * (size_t)(lv->ndof + 1));
+    int pos = 0;
+    for (int c = 0; c < 8; c++)
+        for (int i = 0; i < lv->ndof; i++) {
+            const int *k = lv->dcorner + 3 * (size_t)i;
+            if ((k[0] & 1) + 2 * (k[1] & 1) + 4 * (k[2] & 1) == c) ord[pos++] = i;
+        }
+    double tr = 0.0;
+    for (int i = 0; i < A->n; i++)
+        for (int k = A->rp[i]; k < A->rp[i + 1]; k++)
+            if (A->ci[k] == i) tr += A->a[k];
+    /* a diagonal not above 1e-20 of the level's mean (or not positive) is not relaxed (A17) */
+    double fl = 1e-20 * tr / (A->n > 0 ? A->n : 1);
+    *out = ord;
+    *floor_out = fl > 0.0 ? fl : 0.0;
+}
+
+static void smooth(MG *mg, int d, const double *b, double *x, int sweeps, int backward) {
+    SysLevel *A = &mg->sys[d];
+    for (int s = 0; s < sweeps; s++) {
+        if (mg->coloured) gs_sweep_ordered(A, mg->order[d], mg->floor_d[d], b, x, backward);
+        else gs_sweep(A, b, x, backward);
+    }
+}
+
+/* One multigrid cycle on A_d x = b (Section 4.3): nu1 sweeps, the residual restricted by P^T,
+   gamma visits of the next coarser level on the correction (gamma = 1: V-cycle, 2: W-cycle),
+   the correction prolonged by P and added, nu2 sweeps in the reverse order.  The coarsest level
+   is solved directly, or (coarse_smooth) relaxed by nu1 forward and nu2 backward sweeps. */
+static void mg_cycle(MG *mg, int d, const double *b, double *x) {
+    const orc_hier *h = mg->h;
+    SysLevel *A = &mg->sys[d];
+    if (d == h->d0) {
+        if (mg->coarse_smooth) {
+            smooth(mg, d, b, x, mg->nu1, 0);
+            smooth(mg, d, b, x, mg->nu2, 1);
+        } else {
+            cholesky_solve(A, b, x);
+        }
+        return;
+    }
+    smooth(mg, d, b, x, mg->nu1, 0);
+    residual(A, b, x, mg->r[d]);
+    const Level *lv = &h->lev[d];
+    int nc = h->lev[d - 1].ndof;
+    double *bc = mg->bc[d - 1], *xc = mg->xc[d - 1];
+    memset(bc, 0, sizeof(double) * (size_t)nc);
+    memset(xc, 0, sizeof(double) * (size_t)nc);
+    for (int i = 0; i < lv->ndof; i++)                    /* restriction: P^T r */
+        for (int k = lv->prp[i]; k < lv->prp[i + 1]; k++) bc[lv->pci[k]] += lv->pv[k] * mg->r[d][i];
+    for (int g = 0; g < mg->gamma; g++) mg_cycle(mg, d - 1, bc, xc);
+    for (int i = 0; i < lv->ndof; i++)                    /* prolongation: x += P xc */
+        for (int k = lv->prp[i]; k < lv->prp[i + 1]; k++) x[i] += lv->pv[k] * xc[lv->pci[k]];
+    smooth(mg, d, b, x, mg->nu2, 1);
+}
 
 static void vcycle(MG *mg, int d, const double *b, double *x) {
     const orc_hier *h = mg->h;
@@ -1111,4 +1200,42 @@ int orc_vcycles(const orc_hier *h, double t, const double *rhs, double *x, int n
         free(mg.sys[d].a); free(mg.sys[d].chol); free(mg.r[d]); free(mg.bc[d]); free(mg.xc[d]);
     }
     return rc;
+}
+
+/* Exactly `cycles` multigrid cycles per right-hand side from the given x (no stopping test):
+   gamma = 1 V-cycles, 2 W-cycles; coloured = 1 smooths colour by colour (colours 0..7 forward,
+   7..0 backward) with the diagonal floor of reading A17, 0 lexicographically; coarse_smooth = 1
+   relaxes the coarsest level instead of solving it.  Returns 0, or -1 if the coarse factor
+   failed or an option is out of range. */
+int orc_cycles(const orc_hier *h, double t, const double *rhs, double *x, int nrhs, int cycles, int nu1, int nu2,
+               int gamma, int coloured, int coarse_smooth) {
+    if (gamma < 1 || gamma > 2 || nu1 < 0 || nu2 < 0 || cycles < 0) return -1;
+    MG mg;
+    memset(&mg, 0, sizeof mg);
+    mg.h = h; mg.nu1 = nu1; mg.nu2 = nu2;
+    mg.gamma = gamma; mg.coloured = coloured != 0; mg.coarse_smooth = coarse_smooth != 0;
+    for (int d = h->d0; d <= h->D; d++) {
+        const Level *lv = &h->lev[d];
+        SysLevel *S = &mg.sys[d];
+        S->n = lv->ndof; S->rp = lv->rp; S->ci = lv->ci;
+        S->a = xmalloc(sizeof(double) * (size_t)(lv->nnz ? lv->nnz : 1));
+        for (long k = 0; k < lv->nnz; k++) S->a[k] = lv->M[k] + t * lv->L[k];
+        mg.r[d] = xmalloc(sizeof(double) * (size_t)(lv->ndof + 1));
+        mg.bc[d] = xmalloc(sizeof(double) * (size_t)(lv->ndof + 1));
+        mg.xc[d] = xmalloc(sizeof(double) * (size_t)(lv->ndof + 1));
+        if (mg.coloured) colour_order(h, d, S, &mg.order[d], &mg.floor_d[d]);
+    }
+    int rc = mg.coarse_smooth ? 0 : dense_cholesky(&mg.sys[h->d0]);
+    int n = h->lev[h->D].ndof;
+    double *b = xmalloc(sizeof(double) * (size_t)(n + 1)), *xx = xmalloc(sizeof(double) * (size_t)(n + 1));
+    for (int q = 0; q < nrhs && rc == 0; q++) {
+        for (int i = 0; i < n; i++) { b[i] = rhs[(size_t)i * nrhs + q]; xx[i] = x[(size_t)i * nrhs + q]; }
+        for (int c = 0; c < cycles; c++) mg_cycle(&mg, h->D, b, xx);
+        for (int i = 0; i < n; i++) x[(size_t)i * nrhs + q] = xx[i];
+    }
+    free(b); free(xx);
+    for (int d = h->d0; d <= h->D; d++) {
+        free(mg.sys[d].a); free(mg.sys[d].chol); free(mg.r[d]); free(mg.bc[d]); free(mg.xc[d]); free(mg.order[d]);
+    }
+    return rc == 0 ? 0 : -1;
 }
