@@ -308,6 +308,80 @@ def learned_compare(L, V, F, depth, t, f_dev, tol, nrhs, args, dev):
 
 
 BATCH = "batch64"
+CUBES = "cube_mindepth"
+
+
+def _dof_perm(c, mt, oc, om, nt):
+    """oracle index of every library function: both identify a function by its grid corner and
+    the smallest triangle of its component"""
+    def keys(cc, mm):
+        cc = cc.astype(np.int64)
+        return ((cc[:, 0] * 8192 + cc[:, 1]) * 8192 + cc[:, 2]) * (nt + 1) + mm.astype(np.int64)
+    kl, ko = keys(c, mt), keys(oc, om)
+    order = np.argsort(ko)
+    perm = order[np.minimum(np.searchsorted(ko[order], kl), len(ko) - 1)]
+    if not np.array_equal(ko[perm], kl):
+        raise RuntimeError("library and oracle functions differ")
+    return perm
+
+
+def cube_main(args):
+    """The minimum-depth experiment of Section 5.2 on the 6x6x6 grid of unit cubes one unit apart
+    (depth 5, screening weight alpha = 0.01, i.e. A = M + L / alpha): one W-cycle with ten
+    Gauss-Seidel sweeps per level from a U[0, 1] start, right-hand side 0, the coarsest level
+    relaxed, for every minimum depth 0..5 in the split and the unsplit space.  Prints the
+    residual alpha ||A x_1|| / ||x_0|| of the GPU and of the oracle (the same coloured cycle) and
+    the GPU time of the cycle."""
+    import torch
+
+    import meshgen
+    import oracle
+    import paper_1505_03615_gb300 as L
+    dev = torch.device("cuda", 0)
+    alpha = 0.01
+    t = 1.0 / alpha
+    V, F = meshgen.cube_grid(6, 1.0, 1.0, 2)
+    rows = []
+    for split in (True, False):
+        for m in range(6):
+            h = L.lbmg_build_hierarchy(V, F, 5, min_depth=m, split=int(split), cycle=1, coarse_smooth=1, nu1=10,
+                                       nu2=10)
+            try:
+                L.lbmg_assemble(h, t)
+                n = L.lbmg_level_info(h, 5)[0]
+                x0 = meshgen.random_start(n, 1)
+                zero = torch.zeros((n, 1), dtype=torch.float64, device=dev)
+                x = torch.tensor(x0, device=dev)
+                L.lbmg_vcycles(h, zero, x, 1, L.LBMG_FP64)   # warm-up (graph capture)
+                x = torch.tensor(x0, device=dev)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                L.lbmg_vcycles(h, zero, x, 1, L.LBMG_FP64)
+                e1.record()
+                torch.cuda.synchronize()
+                r = torch.zeros_like(x)
+                L.lbmg_residual(h, 5, zero, x, r)
+                gpu = alpha * float(torch.linalg.norm(r)) / float(np.linalg.norm(x0))
+                o = oracle.Hierarchy(V, F, 5, min_depth=m, split=split)
+                c, mt = L.lbmg_get_dofs(h, 5)
+                oc, om = o.dofs(5)
+                perm = _dof_perm(c, mt, oc, om, F.shape[0])
+                xo0 = np.zeros_like(x0)
+                xo0[perm] = x0
+                Mo, Lo = o.matrices(5)
+                xo = o.cycles(t, np.zeros_like(x0), xo0, cycles=1, nu1=10, nu2=10, gamma=2, coloured=True,
+                              coarse_smooth=True)
+                orc = alpha * float(np.linalg.norm((Mo + t * Lo) @ xo)) / float(np.linalg.norm(x0))
+                rows.append({"split": split, "min_depth": m, "residual_gpu": gpu, "residual_oracle": orc,
+                             "functions_per_level": [L.lbmg_level_info(h, d)[0] for d in range(m, 6)],
+                             "w_cycle_ms": e0.elapsed_time(e1)})
+            finally:
+                L.lbmg_destroy(h)
+    print(json.dumps({"workload": CUBES, "triangles": int(F.shape[0]), "depth": 5, "alpha": alpha,
+                      "cycle": "one W(10,10), coarsest level relaxed, right-hand side 0, start U[0,1]",
+                      "residual": "alpha ||A x1|| / ||x0||", "rows": rows}), flush=True)
+
 
 
 def batch_main(args):
@@ -462,6 +536,8 @@ def main():
                     help="named synthetic workload (meshgen.CONFIGS); the default is the metric's own configuration")
     ap.add_argument("--tune-cache", default=None,
                     help="tuning cache file: loaded before tuning (matching levels are not timed), saved after")
+    ap.add_argument("--cycle", default="v", choices=["v", "w"], help="V-cycle (default) or W-cycle")
+    ap.add_argument("--nu", type=int, default=2, help="smoothing sweeps before and after the coarse correction")
     ap.add_argument("--force-shape", default=None,
                     help="TPR,TPB: after tuning, set the finest level's mixed-precision sweep and residual launch "
                          "shape (profiling runs)")
@@ -472,6 +548,8 @@ def main():
         return reference_main(args)
     if args.workload == BATCH:
         return batch_main(args)
+    if args.workload == CUBES:
+        return cube_main(args)
 
     import torch
 
@@ -490,7 +568,7 @@ def main():
     nv = V.shape[0]
     t_build = time.perf_counter()
     h = L.lbmg_build_hierarchy(V, F, depth, persistent=int(args.persistent), use_graphs=int(not args.no_graphs),
-                               pdl=int(not args.no_pdl))
+                               pdl=int(not args.no_pdl), cycle=int(args.cycle == "w"), nu1=args.nu, nu2=args.nu)
     t_build = time.perf_counter() - t_build
     d0, D = L.lbmg_levels(h)
     n, nnz, nfrag = L.lbmg_level_info(h, D)
@@ -703,6 +781,7 @@ def main():
             "config": {"workload": workload, "triangles": int(F.shape[0]), "depth": depth, "min_depth": d0,
                        "dofs_finest": n, "nnz_finest": nnz, "fragments_finest": nfrag, "nrhs": nrhs, "t": t,
                        "tol": tol, "precision": "mixed", "l2": "inputs larger than L2 (assembly streams >0.5 GB/step)",
+                       "cycle": f"{args.cycle.upper()}({args.nu},{args.nu})",
                        "parallelism": "replicas" if ws > 1 else "single",
                        "solve": ("persistent (one cooperative launch)" if args.persistent else
                                  "one graph launch per solve (conditional loop, device stopping test)"),

@@ -91,6 +91,13 @@ typedef struct lbmg_options {
                            the host synchronizes once, at the end; 1 launches one graph per iteration
                            and reads the norms back after each one (the only mode in which
                            lbmg_stats.ms_fine_smooth is measured) */
+    int cycle;          /* 0 (default): V-cycle; 1: W-cycle, two visits of each coarser level per cycle
+                           (the cycle of the convergence experiment of Section 5.2).  Single meshes,
+                           not with persistent (LBMG_INVALID_ARG) */
+    int coarse_smooth;  /* 0 (default): the coarsest level is solved with its dense factor; 1: it is
+                           relaxed by nu1 + nu2 coloured Gauss-Seidel sweeps like the other levels (the
+                           minimum-depth sweep of Section 5.2, where the minimum depth is the coarsest
+                           level a cycle visits).  Single meshes, not with persistent */
 } lbmg_options;
 
 typedef struct lbmg_stats {

@@ -58,7 +58,8 @@ class Options(C.Structure):
                 ("smoother", C.c_int), ("jacobi_omega", C.c_double), ("split", C.c_int), ("threads", C.c_int),
                 ("persistent", C.c_int), ("narrow_max", C.c_int), ("barrier_phantoms", C.c_int),
                 ("use_graphs", C.c_int), ("pdl", C.c_int), ("copy_phantom_bytes", C.c_int),
-                ("host_alloc_fail", C.c_int), ("host_check", C.c_int)]
+                ("host_alloc_fail", C.c_int), ("host_check", C.c_int), ("cycle", C.c_int),
+                ("coarse_smooth", C.c_int)]
 
 
 class Stats(C.Structure):

@@ -301,6 +301,44 @@ void enqueue_vcycle(Ctx &c, int R, cudaStream_t s, bool timed, Chain *ch, int to
     }
 }
 
+// The general multigrid cycle of Section 4.3, level by level: nu1 sweeps, residual,
+// restriction (which zeroes the coarse correction), gamma visits of the next coarser level
+// (gamma = 2: the W-cycle of the convergence experiment of Section 5.2), prolongation and nu2
+// sweeps in the reverse colour order.  The coarsest level is solved by the dense factor, or
+// (coarse_smooth) relaxed by nu1 + nu2 sweeps like the others.  Used for the W-cycle and for
+// the relaxed coarsest level; the plain V-cycle with a solved coarsest level takes
+// enqueue_vcycle and its one-block bottom.
+template <class T>
+void enqueue_cycle_level(Ctx &c, int d, int R, cudaStream_t s, Chain *ch) {
+    DevLevel &L = c.lev[d];
+    if (d == c.d0) {
+        if (c.coarse_smooth) {
+            DevLevel L0 = L;   // the coarsest level's rows, smoothed by colour like any level
+            for (int q = 0; q < 9; q++) L0.cs[q] = L0.cs_all[q];
+            L0.ns = L0.n;
+            enqueue_smooth<T>(c, L0, R, c.nu1, true, s, ch);
+            enqueue_smooth<T>(c, L0, R, c.nu2, false, s, ch);
+        } else {
+            launch_coarse_apply<T>(c, L, P<T>::inv(c), P<T>::b(L), P<T>::x(L), R, s, ch);
+        }
+        return;
+    }
+    DevLevel &Lc = c.lev[d - 1];
+    enqueue_smooth<T>(c, L, R, c.nu1, true, s, ch);
+    launch_residual<T>(L, P<T>::A(L), P<T>::b(L), P<T>::x(L), P<T>::r(L), R, s, L.ns, ch);
+    launch_restrict<T>(Lc, P<T>::r(L), P<T>::b(Lc), R, s, P<T>::x(Lc), ch);
+    for (int g = 0; g < c.gamma; g++) enqueue_cycle_level<T>(c, d - 1, R, s, ch);
+    launch_prolong_add<T>(L, P<T>::x(Lc), P<T>::x(L), R, s, ch);
+    enqueue_smooth<T>(c, L, R, c.nu2, false, s, ch);
+}
+
+// one cycle on A e = b at the finest level, e zero on entry
+template <class T>
+void enqueue_cycle(Ctx &c, int R, cudaStream_t s, bool timed, Chain *ch) {
+    if (c.gamma == 1 && !c.coarse_smooth) enqueue_vcycle<T>(c, R, s, timed, ch);
+    else enqueue_cycle_level<T>(c, c.D, R, s, ch);
+}
+
 Chain make_chain(const Ctx &c, cudaStream_t s) {
     Chain ch;
     // the legacy and per-thread default streams take no programmatic serialization
@@ -318,12 +356,12 @@ void enqueue_iteration(Ctx &c, int R, int precision, cudaStream_t s, bool timed 
     Chain ch = make_chain(c, s);
     if (precision == LBMG_MIXED) {
         launch_to_float(c.rs, F.b32, m, s, F.x32, &ch);
-        enqueue_vcycle<float>(c, R, s, timed, &ch);
+        enqueue_cycle<float>(c, R, s, timed, &ch);
         launch_add_float(c.xs, F.x32, m, s, &ch);
     } else {
         cudaMemcpyAsync(F.b64, c.rs, m * sizeof(double), cudaMemcpyDeviceToDevice, s);
         cudaMemsetAsync(F.x64, 0, m * sizeof(double), s);
-        enqueue_vcycle<double>(c, R, s, timed, &ch);
+        enqueue_cycle<double>(c, R, s, timed, &ch);
         launch_add_double(c.xs, F.x64, m, s);
         ch.cut();
     }
@@ -342,12 +380,12 @@ void enqueue_pcg_iteration(Ctx &c, int R, int precision, cudaStream_t s, bool ti
     Chain ch = make_chain(c, s);
     if (precision == LBMG_MIXED) {
         launch_to_float(c.rs, F.b32, m, s, F.x32, &ch);
-        enqueue_vcycle<float>(c, R, s, timed, &ch);
+        enqueue_cycle<float>(c, R, s, timed, &ch);
         to_double_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(F.x32, c.pcg_z, m);
     } else {
         cudaMemcpyAsync(F.b64, c.rs, m * sizeof(double), cudaMemcpyDeviceToDevice, s);
         cudaMemsetAsync(F.x64, 0, m * sizeof(double), s);
-        enqueue_vcycle<double>(c, R, s, timed, &ch);
+        enqueue_cycle<double>(c, R, s, timed, &ch);
         cudaMemcpyAsync(c.pcg_z, F.x64, m * sizeof(double), cudaMemcpyDeviceToDevice, s);
     }
     launch_pcg_dot(c.rs, c.pcg_z, F.n, R, c.pcg_part, c.pcg_s, 1, s);
@@ -522,8 +560,9 @@ int upload_hierarchy(lbmg_handle h) {
     for (int d = c.d0; d <= c.D; d++) {
         HostLevel &hl = H.lev[d];
         c.lev[d].cb0 = (int)(c.cblk_host.size() / 5);
-        c.lev[d].ncb = (int)(hl.coarse.size() / 3);
-        for (size_t q = 0; q < hl.coarse.size(); q += 3) {
+        // a relaxed coarsest level has no dense block (and no size limit)
+        c.lev[d].ncb = c.coarse_smooth ? 0 : (int)(hl.coarse.size() / 3);
+        for (size_t q = 0; q < hl.coarse.size() && !c.coarse_smooth; q += 3) {
             const int n0 = hl.coarse[q + 2];
             if (n0 > kMaxCoarse) return LBMG_INVALID_ARG;
             c.cblk_host.insert(c.cblk_host.end(), {d, hl.coarse[q], hl.coarse[q + 1], n0, (int)inv_total});
@@ -542,6 +581,7 @@ int upload_hierarchy(lbmg_handle h) {
         L.ns = hl.ns;
         L.nnz = hl.rp.empty() ? 0 : hl.rp[hl.ndof];
         for (int q = 0; q < 9; q++) L.cs[q] = hl.colour_start[q];
+        for (int q = 0; q < 9; q++) L.cs_all[q] = hl.colour_all[q];
         LBMG_TRY(h->upload(&L.rp, hl.rp));
         LBMG_TRY(h->upload(&L.ci, hl.ci));
         LBMG_TRY(h->alloc(&L.M, L.nnz));
@@ -682,7 +722,9 @@ int upload_hierarchy(lbmg_handle h) {
     LBMG_TRY(h->alloc((char **)&c.persist_views, c.persist_view_bytes));
     LBMG_TRY(h->alloc((char **)&c.persist_state, 64));
     LBMG_CK(cudaMallocHost(&c.h_state, 64 + 16 * sizeof(double)));
-    c.persist_ok = persist_setup(c) == 0 && c.persist_blocks <= 1024;
+    // the one-launch solve and the one-block bottom cycles end in the coarsest level's dense
+    // solve: a relaxed coarsest level runs the general cycle with neither
+    c.persist_ok = !c.coarse_smooth && persist_setup(c) == 0 && c.persist_blocks <= 1024;
     cudaGetLastError();
     if (!c.persist_ok) {   // no narrow levels either: the persistent set-up also picks them
         c.persist_dn = c.d0 - 1;
@@ -692,6 +734,11 @@ int upload_hierarchy(lbmg_handle h) {
     }
     LBMG_TRY(h->alloc((char **)&c.views32, c.persist_view_bytes));
     LBMG_TRY(h->alloc((char **)&c.views64, c.persist_view_bytes));
+    if (c.coarse_smooth) {
+        c.persist_dn = c.d0 - 1;
+        c.narrow.dn = c.d0 - 1;
+        return LBMG_OK;
+    }
     if (narrow_views_setup(c) != 0) return LBMG_CUDA_ERROR;
     if (c.ninst == 1 && narrow_smem_setup(c, 200 * 1024) != 0) {
         cudaGetLastError();
@@ -726,6 +773,9 @@ static double rel_residual(double r2, double b2) {
 
 static int check_build_options(const lbmg_options &o) {
     if (o.host_check != 0 && o.host_check != 1) return LBMG_INVALID_ARG;
+    if ((o.cycle != 0 && o.cycle != 1) || (o.coarse_smooth != 0 && o.coarse_smooth != 1)) return LBMG_INVALID_ARG;
+    // the persistent solve runs the V-cycle with a solved coarsest level only
+    if (o.persistent && (o.cycle != 0 || o.coarse_smooth != 0)) return LBMG_INVALID_ARG;
     if (o.nu1 < 0 || o.nu2 < 0 || o.coarse_max < 1 || o.coarse_max > kMaxCoarse) return LBMG_INVALID_ARG;
     if (o.smoother != LBMG_GS_COLOURED && o.smoother != LBMG_JACOBI) return LBMG_INVALID_ARG;
     if (o.narrow_max < 0 || o.barrier_phantoms < 0 || o.barrier_phantoms > 1024) return LBMG_INVALID_ARG;
@@ -833,6 +883,7 @@ static int check_batch_options(const lbmg_options &o) {
     if (o.nu1 < 0 || o.nu2 < 0 || o.coarse_max < 1 || o.coarse_max > kMaxCoarse) return LBMG_INVALID_ARG;
     if (o.smoother != LBMG_GS_COLOURED || o.narrow_max < 0 || o.barrier_phantoms < 0) return LBMG_INVALID_ARG;
     if (o.host_alloc_fail != 0 && o.host_alloc_fail != 1) return LBMG_INVALID_ARG;
+    if (o.cycle != 0 || o.coarse_smooth != 0 || o.host_check < 0 || o.host_check > 1) return LBMG_INVALID_ARG;
     return LBMG_OK;
 }
 
@@ -881,6 +932,8 @@ void lbmg_default_options(lbmg_options *o) {
     o->copy_phantom_bytes = 0;
     o->host_alloc_fail = 0;
     o->host_check = 0;
+    o->cycle = 0;
+    o->coarse_smooth = 0;
 }
 
 int lbmg_build_hierarchy(const double *V, int nv, const int *F, int nt, int depth, const lbmg_options *opt,
@@ -909,6 +962,8 @@ int lbmg_build_hierarchy(const double *V, int nv, const int *F, int nt, int dept
     h->c.persist_narrow = o.narrow_max;
     h->c.barrier_phantoms = o.barrier_phantoms;
     h->c.host_check = o.host_check;
+    h->c.gamma = o.cycle == 1 ? 2 : 1;
+    h->c.coarse_smooth = o.coarse_smooth;
     st = upload_hierarchy(h);
     if (st != 0) { delete h; return st; }
     *out = h;
@@ -1502,17 +1557,25 @@ int lbmg_launch_counts(lbmg_handle h, int precision, int *assemble, int *project
     const int levels = c.D - c.d0;
     if (assemble) *assemble = 2 + levels + (levels + 1) + 3;
     if (project_rhs) *project_rhs = 2;
-    const bool narrow = c.persist_dn >= c.d0 && c.smoother != LBMG_JACOBI && precision == LBMG_MIXED;
-    const bool smem = c.narrow.dn >= c.d0 && c.smoother != LBMG_JACOBI && precision == LBMG_MIXED;
-    const int bottom = smem ? c.narrow.dn : (narrow ? c.persist_dn : c.d0);
-    int cyc = 1;   // the one-block bottom cycle, or the coarse apply
-    for (int d = bottom + 1; d <= c.D; d++) {
-        int per_sweep = 2;
-        if (c.smoother != LBMG_JACOBI) {
-            per_sweep = 0;
-            for (int q = 0; q < 8; q++) per_sweep += c.lev[d].cs[q + 1] > c.lev[d].cs[q];
-        }
-        cyc += (c.nu1 + c.nu2) * per_sweep + 3 + (c.lev[d].ncb > 0);   // sweeps, residual, restriction, prolongation
+    auto per_sweep = [&](const int *cs) {
+        if (c.smoother == LBMG_JACOBI) return 2;
+        int k = 0;
+        for (int q = 0; q < 8; q++) k += cs[q + 1] > cs[q];
+        return k;
+    };
+    int cyc = 0;
+    if (c.gamma == 1 && !c.coarse_smooth) {
+        const bool narrow = c.persist_dn >= c.d0 && c.smoother != LBMG_JACOBI && precision == LBMG_MIXED;
+        const bool smem = c.narrow.dn >= c.d0 && c.smoother != LBMG_JACOBI && precision == LBMG_MIXED;
+        const int bottom = smem ? c.narrow.dn : (narrow ? c.persist_dn : c.d0);
+        cyc = 1;   // the one-block bottom cycle, or the coarse apply
+        for (int d = bottom + 1; d <= c.D; d++)   // sweeps, residual, restriction, prolongation
+            cyc += (c.nu1 + c.nu2) * per_sweep(c.lev[d].cs) + 3 + (c.lev[d].ncb > 0);
+    } else {
+        // the general cycle: gamma visits of each coarser level
+        long visit = c.coarse_smooth ? (long)(c.nu1 + c.nu2) * per_sweep(c.lev[c.d0].cs_all) : 1;
+        for (int d = c.d0 + 1; d <= c.D; d++) visit = (long)(c.nu1 + c.nu2) * per_sweep(c.lev[d].cs) + 3 + c.gamma * visit;
+        cyc = (int)std::min<long>(visit, 1 << 30);
     }
     cyc += (precision == LBMG_MIXED ? 2 : 1) + 1 + 2;   // conversion/update, FP64 residual, norms
     const bool persistent = c.persistent && c.persist_ok && c.smoother == LBMG_GS_COLOURED;

@@ -67,6 +67,7 @@ int adopt_single(HostHierarchy &P, HostHierarchy &B, std::string &err) {
         std::vector<int32_t>().swap(L.ct_dof);
         if (d < B.d0) continue;
         L.inst.assign(L.ndof, 0);
+        for (int c = 0; c <= 8; c++) L.colour_all[c] = L.colour_start[c];
         if (d == B.d0) {
             // the coarsest level is one dense block and is not smoothed
             for (int c = 0; c <= 8; c++) L.colour_start[c] = 0;

@@ -26,6 +26,8 @@ struct HostLevel {
     int ndof = 0;
     int ns = 0;                         // rows [0, ns) are smoothed; [ns, ndof) are coarsest-level rows
     int colour_start[9] = {0};          // smoothed rows sorted by corner parity colour 0..7
+    int colour_all[9] = {0};            // colour ranges of all rows, kept on a single mesh's coarsest
+                                        // level (whose rows are not smoothed unless it is relaxed)
     std::vector<int32_t> coarse;        // coarsest-level blocks: (instance, first row, rows) triples
     std::vector<int32_t> inst;          // [ndof] instance of each row
     std::vector<int32_t> corner;        // [ndof*3] grid corner index at depth d

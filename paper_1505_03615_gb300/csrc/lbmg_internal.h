@@ -67,6 +67,7 @@ struct DevLevel {
     int cb0 = 0, ncb = 0;                  // this level's coarsest blocks in Ctx::cblk
     int64_t nnz = 0;
     int cs[9] = {0};                       // colour ranges
+    int cs_all[9] = {0};                   // colour ranges of all rows (the coarsest level relaxed)
     int *rp = nullptr, *ci = nullptr;
     double *M = nullptr, *L = nullptr, *A64 = nullptr;
     float *A32 = nullptr;
@@ -153,6 +154,8 @@ struct Ctx {
     double *item_part = nullptr;           // [nnitem][8]
     double *inst_norm = nullptr;           // [ninst][12]: ||r||^2, ||b||^2, initial ||r||^2 per rhs
     int nu1 = 2, nu2 = 2, smoother = 0;
+    int gamma = 1;                         // coarse visits per level: 1 V-cycle, 2 W-cycle
+    int coarse_smooth = 0;                 // 1: the coarsest level is relaxed, not solved
     double omega = 0.6;
     DevLevel lev[kMaxDepth + 1];
     // finest-level geometry
