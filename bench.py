@@ -537,6 +537,7 @@ def main():
     ap.add_argument("--tune-cache", default=None,
                     help="tuning cache file: loaded before tuning (matching levels are not timed), saved after")
     ap.add_argument("--cycle", default="v", choices=["v", "w"], help="V-cycle (default) or W-cycle")
+    ap.add_argument("--cmcf-steps", type=int, default=3, help="flow steps timed after the main measurement")
     ap.add_argument("--nu", type=int, default=2, help="smoothing sweeps before and after the coarse correction")
     ap.add_argument("--force-shape", default=None,
                     help="TPR,TPB: after tuning, set the finest level's mixed-precision sweep and residual launch "
@@ -706,6 +707,31 @@ def main():
         other_res[name] = {"ms_to_tol": g0.elapsed_time(g1) / fp64_steps, "cycles_per_step": its / fp64_steps,
                            "converged": ok}
 
+    # conformalized mean-curvature flow (Section 5.3): a few steps of the library's flow loop
+    # (area weights of the current positions, assembly, projection, warm-started solve, vertex
+    # evaluation, all on the device), the unit of the paper's Table 1
+    cmcf = None
+    if args.cmcf_steps > 0:
+        X = torch.tensor(V, device=dev)
+        xc = torch.zeros((n, 3), dtype=torch.float64, device=dev)
+        Xn = torch.zeros_like(X)
+        solver = 1 if args.solver == "pcg" else 0
+        L.lbmg_cmcf_step(h, X, t, xc, tol, max_cycles, L.LBMG_MIXED, Xn, solver=solver)
+        X, Xn = Xn, X
+        torch.cuda.synchronize()
+        g0.record()
+        ccyc = 0
+        for _ in range(args.cmcf_steps):
+            code, st = L.lbmg_cmcf_step(h, X, t, xc, tol, max_cycles, L.LBMG_MIXED, Xn, solver=solver)
+            ccyc += st.cycles
+            X, Xn = Xn, X
+        g1.record()
+        torch.cuda.synchronize()
+        L.lbmg_set_area_weights(h, None)
+        cmcf = {"steps": args.cmcf_steps, "delta": t, "solver": args.solver, "precision": "mixed",
+                "ms_per_step": g0.elapsed_time(g1) / args.cmcf_steps, "cycles_per_step": ccyc / args.cmcf_steps,
+                "warm_start": True}
+
     learned = None
     if args.learned:
         learned = learned_compare(L, V, F, depth, t, f_dev, tol, nrhs, args, dev)
@@ -791,7 +817,7 @@ def main():
                        "tuned_us_per_sweep_and_residual": tuned_us},
             "setup_s": {"hierarchy_build_and_upload": t_build, "autotune": t_tune},
             "ms_to_tol_mixed": ms_per_step, "ms_to_tol_fp64": fp64_ms, "solver": args.solver,
-            "other_solver": {"solver": other, **other_res}, "learned": learned,
+            "other_solver": {"solver": other, **other_res}, "learned": learned, "cmcf": cmcf,
             "cycles_per_step": cycles / args.steps, "fp64_cycles_per_step": fp64_cycles / fp64_steps,
             "max_rel_residual": rel,
             "roofline": roofline, "cpu_baseline": cpu_baseline,

@@ -259,6 +259,46 @@ int lbmg_solve(lbmg_handle h, const double *rhs, double *x, int nrhs, double tol
 int lbmg_solve_pcg(lbmg_handle h, const double *rhs, double *x, int nrhs, double tol, int max_iters,
                    int precision, lbmg_stats *stats, void *stream);
 
+/*
+ * One step of conformalized mean-curvature flow (Section 5.3) on the build-time
+ * function space: (M_t + delta L_0) x = M_t u_t, u_t the current vertex positions X
+ * (linear per triangle), M_t the mass matrix with every triangle weighted by its
+ * current over its build-time area, L_0 the build-time stiffness; then the new
+ * positions X_next(v) = sum_i x_i b_i(v).  On `stream`: the area weights from X
+ * (device kernels), lbmg_assemble(h, delta), the projection of X, lbmg_solve
+ * (solver 0) or lbmg_solve_pcg (solver 1) warm-started from x, and vertex
+ * evaluation; the call synchronizes once (the solve's status read).
+ *  X, X_next: device double[nv][3] (may not alias); x: device double[n_depth][3],
+ *  in/out: the previous step's solution as warm start (zeros at the first step).
+ * Single meshes only.  Leaves the area weights of X in the handle (the next
+ * lbmg_assemble uses them; lbmg_set_area_weights(h, NULL) restores the build-time
+ * metric).  The first call allocates the step's weight and right-hand-side buffers.
+ * Returns the solve's status (LBMG_NOT_CONVERGED still evaluates X_next); host
+ * pointers or a batch give LBMG_INVALID_ARG.
+ */
+int lbmg_cmcf_step(lbmg_handle h, const double *X, double delta, double *x, double tol, int max_cycles,
+                   int precision, int solver, double *X_next, lbmg_stats *stats, void *stream);
+
+/*
+ * The k smallest eigenpairs of L x = lambda M x on the finest level (the spectral analysis
+ * of Section 5.1: M and L of Eq. 2 on the split space), by LOBPCG (locally optimal block
+ * preconditioned conjugate gradients) preconditioned by one FP64 V-cycle of the assembled
+ * A = M + t L per residual (t from the last lbmg_assemble; a t near 1 / lambda_k suits the
+ * wanted end of the spectrum).  Each iteration does the block products, V-cycles and
+ * Gram matrices on the device and the Rayleigh-Ritz step on the host (at most 48 x 48),
+ * which reads the Gram matrices and residual norms back (two synchronizations per
+ * iteration).  Stops when ||L x_j - lambda_j M x_j|| <= tol ||M x_j|| for every j.
+ *  k: 1..16, 3k <= functions; X0: device double[n_depth][k], the start (e.g. random,
+ *  columns independent); X: device double[n_depth][k], M-orthonormal eigenvectors
+ *  (X may alias X0); lambda: host double[k], ascending; residuals: host double[k] or NULL;
+ *  *iters: iterations taken.  The call allocates and frees its work blocks (about
+ *  9 k n doubles).  Errors: LBMG_NOT_ASSEMBLED, LBMG_INVALID_ARG (sizes, host pointers, a
+ *  batch), LBMG_DIVERGED (the block lost rank), LBMG_NOT_CONVERGED (x, lambda hold the last
+ *  iterate), LBMG_CUDA_ERROR.
+ */
+int lbmg_eigs(lbmg_handle h, int k, double tol, int max_iters, const double *X0, double *lambda, double *X,
+              double *residuals, int *iters, void *stream);
+
 /* Number of kernels each call launches: lbmg_assemble, lbmg_project_rhs, one
    V-cycle step of lbmg_solve/lbmg_vcycles in `precision` (cycle + FP64 residual
    + norms; 0 for the persistent solve, whose cycles run inside its one launch),

@@ -19,6 +19,7 @@ import numpy as np
 __all__ = [
     "icosphere",
     "ellipsoid",
+    "bumpy_sphere",
     "torus",
     "torus_knot_tube",
     "double_sheet",
@@ -77,6 +78,22 @@ def icosphere(level=3, radius=1.0, jitter=1e-3, seed=1):
     V = np.array(V) * radius
     V = _jitter(V, jitter, _rng(seed))
     return np.ascontiguousarray(V, dtype=np.float64), np.ascontiguousarray(F, dtype=np.int32)
+
+
+def bumpy_sphere(level=4, amplitude=0.25, seed=12):
+    """A seeded genus-0 surface with bumps of several sizes: the icosphere of the given level
+    with radius 1 + amplitude * (sum of three products of sines of the coordinates with seeded
+    frequencies 1..4 and phases), normalised to a largest bump of `amplitude`."""
+    V, F = icosphere(level=level, radius=1.0, jitter=0.0, seed=seed)
+    rng = _rng(seed)
+    bump = np.zeros(V.shape[0])
+    for _ in range(3):
+        k = rng.integers(1, 5, size=3)
+        ph = rng.uniform(0, 2 * np.pi, size=3)
+        bump += np.prod(np.sin(k[None, :] * np.pi * V + ph[None, :]), axis=1)
+    bump *= amplitude / np.abs(bump).max()
+    V = V * (1.0 + bump)[:, None]
+    return np.ascontiguousarray(V), F
 
 
 def ellipsoid(axes=(1.0, 0.7, 0.5), level=5, jitter=1e-6, seed=3):

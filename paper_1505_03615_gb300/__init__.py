@@ -24,7 +24,7 @@ __all__ = [
     "lbmg_instance_residuals", "lbmg_row_instances", "lbmg_learned_nparams", "lbmg_learned_params", "lbmg_learned_collect",
     "lbmg_learned_loss_grad", "lbmg_learned_train", "lbmg_learned_enable", "lbmg_learned_omega",
     "lbmg_residual_norms_noalloc", "lbmg_status_string", "lbmg_last_cuda_error", "lbmg_default_options",
-    "lbmg_solve_pcg", "lbmg_autotune", "lbmg_launch_shape", "lbmg_tuned_times", "lbmg_set_launch_shape", "lbmg_set_host_check", "lbmg_tune_cache_save", "lbmg_tune_cache_load",
+    "lbmg_solve_pcg", "lbmg_cmcf_step", "lbmg_eigs", "lbmg_autotune", "lbmg_launch_shape", "lbmg_tuned_times", "lbmg_set_launch_shape", "lbmg_set_host_check", "lbmg_tune_cache_save", "lbmg_tune_cache_load",
     "lbmg_host_build", "lbmg_host_destroy", "lbmg_host_levels", "lbmg_host_level_info", "lbmg_host_get_dofs",
     "lbmg_host_get_pattern", "lbmg_host_get_prolongation", "lbmg_host_build_batch", "lbmg_host_instances",
     "lbmg_host_row_instances",
@@ -104,6 +104,8 @@ def load_library():
         "lbmg_tuned_times": (i, [P, i, i, P]),
         "lbmg_set_launch_shape": (i, [P, i, i, i, i, i]),
         "lbmg_set_host_check": (i, [P, i]),
+        "lbmg_cmcf_step": (i, [P, P, d, P, d, i, i, i, P, P, P]),
+        "lbmg_eigs": (i, [P, i, d, i, P, P, P, P, P, P]),
         "lbmg_tune_cache_save": (i, [C.c_char_p]),
         "lbmg_tune_cache_load": (i, [C.c_char_p]),
         "lbmg_get_matrix": (i, [P, i, P, P, P, P]),
@@ -367,6 +369,30 @@ def lbmg_solve_pcg(h, rhs, x, tol, max_iters, precision, stream=None, raise_not_
                                          int(precision), C.byref(st), _stream(stream))
     _check(code, "lbmg_solve_pcg", allow=() if raise_not_converged else (LBMG_NOT_CONVERGED, LBMG_DEVICE_TIMEOUT))
     return code, st
+
+
+def lbmg_cmcf_step(h, X, delta, x, tol, max_cycles, precision, X_next, solver=0, stream=None):
+    """One conformalized mean-curvature-flow step (device tensors X [nv,3], x [n,3] in/out,
+    X_next [nv,3]); returns (status, Stats) like lbmg_solve."""
+    st = Stats()
+    code = load_library().lbmg_cmcf_step(h, _ptr(X), float(delta), _ptr(x), float(tol), int(max_cycles),
+                                         int(precision), int(solver), _ptr(X_next), C.byref(st), _stream(stream))
+    _check(code, "lbmg_cmcf_step", allow=(LBMG_NOT_CONVERGED,))
+    return code, st
+
+
+def lbmg_eigs(h, X0, tol, max_iters, X=None, stream=None):
+    """The k = X0.shape[1] smallest eigenpairs of L x = lambda M x (device tensors X0 [n,k] and X);
+    returns (status, lambda [k], residuals [k], iterations)."""
+    k = X0.shape[1]
+    X = X0 if X is None else X
+    lam = np.zeros(k)
+    res = np.zeros(k)
+    its = C.c_int(0)
+    code = load_library().lbmg_eigs(h, int(k), float(tol), int(max_iters), _ptr(X0), _ptr(lam), _ptr(X), _ptr(res),
+                                    C.byref(its), _stream(stream))
+    _check(code, "lbmg_eigs", allow=(LBMG_NOT_CONVERGED,))
+    return code, lam, res, its.value
 
 
 def lbmg_vcycles(h, rhs, x, cycles, precision, stream=None):

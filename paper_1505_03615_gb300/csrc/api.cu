@@ -1447,6 +1447,53 @@ static int solve_impl(lbmg_handle h, const double *rhs, double *x, int nrhs, dou
     return status;
 }
 
+int lbmg_cmcf_step(lbmg_handle h, const double *X, double delta, double *x, double tol, int max_cycles,
+                   int precision, int solver, double *X_next, lbmg_stats *stats, void *stream) {
+    if (!h || !X || !x || !X_next || !(delta > 0) || !std::isfinite(delta) || !(tol >= 0)) return LBMG_INVALID_ARG;
+    if (solver != 0 && solver != 1) return LBMG_INVALID_ARG;
+    Ctx &c = h->c;
+    if (c.ninst != 1) return LBMG_INVALID_ARG;   // one mesh: one embedding
+    if (!on_device(X) || !on_device(x) || !on_device(X_next)) {
+        g_cuda_err = "lbmg_cmcf_step: X, x and X_next must be device pointers";
+        return LBMG_INVALID_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!c.cmcf_w) {
+        LBMG_TRY(h->alloc(&c.cmcf_w, (size_t)std::max(c.nt, 1)));
+        LBMG_TRY(h->alloc(&c.cmcf_rhs, 3 * (size_t)c.lev[c.D].n));
+    }
+    // M_t: the build-time mass matrix with every triangle weighted by its current area ratio
+    launch_cmcf_weights(c, X, c.cmcf_w, s);
+    LBMG_TRY(lbmg_assemble(h, delta, stream));
+    // M_t u_t: the current positions, linear per triangle, integrated with the same weights
+    launch_project_rhs(c, X, 3, c.cmcf_rhs, s);
+    const int st = solve_impl(h, c.cmcf_rhs, x, 3, tol, max_cycles, precision, stats, stream, true, solver == 1);
+    if (st != LBMG_OK && st != LBMG_NOT_CONVERGED) return st;
+    launch_eval_vertices(c, x, 3, X_next, s);
+    LBMG_TRY(check_launch());
+    return st;
+}
+
+int lbmg_eigs(lbmg_handle h, int k, double tol, int max_iters, const double *X0, double *lambda, double *X,
+              double *residuals, int *iters, void *stream) {
+    if (!h || !X0 || !lambda || !X || !iters || !(tol > 0) || max_iters < 0) return LBMG_INVALID_ARG;
+    if (!h->c.assembled) return LBMG_NOT_ASSEMBLED;
+    if (h->c.ninst != 1 || !on_device(X0) || !on_device(X)) {
+        g_cuda_err = "lbmg_eigs: single meshes, device pointers X0 and X";
+        return LBMG_INVALID_ARG;
+    }
+    std::string err;
+    const int st = lobpcg(h->c, k, tol, max_iters, X0, lambda, X, residuals, iters, (cudaStream_t)stream, err);
+    if (st != 0) g_cuda_err = err;
+    switch (st) {
+        case 0: return LBMG_OK;
+        case 1: return LBMG_INVALID_ARG;
+        case 2: return LBMG_CUDA_ERROR;
+        case 3: return LBMG_DIVERGED;
+        default: return LBMG_NOT_CONVERGED;
+    }
+}
+
 int lbmg_solve_pcg(lbmg_handle h, const double *rhs, double *x, int nrhs, double tol, int max_iters, int precision,
                    lbmg_stats *stats, void *stream) {
     if (!(tol >= 0)) return LBMG_INVALID_ARG;

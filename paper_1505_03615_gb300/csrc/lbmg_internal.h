@@ -176,6 +176,8 @@ struct Ctx {
     double *cinv64 = nullptr;
     float *cinv32 = nullptr;
     int *flag = nullptr;         // device status word (coarse factor)
+    // a flow step's triangle weights [nt] and right-hand side [n_D][3] (allocated at the first step)
+    double *cmcf_w = nullptr, *cmcf_rhs = nullptr;
     // finest FP64 solve vectors, room for [n][4]
     double *xs = nullptr, *bs = nullptr, *rs = nullptr;
     double *norm_part = nullptr, *norm_out = nullptr;
@@ -255,6 +257,16 @@ int narrow_views_setup(Ctx &c);
 void launch_narrow_cycle(const Ctx &c, int precision, int R, int top, cudaStream_t s);
 int persist_solve(Ctx &c, int precision, int R, int nrhs, double tol, int max_cycles, cudaStream_t s);
 size_t persist_view_bytes();
+
+// ----- conformalized mean-curvature flow (cmcf.cu) -----
+// per-triangle area ratios of the positions X (device [nv][3]) to the build-time surface, and
+// the fragments' mass scales sigma^2 w_T; tri_w: device [nt] scratch
+void launch_cmcf_weights(const Ctx &c, const double *X, double *tri_w, cudaStream_t s);
+
+// ----- smallest eigenpairs of L x = lambda M x (lobpcg.cu) -----
+// 0 converged, 1 bad size, 2 CUDA failure, 3 the block lost rank, 4 not converged in max_iters
+int lobpcg(Ctx &c, int k, double tol, int max_iters, const double *X_user, double *lambda, double *X_out, double *res,
+           int *iters, cudaStream_t s, std::string &err);
 
 // ----- kernels (assemble.cu) -----
 void launch_fragment_moments(const Ctx &c, cudaStream_t s);
