@@ -371,9 +371,11 @@ int lbmg_smooth(lbmg_handle h, int d, const double *rhs, double *x, int nrhs, in
  * of 512 x 4 doubles (16 KiB) that every GPU loading the library keeps until the
  * process exits.
  *  rhs, x: device double[n_d][nrhs] in the library's dof order of level d;
- *  norms: device double[nrhs]; 1 <= nrhs <= 4.  Host pointers or more than 4
- *  right-hand sides are rejected with LBMG_INVALID_ARG (lbmg_last_cuda_error
- *  names the reason).  Needs lbmg_assemble.  Asynchronous on `stream`.
+ *  norms: device double[nrhs]; 1 <= nrhs <= 4.  Host pointers, memory of another
+ *  device, a level outside [min_depth, depth] or more than 4 right-hand sides are
+ *  rejected with LBMG_INVALID_ARG, a handle not yet assembled with
+ *  LBMG_NOT_ASSEMBLED (lbmg_last_cuda_error names the reason).  Asynchronous on
+ *  `stream`.
  *  The first call on each device looks up the array's device address with that
  *  device current and keeps it; make that first call before any stream capture.
  *  Each call overwrites the whole array before reading it; calls that overlap on

@@ -755,10 +755,16 @@ void enqueue_vcycle64_from(Ctx &c, int top, int R, cudaStream_t s) {
     enqueue_vcycle<double>(c, R, s, false, &ch, top);
 }
 
-// level d of an assembled handle, for entry points defined in other files
-const DevLevel *noalloc_level(lbmg_handle h, int d) {
-    if (!h || d < h->c.d0 || d > h->c.D || !h->c.assembled) return nullptr;
-    return &h->c.lev[d];
+// level d of an assembled handle, for entry points defined in other files: LBMG_INVALID_ARG for
+// a null handle or a level outside [min_depth, depth], LBMG_NOT_ASSEMBLED before lbmg_assemble,
+// each with its reason in the error string
+int noalloc_level(lbmg_handle h, int d, const DevLevel **out) {
+    *out = nullptr;
+    if (!h) { g_cuda_err = "null handle"; return LBMG_INVALID_ARG; }
+    if (d < h->c.d0 || d > h->c.D) { g_cuda_err = "level outside [min_depth, depth]"; return LBMG_INVALID_ARG; }
+    if (!h->c.assembled) { g_cuda_err = "the handle is not assembled (lbmg_assemble)"; return LBMG_NOT_ASSEMBLED; }
+    *out = &h->c.lev[d];
+    return LBMG_OK;
 }
 void noalloc_set_error(const std::string &msg) { g_cuda_err = msg; }
 

@@ -17,7 +17,7 @@
 #include "lbmg_internal.h"
 
 namespace lbmg {
-const DevLevel *noalloc_level(lbmg_handle h, int d);
+int noalloc_level(lbmg_handle h, int d, const DevLevel **out);
 void noalloc_set_error(const std::string &msg);
 }  // namespace lbmg
 
@@ -101,10 +101,15 @@ __global__ void finish_kernel(const double *__restrict__ partial, int nblocks, i
     if (threadIdx.x < nrhs) out[threadIdx.x] = sqrt(sh[0][threadIdx.x]);
 }
 
+// device (or managed) memory of the current device: the kernels run there, with the handle's
+// level arrays, so a buffer on another GPU is refused rather than read across devices
 bool on_device_ptr(const void *p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return false; }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) return false;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return false; }
+    return a.type == cudaMemoryTypeManaged || a.device == dev;
 }
 
 // device address of g_partial on the current device, looked up once per device
@@ -131,10 +136,16 @@ int scratch_for_current_device(double **out) {
 
 extern "C" int lbmg_residual_norms_noalloc(lbmg_handle h, int d, const double *rhs, const double *x, int nrhs,
                                            double *norms, void *stream) {
-    const lbmg::DevLevel *L = lbmg::noalloc_level(h, d);
-    if (!L || !rhs || !x || !norms) return LBMG_INVALID_ARG;
+    const lbmg::DevLevel *L = nullptr;
+    const int lst = lbmg::noalloc_level(h, d, &L);
+    if (lst != LBMG_OK) return lst;
+    if (!rhs || !x || !norms) {
+        lbmg::noalloc_set_error("lbmg_residual_norms_noalloc: null rhs, x or norms");
+        return LBMG_INVALID_ARG;
+    }
     if (!on_device_ptr(rhs) || !on_device_ptr(x) || !on_device_ptr(norms)) {
-        lbmg::noalloc_set_error("lbmg_residual_norms_noalloc: rhs, x and norms must be device memory");
+        lbmg::noalloc_set_error("lbmg_residual_norms_noalloc: rhs, x and norms must be device memory of the current "
+                                "device");
         return LBMG_INVALID_ARG;
     }
     if (nrhs < 1 || nrhs > 4) {

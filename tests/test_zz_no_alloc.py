@@ -37,6 +37,19 @@ def test_noalloc_residual_norms_match_the_residual_entry_point():
             ref = torch.linalg.norm(r, dim=0)
             torch.cuda.synchronize()
             assert torch.allclose(norms, ref, rtol=1e-12, atol=0), (call, norms, ref)
+        # the defining property: after the first call (which looks up the scratch array's
+        # address), further calls leave the device's free memory exactly as it was
+        n = L.lbmg_level_info(h, D)[0]
+        b = torch.tensor(rng.normal(size=(n, 3)), device="cuda:0")
+        x = torch.tensor(rng.normal(size=(n, 3)), device="cuda:0")
+        norms = torch.zeros(3, dtype=torch.float64, device="cuda:0")
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
+        for _ in range(50):
+            L.lbmg_residual_norms_noalloc(h, D, b, x, norms)
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        assert free1 == free0
         # more right-hand sides than the scratch holds are refused before any launch
         n = L.lbmg_level_info(h, D)[0]
         b5 = torch.zeros((n, 5), dtype=torch.float64, device="cuda:0")
@@ -44,5 +57,22 @@ def test_noalloc_residual_norms_match_the_residual_entry_point():
         with pytest.raises(L.LbmgError) as e:
             L.lbmg_residual_norms_noalloc(h, D, b5, b5, out5)
         assert e.value.code == 1
+        with pytest.raises(L.LbmgError) as e:
+            L.lbmg_residual_norms_noalloc(h, D + 1, b, x, norms)
+        assert e.value.code == 1
+    finally:
+        L.lbmg_destroy(h)
+
+
+def test_noalloc_before_assembly_reports_not_assembled():
+    V, F = meshgen.icosphere(2, 1.0, 1e-3, 1)
+    h = L.lbmg_build_hierarchy(V, F, 4)
+    try:
+        n = L.lbmg_level_info(h, 4)[0]
+        b = torch.zeros((n, 1), dtype=torch.float64, device="cuda:0")
+        norms = torch.zeros(1, dtype=torch.float64, device="cuda:0")
+        with pytest.raises(L.LbmgError) as e:
+            L.lbmg_residual_norms_noalloc(h, 4, b, b, norms)
+        assert e.value.code == 5
     finally:
         L.lbmg_destroy(h)
