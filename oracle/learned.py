@@ -1,54 +1,75 @@
-"""FP64 oracle of the learned smoother (numpy).
+"""FP64 oracle of the learned residual correction (numpy).
 
 TEST INFRASTRUCTURE, like the rest of ``oracle/``: only tests, the smoke check
 and the benchmark's CPU leg use it; it shares no code with the GPU library.
 
-The paper's smoother is Gauss-Seidel (Sections 4.3 and 5.2).  The learned
-variant keeps the coloured Gauss-Seidel sweep and lets a small network choose a
-relaxation weight per node from that node's stencil:
+The paper has no learned part: its smoother is Gauss-Seidel inside the multigrid
+cycle (Sections 4.3 and 5.2), and the solver iterates that cycle on the residual.
+The learned variant puts a per-node correction of the current residual in front
+of each cycle of that iteration:
 
-    x_i <- x_i + omega_i (b_i - sum_j a_ij x_j) / a_ii,   colours 0..7 in turn,
+    delta_i = omega_i r_i / a_ii        for every right-hand-side column of r
+    e       = delta + V (r - A delta)   V: the plain cycle from zero on what is left
+    x      <- x + e,   r <- b - A x
 
-with omega_i = 1.45 + 0.45 y_i / (1 + |y_i|) in (1, 1.9), y = MLP(features_i):
-the network may only over-relax.  Because every omega_i lies in (0, 2) the
-sweep still converges for any SPD matrix, and omega = 1 is the plain sweep.
-The correction of node i is thus a function of its stencil coefficients and
-its residual.
+which is the plain cycle started from delta instead of zero.  omega_i = 1 + y_i /
+(1 + |y_i|) lies in (0, 2), and y = 0 gives the undamped Jacobi step; rows under
+the relaxation floor (a_ii <= 1e-20 mean diagonal) take no correction.
 
-Features of node i (28): for each neighbour offset o = corner_j - corner_i in
-{-1,0,1}^3, the sum of a_ij / a_ii over the row's entries with that offset
-(27 bins; the centre bin, which holds only the diagonal, is replaced by
-a_ii / mean_k a_kk), and the row's entry count / 27.
+y_i comes from a 30 -> 64 (ReLU) -> 1 network of node i's features:
+  0..26  for each neighbour offset o = corner_j - corner_i in {-1,0,1}^3, the sum of
+         a_ij / a_ii over the row's entries with that offset (the centre bin, which
+         holds only the diagonal, is replaced by a_ii / mean_k a_kk);
+  27     the row's entry count / 27;
+  28     the node's local minimal-residual step: with z = A D^-1 r,
+         q_i = sum_k r_ik z_ik / sum_k z_ik^2 (0 where z_i = 0), fed as q / (1 + |q|);
+  29     the node's share of the residual energy: e_i = sum_k r_ik^2 and e_bar the
+         mean of e, fed as e_i / (e_i + e_bar) (0 when r = 0).
+Both residual features are unchanged when r is multiplied by any nonzero number,
+so the correction is homogeneous of degree one: delta(s r) = s delta(r).
 
-Network: 28 -> 64 (ReLU) -> 1.  Loss over residual samples r0 (columns):
-mean_s ||r_s||^2 / ||r0_s||^2, where r is the residual after one V-cycle on the
-error equation A e = r0 whose finest-level sweeps (nu1 forward, nu2 backward
-colour sweeps) use the learned weights and whose coarse correction is the plain
-V-cycle below (coloured Gauss-Seidel, exact dense solve of A + eps I at the
-coarsest level, eps = 1e-12 mean diag).  Every step is linear in r, so the
-gradient is the exact adjoint: colour steps in reverse, and for the coarse
-correction r <- r - A P V_c P^T r the transpose g <- g - P V_c P^T A g (V_c is
-symmetric because its sweeps mirror each other).  Residual samples come from the
-histories of plain V-cycles.
+Loss of one residual sample R (n x s: the s right-hand sides of one solve at one
+iteration):  L(R) = log(||C (R - A delta(R))||_F^2 / ||R||_F^2) with C = I - A V: the
+logarithm of the residual reduction of one learned iteration, so that the mean over
+samples counts iterations (a ratio, unlike its logarithm, would let the samples that
+converge slowly outweigh those where the correction gains orders of magnitude).  Its
+gradient is the exact adjoint: with R1 the new residual and g = 2 R1 / ||R1||^2,
+C^T g = g - V (A g) (V is symmetric: its sweeps mirror each other and its coarse
+solve is symmetric), dL/d delta = -A C^T g, dL/d omega_i = sum_k (dL/d delta)_ik
+r_ik / a_ii, and dL/dy = dL/d omega / (1 + |y|)^2.  The features depend on R only,
+so no gradient flows through them.
+
+Acceptance rule of a solve: once an iteration with the correction leaves a
+larger residual norm than the iteration before it in some column, the solve
+drops the correction and runs plain cycles from then on.
 """
 from __future__ import annotations
 
 import numpy as np
 
-N_FEATURES = 28
+N_FEATURES = 30
+N_STENCIL = 28
 HIDDEN = 64
+FLOOR = 1e-20
 
 
 def colours(corner):
     return (corner[:, 0] & 1) | ((corner[:, 1] & 1) << 1) | ((corner[:, 2] & 1) << 2)
 
 
+def inverse_diagonal(A):
+    """1 / a_ii, and 0 on rows under the relaxation floor."""
+    d = A.diagonal()
+    keep = d > FLOOR * d.mean()
+    return np.where(keep, 1.0 / np.where(keep, d, 1.0), 0.0)
+
+
 def stencil_features(A, corner):
-    """Per-node features from a CSR matrix A (scipy) and each dof's grid corner."""
+    """Columns 0..27 from a CSR matrix A (scipy) and each dof's grid corner."""
     A = A.tocsr()
     n = A.shape[0]
     diag = A.diagonal()
-    X = np.zeros((n, N_FEATURES))
+    X = np.zeros((n, N_STENCIL))
     rows = np.repeat(np.arange(n), np.diff(A.indptr))
     off = corner[A.indices] - corner[rows] + 1          # in {0,1,2}^3
     assert off.min() >= 0 and off.max() <= 2
@@ -57,6 +78,22 @@ def stencil_features(A, corner):
     X[:, 13] = diag / diag.mean()
     X[:, 27] = np.diff(A.indptr) / 27.0
     return X
+
+
+def residual_features(A, dinv, R):
+    """Columns 28, 29 for the residual R (n x s)."""
+    R = np.asarray(R, dtype=np.float64).reshape(A.shape[0], -1)
+    Z = A @ (dinv[:, None] * R)
+    zz = (Z * Z).sum(1)
+    q = np.where(zz > 0, (R * Z).sum(1) / np.where(zz > 0, zz, 1.0), 0.0)
+    e = (R * R).sum(1)
+    ebar = e.mean()
+    share = e / (e + ebar) if ebar > 0 else np.zeros_like(e)
+    return np.stack([q / (1.0 + np.abs(q)), share], 1)
+
+
+def features(Xs, A, dinv, R):
+    return np.concatenate([Xs, residual_features(A, dinv, R)], 1)
 
 
 def init_params(seed=0, scale=0.1):
@@ -77,150 +114,53 @@ def mlp_forward(p, X):
 
 
 def omega_of(y):
-    return 1.45 + 0.45 * y / (1.0 + np.abs(y))
+    return 1.0 + y / (1.0 + np.abs(y))
 
 
 def domega_dy(y):
-    return 0.45 / (1.0 + np.abs(y)) ** 2
+    return 1.0 / (1.0 + np.abs(y)) ** 2
 
 
-def sweep_residuals(A, col, omega, R0):
-    """Residual form of one coloured sweep with weights omega on A e = r0.
-    Returns the list [r^(0), ..., r^(8)] (each n x s)."""
-    A = A.tocsr()
-    d = A.diagonal()
-    rs = [R0.copy()]
-    r = R0.copy()
-    for c in range(8):
-        rows = np.where(col == c)[0]
-        delta = (omega[rows] / d[rows])[:, None] * r[rows]
-        r = r - A[:, rows] @ delta
-        rs.append(r)
-    return rs
-
-
-def loss(A, col, omega, R0):
-    r8 = sweep_residuals(A, col, omega, R0)[-1]
-    return float(np.mean((r8 ** 2).sum(0) / (R0 ** 2).sum(0)))
-
-
-def loss_grad_omega(A, col, omega, R0):
-    """(loss, dloss/domega) by the reverse of the sweep: for colour c (reversed),
-    with g the gradient w.r.t. r^(c+1):  dL/domega_i = -(A g)_i . r^(c)_i / a_ii for
-    rows i of colour c, and g <- g - P_c Omega D^-1 (A g)."""
-    A = A.tocsr()
-    d = A.diagonal()
-    rs = sweep_residuals(A, col, omega, R0)
-    s = R0.shape[1]
-    w = 1.0 / (s * (R0 ** 2).sum(0))                    # per-sample weight of ||r8||^2
-    L = float(((rs[-1] ** 2).sum(0) * w).sum())
-    g = 2.0 * rs[-1] * w[None, :]
-    dom = np.zeros_like(omega)
-    for c in range(7, -1, -1):
-        rows = np.where(col == c)[0]
-        Ag = (A[rows] @ g)                                # rows of colour c of A g (A symmetric)
-        dom[rows] = -(Ag * rs[c][rows]).sum(1) / d[rows]
-        g = g.copy()
-        g[rows] -= (omega[rows] / d[rows])[:, None] * Ag
-    return L, dom
-
-
-def loss_and_grads(p, X, A, col, R0):
-    """Loss and gradients w.r.t. every network parameter (FP64, analytic)."""
-    Z, H, y = mlp_forward(p, X)
+def correction(p, Xs, A, dinv, R, feature_map=None):
+    """(delta, omega) for the residual R.  feature_map (optional) is applied to the feature
+    matrix first: the rounding a low-precision network input applies."""
+    R = np.asarray(R, dtype=np.float64).reshape(A.shape[0], -1)
+    X = features(Xs, A, dinv, R)
+    _, _, y = mlp_forward(p, X if feature_map is None else feature_map(X))
     om = omega_of(y)
-    L, dom = loss_grad_omega(A, col, om, R0)
-    gy = dom * domega_dy(y)
-    grads = {
-        "w2": H.T @ gy,
-        "b2": np.array([gy.sum()]),
-    }
-    gH = np.outer(gy, p["w2"]) * (Z > 0)
-    grads["W1"] = X.T @ gH
-    grads["b1"] = gH.sum(0)
-    return L, grads
+    return (om * dinv)[:, None] * R, om
 
 
-class Levels:
-    """The plain multigrid below the finest level: matrices A_d (scipy CSR), colours
-    and prolongations P_d (n_d x n_{d-1}), levels d0..D indexed by depth."""
-
-    def __init__(self, A, col, P, d0, D, nu1=2, nu2=2):
-        self.A, self.col, self.P, self.d0, self.D, self.nu1, self.nu2 = A, col, P, d0, D, nu1, nu2
-        A0 = A[d0].toarray()
-        A0 = A0 + 1e-12 * np.mean(np.diag(A0)) * np.eye(A0.shape[0])
-        self.A0inv = np.linalg.inv(A0)
-
-    def sweep(self, d, b, x, order):
-        A, col = self.A[d], self.col[d]
-        dg = A.diagonal()
-        for c in order:
-            rows = np.where(col == c)[0]
-            x[rows] += (b[rows] - A[rows] @ x) / dg[rows, None]
-
-    def vcycle(self, d, b):
-        """Plain V-cycle on A_d x = b from x = 0 (symmetric linear operator of b)."""
-        if d == self.d0:
-            return self.A0inv @ b
-        x = np.zeros_like(b)
-        for _ in range(self.nu1):
-            self.sweep(d, b, x, range(8))
-        r = b - self.A[d] @ x
-        P = self.P[d]
-        x += P @ self.vcycle(d - 1, P.T @ r)
-        for _ in range(self.nu2):
-            self.sweep(d, b, x, range(7, -1, -1))
-        return x
+def loss_of_omega(A, dinv, omega, R, vcycle):
+    """L for a given omega (the map omega -> L that the gradient differentiates)."""
+    D = (omega * dinv)[:, None] * R
+    r1 = R - A @ D
+    R1 = r1 - A @ vcycle(r1)
+    return float(np.log((R1 ** 2).sum() / (R ** 2).sum()))
 
 
-def cycle_steps(lv):
-    steps = []
-    for _ in range(lv.nu1):
-        steps += [("colour", c) for c in range(8)]
-    steps.append(("coarse", None))
-    for _ in range(lv.nu2):
-        steps += [("colour", c) for c in range(7, -1, -1)]
-    return steps
+def loss_grad_omega(A, dinv, omega, R, vcycle):
+    """(L, dL/domega) by the adjoint of the learned iteration."""
+    U = dinv[:, None] * R
+    r1 = R - A @ ((omega[:, None]) * U)
+    R1 = r1 - A @ vcycle(r1)
+    n1 = (R1 ** 2).sum()
+    L = float(np.log(n1 / (R ** 2).sum()))
+    g = 2.0 * R1 / n1
+    ctg = g - vcycle(A @ g)
+    dD = -(A @ ctg)
+    return L, (dD * U).sum(1)
 
 
-def cycle_loss_grad_omega(lv, omega, R0):
-    """Loss and dloss/domega of one V-cycle with learned finest sweeps (residual form)."""
-    D = lv.D
-    A, col, P = lv.A[D], lv.col[D], lv.P[D]
-    dg = A.diagonal()
-    steps = cycle_steps(lv)
-    rs = [R0.copy()]
-    r = R0.copy()
-    for kind, c in steps:
-        if kind == "colour":
-            rows = np.where(col == c)[0]
-            delta = np.zeros_like(r)
-            delta[rows] = (omega[rows] / dg[rows])[:, None] * r[rows]
-            r = r - A @ delta
-        else:
-            r = r - A @ (P @ lv.vcycle(D - 1, P.T @ r))
-        rs.append(r)
-    w = 1.0 / (R0.shape[1] * (R0 ** 2).sum(0))
-    L = float(((r ** 2).sum(0) * w).sum())
-    g = 2.0 * r * w[None, :]
-    dom = np.zeros_like(omega)
-    for s in range(len(steps) - 1, -1, -1):
-        kind, c = steps[s]
-        if kind == "colour":
-            rows = np.where(col == c)[0]
-            Ag = A[rows] @ g
-            dom[rows] += -(Ag * rs[s][rows]).sum(1) / dg[rows]
-            g = g.copy()
-            g[rows] -= (omega[rows] / dg[rows])[:, None] * Ag
-        else:
-            g = g - P @ lv.vcycle(D - 1, P.T @ (A @ g))
-    return L, dom
-
-
-def cycle_loss_and_grads(p, X, lv, R0):
+def loss_and_grads(p, Xs, A, dinv, R, vcycle, feature_map=None):
+    """Loss of one sample and its gradient w.r.t. every network parameter (feature_map as in
+    correction)."""
+    R = np.asarray(R, dtype=np.float64).reshape(A.shape[0], -1)
+    X = features(Xs, A, dinv, R)
+    if feature_map is not None:
+        X = feature_map(X)
     Z, H, y = mlp_forward(p, X)
-    om = omega_of(y)
-    L, dom = cycle_loss_grad_omega(lv, om, R0)
+    L, dom = loss_grad_omega(A, dinv, omega_of(y), R, vcycle)
     gy = dom * domega_dy(y)
     grads = {"w2": H.T @ gy, "b2": np.array([gy.sum()])}
     gH = np.outer(gy, p["w2"]) * (Z > 0)
@@ -229,21 +169,68 @@ def cycle_loss_and_grads(p, X, lv, R0):
     return L, grads
 
 
-def adam_train(p, X, A, col, samples, steps=200, lr=1e-2, seed=0, batch=8):
-    """Reference training loop (Adam on the loss above); returns params and loss history."""
-    rng = np.random.default_rng(seed)
+def adam_train(p, problems, order, lr=1e-2):
+    """Adam over residual samples.  problems[k] = (Xs, A, dinv, vcycle); order is a list of
+    steps, each a list of (problem index, sample array); the step's gradient is the mean over
+    its samples.  Returns the parameters and the loss history (mean loss per step)."""
     m = {k: np.zeros_like(v) for k, v in p.items()}
     v = {k: np.zeros_like(v) for k, v in p.items()}
-    hist = []
     b1, b2, eps = 0.9, 0.999, 1e-8
-    for t in range(1, steps + 1):
-        idx = rng.choice(samples.shape[1], size=min(batch, samples.shape[1]), replace=False)
-        L, g = loss_and_grads(p, X, A, col, samples[:, idx])
-        hist.append(L)
-        for k in p:
-            m[k] = b1 * m[k] + (1 - b1) * g[k]
-            v[k] = b2 * v[k] + (1 - b2) * g[k] ** 2
-            mh = m[k] / (1 - b1 ** t)
-            vh = v[k] / (1 - b2 ** t)
-            p[k] = p[k] - lr * mh / (np.sqrt(vh) + eps)
+    hist = []
+    for t, step in enumerate(order, start=1):
+        gsum = {k: np.zeros_like(val) for k, val in p.items()}
+        lsum = 0.0
+        for k, R in step:
+            Xs, A, dinv, vc = problems[k]
+            L, g = loss_and_grads(p, Xs, A, dinv, R, vc)
+            lsum += L
+            for q in p:
+                gsum[q] += g[q] / len(step)
+        hist.append(lsum / len(step))
+        for q in p:
+            m[q] = b1 * m[q] + (1 - b1) * gsum[q]
+            v[q] = b2 * v[q] + (1 - b2) * gsum[q] ** 2
+            p[q] = p[q] - lr * (m[q] / (1 - b1 ** t)) / (np.sqrt(v[q] / (1 - b2 ** t)) + eps)
     return p, hist
+
+
+def corrector(p, Xs, A, dinv):
+    """The learned correction as a function of the residual."""
+    return lambda r: correction(p, Xs, A, dinv, r)[0]
+
+
+def solve(corr, A, b, vcycle, tol, max_cycles, x0=None):
+    """Defect correction with corr(r) (a correction of the residual, or None for the plain
+    iteration) in front of every cycle and the acceptance rule above.  Returns (x, cycles,
+    dropped): dropped is the iteration after which the correction was dropped (0 if never)."""
+    b = np.asarray(b, dtype=np.float64).reshape(A.shape[0], -1)
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64).reshape(b.shape)
+    nb2 = (b ** 2).sum(0)
+    r = b - A @ x
+
+    def rel(r):
+        return np.sqrt((r ** 2).sum(0) / np.where(nb2 > 0, nb2, 1.0))
+
+    prev = rel(r)
+    on, dropped = corr is not None, 0
+    for k in range(1, max_cycles + 1):
+        d = corr(r) if on else np.zeros_like(r)
+        x = x + d + vcycle(r - A @ d)
+        r = b - A @ x
+        cur = rel(r)
+        if on and (cur > prev).any():
+            on, dropped = False, k
+        prev = cur
+        if (cur <= tol).all():
+            return x, k, dropped
+    return x, max_cycles, dropped
+
+
+def bf16(a):
+    """Round to the nearest bfloat16 (ties to even), returned as float64: the rounding the
+    tensor-core layer applies to its inputs and weights."""
+    f = np.asarray(a, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    lsb = (u >> 16) & 1
+    u = ((u + 0x7FFF + lsb) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
