@@ -28,6 +28,8 @@ if ROOT not in sys.path:
 
 import numpy as np
 
+import meshgen   # seeded synthetic inputs (no method arithmetic)
+
 METRIC = "unknowns×V-cycles/s; ms to 1e-6 rel. residual, mixed/learned vs plain FP64"
 UNIT = "unknowns*V-cycles/s"
 WORKLOAD = "knot35_4m_d10"
@@ -251,60 +253,94 @@ def reference_main(args):
     print(json.dumps(line), flush=True)
 
 
-def learned_compare(L, V, F, depth, t, f_dev, tol, nrhs, args, dev):
-    """Learned relaxation weights on this mesh: residual histories of plain V-cycles on four
-    random right-hand sides (--learned-skip cycles skipped, 20 kept each), --learned-steps Adam
-    steps of 4 samples at --learned-lr from a network that starts near the plain sweep (omega
-    about 1.05), then the persistent mixed solve of the workload's own right-hand sides with and
-    without the weights, K steps each."""
-    import torch
-    h = L.lbmg_build_hierarchy(V, F, depth, persistent=1)
-    try:
-        L.lbmg_assemble(h, t)
-        n = L.lbmg_level_info(h, depth)[0]
-        rng = np.random.default_rng(7)
-        samp = torch.zeros((n, 4), dtype=torch.float64, device=dev)
-        L.lbmg_project_rhs(h, torch.tensor(rng.uniform(-1, 1, size=(V.shape[0], 4)), device=dev), samp)
-        L.lbmg_learned_collect(h, samp, args.learned_skip, 20)
-        p = np.zeros(L.lbmg_learned_nparams())
-        W1 = np.zeros((32, 64))
-        W1[:28] = rng.normal(0, 0.05, size=(28, 64))
-        p[:32 * 64] = W1.ravel()
-        p[-1] = -8.0
-        L.lbmg_learned_params(h, p)
-        hist = L.lbmg_learned_train(h, rng.integers(0, 80, size=(args.learned_steps, 4)), args.learned_lr)
-        rhs = torch.zeros((n, nrhs), dtype=torch.float64, device=dev)
-        x = torch.zeros_like(rhs)
-        res = {}
-        for name, on in (("plain", False), ("learned", True)):
-            L.lbmg_learned_enable(h, on)
+# training meshes of the learned correction: small stand-ins shaped like the plain-method
+# sphere (depth 5), the (2,3) torus-knot tube (depth 7) and the two nearly touching sheets
+# (depth 7); the residual histories of plain V-cycles on them are the training data
+LEARNED_TRAIN = [
+    ("icosphere(3), depth 5, t=1e-3", lambda: meshgen.icosphere(3, 1.0, 1e-3, 1), 5, 1e-3),
+    ("(2,3) knot tube r=0.04 400x40, depth 7, t=1e-4", lambda: meshgen.torus_knot_tube(2, 3, 1.0, 0.04, 400, 40, 1e-6, 2),
+     7, 1e-4),
+    ("double sheet 60, depth 7, t=1e-3", lambda: meshgen.double_sheet(60, 0.05, 6, 0.5, 1e-6, 4), 7, 1e-3),
+]
+LEARNED_HISTORY = (0, 1, 2, 4, 8, 14, 22, 29)
 
-            def lstep():
-                L.lbmg_assemble(h, t)
-                L.lbmg_project_rhs(h, f_dev, rhs)
-                x.zero_()
-                return L.lbmg_solve(h, rhs, x, tol, args.max_cycles, L.LBMG_MIXED)
-            lstep()
+
+def learned_train(L, dev, steps, lr, batch=4, block=5, seed=0):
+    """The learned correction's network, trained on the GPU (setup, untimed).  Data: residual
+    histories of plain FP64 V-cycles from zero on two right-hand sides per training mesh (the
+    projected vertex coordinates and a random vertex function; 30 cycles kept).  Adam steps on
+    the mean gradient of `batch` samples, drawn from the cycles in LEARNED_HISTORY of one mesh,
+    `block` steps per visit of a random mesh (the optimiser state travels between the meshes'
+    handles); the learning rate drops to lr/3 after half the steps and to lr/10 after three
+    quarters.  Returns (parameters, loss history, seconds)."""
+    import torch
+    rng = np.random.default_rng(seed + 100)
+    handles = []
+    t0 = time.perf_counter()
+    try:
+        data = np.random.default_rng(seed)
+        for _, make, depth, t in LEARNED_TRAIN:
+            V, F = make()
+            h = L.lbmg_build_hierarchy(V, F, depth)
+            handles.append(h)
+            L.lbmg_assemble(h, t)
+            n = L.lbmg_level_info(h, depth)[0]
+            for f in (V, data.uniform(-1, 1, size=V.shape)):
+                rhs = torch.zeros((n, 3), dtype=torch.float64, device=dev)
+                L.lbmg_project_rhs(h, torch.tensor(np.ascontiguousarray(f), device=dev), rhs)
+                L.lbmg_learned_collect(h, rhs, 0, 30)
+        P = L.lbmg_learned_nparams()
+        init = np.random.default_rng(seed)
+        W1 = np.zeros((32, 64))
+        W1[:30] = init.normal(0, 0.05, size=(30, 64))
+        p = np.concatenate([W1.ravel(), np.zeros(64), init.normal(0, 0.05, size=64), np.zeros(1)])
+        state = np.concatenate([p, np.zeros(2 * P + 1)])
+        hist = []
+        done = 0
+        while done < steps:
+            frac = done / steps
+            lr_now = lr if frac < 0.5 else (lr / 3 if frac < 0.75 else lr / 10)
+            k = rng.integers(len(handles))
+            L.lbmg_learned_state(handles[k], state)
+            picks = (rng.choice(LEARNED_HISTORY, size=(block, batch)) +
+                     30 * rng.integers(0, 2, size=(block, batch)))
+            hist += list(L.lbmg_learned_train(handles[k], picks, lr_now))
+            state = L.lbmg_learned_state(handles[k])
+            done += block
+        return state[:P], np.array(hist), time.perf_counter() - t0
+    finally:
+        for h in handles:
+            L.lbmg_destroy(h)
+
+
+def learned_compare(L, h, step, nsteps, params, hist, train_s, args):
+    """The workload's own step with the learned correction in front of every cycle (trained
+    params), and with the untrained one (zero network: the plain Jacobi start), nsteps each."""
+    import torch
+    out = {"trained_on": [m[0] for m in LEARNED_TRAIN], "train_steps": int(len(hist)), "batch": 4,
+           "lr": args.learned_lr,
+           "train_s": train_s, "loss_first50": float(np.mean(hist[:50])), "loss_last50": float(np.mean(hist[-50:])),
+           "loss": "mean log(||r after||^2 / ||r before||^2) of one learned iteration",
+           "solve": "mixed V(2,2) defect correction, one graph launch per solve"}
+    try:
+        for name, prm, k in (("learned", params, nsteps), ("jacobi_start", np.zeros_like(params), max(1, min(3, nsteps)))):
+            L.lbmg_learned_params(h, prm)
+            L.lbmg_learned_enable(h, True)
+            step()
             torch.cuda.synchronize()
             g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             g0.record()
-            cyc, ok, fb = 0, True, 0
-            for _ in range(args.steps):
-                code, st = lstep()
+            cyc, fb = 0, 0
+            for _ in range(k):
+                st = step()
                 cyc += st.cycles
-                ok = ok and code == L.LBMG_OK
                 fb = max(fb, st.learned_fallback)
             g1.record()
             torch.cuda.synchronize()
-            res[name] = {"ms_to_tol": g0.elapsed_time(g1) / args.steps, "cycles_per_step": cyc / args.steps,
-                         "converged": ok, "fallback": fb}
-        om = L.lbmg_learned_omega(h)
-        return {"solve": "persistent, mixed", "train_steps": len(hist), "lr": args.learned_lr,
-                "history_skip": args.learned_skip, "loss_first": float(hist[0]),
-                "loss_last20_mean": float(np.mean(hist[-20:])), "omega_range": [float(om.min()), float(om.max())],
-                **res}
+            out[name] = {"ms_to_tol": g0.elapsed_time(g1) / k, "cycles_per_step": cyc / k, "fallback": fb, "steps": k}
     finally:
-        L.lbmg_destroy(h)
+        L.lbmg_learned_enable(h, False)
+    return out
 
 
 BATCH = "batch64"
@@ -523,13 +559,11 @@ def main():
     ap.add_argument("--only-timed", action="store_true", help="stop after the timed steps (profiling runs)")
     ap.add_argument("--no-pdl", action="store_true", help="plain stream order between the cycle's kernels")
     ap.add_argument("--no-tune", action="store_true", help="default launch shapes (no autotuning at setup)")
-    ap.add_argument("--learned", action="store_true",
-                    help="also train the learned relaxation weights on this mesh (setup, untimed) and time the "
-                         "persistent mixed solve with and without them")
-    ap.add_argument("--learned-steps", type=int, default=150, help="Adam steps of the learned weights")
-    ap.add_argument("--learned-lr", type=float, default=2e-3)
-    ap.add_argument("--learned-skip", type=int, default=3,
-                    help="plain V-cycles skipped before residuals are kept for training")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the learned correction (trained on three small meshes as setup, then timed on the "
+                         "workload's own step)")
+    ap.add_argument("--learned-steps", type=int, default=800, help="Adam steps of the learned network")
+    ap.add_argument("--learned-lr", type=float, default=1e-2)
     ap.add_argument("--solver", default="vcycle", choices=["vcycle", "pcg"],
                     help="V-cycle iteration (the paper's solver, default) or V-cycle-preconditioned CG")
     ap.add_argument("--workload", default=WORKLOAD,
@@ -733,8 +767,10 @@ def main():
                 "warm_start": True}
 
     learned = None
-    if args.learned:
-        learned = learned_compare(L, V, F, depth, t, f_dev, tol, nrhs, args, dev)
+    if not args.no_learned and args.solver == "vcycle" and not args.persistent:
+        params, hist, train_s = learned_train(L, dev, args.learned_steps, args.learned_lr)
+        learned = learned_compare(L, h, step, args.steps, params, hist, train_s, args)
+        learned["vs_plain_mixed"] = (ms_per_step / learned["learned"]["ms_to_tol"]) if ws == 1 else None
 
     # roofline of the dominant kernel (the finest-level Gauss-Seidel colour), timed live with
     # CUDA events on its stream: the timed steps run each solve as one graph launch, whose

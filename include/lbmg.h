@@ -108,9 +108,9 @@ typedef struct lbmg_stats {
     float ms_total;          /* device time of the solve, CUDA events */
     float ms_fine_smooth;    /* device time of the finest-level smoothing sweeps summed over all cycles
                                 (events in the per-cycle graph; %globaltimer in the persistent solve) */
-    int learned;             /* 1 if the finest sweeps started with learned weights (lbmg_learned_enable) */
-    int learned_fallback;    /* 1 if a learned cycle failed to reduce a residual and the solve went on
-                                with plain Gauss-Seidel weights */
+    int learned;             /* 1 if the learned correction preceded the cycles (lbmg_learned_enable) */
+    int learned_fallback;    /* 1 if an iteration with it raised a residual and the solve went on with
+                                plain cycles (the acceptance test) */
     int host_syncs;          /* times the call waited for the device: 1 for a solve run as one graph
                                 launch or one persistent launch (the final status read); one more per
                                 iteration with host_check = 1 or without graphs */
@@ -441,41 +441,59 @@ int lbmg_host_instances(lbmg_host_handle h, int *ninst, int *depth, int *min_dep
 int lbmg_host_row_instances(lbmg_host_handle h, int d, int *inst);
 
 /*
- * Learned relaxation weights for the finest-level Gauss-Seidel sweeps.  The paper
- * has no counterpart: its smoother is plain Gauss-Seidel (Sections 4.3, 5.2), which
- * is also the fallback here and the yardstick of the learned sweep.  A network 28 -> 64 (ReLU) -> 1 maps each
- * finest node's stencil (coefficients / A_ii summed per neighbour-corner offset,
- * A_ii / mean diagonal, entry count / 27) to y, and the node's sweep update is
- * scaled by omega = 1.45 + 0.45 y / (1 + |y|) in (1, 1.9), so the sweep stays
- * convergent for SPD systems.  Dense layers run on the tensor cores (BF16 inputs,
- * FP32 accumulation).  Training minimises mean ||r_after||^2 / ||r_before||^2 over
- * one V-cycle (learned finest sweeps, plain coarse correction), in FP64, by the
- * exact adjoint of the cycle, with Adam on FP32 master weights.  Single-mesh
- * hierarchies with at least two levels; needs lbmg_assemble first.
+ * Learned residual correction in front of each cycle.  The paper has no counterpart:
+ * its solver iterates the plain cycle on the residual (Section 4.3, Gauss-Seidel
+ * smoothing of Section 5.2), which is also the fallback here and the yardstick of the
+ * learned form.  Before each cycle of lbmg_solve / lbmg_vcycles the residual r gets
+ * delta_i = omega_i r_i / a_ii (every lane; 0 on rows under the relaxation floor) and
+ * the cycle starts from delta instead of zero.  omega_i = 1 + y_i / (1 + |y_i|) in
+ * (0, 2) comes from a network 30 -> 64 (ReLU) -> 1 of node i's features: 27
+ * neighbour-offset sums of a_ij / a_ii (centre: a_ii / mean diagonal), the entry
+ * count / 27, and two residual features, q / (1 + |q|) with q_i = r_i.z_i / z_i.z_i,
+ * z = A D^-1 r, and e_i / (e_i + mean e) with e_i = r_i.r_i (sums over the lanes).
+ * The dense layer runs on the tensor cores (BF16 inputs and weights, FP32
+ * accumulation).  Training minimises log(||C (r - A delta)||^2 / ||r||^2), C = I - A V
+ * (the residual reduction of one learned iteration, V the plain V-cycle), in FP64 by the
+ * exact adjoint, with Adam on FP32 master weights.  Acceptance test: once an
+ * iteration with the correction leaves a larger relative residual than the one
+ * before in some lane, the solve drops it and runs plain cycles (the host loop
+ * without a stopping test does not apply it).  Conjugate gradients and the
+ * persistent solve do not use the correction (lbmg_solve returns
+ * LBMG_INVALID_ARG for a persistent handle with it on).  Single-mesh hierarchies
+ * with at least two levels; lbmg_assemble first (else LBMG_NOT_ASSEMBLED).
  *  lbmg_learned_nparams: length P of the flat parameter vector: W1 [32][64]
- *    row-major (rows 28..31 unused, zero), b1 [64], w2 [64], b2 [1].
+ *    row-major (rows 30, 31 unused, zero), b1 [64], w2 [64], b2 [1].
  *  lbmg_learned_params: get (host double[P], may be NULL) and/or set (host
  *    double[P], may be NULL; resets the Adam moments).
- *  lbmg_learned_collect: runs plain FP64 V-cycles from x = 0 on each column of
- *    rhs [n_depth][ns] (user order) and stores the residuals of cycles
- *    skip..skip+keep-1 as training samples (appended to the bank).
- *  lbmg_learned_loss_grad: loss and gradient (host double[P], may be NULL) at
- *    the current parameters for residual samples r0 [n_depth][ns], ns <= 4.
- *  lbmg_learned_train: `steps` Adam steps; order (host int[steps][batch],
- *    batch <= 4) lists the bank samples of each step; loss_hist (host
- *    double[steps], may be NULL) receives each step's loss.
- *  lbmg_learned_enable: on = 1 evaluates omega for the current matrix and makes
- *    lbmg_solve use it (persistent solve only); 0 switches back.
- *  lbmg_learned_omega: omega per finest function in user order (host double[n]).
+ *  lbmg_learned_state: get and/or set (host double[3 P + 1], may be NULL) the
+ *    optimiser state: parameters, Adam's first and second moments, its step count;
+ *    carries training from one handle (mesh) to the next.
+ *  lbmg_learned_collect: runs plain FP64 V-cycles from x = 0 on rhs [n_depth][ns]
+ *    (user order, ns <= 4 lanes) and stores the residual block before cycles
+ *    skip .. skip + keep - 1 as `keep` training samples (appended to the bank).
+ *  lbmg_learned_loss_grad: loss and gradient (host double[P], may be NULL) at the
+ *    current parameters for one residual sample r0 [n_depth][ns], ns <= 4.
+ *  lbmg_learned_train: `steps` Adam steps with learning rate lr; order (host
+ *    int[steps][batch], batch <= 8) lists the bank samples of each step, whose
+ *    mean gradient the step takes; loss_hist (host double[steps], may be NULL)
+ *    receives each step's mean loss.
+ *  lbmg_learned_enable: on = 1 puts the correction in front of every cycle of this
+ *    handle's solves (its stencil features follow each lbmg_assemble); 0 removes it.
+ *  lbmg_learned_apply: the correction of one residual r [n_depth][ns] (ns <= 4) by
+ *    the solve's own kernels in the given precision (LBMG_MIXED: FP32 features and
+ *    start, LBMG_FP64: FP64): omega [n_depth] and delta [n_depth][ns], user order.
+ *    r, omega and delta are device pointers (else LBMG_INVALID_ARG).
  */
 int lbmg_learned_nparams(void);
 int lbmg_learned_params(lbmg_handle h, double *get, const double *set, void *stream);
+int lbmg_learned_state(lbmg_handle h, double *get, const double *set, void *stream);
 int lbmg_learned_collect(lbmg_handle h, const double *rhs, int ns, int skip, int keep, void *stream);
 int lbmg_learned_loss_grad(lbmg_handle h, const double *r0, int ns, double *loss, double *grad, void *stream);
 int lbmg_learned_train(lbmg_handle h, int steps, double lr, const int *order, int batch, double *loss_hist,
                        void *stream);
 int lbmg_learned_enable(lbmg_handle h, int on, void *stream);
-int lbmg_learned_omega(lbmg_handle h, double *omega);
+int lbmg_learned_apply(lbmg_handle h, const double *r, int ns, int precision, double *omega, double *delta,
+                       void *stream);
 
 #ifdef __cplusplus
 }

@@ -22,7 +22,8 @@ __all__ = [
     "lbmg_restrict", "lbmg_prolong_add", "lbmg_eval_vertices", "lbmg_get_dofs", "lbmg_get_matrix",
     "lbmg_get_prolongation", "lbmg_launch_counts", "lbmg_build_batch", "lbmg_instances", "lbmg_instance_info",
     "lbmg_instance_residuals", "lbmg_row_instances", "lbmg_learned_nparams", "lbmg_learned_params", "lbmg_learned_collect",
-    "lbmg_learned_loss_grad", "lbmg_learned_train", "lbmg_learned_enable", "lbmg_learned_omega",
+    "lbmg_learned_loss_grad", "lbmg_learned_train", "lbmg_learned_enable", "lbmg_learned_apply",
+    "lbmg_learned_state",
     "lbmg_residual_norms_noalloc", "lbmg_status_string", "lbmg_last_cuda_error", "lbmg_default_options",
     "lbmg_solve_pcg", "lbmg_cmcf_step", "lbmg_eigs", "lbmg_autotune", "lbmg_launch_shape", "lbmg_tuned_times", "lbmg_set_launch_shape", "lbmg_set_host_check", "lbmg_tune_cache_save", "lbmg_tune_cache_load",
     "lbmg_host_build", "lbmg_host_destroy", "lbmg_host_levels", "lbmg_host_level_info", "lbmg_host_get_dofs",
@@ -121,7 +122,8 @@ def load_library():
         "lbmg_learned_loss_grad": (i, [P, P, i, P, P, P]),
         "lbmg_learned_train": (i, [P, i, d, P, i, P, P]),
         "lbmg_learned_enable": (i, [P, i, P]),
-        "lbmg_learned_omega": (i, [P, P]),
+        "lbmg_learned_apply": (i, [P, P, i, i, P, P, P]),
+        "lbmg_learned_state": (i, [P, P, P, P]),
         "lbmg_residual_norms_noalloc": (i, [P, i, P, P, i, P, P]),
         "lbmg_host_build": (i, [P, i, P, i, i, P, P]),
         "lbmg_host_destroy": (None, [P]),
@@ -270,7 +272,7 @@ def lbmg_learned_nparams():
 
 
 def lbmg_learned_params(h, set_params=None, stream=None):
-    """Set (if given, flat float64) and return the flat parameter vector W1 [32][64], b1, w2, b2."""
+    """Set (if given, flat float64; resets Adam) and return the flat parameters W1 [32][64], b1, w2, b2."""
     P = lbmg_learned_nparams()
     out = np.zeros(P)
     s = None if set_params is None else np.ascontiguousarray(set_params, dtype=np.float64)
@@ -307,11 +309,21 @@ def lbmg_learned_enable(h, on=True, stream=None):
     return _check(load_library().lbmg_learned_enable(h, int(bool(on)), _stream(stream)), "lbmg_learned_enable")
 
 
-def lbmg_learned_omega(h):
-    n, _, _ = lbmg_level_info(h, lbmg_levels(h)[1])
-    out = np.zeros(n)
-    _check(load_library().lbmg_learned_omega(h, _ptr(out)), "lbmg_learned_omega")
+def lbmg_learned_state(h, set_state=None, stream=None):
+    """Set (if given) and return the optimiser state: parameters, Adam moments, step count."""
+    P = lbmg_learned_nparams()
+    out = np.zeros(3 * P + 1)
+    st = None if set_state is None else np.ascontiguousarray(set_state, dtype=np.float64)
+    if st is not None and st.size != 3 * P + 1:
+        raise ValueError(f"expected {3 * P + 1} values")
+    _check(load_library().lbmg_learned_state(h, _ptr(out), _ptr(st), _stream(stream)), "lbmg_learned_state")
     return out
+
+
+def lbmg_learned_apply(h, r, precision, omega, delta, stream=None):
+    """The solve's correction of the residual r (device [n][ns]): omega [n] and delta [n][ns] (device)."""
+    return _check(load_library().lbmg_learned_apply(h, _ptr(r), _nrhs(r), int(precision), _ptr(omega), _ptr(delta),
+                                                    _stream(stream)), "lbmg_learned_apply")
 
 
 def lbmg_destroy(h):

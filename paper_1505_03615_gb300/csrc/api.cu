@@ -78,6 +78,7 @@ __global__ void ctl_setup_kernel(SolveCtl *ctl, double tol, int max_cycles, int 
     ctl->status = kCtlRunning;
     ctl->fixed = fixed;
     ctl->nrhs = nrhs;
+    ctl->learned_off = 0;
     if (pcg_tol) *pcg_tol = tol;
 }
 
@@ -133,6 +134,9 @@ __global__ void ctl_step_kernel(SolveCtl *ctl, const double *nr, const double *i
     c.cycles++;
     double rel[4];
     ctl_worst(c, nr, inst, ninst, rel);
+    // acceptance test of the learned correction: a residual that grew drops it for good
+    for (int q = 0; q < c.nrhs; q++)
+        if (rel[q] > c.rel[q]) c.learned_off = 1;
     ctl_decide(c, rel, tstat, cflag, h);
 }
 
@@ -355,12 +359,17 @@ void enqueue_iteration(Ctx &c, int R, int precision, cudaStream_t s, bool timed 
     const int64_t m = (int64_t)F.n * R;
     Chain ch = make_chain(c, s);
     if (precision == LBMG_MIXED) {
-        launch_to_float(c.rs, F.b32, m, s, F.x32, &ch);
+        if (c.learned_on) learned_enqueue(c, R, precision, s, &ch);   // the cycle starts from the correction
+        else launch_to_float(c.rs, F.b32, m, s, F.x32, &ch);
         enqueue_cycle<float>(c, R, s, timed, &ch);
         launch_add_float(c.xs, F.x32, m, s, &ch);
     } else {
-        cudaMemcpyAsync(F.b64, c.rs, m * sizeof(double), cudaMemcpyDeviceToDevice, s);
-        cudaMemsetAsync(F.x64, 0, m * sizeof(double), s);
+        if (c.learned_on) {
+            learned_enqueue(c, R, precision, s, &ch);
+        } else {
+            cudaMemcpyAsync(F.b64, c.rs, m * sizeof(double), cudaMemcpyDeviceToDevice, s);
+            cudaMemsetAsync(F.x64, 0, m * sizeof(double), s);
+        }
         enqueue_cycle<double>(c, R, s, timed, &ch);
         launch_add_double(c.xs, F.x64, m, s);
         ch.cut();
@@ -429,7 +438,7 @@ int get_graph(lbmg_handle h, int R, int precision, bool pcg, cudaGraphExec_t *ou
     Ctx &c = h->c;
     GraphCache &g = c.graph;
     if (g.exec && g.R == R && g.precision == precision && g.nu1 == c.nu1 && g.nu2 == c.nu2 && g.smoother == c.smoother &&
-        g.pcg == (int)pcg && g.cond == 0) {
+        g.pcg == (int)pcg && g.cond == 0 && g.learned == c.learned_on) {
         *out = g.exec;
         return LBMG_OK;
     }
@@ -449,6 +458,7 @@ int get_graph(lbmg_handle h, int R, int precision, bool pcg, cudaGraphExec_t *ou
     }
     g.R = R; g.precision = precision; g.nu1 = c.nu1; g.nu2 = c.nu2; g.smoother = c.smoother; g.pcg = pcg;
     g.cond = 0;
+    g.learned = c.learned_on;
     *out = g.exec;
     return LBMG_OK;
 }
@@ -501,7 +511,7 @@ int get_cond_graph(lbmg_handle h, int R, int precision, bool pcg, cudaGraphExec_
     Ctx &c = h->c;
     GraphCache &g = c.graph;
     if (g.exec && g.R == R && g.precision == precision && g.nu1 == c.nu1 && g.nu2 == c.nu2 && g.smoother == c.smoother &&
-        g.pcg == (int)pcg && g.cond == 1) {
+        g.pcg == (int)pcg && g.cond == 1 && g.learned == c.learned_on) {
         *out = g.exec;
         return LBMG_OK;
     }
@@ -521,6 +531,7 @@ int get_cond_graph(lbmg_handle h, int R, int precision, bool pcg, cudaGraphExec_
     }
     g.R = R; g.precision = precision; g.nu1 = c.nu1; g.nu2 = c.nu2; g.smoother = c.smoother; g.pcg = pcg;
     g.cond = 1;
+    g.learned = c.learned_on;
     *out = g.exec;
     return LBMG_OK;
 }
@@ -1094,7 +1105,7 @@ int lbmg_assemble(lbmg_handle h, double t, void *stream) {
     // the coarse-factor flag stays on the device: the next solve reports a failed factor
     c.assembled = true;
     c.t = t;
-    if (c.learned_on && learned_enable(c, 1, s) != 0) return LBMG_CUDA_ERROR;   // weights of the new matrix
+    learned_refresh(c, s);   // stencil features of the new matrix for the learned correction
     return LBMG_OK;
 }
 
@@ -1192,8 +1203,8 @@ static int solve_cond(lbmg_handle h, cudaGraphExec_t exec, const double *rd, con
         }
         stats->ms_total = ms;
         stats->ms_fine_smooth = 0.f;
-        stats->learned = 0;
-        stats->learned_fallback = 0;
+        stats->learned = (!pcg && c.learned_on) ? 1 : 0;
+        stats->learned_fallback = stats->learned && hc.learned_off ? 1 : 0;
         stats->host_syncs = h->syncs;
     }
     return status;
@@ -1298,6 +1309,10 @@ static int solve_impl(lbmg_handle h, const double *rhs, double *x, int nrhs, dou
     LBMG_TRY(input_ptr(h, x, cnt, 1, s, &xin));
     LBMG_TRY(output_ptr(h, x, cnt, 1, &xout, &host_out));
     if (!pcg && c.persistent && c.persist_ok && c.smoother == LBMG_GS_COLOURED) {
+        if (c.learned_on) {
+            g_cuda_err = "the learned correction runs on the graph and host-loop solves, not the persistent one";
+            return LBMG_INVALID_ARG;
+        }
         LBMG_CK(cudaEventRecord(c.ev0, s));
         launch_pack(rd, Fl.n, nrhs, R, c.bs, s, c.fperm);
         launch_pack(xin, Fl.n, nrhs, R, c.xs, s, c.fperm);
@@ -1352,8 +1367,9 @@ static int solve_impl(lbmg_handle h, const double *rhs, double *x, int nrhs, dou
             cudaEventElapsedTime(&ms, c.ev0, c.ev1);
             stats->ms_total = ms;
             stats->ms_fine_smooth = (float)(sns * 1e-6);
-            stats->learned = c.learned_on;
-            stats->learned_fallback = c.learned_on ? dfall : 0;
+            stats->learned = 0;
+            stats->learned_fallback = 0;
+            (void)dfall;
         }
         return status;
     }
@@ -1385,6 +1401,12 @@ static int solve_impl(lbmg_handle h, const double *rhs, double *x, int nrhs, dou
     int cycles = 0, status = LBMG_OK;
     float smooth_ms = 0.0f;
     bool conv = false;
+    const bool learned = !pcg && c.learned_on;
+    bool dropped = false;
+    if (learned) {
+        LBMG_CK(cudaMemsetAsync(&c.ctl->learned_off, 0, sizeof(int), s));
+        if (!check) launch_norms(c.rs, Fl.n, R, c.norm_part, c.norm_out, s);   // the correction reads them
+    }
     if (check) {
         launch_norms(c.bs, Fl.n, R, c.norm_part, c.norm_out, s);
         LBMG_TRY(read_norms(h, R, s, nb));
@@ -1403,10 +1425,17 @@ static int solve_impl(lbmg_handle h, const double *rhs, double *x, int nrhs, dou
             }
             if (bad) { status = LBMG_DIVERGED; break; }
             if (conv || cycles >= max_cycles) break;
+            double prev[4];
+            for (int r = 0; r < nrhs; r++) prev[r] = rel(r);
             if (exec) LBMG_CK(cudaGraphLaunch(exec, s));
             else if (pcg) enqueue_pcg_iteration(c, R, precision, s);
             else enqueue_iteration(c, R, precision, s);
             LBMG_TRY(read_norms(h, R, s, nr));
+            // acceptance test of the learned correction: a residual that grew drops it for good
+            if (learned && !dropped)
+                for (int r = 0; r < nrhs; r++)
+                    if (rel(r) > prev[r]) dropped = true;
+            if (dropped) LBMG_CK(cudaMemsetAsync(&c.ctl->learned_off, 1, sizeof(int), s));
             if (c.D > c.d0) {
                 float a0 = 0, a1 = 0;
                 if (cudaEventElapsedTime(&a0, c.ev_smooth[0], c.ev_smooth[1]) != cudaSuccess ||
@@ -1446,8 +1475,8 @@ static int solve_impl(lbmg_handle h, const double *rhs, double *x, int nrhs, dou
         stats->ms_total = ms;
         stats->ms_fine_smooth = smooth_ms;
         stats->host_syncs = h->syncs;
-        stats->learned = 0;
-        stats->learned_fallback = 0;
+        stats->learned = learned ? 1 : 0;
+        stats->learned_fallback = dropped ? 1 : 0;
         if (!check) stats->cycles = cycles;
     }
     return status;
@@ -1707,6 +1736,10 @@ int lbmg_tune_cache_load(const char *path) {
 static int learned_ready(lbmg_handle h, cudaStream_t s) {
     if (!h) return LBMG_INVALID_ARG;
     if (!h->c.assembled) return LBMG_NOT_ASSEMBLED;
+    if (h->c.ninst != 1) {
+        g_cuda_err = "the learned correction needs a single-mesh handle";
+        return LBMG_INVALID_ARG;
+    }
     const int st = learned_setup(h->c, s);
     if (st == 1) return LBMG_INVALID_ARG;
     if (st) return LBMG_OUT_OF_MEMORY;
@@ -1721,15 +1754,20 @@ int lbmg_learned_params(lbmg_handle h, double *get, const double *set, void *str
     return learned_params(h->c, get, set, s) ? LBMG_CUDA_ERROR : LBMG_OK;
 }
 
+int lbmg_learned_state(lbmg_handle h, double *get, const double *set, void *stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    LBMG_TRY(learned_ready(h, s));
+    if (set && !(set[3 * (size_t)learned_nparams()] >= 0)) return LBMG_INVALID_ARG;
+    return learned_state(h->c, get, set, s) ? LBMG_CUDA_ERROR : LBMG_OK;
+}
+
 int lbmg_learned_collect(lbmg_handle h, const double *rhs, int ns, int skip, int keep, void *stream) {
     cudaStream_t s = (cudaStream_t)stream;
-    if (!rhs || ns < 1 || skip < 0 || keep < 1) return LBMG_INVALID_ARG;
+    if (!rhs || ns < 1 || ns > 4 || skip < 0 || keep < 1) return LBMG_INVALID_ARG;
     LBMG_TRY(learned_ready(h, s));
     const double *rd;
     const size_t cnt = (size_t)h->c.lev[h->c.D].n * ns;
-    if (!on_device(rhs)) {
-        if (cnt > h->io_cap) return LBMG_INVALID_ARG;
-    }
+    if (!on_device(rhs) && cnt > h->io_cap) return LBMG_INVALID_ARG;
     LBMG_TRY(input_ptr(h, rhs, cnt, 0, s, &rd));
     return learned_collect(h->c, rd, ns, skip, keep, s) ? LBMG_CUDA_ERROR : LBMG_OK;
 }
@@ -1746,7 +1784,7 @@ int lbmg_learned_loss_grad(lbmg_handle h, const double *r0, int ns, double *loss
 int lbmg_learned_train(lbmg_handle h, int steps, double lr, const int *order, int batch, double *loss_hist,
                        void *stream) {
     cudaStream_t s = (cudaStream_t)stream;
-    if (steps < 0 || !order || batch < 1 || batch > 4 || !(lr > 0)) return LBMG_INVALID_ARG;
+    if (steps < 0 || !order || batch < 1 || batch > 8 || !(lr > 0)) return LBMG_INVALID_ARG;
     LBMG_TRY(learned_ready(h, s));
     const int st = learned_train(h->c, steps, lr, order, batch, loss_hist, s);
     return st == 1 ? LBMG_INVALID_ARG : (st ? LBMG_CUDA_ERROR : LBMG_OK);
@@ -1755,12 +1793,24 @@ int lbmg_learned_train(lbmg_handle h, int steps, double lr, const int *order, in
 int lbmg_learned_enable(lbmg_handle h, int on, void *stream) {
     cudaStream_t s = (cudaStream_t)stream;
     LBMG_TRY(learned_ready(h, s));
+    if (on && h->c.persistent) {
+        g_cuda_err = "the learned correction runs on the graph and host-loop solves, not the persistent one";
+        return LBMG_INVALID_ARG;
+    }
     return learned_enable(h->c, on, s) ? LBMG_CUDA_ERROR : LBMG_OK;
 }
 
-int lbmg_learned_omega(lbmg_handle h, double *omega) {
-    if (!h || !omega || !h->c.learned) return LBMG_INVALID_ARG;
-    return learned_omega(h->c, omega) ? LBMG_CUDA_ERROR : LBMG_OK;
+int lbmg_learned_apply(lbmg_handle h, const double *r, int ns, int precision, double *omega, double *delta,
+                       void *stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!r || !omega || !delta || ns < 1 || ns > 4) return LBMG_INVALID_ARG;
+    if (precision != LBMG_FP64 && precision != LBMG_MIXED) return LBMG_INVALID_ARG;
+    if (!on_device(r) || !on_device(omega) || !on_device(delta)) {
+        g_cuda_err = "lbmg_learned_apply: r, omega and delta must be device pointers";
+        return LBMG_INVALID_ARG;
+    }
+    LBMG_TRY(learned_ready(h, s));
+    return learned_apply(h->c, r, ns, precision, omega, delta, s) ? LBMG_CUDA_ERROR : LBMG_OK;
 }
 
 int lbmg_get_dofs(lbmg_handle h, int d, int *corner, int *mintri) {

@@ -123,6 +123,7 @@ struct GraphCache {
     cudaGraphExec_t exec = nullptr;
     int R = 0, precision = -1, nu1 = -1, nu2 = -1, smoother = -1, pcg = -1;
     int cond = -1;   // 1: the whole solve (conditional WHILE node), 0: one iteration
+    int learned = -1;   // the learned correction in front of each cycle
 };
 
 // Device-side control of a solve that runs as one graph launch: a conditional WHILE node
@@ -131,7 +132,9 @@ struct GraphCache {
 struct SolveCtl {
     double tol;
     int max_cycles, cycles, status, fixed;   // fixed: run exactly max_cycles iterations
-    int nrhs, pad[3];
+    int nrhs;
+    int learned_off;                         // a learned iteration raised a residual: plain cycles from now on
+    int pad[2];
     double nb[4], r0[4], rel[4];            // ||b||^2, initial and current relative residual per lane
 };
 enum { kCtlRunning = 0, kCtlConverged = 1, kCtlDiverged = 2, kCtlTimeout = 3, kCtlMaxCycles = 4, kCtlCoarse = 5 };
@@ -223,11 +226,9 @@ struct Ctx {
     void *persist_state = nullptr;    // 64 bytes: barrier, status, cycles, timer
     void *h_state = nullptr;          // pinned mirror: 64 bytes state + 16 doubles norms
     NarrowState narrow;               // shared-memory bottom of the V-cycle (narrow.cu)
-    // learned relaxation weights at the finest level (learned.cu)
+    // learned residual correction in front of each cycle (learned.cu)
     Learned *learned = nullptr;
     int learned_on = 0;
-    double *learned_dinv64 = nullptr;
-    float *learned_dinv32 = nullptr;
 };
 
 // ----- shared-memory bottom cycle (narrow.cu) -----
@@ -240,15 +241,19 @@ int autotune(Ctx &c, int R, int precision, int reps, cudaStream_t s, int *timed)
 int tune_cache_save(const char *path);
 int tune_cache_load(const char *path);
 
-// ----- learned relaxation weights (learned.cu) -----
+// ----- learned residual correction (learned.cu) -----
 int learned_setup(Ctx &c, cudaStream_t s);
 void learned_free(Ctx &c);
 int learned_params(Ctx &c, double *get, const double *set, cudaStream_t s);
+int learned_state(Ctx &c, double *get, const double *set, cudaStream_t s);
 int learned_collect(Ctx &c, const double *rhs_user, int ns, int skip, int keep, cudaStream_t s);
 int learned_loss_grad(Ctx &c, const double *r0_user, int ns, double *loss, double *grad, cudaStream_t s);
 int learned_train(Ctx &c, int steps, double lr, const int *order, int batch, double *loss_hist, cudaStream_t s);
 int learned_enable(Ctx &c, int on, cudaStream_t s);
-int learned_omega(Ctx &c, double *omega_user);
+void learned_refresh(Ctx &c, cudaStream_t s);
+void learned_enqueue(Ctx &c, int R, int precision, cudaStream_t s, Chain *ch);
+int learned_apply(Ctx &c, const double *r_user, int ns, int precision, double *omega_dev, double *delta_dev,
+                  cudaStream_t s);
 int learned_nparams();
 
 // ----- persistent solve (persist.cu) -----

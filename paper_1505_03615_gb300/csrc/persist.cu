@@ -95,7 +95,6 @@ struct Lv {
     int n, ns, ncb;
     int cs[9];
     const int *cb;                  // this level's coarsest blocks: (level, mesh, first row, rows, inverse offset)
-    const T *dinvL;                 // learned omega / a_ii (finest level, when enabled), else null
     const int *rp, *ci;
     const T *A, *dinv;
     const int *par;
@@ -141,8 +140,8 @@ __device__ __forceinline__ void row_dot(const Lv<T, R> &L, int row, bool active,
 }
 
 template <class T, int R>
-__device__ void gs_colour(const Lv<T, R> &L, int c, Team tm, bool learned = false) {
-    const T *dv = (learned && L.dinvL) ? L.dinvL : L.dinv;
+__device__ void gs_colour(const Lv<T, R> &L, int c, Team tm) {
+    const T *dv = L.dinv;
     for_rows<T, R>(L.cs[c], L.cs[c + 1], tm, [&](int row, bool active, int lane) {
         T acc[R];
         row_dot<T, R>(L, row, active, lane, L.x, acc);
@@ -287,7 +286,6 @@ struct PersistParams {
     int nitems, ninst;
     double *part;             // [nitems][8]
     double *norm;             // [ninst][16]: ||r||^2, ||b||^2, initial ||r||^2, previous ||r||^2 (4 each)
-    int *fallback;            // set when a learned cycle did not reduce some residual
     unsigned *bar;
     unsigned expected;        // arrivals that complete a barrier
     int *status;
@@ -302,7 +300,6 @@ __global__ void __launch_bounds__(1024, 1) solve_persistent_kernel(PersistParams
     const Team blk{(int)threadIdx.x, (int)blockDim.x};
     const bool b0 = blockIdx.x == 0;
     unsigned long long t_smooth = 0;
-    bool use_learned = lev[p.D].dinvL != nullptr;
 
     // per-mesh norms of the FP64 residual rs (and, the first time, of bs): one warp per
     // work item (a chunk of the rows of one mesh and colour), then block 0 adds the
@@ -343,7 +340,6 @@ __global__ void __launch_bounds__(1024, 1) solve_persistent_kernel(PersistParams
                 if (q < 4) {
                     const double prev = p.norm[16 * m + q];
                     p.norm[16 * m + 12 + q] = prev;
-                    if (!with_b && use_learned && q < p.nrhs && !(s < prev)) atomicExch(p.fallback, 1);
                 }
                 p.norm[16 * m + q] = s;
             }
@@ -417,7 +413,7 @@ __global__ void __launch_bounds__(1024, 1) solve_persistent_kernel(PersistParams
             for (int s = 0; s < p.nu1; s++)
                 for (int c = 0; c < 8; c++) {
                     if (L.cs[c + 1] == L.cs[c]) continue;
-                    gs_colour<T, R>(L, c, grid, use_learned && d == p.D);
+                    gs_colour<T, R>(L, c, grid);
                     if (!grid_sync(p.bar, p.status, p.expected)) return;
                 }
             if (d == p.D && b0 && threadIdx.x == 0) t_smooth += globaltimer() - t0;
@@ -440,7 +436,7 @@ __global__ void __launch_bounds__(1024, 1) solve_persistent_kernel(PersistParams
             for (int s = 0; s < p.nu2; s++)
                 for (int c = 7; c >= 0; c--) {
                     if (L.cs[c + 1] == L.cs[c]) continue;
-                    gs_colour<T, R>(L, c, grid, use_learned && d == p.D);
+                    gs_colour<T, R>(L, c, grid);
                     if (!grid_sync(p.bar, p.status, p.expected)) return;
                 }
             if (d == p.D && b0 && threadIdx.x == 0) t_smooth += globaltimer() - t0;
@@ -454,13 +450,11 @@ __global__ void __launch_bounds__(1024, 1) solve_persistent_kernel(PersistParams
         fine_residual();
         if (!grid_sync(p.bar, p.status, p.expected)) return;
         if (!norms(false)) return;
-        if (use_learned && *(volatile int *)p.fallback) use_learned = false;   // plain sweeps from now on
     }
     if (b0 && threadIdx.x == 0) {
         *p.cycles = cyc;
         *p.smooth_ns = t_smooth;
     }
-    (void)use_learned;
 }
 
 // host side -------------------------------------------------------------------
@@ -505,9 +499,6 @@ static void fill_views(const Ctx &c, std::vector<char> &buf) {
             o.x = (T *)L.x64; o.b = (T *)L.b64; o.r = (T *)L.r64;
         }
         o.par = L.par; o.npl2 = L.npl2; o.crp = L.crp; o.cch = L.cch;
-        o.dinvL = nullptr;
-        if (d == c.D && c.learned_on)
-            o.dinvL = (sizeof(T) == 4) ? (const T *)(const void *)c.learned_dinv32 : (const T *)(const void *)c.learned_dinv64;
     }
 }
 
@@ -586,7 +577,6 @@ int persist_solve(Ctx &c, int precision, int R, int nrhs, double tol, int max_cy
     prm.status = reinterpret_cast<int *>(st + 16);
     prm.cycles = reinterpret_cast<int *>(st + 20);
     prm.smooth_ns = reinterpret_cast<unsigned long long *>(st + 24);
-    prm.fallback = reinterpret_cast<int *>(st + 32);
     const int B = c.persist_blocks;
     if (f32) {
         if (R == 1) return launch_persist_t<float, 1>(prm, B, s);
