@@ -557,6 +557,9 @@ def main():
     ap.add_argument("--persistent", action="store_true", help="one cooperative launch per solve")
     ap.add_argument("--no-graphs", action="store_true", help="launch each cycle's kernels directly (profilers)")
     ap.add_argument("--only-timed", action="store_true", help="stop after the timed steps (profiling runs)")
+    ap.add_argument("--learned-zero", action="store_true",
+                    help="with --only-timed: time the solve with the learned correction of the zero network (the "
+                         "Jacobi start; the same kernels and cost as a trained one) instead of plain cycles")
     ap.add_argument("--no-pdl", action="store_true", help="plain stream order between the cycle's kernels")
     ap.add_argument("--no-tune", action="store_true", help="default launch shapes (no autotuning at setup)")
     ap.add_argument("--no-learned", action="store_true",
@@ -632,6 +635,12 @@ def main():
     x = torch.zeros_like(rhs)
     u = torch.zeros((nv, nrhs), dtype=torch.float64, device=dev)
     max_cycles = args.max_cycles
+
+    if args.learned_zero:
+        if not args.only_timed:
+            raise SystemExit("--learned-zero is a profiling switch: use it with --only-timed")
+        L.lbmg_learned_params(h, np.zeros(L.lbmg_learned_nparams()))
+        L.lbmg_learned_enable(h, True)
 
     def step(precision=L.LBMG_MIXED):
         L.lbmg_assemble(h, t)

@@ -333,9 +333,13 @@ int lbmg_launch_shape(lbmg_handle h, int d, int precision, int *out);
    launch; 0 where the shape came from the cache or was set by hand.  Host only. */
 int lbmg_tuned_times(lbmg_handle h, int d, int precision, float *ms);
 /* set a launch shape of level d by hand: kind 0 = Gauss-Seidel sweep, 1 = residual;
-   tpr in {4, 8, 16} (see lbmg_autotune); tpb a multiple of 32 in [32, 512]
-   (LBMG_INVALID_ARG otherwise).  Results change only by the summation order inside a
-   row.  Host only. */
+   tpr in {4, 8, 16} (see lbmg_autotune); tpb a multiple of 32 in [32, 512], or, for an
+   LBMG_MIXED sweep with tpr = 4, tpb = 1024: the whole sweep (all colour steps of the
+   sweeps of one smoothing) in one cooperative launch of the packed-copy kernel, whose
+   blocks meet at a bounded grid barrier between colours (a timeout gives
+   LBMG_DEVICE_TIMEOUT); it computes exactly what the colour launches of tpr = 4 compute.
+   LBMG_INVALID_ARG otherwise.  Results change only by the summation order inside a row.
+   Host only. */
 int lbmg_set_launch_shape(lbmg_handle h, int d, int precision, int kind, int tpr, int tpb);
 /* options.host_check of an existing handle (0 or 1; LBMG_INVALID_ARG otherwise).  Host only. */
 int lbmg_set_host_check(lbmg_handle h, int on);

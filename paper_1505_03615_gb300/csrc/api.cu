@@ -240,17 +240,14 @@ template <> struct P<double> {
 
 template <class T>
 void enqueue_smooth(Ctx &c, DevLevel &L, int R, int sweeps, bool forward, cudaStream_t s, Chain *ch) {
-    for (int sw = 0; sw < sweeps; sw++) {
-        if (c.smoother == LBMG_JACOBI) {
+    if (c.smoother == LBMG_JACOBI) {
+        for (int sw = 0; sw < sweeps; sw++) {
             launch_residual<T>(L, P<T>::A(L), P<T>::b(L), P<T>::x(L), P<T>::r(L), R, s, L.ns, ch);
             launch_jacobi_update<T>(L, P<T>::dinv(L), P<T>::r(L), P<T>::x(L), (T)c.omega, R, s);
             if (ch) ch->cut();
-        } else {
-            for (int q = 0; q < 8; q++) {
-                const int colour = forward ? q : 7 - q;
-                launch_smooth_colour<T>(L, colour, P<T>::A(L), P<T>::dinv(L), P<T>::b(L), P<T>::x(L), R, s, ch);
-            }
         }
+    } else {
+        launch_sweeps<T>(c, L, sweeps, forward, P<T>::A(L), P<T>::dinv(L), P<T>::b(L), P<T>::x(L), R, s, ch);
     }
 }
 
@@ -617,6 +614,8 @@ int upload_hierarchy(lbmg_handle h) {
             if (packed_layout(hl, gq, rows, map, col, L.pk_gs, &L.pk_total)) {
                 std::vector<int2> gq2(gq.size() / 2);
                 for (size_t g = 0; g < gq2.size(); g++) gq2[g] = make_int2(gq[2 * g], gq[2 * g + 1]);
+                for (int q = 0; q < 10; q++)
+                    L.pk_es[q] = L.pk_gs[q] < (int)gq2.size() ? (int64_t)(unsigned)gq2[L.pk_gs[q]].x * 32 : L.pk_total;
                 LBMG_TRY(h->upload(&L.pk_gq, gq2));
                 LBMG_TRY(h->upload(&L.pk_rows, rows));
                 LBMG_TRY(h->upload(&L.pk_map, map));
@@ -716,6 +715,9 @@ int upload_hierarchy(lbmg_handle h) {
     LBMG_TRY(h->alloc(&c.norm_out, 8));
     LBMG_CK(cudaMemset(c.norm_out, 0, 8 * sizeof(double)));
     c.narrow.status = reinterpret_cast<int *>(c.norm_out + 4);
+    LBMG_TRY(h->alloc(&c.sweep_bar, 1));
+    for (int r : {1, 2, 4}) c.sweep_blocks[r] = packed_sweep_blocks(r);
+    cudaGetLastError();
     h->io_cap = 4 * std::max(std::max(nD, (size_t)c.nv), (size_t)c.nu);
     LBMG_TRY(h->alloc(&c.dev_io, 2 * h->io_cap));
     LBMG_CK(cudaMallocHost((void **)&c.h_norm, 8 * sizeof(double)));
@@ -1708,7 +1710,10 @@ int lbmg_set_launch_shape(lbmg_handle h, int d, int precision, int kind, int tpr
     LBMG_TRY(check_level(h, d));
     if (precision != LBMG_FP64 && precision != LBMG_MIXED) return LBMG_INVALID_ARG;
     if (kind != 0 && kind != 1) return LBMG_INVALID_ARG;
-    if ((tpr != 4 && tpr != 8 && tpr != 16) || tpb < 32 || tpb > 512 || tpb % 32 != 0) return LBMG_INVALID_ARG;
+    // tpb = 1024 with 4 threads per row: the whole-sweep cooperative kernel (FP32 sweeps only)
+    const bool sweep = tpb == kSweepShapeTpb && tpr == 4 && kind == kShapeSmooth && precision == LBMG_MIXED;
+    if ((tpr != 4 && tpr != 8 && tpr != 16) || tpb < 32 || (tpb > 512 && !sweep) || tpb % 32 != 0)
+        return LBMG_INVALID_ARG;
     LaunchShape &sh = h->c.lev[d].shape[precision == LBMG_FP64][kind];
     sh.tpr = tpr;
     sh.tpb = tpb;

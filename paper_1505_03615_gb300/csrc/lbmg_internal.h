@@ -17,8 +17,9 @@ constexpr int kNormBlocks = 256;  // partial sums of the two-pass norm reduction
 // tpr threads share one matrix row (4, 8 or 16), tpb threads per block (128-512).  With
 // 4 threads per row the kernels read the packed copy of the matrix (packed.cu).
 struct LaunchShape {
-    int tpr = 4, tpb = 256;
+    int tpr = 4, tpb = 256;   // Gauss-Seidel with tpb = 1024: the whole-sweep cooperative kernel (packed.cu)
 };
+constexpr int kSweepShapeTpb = 1024;
 enum { kShapeSmooth = 0, kShapeResidual = 1 };
 
 // Programmatic dependent launch (sm_90 and later).  A kernel launched with
@@ -92,6 +93,7 @@ struct DevLevel {
     double *pk_v64 = nullptr;              // [total] FP64 values
     int64_t pk_total = 0;
     int pk_gs[10] = {0};                   // group ranges of colours 0..7, then rows [ns, n)
+    int64_t pk_es[10] = {0};               // entry offset of the first group of each range (pk_es[9]: total)
     LaunchShape shape[2][2];               // [FP64][kShapeSmooth / kShapeResidual], set by the autotuner
     float tuned_ms[2][2] = {{0, 0}, {0, 0}};   // device time of the chosen shape when the tuner timed it
 };
@@ -226,6 +228,9 @@ struct Ctx {
     void *persist_state = nullptr;    // 64 bytes: barrier, status, cycles, timer
     void *h_state = nullptr;          // pinned mirror: 64 bytes state + 16 doubles norms
     NarrowState narrow;               // shared-memory bottom of the V-cycle (narrow.cu)
+    // whole-sweep cooperative kernel (packed.cu): arrival counter and grid per lane count
+    unsigned *sweep_bar = nullptr;
+    int sweep_blocks[5] = {0, 0, 0, 0, 0};
     // learned residual correction in front of each cycle (learned.cu)
     Learned *learned = nullptr;
     int learned_on = 0;
@@ -293,14 +298,27 @@ void launch_packed_fill(const DevLevel &L, cudaStream_t s);
 // packed Gauss-Seidel colour / residual over rows [0, nrows); false when the level or the
 // matrix has no packed copy (the caller then uses the CSR kernels)
 template <class T> bool launch_packed_smooth(const DevLevel &L, int colour, const T *A, const T *dinv, const T *b,
-                                             T *x, int R, int tpb, cudaStream_t s, Chain *ch);
+                                             T *x, int R, int tpb, cudaStream_t s, Chain *ch, int next = -1);
 template <class T> bool launch_packed_residual(const DevLevel &L, const T *A, const T *b, const T *x, T *r, int R,
                                                int nrows, int tpb, cudaStream_t s, Chain *ch);
+// a colour sequence (FP32) in one cooperative launch; bar: a device counter, status: the
+// bounded-wait word; false if the level has no packed copy or the launch is refused
+bool launch_packed_sweep(const DevLevel &L, const int *seq, int nseq, const float *dinv, const float *b, float *x,
+                         int R, unsigned *bar, int *status, int blocks, cudaStream_t s);
+int packed_sweep_blocks(int R);   // the grid of the sweep kernel (resident blocks per SM x SMs)
 
 // ----- kernels (relax.cu) -----
 // vectors below are [n][R] with stride R in {1, 2, 4} (3 right-hand sides padded to 4)
+// `sweeps` Gauss-Seidel sweeps of level L (colours 0..7, or 7..0 backwards): one cooperative
+// launch per call when the level's tuned shape is the whole-sweep kernel (FP32), else one
+// launch per colour, each prefetching the next colour's entries
+template <class T> void launch_sweeps(const Ctx &c, const DevLevel &L, int sweeps, bool forward, const T *A,
+                                      const T *dinv, const T *b, T *x, int R, cudaStream_t s, Chain *ch);
+// next: the colour launched after this one on the same level (-1: none); its packed entries
+// are prefetched into L2 while this colour runs
 template <class T> void launch_smooth_colour(const DevLevel &L, int colour, const T *A, const T *dinv,
-                                             const T *b, T *x, int R, cudaStream_t s, Chain *ch = nullptr);
+                                             const T *b, T *x, int R, cudaStream_t s, Chain *ch = nullptr,
+                                             int next = -1);
 template <class T> void launch_residual(const DevLevel &L, const T *A, const T *b, const T *x, T *r, int R,
                                         cudaStream_t s, int nrows = -1, Chain *ch = nullptr);
 template <class T> void launch_jacobi_update(const DevLevel &L, const T *dinv, const T *r, T *x, T omega, int R,

@@ -30,6 +30,7 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kPkPrefetch = 8;   // quads per lane held in registers before the grid-dependency wait
+constexpr int kMaxSweepColours = 32;
 
 template <class T> struct PkMat;
 template <> struct PkMat<float> {
@@ -80,7 +81,17 @@ template <class T, int R, bool kGs>
 __global__ void __launch_bounds__(512) pk_row_kernel(int g0, int g1, const int2 *__restrict__ gq,
                                                      const int *__restrict__ rows, PkMat<T> m,
                                                      const T *__restrict__ dinv, const T *__restrict__ b, T *x,
-                                                     T *__restrict__ r) {
+                                                     T *__restrict__ r, const char *__restrict__ pf, int64_t pf_bytes,
+                                                     int pf_chunk) {
+    // the next colour's entries into L2 (static data, so before the grid-dependency wait):
+    // one bulk prefetch of a 256-byte-aligned slice per block
+    if (pf && threadIdx.x == 0) {
+        const int64_t off = (int64_t)blockIdx.x * pf_chunk;
+        if (off < pf_bytes) {
+            const unsigned len = (unsigned)(pf_bytes - off < pf_chunk ? pf_bytes - off : pf_chunk);
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(pf + off), "r"(len) : "memory");
+        }
+    }
     const int lane = threadIdx.x & 31;
     const int g = g0 + (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
     if (g >= g1) return;   // whole warps only (blockDim is a multiple of 32)
@@ -161,15 +172,183 @@ template <class T> const T *level_A(const DevLevel &L);
 template <> const float *level_A<float>(const DevLevel &L) { return L.A32; }
 template <> const double *level_A<double>(const DevLevel &L) { return L.A64; }
 
+// pf, pf_bytes: a byte range to prefetch into L2 (null: none), split over the blocks in
+// 256-byte-aligned slices
 template <class T, bool kGs>
 void launch_rows(const DevLevel &L, int g0, int g1, const T *dinv, const T *b, T *x, T *r, int R, int tpb,
-                 cudaStream_t s, Chain *ch) {
+                 cudaStream_t s, Chain *ch, const char *pf = nullptr, int64_t pf_bytes = 0) {
     if (g1 <= g0) return;
     tpb = std::max(32, std::min(512, tpb / 32 * 32));
     const unsigned blocks = (unsigned)(((int64_t)(g1 - g0) * 32 + tpb - 1) / tpb);
+    int chunk = 0;
+    if (pf && pf_bytes > 0) {
+        const int64_t per = (pf_bytes + blocks - 1) / blocks;
+        chunk = (int)std::min<int64_t>((per + 255) / 256 * 256, 1 << 20);
+        if ((int64_t)chunk * blocks < pf_bytes) pf = nullptr;   // slices would not cover it: skip
+    } else {
+        pf = nullptr;
+    }
     auto k = R == 1 ? pk_row_kernel<T, 1, kGs> : R == 2 ? pk_row_kernel<T, 2, kGs> : pk_row_kernel<T, 4, kGs>;
     klaunch(k, blocks, (unsigned)tpb, 0, s, ch, g0, g1, (const int2 *)L.pk_gq, (const int *)L.pk_rows, pk_mat<T>(L),
-            dinv, b, x, r);
+            dinv, b, x, r, pf, pf ? pf_bytes : (int64_t)0, chunk);
+}
+
+// ---- the finest level's whole sweep (all its colour steps) in one cooperative launch ----
+// The colour launches of a sweep are serialised: each waits for the previous one to drain
+// and fills the GPU again.  Here one block per SM walks the colour sequence and the blocks
+// meet at a grid barrier between colours; before the barrier every warp loads the header
+// and entries of its first group of the next colour, so that after it only the x gathers
+// remain.  x is read with L2-only loads (another SM may have written it in the previous
+// colour).  The barrier is bounded: after about a second it sets *status and every block
+// returns.
+struct SweepArgs {
+    const int2 *gq;
+    const int *rows;
+    const int2 *e;
+    const float *dinv, *b;
+    float *x;
+    int gs[9];
+    int seq[kMaxSweepColours];
+    int nseq;
+    unsigned *bar;   // arrival counter, zero at launch
+    int *status;
+};
+
+__device__ __forceinline__ unsigned sweep_ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long sweep_timer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// barrier k completes when the counter reaches (k + 1) * gridDim.x; false after a timeout
+__device__ bool sweep_sync(unsigned *bar, int *status, unsigned target) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
+        const unsigned long long t0 = sweep_timer();
+        unsigned long long spins = 0;
+        while (sweep_ld_acquire(bar) < target) {
+            ++spins;
+            if (((spins & 1023) == 0 && sweep_timer() - t0 > 1000000000ull) || spins > (1ull << 28)) {
+                atomicExch(status, 1);
+                ok = 0;
+                break;
+            }
+            if (*(volatile int *)status != 0) { ok = 0; break; }   // another block gave up
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <int R>
+__device__ __forceinline__ void ldcg_row(const float *p, float (&v)[R]) {
+#pragma unroll
+    for (int r = 0; r < R; r++) v[r] = __ldcg(p + r);
+}
+template <>
+__device__ __forceinline__ void ldcg_row<4>(const float *p, float (&v)[4]) {
+    const float4 q = __ldcg(reinterpret_cast<const float4 *>(p));
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+
+// the static part of one group: header, this lane's row and its first kPkPrefetch quads
+struct GroupRegs {
+    int64_t base;
+    int Q, row;
+    float d;
+    int j[kPkPrefetch];
+    float a[kPkPrefetch];
+};
+
+__device__ __forceinline__ void load_group(const SweepArgs &p, int g, int lane, GroupRegs &G) {
+    const int2 hd = __ldg(p.gq + g);
+    G.base = (int64_t)(unsigned)hd.x * 32;
+    G.Q = hd.y;
+    G.row = __ldg(p.rows + 8 * (size_t)g + (lane >> 2));
+    G.d = (G.row >= 0 && (lane & 3) == 0) ? __ldg(p.dinv + G.row) : 0.f;
+#pragma unroll
+    for (int q = 0; q < kPkPrefetch; q++) {
+        G.j[q] = -1;
+        G.a[q] = 0.f;
+        if (q < G.Q) {
+            const int2 v = __ldg(p.e + G.base + 32 * q + lane);
+            G.j[q] = v.x;
+            G.a[q] = __int_as_float(v.y);
+        }
+    }
+}
+
+template <int R>
+__device__ __forceinline__ void relax_group(const SweepArgs &p, int lane, const GroupRegs &G) {
+    const bool lead = G.row >= 0 && (lane & 3) == 0;
+    float bv[R], xo[R], acc[R];
+    if (lead) {
+#pragma unroll
+        for (int c = 0; c < R; c++) bv[c] = __ldg(p.b + (size_t)G.row * R + c);
+        ldcg_row<R>(p.x + (size_t)G.row * R, xo);
+    }
+#pragma unroll
+    for (int c = 0; c < R; c++) acc[c] = 0.f;
+#pragma unroll
+    for (int q = 0; q < kPkPrefetch; q++) {
+        if (G.j[q] >= 0) {
+            float xv[R];
+            ldcg_row<R>(p.x + (size_t)G.j[q] * R, xv);
+#pragma unroll
+            for (int c = 0; c < R; c++) acc[c] = fmaf(G.a[q], xv[c], acc[c]);
+        }
+    }
+    for (int q = kPkPrefetch; q < G.Q; q++) {   // rows of more than 32 entries
+        const int2 v = __ldg(p.e + G.base + 32 * q + lane);
+        if (v.x >= 0) {
+            float xv[R];
+            ldcg_row<R>(p.x + (size_t)v.x * R, xv);
+#pragma unroll
+            for (int c = 0; c < R; c++) acc[c] = fmaf(__int_as_float(v.y), xv[c], acc[c]);
+        }
+    }
+#pragma unroll
+    for (int o = 2; o > 0; o >>= 1)
+#pragma unroll
+        for (int c = 0; c < R; c++) acc[c] += __shfl_xor_sync(kFull, acc[c], o, 4);
+    if (lead) {
+#pragma unroll
+        for (int c = 0; c < R; c++) p.x[(size_t)G.row * R + c] = xo[c] + (bv[c] - acc[c]) * G.d;
+    }
+}
+
+template <int R>
+__global__ void __launch_bounds__(1024, 1) pk_sweep_kernel(SweepArgs p) {
+    const int lane = threadIdx.x & 31;
+    const int wid = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+    const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+    GroupRegs G;
+    {
+        const int c = p.seq[0];
+        if (p.gs[c] + wid < p.gs[c + 1]) load_group(p, p.gs[c] + wid, lane, G);
+    }
+    for (int si = 0; si < p.nseq; si++) {
+        const int c = p.seq[si];
+        for (int g = p.gs[c] + wid; g < p.gs[c + 1]; g += nw) {
+            if (g != p.gs[c] + wid) load_group(p, g, lane, G);
+            relax_group<R>(p, lane, G);
+        }
+        if (si + 1 < p.nseq) {
+            const int cn = p.seq[si + 1];
+            if (p.gs[cn] + wid < p.gs[cn + 1]) load_group(p, p.gs[cn] + wid, lane, G);
+            if (!sweep_sync(p.bar, p.status, (unsigned)(si + 1) * gridDim.x)) return;
+        }
+    }
 }
 
 }  // namespace
@@ -242,9 +421,15 @@ void launch_packed_fill(const DevLevel &L, cudaStream_t s) {
 
 template <class T>
 bool launch_packed_smooth(const DevLevel &L, int colour, const T *A, const T *dinv, const T *b, T *x, int R, int tpb,
-                          cudaStream_t s, Chain *ch) {
+                          cudaStream_t s, Chain *ch, int next) {
     if (!L.pk_map || A != level_A<T>(L)) return false;
-    launch_rows<T, true>(L, L.pk_gs[colour], L.pk_gs[colour + 1], dinv, b, x, nullptr, R, tpb, s, ch);
+    const char *pf = nullptr;
+    int64_t pf_bytes = 0;
+    if (sizeof(T) == 4 && next >= 0 && next < 8) {   // FP32 entries: (column, value) pairs
+        pf = reinterpret_cast<const char *>(L.pk_e32 + L.pk_es[next]);
+        pf_bytes = (L.pk_es[next + 1] - L.pk_es[next]) * (int64_t)sizeof(int2);
+    }
+    launch_rows<T, true>(L, L.pk_gs[colour], L.pk_gs[colour + 1], dinv, b, x, nullptr, R, tpb, s, ch, pf, pf_bytes);
     return true;
 }
 
@@ -261,10 +446,57 @@ bool launch_packed_residual(const DevLevel &L, const T *A, const T *b, const T *
     return true;
 }
 
+// the whole sweep sequence `seq` (colours, in order) of level L in one cooperative launch;
+// false when the level has no packed copy or the launch is refused
+bool launch_packed_sweep(const DevLevel &L, const int *seq, int nseq, const float *dinv, const float *b, float *x,
+                         int R, unsigned *bar, int *status, int blocks, cudaStream_t s) {
+    if (!L.pk_map || nseq < 1 || nseq > kMaxSweepColours || blocks < 1) return false;
+    SweepArgs p;
+    p.gq = (const int2 *)L.pk_gq;
+    p.rows = L.pk_rows;
+    p.e = L.pk_e32;
+    p.dinv = dinv;
+    p.b = b;
+    p.x = x;
+    for (int q = 0; q < 9; q++) p.gs[q] = L.pk_gs[q];
+    for (int q = 0; q < kMaxSweepColours; q++) p.seq[q] = q < nseq ? seq[q] : 0;
+    p.nseq = nseq;
+    p.bar = bar;
+    p.status = status;
+    if (cudaMemsetAsync(bar, 0, sizeof(unsigned), s) != cudaSuccess) return false;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)blocks);
+    cfg.blockDim = dim3(1024);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaError_t e;
+    if (R == 1) e = cudaLaunchKernelEx(&cfg, pk_sweep_kernel<1>, p);
+    else if (R == 2) e = cudaLaunchKernelEx(&cfg, pk_sweep_kernel<2>, p);
+    else e = cudaLaunchKernelEx(&cfg, pk_sweep_kernel<4>, p);
+    return e == cudaSuccess;
+}
+
+// resident blocks of the sweep kernel (1024 threads) per SM times the SMs: the largest grid a
+// cooperative launch accepts
+int packed_sweep_blocks(int R) {
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    cudaError_t e = R == 1   ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pk_sweep_kernel<1>, 1024, 0)
+                    : R == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pk_sweep_kernel<2>, 1024, 0)
+                             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pk_sweep_kernel<4>, 1024, 0);
+    if (e != cudaSuccess) return 0;
+    return per * sms;
+}
+
 template bool launch_packed_smooth<float>(const DevLevel &, int, const float *, const float *, const float *, float *,
-                                          int, int, cudaStream_t, Chain *);
+                                          int, int, cudaStream_t, Chain *, int);
 template bool launch_packed_smooth<double>(const DevLevel &, int, const double *, const double *, const double *,
-                                           double *, int, int, cudaStream_t, Chain *);
+                                           double *, int, int, cudaStream_t, Chain *, int);
 template bool launch_packed_residual<float>(const DevLevel &, const float *, const float *, const float *, float *,
                                             int, int, int, cudaStream_t, Chain *);
 template bool launch_packed_residual<double>(const DevLevel &, const double *, const double *, const double *,

@@ -161,16 +161,42 @@ ResidualFn<T> residual_fn(int tpr) {
 }
 
 template <class T>
+void launch_sweeps(const Ctx &c, const DevLevel &L, int sweeps, bool forward, const T *A, const T *dinv, const T *b,
+                   T *x, int R, cudaStream_t s, Chain *ch) {
+    if (sweeps <= 0) return;
+    const LaunchShape &sh = L.shape[sizeof(T) == 8][kShapeSmooth];
+    if (sizeof(T) == 4 && sh.tpb == kSweepShapeTpb && 8 * sweeps <= 32 && c.sweep_bar && A == (const T *)L.A32) {
+        int seq[32];
+        for (int q = 0; q < 8 * sweeps; q++) seq[q] = forward ? q % 8 : 7 - q % 8;
+        const int blocks = c.sweep_blocks[R];
+        if (ch) ch->cut();   // a cooperative launch takes no programmatic serialisation
+        if (launch_packed_sweep(L, seq, 8 * sweeps, (const float *)dinv, (const float *)b, (float *)x, R, c.sweep_bar,
+                                c.narrow.status, blocks, s))
+            return;
+        cudaGetLastError();   // refused: the per-colour launches below
+    }
+    for (int sw = 0; sw < sweeps; sw++)
+        for (int q = 0; q < 8; q++) {
+            const int colour = forward ? q : 7 - q;
+            // the colour that follows on this level: the next of this sweep, or the first of the next sweep
+            const int nq = q < 7 ? q + 1 : (sw + 1 < sweeps ? 0 : -1);
+            const int next = nq < 0 ? -1 : (forward ? nq : 7 - nq);
+            launch_smooth_colour<T>(L, colour, A, dinv, b, x, R, s, ch, next);
+        }
+}
+
+template <class T>
 void launch_smooth_colour(const DevLevel &L, int colour, const T *A, const T *dinv, const T *b, T *x, int R,
-                          cudaStream_t s, Chain *ch) {
+                          cudaStream_t s, Chain *ch, int next) {
     const int r0 = L.cs[colour], r1 = L.cs[colour + 1];
     if (r1 <= r0) return;
     const LaunchShape &sh = L.shape[sizeof(T) == 8][kShapeSmooth];
     // four threads per row: the packed copy of the matrix (one 256-byte load per warp and quad)
-    if (sh.tpr == 4 && launch_packed_smooth<T>(L, colour, A, dinv, b, x, R, sh.tpb, s, ch)) return;
-    const unsigned blocks = (unsigned)(((int64_t)(r1 - r0) * sh.tpr + sh.tpb - 1) / sh.tpb);
+    const int tpb = sh.tpb == kSweepShapeTpb ? 256 : sh.tpb;   // one colour of a whole-sweep level
+    if (sh.tpr == 4 && launch_packed_smooth<T>(L, colour, A, dinv, b, x, R, tpb, s, ch, next)) return;
+    const unsigned blocks = (unsigned)(((int64_t)(r1 - r0) * sh.tpr + tpb - 1) / tpb);
     const SmoothFn<T> k = R == 1 ? smooth_fn<T, 1>(sh.tpr) : R == 2 ? smooth_fn<T, 2>(sh.tpr) : smooth_fn<T, 4>(sh.tpr);
-    klaunch(k, blocks, (unsigned)sh.tpb, 0, s, ch, r0, r1, L.rp, L.ci, A, dinv, b, x);
+    klaunch(k, blocks, (unsigned)tpb, 0, s, ch, r0, r1, L.rp, L.ci, A, dinv, b, x);
 }
 
 template <class T>
@@ -739,8 +765,10 @@ void launch_add_double(double *x, const double *e, int64_t n, cudaStream_t s) {
 
 // explicit instantiations
 #define LBMG_INST(T)                                                                                           \
+    template void launch_sweeps<T>(const Ctx &, const DevLevel &, int, bool, const T *, const T *, const T *, T *, \
+                                   int, cudaStream_t, Chain *);                                               \
     template void launch_smooth_colour<T>(const DevLevel &, int, const T *, const T *, const T *, T *, int,   \
-                                          cudaStream_t, Chain *);                                              \
+                                          cudaStream_t, Chain *, int);                                         \
     template void launch_residual<T>(const DevLevel &, const T *, const T *, const T *, T *, int, cudaStream_t, int, \
                                      Chain *);                                                                 \
     template void launch_jacobi_update<T>(const DevLevel &, const T *, const T *, T *, T, int, cudaStream_t);   \

@@ -65,8 +65,7 @@ cudaError_t time_kernel(Ctx &c, DevLevel &L, int kind, int R, int reps, cudaEven
     ch.on = c.pdl != 0;   // the capture stream is an ordinary stream
     for (int q = 0; q < reps; q++) {
         if (kind == kShapeSmooth) {
-            for (int col = 0; col < 8; col++)
-                launch_smooth_colour<T>(L, col, V<T>::A(L), V<T>::dinv(L), V<T>::b(L), V<T>::x(L), R, cs, &ch);
+            launch_sweeps<T>(c, L, 1, true, V<T>::A(L), V<T>::dinv(L), V<T>::b(L), V<T>::x(L), R, cs, &ch);
         } else {
             launch_residual<T>(L, V<T>::A(L), V<T>::b(L), V<T>::x(L), V<T>::r(L), R, cs, L.ns, &ch);
         }
@@ -132,6 +131,21 @@ cudaError_t tune_levels(Ctx &c, int R, int reps, int *timed) {
             if (e != cudaSuccess) { L.shape[fp64][kind] = dflt; break; }
             // keep the default unless another shape is clearly faster (timing noise)
             if (dflt_ms > 0.f && best_ms > 0.98f * dflt_ms) { best = dflt; best_ms = dflt_ms; }
+            // FP32 sweeps of a level with a packed copy: the whole-sweep cooperative kernel, kept when it
+            // beats the colour launches by 2% (a refused launch or capture just leaves it out)
+            if (kind == kShapeSmooth && !fp64 && L.pk_map && c.sweep_bar && c.sweep_blocks[R] > 0) {
+                LaunchShape sw;
+                sw.tpr = 4;
+                sw.tpb = kSweepShapeTpb;
+                L.shape[fp64][kind] = sw;
+                float ms = 0.f;
+                const cudaError_t es = time_kernel<T>(c, L, kind, R, reps, e0, e1, &ms);
+                if (es == cudaSuccess && ms > 0.f && ms < 0.98f * best_ms) { best = sw; best_ms = ms; }
+                if (es != cudaSuccess) {
+                    cudaGetLastError();
+                    cudaStreamSynchronize(c.capture_stream);
+                }
+            }
             L.shape[fp64][kind] = best;
             L.tuned_ms[fp64][kind] = best_ms;
             {
@@ -190,7 +204,7 @@ int tune_cache_load(const char *path) {
         long long n, nnz;
         if (std::sscanf(line, "%255s %d %d %d %lld %lld %d %d", name, &fp64, &kind, &R, &n, &nnz, &tpr, &tpb) != 8 ||
             (fp64 != 0 && fp64 != 1) || (kind != 0 && kind != 1) || (tpr != 4 && tpr != 8 && tpr != 16) ||
-            tpb < 32 || tpb > 512 || tpb % 32 != 0) {
+            tpb < 32 || (tpb > 512 && !(tpb == kSweepShapeTpb && tpr == 4 && kind == kShapeSmooth)) || tpb % 32 != 0) {
             bad = 1;
             continue;
         }

@@ -181,3 +181,34 @@ def test_autotuned_shapes_are_valid_cached_and_solve_correctly(tmp_path):
     finally:
         L.lbmg_destroy(h1)
         L.lbmg_destroy(h2)
+
+
+@pytest.mark.parametrize("graphs", [1, 0])
+def test_whole_sweep_kernel_changes_no_bit(graphs):
+    """The whole-sweep cooperative kernel (shape 4 x 1024: every colour step of a smoothing in
+    one launch, blocks meeting at a bounded grid barrier) computes exactly what the colour
+    launches of 4 threads per row compute; it is refused for FP64 sweeps and for residuals."""
+    V, F = _knot()
+    h = L.lbmg_build_hierarchy(V, F, 5, min_depth=1, use_graphs=graphs)
+    try:
+        L.lbmg_assemble(h, 1e-2)
+        d0, D = L.lbmg_levels(h)
+        n = L.lbmg_level_info(h, D)[0]
+        rhs = torch.zeros((n, 3), dtype=torch.float64, device=DEV)
+        L.lbmg_project_rhs(h, _dev(V), rhs)
+        xs = []
+        for tpb in (256, 1024):
+            for d in range(d0 + 1, D + 1):
+                L.lbmg_set_launch_shape(h, d, L.LBMG_MIXED, 0, 4, tpb)
+            x = torch.zeros_like(rhs)
+            assert L.lbmg_vcycles(h, rhs, x, 5, L.LBMG_MIXED) == L.LBMG_OK
+            code, st = L.lbmg_solve(h, rhs, torch.zeros_like(rhs), 1e-6, 3000, L.LBMG_MIXED)
+            assert code == L.LBMG_OK
+            xs.append((x, st.cycles))
+        assert torch.equal(xs[0][0], xs[1][0]) and xs[0][1] == xs[1][1]
+        for prec, kind in ((L.LBMG_FP64, 0), (L.LBMG_MIXED, 1)):
+            with pytest.raises(L.LbmgError) as e:
+                L.lbmg_set_launch_shape(h, D, prec, kind, 4, 1024)
+            assert e.value.code == 1
+    finally:
+        L.lbmg_destroy(h)
