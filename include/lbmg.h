@@ -358,6 +358,17 @@ int lbmg_vcycles(lbmg_handle h, const double *rhs, double *x, int nrhs, int cycl
 /* r = rhs - A_d x on level d in FP64 (Eq. 2 operator); all [n_d][nrhs]. */
 int lbmg_residual(lbmg_handle h, int d, const double *rhs, const double *x, double *r, int nrhs,
                   void *stream);
+/* The mixed solve's outer residual r = rhs - A_d x (Section 4.3's defect correction) as
+   lbmg_residual computes it, arguments and layout the same, with FP64 values carried as
+   pairs of FP32 numbers (value = hi + lo): every product a x = ah xh + (ah xl + al xh + the
+   exact rounding error of ah xh) and every partial sum is an FP32 pair (Knuth's two-sum),
+   and rhs - sum is formed in FP64.  The result agrees with the FP64 residual to about 2^-44
+   of sum_j |a_ij x_j| (the dropped al xl term and FP32 rounding of the small terms).  Why:
+   GB300 executes FP64 arithmetic at a small fraction of its FP32 rate, which made the FP64
+   residual of the finest level compute-bound.  Levels with a packed copy only (not the
+   coarsest): LBMG_INVALID_ARG there. */
+int lbmg_residual_split(lbmg_handle h, int d, const double *rhs, const double *x, double *r, int nrhs,
+                        void *stream);
 
 /* `sweeps` smoothing sweeps of the configured smoother on level d, in the
    given precision, on A_d x = rhs; x in/out.  Colour order 0..7. */

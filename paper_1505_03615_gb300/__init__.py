@@ -23,7 +23,7 @@ __all__ = [
     "lbmg_get_prolongation", "lbmg_launch_counts", "lbmg_build_batch", "lbmg_instances", "lbmg_instance_info",
     "lbmg_instance_residuals", "lbmg_row_instances", "lbmg_learned_nparams", "lbmg_learned_params", "lbmg_learned_collect",
     "lbmg_learned_loss_grad", "lbmg_learned_train", "lbmg_learned_enable", "lbmg_learned_apply",
-    "lbmg_learned_state",
+    "lbmg_learned_state", "lbmg_residual_split",
     "lbmg_residual_norms_noalloc", "lbmg_status_string", "lbmg_last_cuda_error", "lbmg_default_options",
     "lbmg_solve_pcg", "lbmg_cmcf_step", "lbmg_eigs", "lbmg_autotune", "lbmg_launch_shape", "lbmg_tuned_times", "lbmg_set_launch_shape", "lbmg_set_host_check", "lbmg_tune_cache_save", "lbmg_tune_cache_load",
     "lbmg_host_build", "lbmg_host_destroy", "lbmg_host_levels", "lbmg_host_level_info", "lbmg_host_get_dofs",
@@ -94,6 +94,7 @@ def load_library():
         "lbmg_solve_pcg": (i, [P, P, P, i, d, i, i, P, P]),
         "lbmg_vcycles": (i, [P, P, P, i, i, i, P]),
         "lbmg_residual": (i, [P, i, P, P, P, i, P]),
+        "lbmg_residual_split": (i, [P, i, P, P, P, i, P]),
         "lbmg_smooth": (i, [P, i, P, P, i, i, i, P]),
         "lbmg_restrict": (i, [P, i, P, P, i, P]),
         "lbmg_prolong_add": (i, [P, i, P, P, i, P]),
@@ -421,6 +422,12 @@ def lbmg_residual_norms_noalloc(h, d, rhs, x, norms, stream=None):
     """Per-column ||rhs - A_d x||_2 into `norms` (all device tensors); the call allocates nothing."""
     return _check(load_library().lbmg_residual_norms_noalloc(h, int(d), _ptr(rhs), _ptr(x), _nrhs(rhs), _ptr(norms),
                                                              _stream(stream)), "lbmg_residual_norms_noalloc")
+
+
+def lbmg_residual_split(h, d, rhs, x, r, stream=None):
+    """The mixed solve's outer residual (FP64 values as FP32 pairs), same conventions as lbmg_residual."""
+    return _check(load_library().lbmg_residual_split(h, int(d), _ptr(rhs), _ptr(x), _ptr(r), _nrhs(rhs),
+                                                     _stream(stream)), "lbmg_residual_split")
 
 
 def lbmg_smooth(h, d, rhs, x, sweeps, precision, stream=None):

@@ -359,6 +359,14 @@ void enqueue_iteration(Ctx &c, int R, int precision, cudaStream_t s, bool timed 
         if (c.learned_on) learned_enqueue(c, R, precision, s, &ch);   // the cycle starts from the correction
         else launch_to_float(c.rs, F.b32, m, s, F.x32, &ch);
         enqueue_cycle<float>(c, R, s, timed, &ch);
+        // x += e, and the outer residual with FP64 values carried as FP32 pairs (GB300's FP64
+        // rate would bound an FP64 residual of the finest level)
+        if (F.pk_v2) {
+            launch_add_split(c.xs, F.x32, c.xs_hi, c.xs_lo, m, s, &ch);
+            launch_packed_residual_split(F, c.bs, c.xs_hi, c.xs_lo, c.rs, R, s, &ch);
+            launch_norms(c.rs, F.n, R, c.norm_part, c.norm_out, s, &ch);
+            return;
+        }
         launch_add_float(c.xs, F.x32, m, s, &ch);
     } else {
         if (c.learned_on) {
@@ -373,6 +381,16 @@ void enqueue_iteration(Ctx &c, int R, int precision, cudaStream_t s, bool timed 
     }
     launch_residual<double>(F, F.A64, c.bs, c.xs, c.rs, R, s, -1, &ch);
     launch_norms(c.rs, F.n, R, c.norm_part, c.norm_out, s, &ch);
+}
+
+// q = -A p of a CG step: in mixed precision with p's FP64 values carried as FP32 pairs
+// (the product of the outer residual), else in FP64
+void enqueue_pcg_product(Ctx &c, DevLevel &F, int R, int precision, int64_t m, cudaStream_t s) {
+    if (precision == LBMG_MIXED && F.pk_v2) {
+        launch_split(c.pcg_p, c.xs_hi, c.xs_lo, m, s);
+        if (launch_packed_residual_split(F, c.pcg_zero, c.xs_hi, c.xs_lo, c.pcg_q, R, s, nullptr)) return;
+    }
+    launch_residual<double>(F, F.A64, c.pcg_zero, c.pcg_p, c.pcg_q, R, s);
 }
 
 // one step of conjugate gradients preconditioned by the V-cycle, in the flexible
@@ -396,7 +414,7 @@ void enqueue_pcg_iteration(Ctx &c, int R, int precision, cudaStream_t s, bool ti
     }
     launch_pcg_dot(c.rs, c.pcg_z, F.n, R, c.pcg_part, c.pcg_s, 1, s);
     launch_pcg_direction(c.pcg_z, c.pcg_p, c.pcg_s, F.n, R, s);
-    launch_residual<double>(F, F.A64, c.pcg_zero, c.pcg_p, c.pcg_q, R, s);
+    enqueue_pcg_product(c, F, R, precision, m, s);
     launch_pcg_dot(c.pcg_p, c.pcg_q, F.n, R, c.pcg_part, c.pcg_s, 2, s);
     launch_pcg_update(c.xs, c.rs, c.pcg_p, c.pcg_q, c.pcg_s, F.n, R, s);
     launch_norms(c.rs, F.n, R, c.norm_part, c.norm_out, s);
@@ -423,7 +441,7 @@ void enqueue_pcg_batch_iteration(Ctx &c, int R, int precision, cudaStream_t s) {
     launch_item_dot2(c.nitem, c.nnitem, c.rs, c.pcg_z, nullptr, nullptr, R, c.item_part, s);
     launch_inst_pcg_scalar(c.item_start, c.ninst, R, c.item_part, c.pcg_si, 1, c.inst_norm, c.pcg_tol, s);
     launch_inst_pcg_direction(c.pcg_z, c.pcg_p, c.pcg_si, c.row_inst, F.n, R, s);
-    launch_residual<double>(F, F.A64, c.pcg_zero, c.pcg_p, c.pcg_q, R, s);
+    enqueue_pcg_product(c, F, R, precision, m, s);
     launch_item_dot2(c.nitem, c.nnitem, c.pcg_p, c.pcg_q, nullptr, nullptr, R, c.item_part, s);
     launch_inst_pcg_scalar(c.item_start, c.ninst, R, c.item_part, c.pcg_si, 2, c.inst_norm, c.pcg_tol, s);
     launch_inst_pcg_update(c.xs, c.rs, c.pcg_p, c.pcg_q, c.pcg_si, c.row_inst, F.n, R, s);
@@ -622,6 +640,7 @@ int upload_hierarchy(lbmg_handle h) {
                 LBMG_TRY(h->upload(&L.pk_col, col));
                 LBMG_TRY(h->alloc(&L.pk_e32, (size_t)L.pk_total));
                 LBMG_TRY(h->alloc(&L.pk_v64, (size_t)L.pk_total));
+                LBMG_TRY(h->alloc(&L.pk_v2, (size_t)L.pk_total));
             }
         }
         const size_t v4 = 4 * (size_t)L.n;
@@ -703,6 +722,8 @@ int upload_hierarchy(lbmg_handle h) {
     LBMG_TRY(h->alloc(&c.xs, 4 * nD));
     LBMG_TRY(h->alloc(&c.bs, 4 * nD));
     LBMG_TRY(h->alloc(&c.rs, 4 * nD));
+    LBMG_TRY(h->alloc(&c.xs_hi, 4 * nD));
+    LBMG_TRY(h->alloc(&c.xs_lo, 4 * nD));
     LBMG_TRY(h->alloc(&c.norm_part, 4 * (size_t)kNormBlocks));
     LBMG_TRY(h->alloc(&c.pcg_z, 4 * nD));
     LBMG_TRY(h->alloc(&c.pcg_p, 4 * nD));
@@ -1563,6 +1584,33 @@ int lbmg_residual(lbmg_handle h, int d, const double *rhs, const double *x, doub
     LBMG_TRY(input_ptr(h, x, cnt, 1, s, &xd));
     launch_pack(xd, L.n, nrhs, R, L.x64, s);
     launch_residual<double>(L, L.A64, L.b64, L.x64, L.r64, R, s);
+    LBMG_TRY(output_ptr(h, r, cnt, 0, &rd, &host_out));
+    launch_unpack(L.r64, L.n, nrhs, R, rd, s);
+    return finish_output(r, rd, cnt, host_out, s);
+}
+
+int lbmg_residual_split(lbmg_handle h, int d, const double *rhs, const double *x, double *r, int nrhs,
+                        void *stream) {
+    LBMG_TRY(check_level(h, d));
+    if (!rhs || !x || !r || nrhs < 1 || nrhs > 4) return LBMG_INVALID_ARG;
+    if (!h->c.assembled) return LBMG_NOT_ASSEMBLED;
+    DevLevel &L = h->c.lev[d];
+    if (!L.pk_v2) {
+        g_cuda_err = "lbmg_residual_split: the level has no packed copy (the coarsest level)";
+        return LBMG_INVALID_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    const int R = stride_for(nrhs);
+    const size_t cnt = (size_t)L.n * nrhs;
+    const double *bd, *xd;
+    double *rd;
+    bool host_out;
+    LBMG_TRY(input_ptr(h, rhs, cnt, 0, s, &bd));
+    launch_pack(bd, L.n, nrhs, R, L.b64, s);
+    LBMG_TRY(input_ptr(h, x, cnt, 1, s, &xd));
+    launch_pack(xd, L.n, nrhs, R, L.x64, s);
+    launch_split(L.x64, L.x32, L.r32, (int64_t)L.n * R, s);   // the level's FP32 vectors as scratch
+    launch_packed_residual_split(L, L.b64, L.x32, L.r32, L.r64, R, s, nullptr);
     LBMG_TRY(output_ptr(h, r, cnt, 0, &rd, &host_out));
     launch_unpack(L.r64, L.n, nrhs, R, rd, s);
     return finish_output(r, rd, cnt, host_out, s);

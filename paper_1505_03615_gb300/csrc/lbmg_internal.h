@@ -91,6 +91,7 @@ struct DevLevel {
     int *pk_col = nullptr;                 // [total] columns in packed order, -1 pad (FP64 kernels)
     int2 *pk_e32 = nullptr;                // [total] (column, FP32 value bits)
     double *pk_v64 = nullptr;              // [total] FP64 values
+    float2 *pk_v2 = nullptr;               // [total] FP64 values as FP32 pairs (hi, lo = value - hi)
     int64_t pk_total = 0;
     int pk_gs[10] = {0};                   // group ranges of colours 0..7, then rows [ns, n)
     int64_t pk_es[10] = {0};               // entry offset of the first group of each range (pk_es[9]: total)
@@ -228,6 +229,8 @@ struct Ctx {
     void *persist_state = nullptr;    // 64 bytes: barrier, status, cycles, timer
     void *h_state = nullptr;          // pinned mirror: 64 bytes state + 16 doubles norms
     NarrowState narrow;               // shared-memory bottom of the V-cycle (narrow.cu)
+    // the mixed solve's iterate as FP32 pairs for its outer residual (packed.cu)
+    float *xs_hi = nullptr, *xs_lo = nullptr;
     // whole-sweep cooperative kernel (packed.cu): arrival counter and grid per lane count
     unsigned *sweep_bar = nullptr;
     int sweep_blocks[5] = {0, 0, 0, 0, 0};
@@ -301,6 +304,15 @@ template <class T> bool launch_packed_smooth(const DevLevel &L, int colour, cons
                                              T *x, int R, int tpb, cudaStream_t s, Chain *ch, int next = -1);
 template <class T> bool launch_packed_residual(const DevLevel &L, const T *A, const T *b, const T *x, T *r, int R,
                                                int nrows, int tpb, cudaStream_t s, Chain *ch);
+// r = b - A x at all rows of level L for the mixed solve's outer residual: x given as FP32 pairs
+// (xh + xl), the matrix as FP32 pairs, products and sums in pairs of FP32 (about 44 significant
+// bits) and b - sum in FP64; false when the level has no packed copy
+bool launch_packed_residual_split(const DevLevel &L, const double *b, const float *xh, const float *xl, double *r,
+                                  int R, cudaStream_t s, Chain *ch);
+// x += e (FP64 += FP32) and its FP32 pair split: xh = fl32(x), xl = fl32(x - xh)
+void launch_add_split(double *x, const float *e, float *xh, float *xl, int64_t n, cudaStream_t s, Chain *ch);
+// xh, xl of an FP64 vector
+void launch_split(const double *x, float *xh, float *xl, int64_t n, cudaStream_t s);
 // a colour sequence (FP32) in one cooperative launch; bar: a device counter, status: the
 // bounded-wait word; false if the level has no packed copy or the launch is refused
 bool launch_packed_sweep(const DevLevel &L, const int *seq, int nseq, const float *dinv, const float *b, float *x,

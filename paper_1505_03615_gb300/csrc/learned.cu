@@ -291,11 +291,13 @@ __global__ void __launch_bounds__(256) lr_solve_kernel(int n, const __nv_bfloat1
     for (int q = threadIdx.x; q < 2 * kH + 1; q += blockDim.x) sP[q] = prm[kF * kH + q];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const int row0 = (blockIdx.x * (blockDim.x >> 5) + warp) * 16;
+    __shared__ float s_ebar;
     uint32_t a[2][4] = {{0u, 0u, 0u, 0u}, {0u, 0u, 0u, 0u}};
     if (row0 < n) load_features(X, row0, g, t, a);
-    __syncthreads();
     grid_dep_wait();
     grid_dep_launch();
+    if (threadIdx.x == 0) s_ebar = mean_energy(nr, R, n);   // once per block (FP64 is scarce)
+    __syncthreads();
     if (row0 >= n) return;
     const int ra = row0 + g, rb = row0 + g + 8;
     if (off && *(volatile const int *)off != 0) {
@@ -310,7 +312,7 @@ __global__ void __launch_bounds__(256) lr_solve_kernel(int n, const __nv_bfloat1
         return;
     }
     if (t == 2) {   // this lane's ks = 1 fragment holds columns 28, 29 of rows g and g + 8
-        const float eb = mean_energy(nr, R, n);
+        const float eb = s_ebar;
         float fa28 = 0.f, fa29 = 0.f, fb28 = 0.f, fb29 = 0.f;
         if (ra < n) residual_features<T, R>(r + (size_t)ra * R, w + (size_t)ra * R, eb, fa28, fa29);
         if (rb < n) residual_features<T, R>(r + (size_t)rb * R, w + (size_t)rb * R, eb, fb28, fb29);

@@ -157,12 +157,135 @@ __global__ void __launch_bounds__(512) pk_row_kernel(int g0, int g1, const int2 
 
 __global__ void pk_fill_kernel(int64_t total, const int *__restrict__ map, const int *__restrict__ col,
                                const float *__restrict__ A32, const double *__restrict__ A64, int2 *__restrict__ e32,
-                               double *__restrict__ v64) {
+                               double *__restrict__ v64, float2 *__restrict__ v2) {
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= total) return;
     const int src = __ldg(map + k);
     e32[k] = make_int2(__ldg(col + k), src >= 0 ? __float_as_int(__ldg(A32 + src)) : 0);
-    v64[k] = src >= 0 ? __ldg(A64 + src) : 0.0;
+    const double a = src >= 0 ? __ldg(A64 + src) : 0.0;
+    v64[k] = a;
+    const float hi = (float)a;
+    v2[k] = make_float2(hi, (float)(a - (double)hi));
+}
+
+// ---- the mixed solve's outer residual in pairs of FP32 ----
+// GB300 executes FP64 at a small fraction of its FP32 rate, so an FP64 residual over the
+// finest level is bound by FP64 arithmetic, not by memory.  Here each FP64 value is a pair
+// of FP32 numbers (hi + lo) and every product and sum is carried as such a pair:
+//   a x = ah xh + (ah xl + al xh + e),  e = fma(ah, xh, -ah xh) the exact rounding error,
+// and the running sum (s, c) absorbs each term by Knuth's two-sum.  The dropped al xl and the
+// FP32 rounding of the small terms leave about 2^-44 relative to sum |a x|; b - (s + c) is
+// formed in FP64.  Same traversal as pk_row_kernel (one warp per 8-row group).
+// (the _rn intrinsics keep the compiler from fusing these into FMAs, which would break the
+// error-free transformations)
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+template <int R>
+__device__ __forceinline__ void ld_pair_row(const float *h, const float *l, float (&vh)[R], float (&vl)[R]) {
+#pragma unroll
+    for (int c = 0; c < R; c++) { vh[c] = h[c]; vl[c] = l[c]; }
+}
+template <>
+__device__ __forceinline__ void ld_pair_row<4>(const float *h, const float *l, float (&vh)[4], float (&vl)[4]) {
+    const float4 a = *reinterpret_cast<const float4 *>(h), b = *reinterpret_cast<const float4 *>(l);
+    vh[0] = a.x; vh[1] = a.y; vh[2] = a.z; vh[3] = a.w;
+    vl[0] = b.x; vl[1] = b.y; vl[2] = b.z; vl[3] = b.w;
+}
+
+template <int R>
+__global__ void __launch_bounds__(256) pk_split_residual_kernel(int g1, const int2 *__restrict__ gq,
+                                                                const int *__restrict__ rows,
+                                                                const int *__restrict__ col,
+                                                                const float2 *__restrict__ v2,
+                                                                const double *__restrict__ b,
+                                                                const float *__restrict__ xh,
+                                                                const float *__restrict__ xl,
+                                                                double *__restrict__ r) {
+    const int lane = threadIdx.x & 31;
+    const int g = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
+    if (g >= g1) return;   // whole warps only
+    const int2 hd = __ldg(gq + g);
+    const int64_t base = (int64_t)(unsigned)hd.x * 32;
+    const int Q = hd.y;
+    const int row = __ldg(rows + 8 * (size_t)g + (lane >> 2));
+    const bool lead = row >= 0 && (lane & 3) == 0;
+    int j[kPkPrefetch];
+    float2 a[kPkPrefetch];
+#pragma unroll
+    for (int q = 0; q < kPkPrefetch; q++) {
+        j[q] = -1;
+        a[q] = make_float2(0.f, 0.f);
+        if (q < Q) {
+            j[q] = __ldg(col + base + 32 * q + lane);
+            a[q] = __ldg(v2 + base + 32 * q + lane);
+        }
+    }
+    grid_dep_wait();
+    grid_dep_launch();
+    float sh[R], sl[R];
+#pragma unroll
+    for (int c = 0; c < R; c++) { sh[c] = 0.f; sl[c] = 0.f; }
+    auto term = [&](int jj, float2 aa) {
+        float vh[R], vl[R];
+        ld_pair_row<R>(xh + (size_t)jj * R, xl + (size_t)jj * R, vh, vl);
+#pragma unroll
+        for (int c = 0; c < R; c++) {
+            const float p = __fmul_rn(aa.x, vh[c]);
+            const float t = fmaf(aa.x, vl[c], fmaf(aa.y, vh[c], fmaf(aa.x, vh[c], -p)));
+            float s2, e2;
+            two_sum(sh[c], p, s2, e2);
+            sh[c] = s2;
+            sl[c] += e2 + t;
+        }
+    };
+#pragma unroll
+    for (int q = 0; q < kPkPrefetch; q++)
+        if (j[q] >= 0) term(j[q], a[q]);
+    for (int q = kPkPrefetch; q < Q; q++) {   // rows of more than 32 entries
+        const int jj = __ldg(col + base + 32 * q + lane);
+        if (jj >= 0) term(jj, __ldg(v2 + base + 32 * q + lane));
+    }
+#pragma unroll
+    for (int o = 2; o > 0; o >>= 1)
+#pragma unroll
+        for (int c = 0; c < R; c++) {
+            const float oh = __shfl_xor_sync(kFull, sh[c], o, 4), ol = __shfl_xor_sync(kFull, sl[c], o, 4);
+            float s2, e2;
+            two_sum(sh[c], oh, s2, e2);
+            sh[c] = s2;
+            sl[c] += ol + e2;
+        }
+    if (lead) {
+#pragma unroll
+        for (int c = 0; c < R; c++)
+            r[(size_t)row * R + c] = b[(size_t)row * R + c] - ((double)sh[c] + (double)sl[c]);
+    }
+}
+
+__global__ void add_split_kernel(double *__restrict__ x, const float *__restrict__ e, float *__restrict__ xh,
+                                 float *__restrict__ xl, int64_t n) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    grid_dep_wait();
+    grid_dep_launch();
+    if (q >= n) return;
+    const double v = x[q] + (double)e[q];
+    x[q] = v;
+    const float h = (float)v;
+    xh[q] = h;
+    xl[q] = (float)(v - (double)h);
+}
+
+__global__ void split_kernel(const double *__restrict__ x, float *__restrict__ xh, float *__restrict__ xl, int64_t n) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const double v = x[q];
+    const float h = (float)v;
+    xh[q] = h;
+    xl[q] = (float)(v - (double)h);
 }
 
 template <class T> PkMat<T> pk_mat(const DevLevel &L);
@@ -416,7 +539,27 @@ bool packed_layout(const HostLevel &hl, std::vector<int32_t> &gq, std::vector<in
 void launch_packed_fill(const DevLevel &L, cudaStream_t s) {
     if (!L.pk_map || L.pk_total == 0) return;
     pk_fill_kernel<<<(unsigned)((L.pk_total + 255) / 256), 256, 0, s>>>(L.pk_total, L.pk_map, L.pk_col, L.A32, L.A64,
-                                                                        L.pk_e32, L.pk_v64);
+                                                                        L.pk_e32, L.pk_v64, L.pk_v2);
+}
+
+bool launch_packed_residual_split(const DevLevel &L, const double *b, const float *xh, const float *xl, double *r,
+                                  int R, cudaStream_t s, Chain *ch) {
+    if (!L.pk_map || !L.pk_v2) return false;
+    const int g1 = L.pk_gs[9];
+    if (g1 <= 0) return true;
+    const unsigned blocks = (unsigned)(((int64_t)g1 * 32 + 255) / 256);
+    auto k = R == 1 ? pk_split_residual_kernel<1> : R == 2 ? pk_split_residual_kernel<2> : pk_split_residual_kernel<4>;
+    klaunch(k, blocks, 256u, 0, s, ch, g1, (const int2 *)L.pk_gq, (const int *)L.pk_rows, (const int *)L.pk_col,
+            (const float2 *)L.pk_v2, b, xh, xl, r);
+    return true;
+}
+
+void launch_add_split(double *x, const float *e, float *xh, float *xl, int64_t n, cudaStream_t s, Chain *ch) {
+    if (n) klaunch(add_split_kernel, (unsigned)((n + 255) / 256), 256u, 0, s, ch, x, e, xh, xl, n);
+}
+
+void launch_split(const double *x, float *xh, float *xl, int64_t n, cudaStream_t s) {
+    if (n) split_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, xh, xl, n);
 }
 
 template <class T>
