@@ -349,6 +349,13 @@ Chain make_chain(const Ctx &c, cudaStream_t s) {
     return ch;
 }
 
+// the mixed V-cycle iteration keeps its iterate as an FP32 pair (c.xs_hi + c.xs_lo, updated by
+// an FP32 two-sum) and forms the outer residual from it; c.xs holds it in FP64 only before and
+// after the solve (split at the start, joined at the end)
+inline bool pair_iterate(const Ctx &c, int precision, bool pcg) {
+    return precision == LBMG_MIXED && !pcg && c.lev[c.D].pk_v2 != nullptr;
+}
+
 // one defect-correction step: x += Vcycle(r); r = b - A x; norms(r)
 // timed: events around the finest smoothing (not inside the body of a conditional node)
 void enqueue_iteration(Ctx &c, int R, int precision, cudaStream_t s, bool timed = true) {
@@ -361,8 +368,8 @@ void enqueue_iteration(Ctx &c, int R, int precision, cudaStream_t s, bool timed 
         enqueue_cycle<float>(c, R, s, timed, &ch);
         // x += e, and the outer residual with FP64 values carried as FP32 pairs (GB300's FP64
         // rate would bound an FP64 residual of the finest level)
-        if (F.pk_v2) {
-            launch_add_split(c.xs, F.x32, c.xs_hi, c.xs_lo, m, s, &ch);
+        if (pair_iterate(c, precision, false)) {
+            launch_add_pair(F.x32, c.xs_hi, c.xs_lo, m, s, &ch);
             launch_packed_residual_split(F, c.bs, c.xs_hi, c.xs_lo, c.rs, R, s, &ch);
             launch_norms(c.rs, F.n, R, c.norm_part, c.norm_out, s, &ch);
             return;
@@ -1164,7 +1171,7 @@ int lbmg_eval_vertices(lbmg_handle h, const double *x, int nrhs, double *u, void
 // to read the final status (and the solution, for a host output buffer).
 static int solve_cond(lbmg_handle h, cudaGraphExec_t exec, const double *rd, const double *xin, double *xout,
                       bool host_out, double *x, size_t cnt, int nrhs, int R, double tol, int max_cycles, bool pcg,
-                      bool check, lbmg_stats *stats, cudaStream_t s) {
+                      bool check, int precision, lbmg_stats *stats, cudaStream_t s) {
     Ctx &c = h->c;
     DevLevel &Fl = c.lev[c.D];
     const bool batch = c.ninst > 1;
@@ -1174,6 +1181,8 @@ static int solve_cond(lbmg_handle h, cudaGraphExec_t exec, const double *rd, con
     launch_pack(xin, Fl.n, nrhs, R, c.xs, s, c.fperm);
     launch_residual<double>(Fl, Fl.A64, c.bs, c.xs, c.rs, R, s);
     const size_t m = (size_t)Fl.n * R;
+    const bool pairs = pair_iterate(c, precision, pcg);
+    if (pairs) launch_split(c.xs, c.xs_hi, c.xs_lo, (int64_t)m, s);
     if (pcg) {
         LBMG_CK(cudaMemsetAsync(c.pcg_z, 0, m * sizeof(double), s));
         LBMG_CK(cudaMemsetAsync(c.pcg_p, 0, m * sizeof(double), s));
@@ -1190,6 +1199,7 @@ static int solve_cond(lbmg_handle h, cudaGraphExec_t exec, const double *rd, con
         launch_norms(c.rs, Fl.n, R, c.norm_part, c.norm_out, s);
     }
     LBMG_CK(cudaGraphLaunch(exec, s));
+    if (pairs) launch_join(c.xs_hi, c.xs_lo, c.xs, (int64_t)m, s);
     launch_unpack(c.xs, Fl.n, nrhs, R, xout, s, c.fperm);
     LBMG_CK(cudaEventRecord(c.ev1, s));
     LBMG_CK(cudaMemcpyAsync(c.h_ctl, c.ctl, sizeof(SolveCtl), cudaMemcpyDeviceToHost, s));
@@ -1401,8 +1411,8 @@ static int solve_impl(lbmg_handle h, const double *rhs, double *x, int nrhs, dou
     if (c.use_graphs && !c.host_check && !c.cond_failed) {
         cudaGraphExec_t cexec = nullptr;
         if (get_cond_graph(h, R, precision, pcg, &cexec) == LBMG_OK)
-            return solve_cond(h, cexec, rd, xin, xout, host_out, x, cnt, nrhs, R, tol, max_cycles, pcg, check, stats,
-                              s);
+            return solve_cond(h, cexec, rd, xin, xout, host_out, x, cnt, nrhs, R, tol, max_cycles, pcg, check,
+                              precision, stats, s);
         c.cond_failed = true;   // no conditional graphs here: the host reads the norms each iteration
     }
     if (pcg && c.ninst > 1)
@@ -1415,6 +1425,8 @@ static int solve_impl(lbmg_handle h, const double *rhs, double *x, int nrhs, dou
     launch_pack(rd, Fl.n, nrhs, R, c.bs, s, c.fperm);
     launch_pack(xin, Fl.n, nrhs, R, c.xs, s, c.fperm);
     launch_residual<double>(Fl, Fl.A64, c.bs, c.xs, c.rs, R, s);
+    const bool pairs = pair_iterate(c, precision, pcg);
+    if (pairs) launch_split(c.xs, c.xs_hi, c.xs_lo, (int64_t)Fl.n * R, s);
     if (pcg) {
         LBMG_CK(cudaMemsetAsync(c.pcg_z, 0, (size_t)Fl.n * R * sizeof(double), s));
         LBMG_CK(cudaMemsetAsync(c.pcg_p, 0, (size_t)Fl.n * R * sizeof(double), s));
@@ -1487,6 +1499,7 @@ static int solve_impl(lbmg_handle h, const double *rhs, double *x, int nrhs, dou
         }
         cycles = max_cycles;
     }
+    if (pairs) launch_join(c.xs_hi, c.xs_lo, c.xs, (int64_t)Fl.n * R, s);
     launch_unpack(c.xs, Fl.n, nrhs, R, xout, s, c.fperm);
     LBMG_CK(cudaEventRecord(c.ev1, s));
     LBMG_TRY(finish_output(x, xout, cnt, host_out, s, &h->syncs));

@@ -309,10 +309,10 @@ template <class T> bool launch_packed_residual(const DevLevel &L, const T *A, co
 // bits) and b - sum in FP64; false when the level has no packed copy
 bool launch_packed_residual_split(const DevLevel &L, const double *b, const float *xh, const float *xl, double *r,
                                   int R, cudaStream_t s, Chain *ch);
-// x += e (FP64 += FP32) and its FP32 pair split: xh = fl32(x), xl = fl32(x - xh)
-void launch_add_split(double *x, const float *e, float *xh, float *xl, int64_t n, cudaStream_t s, Chain *ch);
-// xh, xl of an FP64 vector
+// xh, xl of an FP64 vector; x = xh + xl in FP64; x += e on the pair (FP32 two-sum)
 void launch_split(const double *x, float *xh, float *xl, int64_t n, cudaStream_t s);
+void launch_join(const float *xh, const float *xl, double *x, int64_t n, cudaStream_t s);
+void launch_add_pair(const float *e, float *xh, float *xl, int64_t n, cudaStream_t s, Chain *ch);
 // a colour sequence (FP32) in one cooperative launch; bar: a device counter, status: the
 // bounded-wait word; false if the level has no packed copy or the launch is refused
 bool launch_packed_sweep(const DevLevel &L, const int *seq, int nseq, const float *dinv, const float *b, float *x,

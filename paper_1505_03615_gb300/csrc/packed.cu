@@ -212,7 +212,6 @@ __global__ void __launch_bounds__(256) pk_split_residual_kernel(int g1, const in
     const int64_t base = (int64_t)(unsigned)hd.x * 32;
     const int Q = hd.y;
     const int row = __ldg(rows + 8 * (size_t)g + (lane >> 2));
-    const bool lead = row >= 0 && (lane & 3) == 0;
     int j[kPkPrefetch];
     float2 a[kPkPrefetch];
 #pragma unroll
@@ -259,24 +258,38 @@ __global__ void __launch_bounds__(256) pk_split_residual_kernel(int g1, const in
             sh[c] = s2;
             sl[c] += ol + e2;
         }
-    if (lead) {
+    // every lane of the row holds the sums: lane l forms component l in FP64, so a warp issues
+    // R FP64 instructions per step instead of 4 R (the FP64 pipe counts warp instructions)
+    const int l = lane & 3;
+    if (row >= 0 && l < R) {
+        float h = sh[0], lo = sl[0];
 #pragma unroll
-        for (int c = 0; c < R; c++)
-            r[(size_t)row * R + c] = b[(size_t)row * R + c] - ((double)sh[c] + (double)sl[c]);
+        for (int c = 1; c < R; c++)
+            if (l == c) { h = sh[c]; lo = sl[c]; }
+        r[(size_t)row * R + l] = b[(size_t)row * R + l] - ((double)h + (double)lo);
     }
 }
 
-__global__ void add_split_kernel(double *__restrict__ x, const float *__restrict__ e, float *__restrict__ xh,
-                                 float *__restrict__ xl, int64_t n) {
+// x += e on the FP32 pair (xh, xl): two-sum, then renormalise so that |xl| <= ulp(xh) / 2
+__global__ void add_pair_kernel(const float *__restrict__ e, float *__restrict__ xh, float *__restrict__ xl,
+                                int64_t n) {
     const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     grid_dep_wait();
     grid_dep_launch();
     if (q >= n) return;
-    const double v = x[q] + (double)e[q];
-    x[q] = v;
-    const float h = (float)v;
+    float s, err;
+    two_sum(xh[q], e[q], s, err);
+    const float t = __fadd_rn(xl[q], err);
+    const float h = __fadd_rn(s, t);                   // fast two-sum (|s| >= |t| after a two-sum)
     xh[q] = h;
-    xl[q] = (float)(v - (double)h);
+    xl[q] = __fsub_rn(t, __fsub_rn(h, s));
+}
+
+// x = xh + xl in FP64
+__global__ void join_kernel(const float *__restrict__ xh, const float *__restrict__ xl, double *__restrict__ x,
+                            int64_t n) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q < n) x[q] = (double)xh[q] + (double)xl[q];
 }
 
 __global__ void split_kernel(const double *__restrict__ x, float *__restrict__ xh, float *__restrict__ xl, int64_t n) {
@@ -554,8 +567,12 @@ bool launch_packed_residual_split(const DevLevel &L, const double *b, const floa
     return true;
 }
 
-void launch_add_split(double *x, const float *e, float *xh, float *xl, int64_t n, cudaStream_t s, Chain *ch) {
-    if (n) klaunch(add_split_kernel, (unsigned)((n + 255) / 256), 256u, 0, s, ch, x, e, xh, xl, n);
+void launch_add_pair(const float *e, float *xh, float *xl, int64_t n, cudaStream_t s, Chain *ch) {
+    if (n) klaunch(add_pair_kernel, (unsigned)((n + 255) / 256), 256u, 0, s, ch, e, xh, xl, n);
+}
+
+void launch_join(const float *xh, const float *xl, double *x, int64_t n, cudaStream_t s) {
+    if (n) join_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(xh, xl, x, n);
 }
 
 void launch_split(const double *x, float *xh, float *xl, int64_t n, cudaStream_t s) {
