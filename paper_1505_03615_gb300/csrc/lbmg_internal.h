@@ -18,6 +18,7 @@ constexpr int kNormBlocks = 256;  // partial sums of the two-pass norm reduction
 // 4 threads per row the kernels read the packed copy of the matrix (packed.cu).
 struct LaunchShape {
     int tpr = 4, tpb = 256;   // Gauss-Seidel with tpb = 1024: the whole-sweep cooperative kernel (packed.cu)
+    int grid = 0;             // its blocks (0: one per SM; fewer make the grid barrier cheaper on small levels)
 };
 constexpr int kSweepShapeTpb = 1024;
 enum { kShapeSmooth = 0, kShapeResidual = 1 };

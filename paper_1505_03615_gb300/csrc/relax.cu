@@ -168,7 +168,7 @@ void launch_sweeps(const Ctx &c, const DevLevel &L, int sweeps, bool forward, co
     if (sizeof(T) == 4 && sh.tpb == kSweepShapeTpb && 8 * sweeps <= 32 && c.sweep_bar && A == (const T *)L.A32) {
         int seq[32];
         for (int q = 0; q < 8 * sweeps; q++) seq[q] = forward ? q % 8 : 7 - q % 8;
-        const int blocks = c.sweep_blocks[R];
+        const int blocks = sh.grid > 0 && sh.grid < c.sweep_blocks[R] ? sh.grid : c.sweep_blocks[R];
         if (ch) ch->cut();   // a cooperative launch takes no programmatic serialisation
         if (launch_packed_sweep(L, seq, 8 * sweeps, (const float *)dinv, (const float *)b, (float *)x, R, c.sweep_bar,
                                 c.narrow.status, blocks, s))

@@ -133,17 +133,23 @@ cudaError_t tune_levels(Ctx &c, int R, int reps, int *timed) {
             if (dflt_ms > 0.f && best_ms > 0.98f * dflt_ms) { best = dflt; best_ms = dflt_ms; }
             // FP32 sweeps of a level with a packed copy: the whole-sweep cooperative kernel, kept when it
             // beats the colour launches by 2% (a refused launch or capture just leaves it out)
+            // (grids of all SMs down to an eighth of them: on small levels fewer blocks make the grid
+            // barrier between colours cheaper)
             if (kind == kShapeSmooth && !fp64 && L.pk_map && c.sweep_bar && c.sweep_blocks[R] > 0) {
-                LaunchShape sw;
-                sw.tpr = 4;
-                sw.tpb = kSweepShapeTpb;
-                L.shape[fp64][kind] = sw;
-                float ms = 0.f;
-                const cudaError_t es = time_kernel<T>(c, L, kind, R, reps, e0, e1, &ms);
-                if (es == cudaSuccess && ms > 0.f && ms < 0.98f * best_ms) { best = sw; best_ms = ms; }
-                if (es != cudaSuccess) {
-                    cudaGetLastError();
-                    cudaStreamSynchronize(c.capture_stream);
+                for (int div = 1; div <= 8; div *= 2) {
+                    LaunchShape sw;
+                    sw.tpr = 4;
+                    sw.tpb = kSweepShapeTpb;
+                    sw.grid = div == 1 ? 0 : std::max(1, c.sweep_blocks[R] / div);
+                    L.shape[fp64][kind] = sw;
+                    float ms = 0.f;
+                    const cudaError_t es = time_kernel<T>(c, L, kind, R, reps, e0, e1, &ms);
+                    if (es == cudaSuccess && ms > 0.f && ms < 0.98f * best_ms) { best = sw; best_ms = ms; }
+                    if (es != cudaSuccess) {
+                        cudaGetLastError();
+                        cudaStreamSynchronize(c.capture_stream);
+                        break;
+                    }
                 }
             }
             L.shape[fp64][kind] = best;
@@ -182,12 +188,12 @@ int tune_cache_save(const char *path) {
     FILE *f = std::fopen(path, "w");
     if (!f) return 1;
     std::lock_guard<std::mutex> lk(g_mu);
-    std::fprintf(f, "# device fp64 kind lanes rows nnz threads_per_row threads_per_block\n");
+    std::fprintf(f, "# device fp64 kind lanes rows nnz threads_per_row threads_per_block [sweep_grid]\n");
     for (const auto &kv : g_cache) {
         const Key &k = kv.first;
-        std::fprintf(f, "%s %d %d %d %lld %lld %d %d\n", std::get<0>(k).c_str(), std::get<1>(k), std::get<2>(k),
+        std::fprintf(f, "%s %d %d %d %lld %lld %d %d %d\n", std::get<0>(k).c_str(), std::get<1>(k), std::get<2>(k),
                      std::get<3>(k), (long long)std::get<4>(k), (long long)std::get<5>(k), kv.second.tpr,
-                     kv.second.tpb);
+                     kv.second.tpb, kv.second.grid);
     }
     return std::fclose(f) == 0 ? 0 : 1;
 }
@@ -200,9 +206,11 @@ int tune_cache_load(const char *path) {
     std::lock_guard<std::mutex> lk(g_mu);
     while (std::fgets(line, sizeof line, f)) {
         if (line[0] == '#' || line[0] == '\n') continue;
-        int fp64, kind, R, tpr, tpb;
+        int fp64, kind, R, tpr, tpb, grid = 0;
         long long n, nnz;
-        if (std::sscanf(line, "%255s %d %d %d %lld %lld %d %d", name, &fp64, &kind, &R, &n, &nnz, &tpr, &tpb) != 8 ||
+        const int got = std::sscanf(line, "%255s %d %d %d %lld %lld %d %d %d", name, &fp64, &kind, &R, &n, &nnz, &tpr,
+                                    &tpb, &grid);
+        if ((got != 8 && got != 9) || grid < 0 ||
             (fp64 != 0 && fp64 != 1) || (kind != 0 && kind != 1) || (tpr != 4 && tpr != 8 && tpr != 16) ||
             tpb < 32 || (tpb > 512 && !(tpb == kSweepShapeTpb && tpr == 4 && kind == kShapeSmooth)) || tpb % 32 != 0) {
             bad = 1;
@@ -211,6 +219,7 @@ int tune_cache_load(const char *path) {
         LaunchShape sh;
         sh.tpr = tpr;
         sh.tpb = tpb;
+        sh.grid = tpb == kSweepShapeTpb ? grid : 0;
         g_cache[Key{std::string(name), fp64, kind, R, (int64_t)n, (int64_t)nnz}] = sh;
     }
     std::fclose(f);

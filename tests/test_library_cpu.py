@@ -72,17 +72,21 @@ def test_null_handle_rejected():
 def test_tune_cache_file_round_trip_and_bad_lines(tmp_path):
     """The tuning cache is plain text: valid lines load, malformed ones are reported."""
     good = tmp_path / "tune.txt"
-    good.write_text("# device fp64 kind lanes rows nnz threads_per_row threads_per_block\n"
+    # eight columns, or nine with the grid of the whole-sweep kernel (threads per block 1024)
+    good.write_text("# device fp64 kind lanes rows nnz threads_per_row threads_per_block [sweep_grid]\n"
                     "Test_GPU 0 0 4 1000 18000 4 128\n"
-                    "Test_GPU 1 1 1 1000 18000 16 512\n")
+                    "Test_GPU 1 1 1 1000 18000 16 512\n"
+                    "Test_GPU 0 0 4 2000 36000 4 1024 38\n")
     L.lbmg_tune_cache_load(str(good))
     out = tmp_path / "saved.txt"
     L.lbmg_tune_cache_save(str(out))
     lines = [ln.split() for ln in out.read_text().splitlines() if not ln.startswith("#")]
-    assert ["Test_GPU", "0", "0", "4", "1000", "18000", "4", "128"] in lines
-    assert ["Test_GPU", "1", "1", "1", "1000", "18000", "16", "512"] in lines
+    assert ["Test_GPU", "0", "0", "4", "1000", "18000", "4", "128", "0"] in lines
+    assert ["Test_GPU", "1", "1", "1", "1000", "18000", "16", "512", "0"] in lines
+    assert ["Test_GPU", "0", "0", "4", "2000", "36000", "4", "1024", "38"] in lines
     bad = tmp_path / "bad.txt"
-    bad.write_text("Test_GPU 0 0 4 1000 18000 5 128\nnot a line\n")   # 5 threads per row is not a shape
+    # 5 threads per row is not a shape; 1024 threads per block only for a sweep with 4 per row
+    bad.write_text("Test_GPU 0 0 4 1000 18000 5 128\nnot a line\nTest_GPU 0 1 4 1000 18000 4 1024 0\n")
     with pytest.raises(L.LbmgError) as e:
         L.lbmg_tune_cache_load(str(bad))
     assert e.value.code == 1
