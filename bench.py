@@ -518,7 +518,7 @@ def batch_main(args):
         print(json.dumps({
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32 relax / f64 residual+assembly", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32 relax / f64 assembly, residual with f64 values as f32 pairs", "data": "synthetic",
             "config": {"workload": BATCH, "meshes": ninst, "triangles": int(sum(F.shape[0] for _, F, _ in meshes)),
                        "depths": sorted({int(d) for _, _, d in meshes}), "dofs_finest_total": nu, "nrhs": nrhs,
                        "t": t, "tol": tol, "precision": "mixed",
@@ -848,11 +848,16 @@ def main():
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 relax / f64 residual+assembly", "data": "synthetic",
+            "dtype": "f32 relax / f64 assembly, residual with f64 values as f32 pairs", "data": "synthetic",
             "config": {"workload": workload, "triangles": int(F.shape[0]), "depth": depth, "min_depth": d0,
                        "dofs_finest": n, "nnz_finest": nnz, "fragments_finest": nfrag, "nrhs": nrhs, "t": t,
                        "tol": tol, "precision": "mixed", "l2": "inputs larger than L2 (assembly streams >0.5 GB/step)",
                        "cycle": f"{args.cycle.upper()}({args.nu},{args.nu})",
+                       "assembly": ("every step: the finest entries gathered from the pieces' local integrals (mass "
+                                    "scaled by the current area weights), the Galerkin products of every coarser "
+                                    "level, A = M + tL and its packed and FP32 copies; the pieces' moments and local "
+                                    "integrals depend only on the build-time geometry and are computed by the first "
+                                    "assembly (setup)"),
                        "parallelism": "replicas" if ws > 1 else "single",
                        "solve": ("persistent (one cooperative launch)" if args.persistent else
                                  "one graph launch per solve (conditional loop, device stopping test)"),

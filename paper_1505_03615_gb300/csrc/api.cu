@@ -1123,7 +1123,10 @@ int lbmg_assemble(lbmg_handle h, double t, void *stream) {
     if (!h || !(t >= 0) || !std::isfinite(t)) return LBMG_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     Ctx &c = h->c;
-    launch_fragment_moments(c, s);
+    if (!c.moments_ready) {   // build-time geometry: once per hierarchy
+        launch_fragment_moments(c, s);
+        c.moments_ready = true;
+    }
     launch_fine_gather(c, t, s);
     for (int d = c.D - 1; d >= c.d0; d--) launch_galerkin(c, d, t, s);
     for (int d = c.d0; d <= c.D; d++) launch_inverse_diag(c.lev[d], c.diag_part, s);

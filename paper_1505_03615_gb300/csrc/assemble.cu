@@ -102,11 +102,12 @@ constexpr int kMomThreads = 128;
 
 // One thread per fragment (taken in the order forder).  Writes the 27 moments and
 // the 36 (M, L) local pair entries, pairs (a, b), a <= b, in upper-triangular order.
+constexpr int kStagePerFrag = 36;   // local (M, L) pairs a <= b of the 8 corner functions of a piece
+
 __global__ void __launch_bounds__(kMomThreads)
 fragment_moments_kernel(int nfrag, const int *__restrict__ forder, const double *__restrict__ poly,
                         const int *__restrict__ pstart, const int *__restrict__ ftri,
-                        const double *__restrict__ tnormal, const double *__restrict__ fscale,
-                        double *__restrict__ moments, double *__restrict__ stage) {
+                        const double *__restrict__ tnormal, double *__restrict__ moments, double *__restrict__ stage) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nfrag) return;
     const int f = __ldg(forder + t);
@@ -155,8 +156,7 @@ fragment_moments_kernel(int nfrag, const int *__restrict__ forder, const double 
     for (int q = 0; q < 27; q++) mo[q] = m[q];
     // tangential projector I - n n^T
     const double nv[3] = {n0, n1, n2};
-    const double fs = __ldg(fscale + f);
-    double2 *st = reinterpret_cast<double2 *>(stage) + 36 * (size_t)f;
+    double2 *st = reinterpret_cast<double2 *>(stage) + kStagePerFrag * (size_t)f;
     int p = 0;
 #pragma unroll
     for (int a = 0; a < 8; a++) {
@@ -167,7 +167,7 @@ fragment_moments_kernel(int nfrag, const int *__restrict__ forder, const double 
             int pt[3];
 #pragma unroll
             for (int k = 0; k < 3; k++) pt[k] = 3 + ab[k] + bb[k];     // phi_a phi_b along axis k
-            const double Mab = G3(m, pt[0], pt[1], pt[2]) * fs;
+            const double Mab = G3(m, pt[0], pt[1], pt[2]);   // in finest-unit area: fine_gather scales it
             double Lab = 0.0;
 #pragma unroll
             for (int pp = 0; pp < 3; pp++)
@@ -200,13 +200,14 @@ void launch_fragment_moments(const Ctx &c, cudaStream_t s) {
     if (c.nfrag == 0) return;
     const int blocks = (c.nfrag + kMomThreads - 1) / kMomThreads;
     fragment_moments_kernel<<<blocks, kMomThreads, 0, s>>>(c.nfrag, c.forder, c.poly, c.pstart, c.ftri, c.tnormal,
-                                                           c.frag_scale, c.moments, c.stage);
+                                                           c.moments, c.stage);
 }
 
 // finest level: sum the local-pair contributions of every stored entry
 __global__ void fine_gather_kernel(int64_t nnz, const int64_t *__restrict__ arp, const uint32_t *__restrict__ aidx,
-                                   const double2 *__restrict__ stage, double t, double *__restrict__ M,
-                                   double *__restrict__ L, double *__restrict__ A64, float *__restrict__ A32) {
+                                   const double2 *__restrict__ stage, const double *__restrict__ fscale, double t,
+                                   double *__restrict__ M, double *__restrict__ L, double *__restrict__ A64,
+                                   float *__restrict__ A32) {
     const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (s >= nnz) return;
     double m = 0.0, l = 0.0;
@@ -218,14 +219,16 @@ __global__ void fine_gather_kernel(int64_t nnz, const int64_t *__restrict__ arp,
 #pragma unroll
         for (int u = 0; u < 8; u++) ix[u] = __ldg(aidx + k + u);
         double2 v[8];
+        double w[8];
 #pragma unroll
-        for (int u = 0; u < 8; u++) v[u] = __ldg(stage + ix[u]);
+        for (int u = 0; u < 8; u++) { v[u] = __ldg(stage + ix[u]); w[u] = __ldg(fscale + ix[u] / kStagePerFrag); }
 #pragma unroll
-        for (int u = 0; u < 8; u++) { m += v[u].x; l += v[u].y; }
+        for (int u = 0; u < 8; u++) { m = fma(v[u].x, w[u], m); l += v[u].y; }
     }
     for (; k < k1; k++) {
-        const double2 v = __ldg(stage + aidx[k]);
-        m += v.x;
+        const uint32_t ix = aidx[k];
+        const double2 v = __ldg(stage + ix);
+        m = fma(v.x, __ldg(fscale + ix / kStagePerFrag), m);
         l += v.y;
     }
     M[s] = m;
@@ -239,7 +242,7 @@ void launch_fine_gather(const Ctx &c, double t, cudaStream_t s) {
     const DevLevel &L = c.lev[c.D];
     const int threads = 256;
     fine_gather_kernel<<<(unsigned)((L.nnz + threads - 1) / threads), threads, 0, s>>>(
-        L.nnz, c.arp, c.aidx, reinterpret_cast<const double2 *>(c.stage), t, L.M, L.L, L.A64, L.A32);
+        L.nnz, c.arp, c.aidx, reinterpret_cast<const double2 *>(c.stage), c.frag_scale, t, L.M, L.L, L.A64, L.A32);
 }
 
 // coarse level: (P^T A P)_ab = sum over listed fine entries of 2^-e A_il

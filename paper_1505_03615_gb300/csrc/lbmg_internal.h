@@ -148,6 +148,10 @@ struct Ctx {
     int D = 0, d0 = 0, nv = 0, nt = 0, nfrag = 0;
     int ninst = 1, nu = 0;                 // meshes; rows of a user finest vector
     double *frag_scale = nullptr;          // [nfrag] physical area per finest-unit area
+    // the pieces' moments and local (M, L) integrals in finest-unit area depend only on the
+    // build-time geometry: computed by the first assembly, reused by the next (frag_scale enters
+    // in fine_gather_kernel)
+    bool moments_ready = false;
     int *fperm = nullptr;                  // [nu] user finest index -> finest row
     int *fiperm = nullptr;                 // [n_D] finest row -> user index
     // coarsest blocks, one per mesh: (level, mesh, first row, rows, inverse offset), sorted by level
