@@ -555,6 +555,8 @@ def main():
     ap.add_argument("--oracle-min-depth", type=int, default=1,
                     help="coarsest depth of the oracle's V-cycle on its sample (the library's on the default workload)")
     ap.add_argument("--persistent", action="store_true", help="one cooperative launch per solve")
+    ap.add_argument("--gpu-clip", action="store_true",
+                    help="cut the triangles into finest-voxel pieces on the GPU during the hierarchy build")
     ap.add_argument("--no-graphs", action="store_true", help="launch each cycle's kernels directly (profilers)")
     ap.add_argument("--only-timed", action="store_true", help="stop after the timed steps (profiling runs)")
     ap.add_argument("--learned-zero", action="store_true",
@@ -606,6 +608,7 @@ def main():
     nv = V.shape[0]
     t_build = time.perf_counter()
     h = L.lbmg_build_hierarchy(V, F, depth, persistent=int(args.persistent), use_graphs=int(not args.no_graphs),
+                               gpu_clip=int(args.gpu_clip),
                                pdl=int(not args.no_pdl), cycle=int(args.cycle == "w"), nu1=args.nu, nu2=args.nu)
     t_build = time.perf_counter() - t_build
     d0, D = L.lbmg_levels(h)
@@ -865,7 +868,8 @@ def main():
                        "launch_shapes_mixed": {d: {"sweep": list(v[0]), "residual": list(v[1])}
                                                for d, v in shapes.items()},
                        "tuned_us_per_sweep_and_residual": tuned_us},
-            "setup_s": {"hierarchy_build_and_upload": t_build, "autotune": t_tune},
+            "setup_s": {"hierarchy_build_and_upload": t_build, "autotune": t_tune,
+                        "pieces_cut_on": "gpu" if args.gpu_clip else "host cores"},
             "ms_to_tol_mixed": ms_per_step, "ms_to_tol_fp64": fp64_ms, "solver": args.solver,
             "other_solver": {"solver": other, **other_res}, "learned": learned, "cmcf": cmcf,
             "cycles_per_step": cycles / args.steps, "fp64_cycles_per_step": fp64_cycles / fp64_steps,

@@ -60,7 +60,7 @@ class Options(C.Structure):
                 ("persistent", C.c_int), ("narrow_max", C.c_int), ("barrier_phantoms", C.c_int),
                 ("use_graphs", C.c_int), ("pdl", C.c_int), ("copy_phantom_bytes", C.c_int),
                 ("host_alloc_fail", C.c_int), ("host_check", C.c_int), ("cycle", C.c_int),
-                ("coarse_smooth", C.c_int)]
+                ("coarse_smooth", C.c_int), ("gpu_clip", C.c_int)]
 
 
 class Stats(C.Structure):

@@ -828,6 +828,7 @@ static int check_build_options(const lbmg_options &o) {
     if (o.narrow_max < 0 || o.barrier_phantoms < 0 || o.barrier_phantoms > 1024) return LBMG_INVALID_ARG;
     if (o.copy_phantom_bytes < 0 || o.copy_phantom_bytes > 65536) return LBMG_INVALID_ARG;
     if (o.host_alloc_fail != 0 && o.host_alloc_fail != 1) return LBMG_INVALID_ARG;
+    if (o.gpu_clip != 0 && o.gpu_clip != 1) return LBMG_INVALID_ARG;
     return LBMG_OK;
 }
 
@@ -840,7 +841,7 @@ static int build_single_host(const double *V, int nv, const int *F, int nt, int 
     try {
         std::vector<HostHierarchy> parts(1);
         st = build_host_hierarchy(V, nv, F, nt, depth, o.min_depth, o.coarse_max, o.split, o.threads, parts[0], err,
-                                  o.host_alloc_fail != 0);
+                                  o.host_alloc_fail != 0, o.gpu_clip != 0);
         if (st == 0) st = combine_batch(parts, out, err);
     } catch (const std::bad_alloc &) {
         st = LBMG_OUT_OF_MEMORY;
@@ -898,7 +899,8 @@ static int build_batch_host(const double *const *V, const int *nv, const int *co
             for (int i = 0; i < ninst; i++) {
                 try {
                     sti[i] = build_host_hierarchy(V[i], nv[i], F[i], nt[i], depth[i], o.min_depth, o.coarse_max,
-                                                  o.split, 0, parts[i], erri[i], o.host_alloc_fail != 0);
+                                                  o.split, 0, parts[i], erri[i], o.host_alloc_fail != 0,
+                                                  o.gpu_clip != 0);
                 } catch (const std::bad_alloc &) {
                     sti[i] = LBMG_OUT_OF_MEMORY;
                     erri[i] = "host memory exhausted";
@@ -930,6 +932,7 @@ static int check_batch_options(const lbmg_options &o) {
     if (o.nu1 < 0 || o.nu2 < 0 || o.coarse_max < 1 || o.coarse_max > kMaxCoarse) return LBMG_INVALID_ARG;
     if (o.smoother != LBMG_GS_COLOURED || o.narrow_max < 0 || o.barrier_phantoms < 0) return LBMG_INVALID_ARG;
     if (o.host_alloc_fail != 0 && o.host_alloc_fail != 1) return LBMG_INVALID_ARG;
+    if (o.gpu_clip != 0 && o.gpu_clip != 1) return LBMG_INVALID_ARG;
     if (o.cycle != 0 || o.coarse_smooth != 0 || o.host_check < 0 || o.host_check > 1) return LBMG_INVALID_ARG;
     return LBMG_OK;
 }
@@ -981,6 +984,7 @@ void lbmg_default_options(lbmg_options *o) {
     o->host_check = 0;
     o->cycle = 0;
     o->coarse_smooth = 0;
+    o->gpu_clip = 0;
 }
 
 int lbmg_build_hierarchy(const double *V, int nv, const int *F, int nt, int depth, const lbmg_options *opt,

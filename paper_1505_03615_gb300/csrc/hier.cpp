@@ -86,8 +86,6 @@ double poly_area(const Poly &p) {
     return 0.5 * std::sqrt(s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
 }
 
-struct FragOut { uint64_t key; int tri; int vox[3]; std::vector<double> poly; };
-
 // cut triangle t into finest-voxel pieces by sweeping planes along x, then y, then z
 void cut_triangle(const HostHierarchy &H, int t, int N, std::vector<FragOut> &out) {
     Poly tri(3);
@@ -416,7 +414,7 @@ void rows_with_lists(int n, int ncols, const Emit &emit, HostLevel &L, std::vect
 
 int build_host_hierarchy(const double *V, int nv, const int *F, int nt, int depth, int min_depth,
                          int coarse_max, int split, int threads, HostHierarchy &H, std::string &err,
-                         bool fail_alloc) {
+                         bool fail_alloc, bool gpu_clip) {
     if (!V || !F || nv < 3 || nt < 1 || depth < 1 || depth > kMaxDepth) { err = "bad mesh size or depth"; return 1; }
     for (int64_t i = 0; i < 3 * (int64_t)nt; i++)
         if (F[i] < 0 || F[i] >= nv) { err = "triangle index out of range"; return 1; }
@@ -493,7 +491,11 @@ int build_host_hierarchy(const double *V, int nv, const int *F, int nt, int dept
 
     // finest fragments
     std::vector<FragOut> frags;
-    {
+    if (gpu_clip) {
+        const int st = gpu_cut_triangles(H, N, frags, err);
+        if (st) return st;
+        for (auto &f : frags) f.key = morton(f.vox[0], f.vox[1], f.vox[2]);
+    } else {
 #ifdef _OPENMP
         int nth = omp_get_max_threads();
 #else

@@ -16,6 +16,10 @@ constexpr uint32_t kPackMask = (1u << kPackShift) - 1u;
 constexpr int kGalShift = 29;
 constexpr uint32_t kGalMask = (1u << kGalShift) - 1u;
 
+// one finest piece of a triangle: its voxel's Morton key, the triangle, the voxel and the
+// polygon's vertices in voxel-local coordinates (x, y, z per vertex)
+struct FragOut { uint64_t key; int tri; int vox[3]; std::vector<double> poly; };
+
 struct CornerTri {
     uint64_t key;   // Morton key of a grid corner
     int32_t tri;    // a triangle meeting that corner's support
@@ -98,6 +102,13 @@ int combine_batch(std::vector<HostHierarchy> &parts, HostHierarchy &B, std::stri
 // allocation would.
 int build_host_hierarchy(const double *V, int nv, const int *F, int nt, int depth, int min_depth,
                          int coarse_max, int split, int threads, HostHierarchy &H, std::string &err,
-                         bool fail_alloc = false);
+                         bool fail_alloc = false, bool gpu_clip = false);
+
+// Row a1 on the GPU (clip.cu): the finest pieces of every triangle of H (H.Vg, H.F, N = 2^depth
+// voxels per axis), cut by the same sweep of axis planes as the host builder and kept when their
+// area exceeds kFragTau; out gets them unsorted with key = 0.  Returns 0, or an lbmg status
+// with a message in err (no device, a failed allocation, or a piece with more vertices than the
+// kernel holds, which a triangle clipped by a box cannot have).
+int gpu_cut_triangles(const HostHierarchy &H, int N, std::vector<FragOut> &out, std::string &err);
 
 }  // namespace lbmg

@@ -128,3 +128,43 @@ def test_full_size_pcg_solve_reaches_tolerance(workload):
     r = b - (M + t * Lm) @ xx
     rel = np.linalg.norm(r, axis=0) / np.linalg.norm(b, axis=0)
     assert np.all(rel <= 2 * tol)
+
+
+@pytest.fixture(scope="module")
+def knot35():
+    w = _build("knot35_4m_d10")
+    yield w
+    L.lbmg_destroy(w[-1])
+
+
+def _host_rel(h, depth, t, rhs, x):
+    M, Lm = _csr(h, depth)
+    b, xx = rhs.cpu().numpy(), x.cpu().numpy()
+    r = b - (M + t * Lm) @ xx
+    return np.linalg.norm(r, axis=0) / np.linalg.norm(b, axis=0)
+
+
+def test_full_size_headline_mixed_and_learned_solves_reach_tolerance(knot35):
+    """The bench's headline configuration: the 4M-triangle (3,5) knot at depth 10, three right-hand
+    sides, mixed V(2,2) to 1e-6, plain and with the learned correction (trained by the bench's recipe
+    on three small meshes), each checked by an FP64 residual recomputed on the host; the learned solve
+    needs fewer cycles."""
+    import bench
+    V, F, depth, t, f, tol, h = knot35
+    n = L.lbmg_level_info(h, depth)[0]
+    rhs = torch.zeros((n, 3), dtype=torch.float64, device="cuda:0")
+    L.lbmg_project_rhs(h, torch.tensor(f, device="cuda:0"), rhs)
+    params, _, _ = bench.learned_train(L, "cuda:0", 800, 1e-2)
+    cycles = {}
+    for mode in ("plain", "learned"):
+        if mode == "learned":
+            L.lbmg_learned_params(h, params)
+        L.lbmg_learned_enable(h, mode == "learned")
+        x = torch.zeros_like(rhs)
+        code, st = L.lbmg_solve(h, rhs, x, tol, 2000, L.LBMG_MIXED)
+        assert code == L.LBMG_OK and st.converged and st.learned == (mode == "learned")
+        rel = _host_rel(h, depth, t, rhs, x)
+        assert np.all(rel <= 1.05 * tol), (mode, rel)
+        cycles[mode] = st.cycles
+    L.lbmg_learned_enable(h, False)
+    assert cycles["learned"] < 0.85 * cycles["plain"], cycles
