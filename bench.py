@@ -756,8 +756,17 @@ def main():
     # conformalized mean-curvature flow (Section 5.3): a few steps of the library's flow loop
     # (area weights of the current positions, assembly, projection, warm-started solve, vertex
     # evaluation, all on the device), the unit of the paper's Table 1
-    cmcf = None
-    if args.cmcf_steps > 0:
+    learned, params = None, None
+    if not args.no_learned and args.solver == "vcycle" and not args.persistent:
+        params, hist, train_s = learned_train(L, dev, args.learned_steps, args.learned_lr)
+        learned = learned_compare(L, h, step, args.steps, params, hist, train_s, args)
+        learned["vs_plain_mixed"] = (ms_per_step / learned["learned"]["ms_to_tol"]) if ws == 1 else None
+
+    def flow(k, with_learned):
+        """k steps of the library's flow loop from the build-time positions, after one untimed step"""
+        if with_learned:
+            L.lbmg_learned_params(h, params)
+        L.lbmg_learned_enable(h, with_learned)
         X = torch.tensor(V, device=dev)
         xc = torch.zeros((n, 3), dtype=torch.float64, device=dev)
         Xn = torch.zeros_like(X)
@@ -766,23 +775,28 @@ def main():
         X, Xn = Xn, X
         torch.cuda.synchronize()
         g0.record()
-        ccyc = 0
-        for _ in range(args.cmcf_steps):
+        ccyc, fb = 0, 0
+        for _ in range(k):
             code, st = L.lbmg_cmcf_step(h, X, t, xc, tol, max_cycles, L.LBMG_MIXED, Xn, solver=solver)
             ccyc += st.cycles
+            fb = max(fb, st.learned_fallback)
             X, Xn = Xn, X
         g1.record()
         torch.cuda.synchronize()
         L.lbmg_set_area_weights(h, None)
-        cmcf = {"steps": args.cmcf_steps, "delta": t, "solver": args.solver, "precision": "mixed",
-                "ms_per_step": g0.elapsed_time(g1) / args.cmcf_steps, "cycles_per_step": ccyc / args.cmcf_steps,
-                "warm_start": True}
+        L.lbmg_learned_enable(h, False)
+        return {"ms_per_step": g0.elapsed_time(g1) / k, "cycles_per_step": ccyc / k, "fallback": fb}
 
-    learned = None
-    if not args.no_learned and args.solver == "vcycle" and not args.persistent:
-        params, hist, train_s = learned_train(L, dev, args.learned_steps, args.learned_lr)
-        learned = learned_compare(L, h, step, args.steps, params, hist, train_s, args)
-        learned["vs_plain_mixed"] = (ms_per_step / learned["learned"]["ms_to_tol"]) if ws == 1 else None
+    # conformalized mean-curvature flow (Section 5.3): a few steps of the library's flow loop
+    # (area weights of the current positions, assembly, projection, warm-started solve, vertex
+    # evaluation, all on the device), the unit of the paper's Table 1; also with the learned
+    # correction when it was trained
+    cmcf = None
+    if args.cmcf_steps > 0:
+        cmcf = {"steps": args.cmcf_steps, "delta": t, "solver": args.solver, "precision": "mixed",
+                "warm_start": True, **flow(args.cmcf_steps, False)}
+        if params is not None:
+            cmcf["learned"] = flow(args.cmcf_steps, True)
 
     # roofline of the dominant kernel (the finest-level Gauss-Seidel colour), timed live with
     # CUDA events on its stream: the timed steps run each solve as one graph launch, whose

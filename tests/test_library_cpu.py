@@ -38,7 +38,8 @@ def test_status_strings_and_defaults():
     assert (o.min_depth, o.coarse_max, o.nu1, o.nu2, o.split) == (-1, 160, 2, 2, 1)
 
 
-@pytest.mark.parametrize("case", ["bad_index", "nan_vertex", "depth0", "depth13", "min_gt_depth", "bad_smoother"])
+@pytest.mark.parametrize("case", ["bad_index", "nan_vertex", "depth0", "depth13", "min_gt_depth", "bad_smoother",
+                                  "bad_gpu_clip"])
 def test_invalid_input_rejected_on_host(case):
     V = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], dtype=np.float64)
     F = np.array([[0, 1, 2], [0, 1, 3]], dtype=np.int32)
@@ -55,9 +56,15 @@ def test_invalid_input_rejected_on_host(case):
         opts = {"min_depth": 5}
     elif case == "bad_smoother":
         opts = {"smoother": 9}
+    elif case == "bad_gpu_clip":
+        opts = {"gpu_clip": 2}
     with pytest.raises(L.LbmgError) as e:
         L.lbmg_build_hierarchy(V, F, depth, **opts)
     assert e.value.code == 1
+    if case == "bad_gpu_clip":   # the host-only build checks its options the same way, without a GPU
+        with pytest.raises(L.LbmgError) as e:
+            L.lbmg_host_build(V, F, depth, **opts)
+        assert e.value.code == 1
 
 
 def test_null_handle_rejected():
@@ -67,6 +74,11 @@ def test_null_handle_rejected():
     assert lib.lbmg_levels(None, None, None) == 1
     assert lib.lbmg_set_area_weights(None, None, None) == 1
     assert lib.lbmg_host_levels(None, None, None) == 1
+    # the learned correction and the split residual on a null handle
+    assert lib.lbmg_learned_enable(None, 1, None) == 1
+    assert lib.lbmg_learned_state(None, None, None, None) == 1
+    assert lib.lbmg_learned_apply(None, None, 1, 1, None, None, None) == 1
+    assert lib.lbmg_residual_split(None, 0, None, None, None, 1, None) == 1
 
 
 def test_tune_cache_file_round_trip_and_bad_lines(tmp_path):
