@@ -98,12 +98,15 @@ typedef struct lbmg_options {
                            relaxed by nu1 + nu2 coloured Gauss-Seidel sweeps like the other levels (the
                            minimum-depth sweep of Section 5.2, where the minimum depth is the coarsest
                            level a cycle visits).  Single meshes, not with persistent */
-    int gpu_clip;       /* 0 (default): the hierarchy build cuts the triangles into finest-voxel pieces
-                           on the host cores; 1: on the GPU (row a1: one thread per triangle, the same
-                           sweep of axis planes; the labelling, prolongation and lists stay on the host).
-                           The pieces agree with the host's up to FMA contraction in the plane
-                           intersections.  Needs a GPU (LBMG_CUDA_ERROR otherwise), also for
-                           lbmg_host_build */
+    int gpu_clip;       /* 0 (default): the hierarchy build runs on the host cores; 1: two of its steps
+                           run on the GPU: the cut of the triangles into finest-voxel pieces (one thread
+                           per triangle, the same sweep of axis planes) and, on every level, the sorted
+                           (corner, triangle) pairs and the split labelling of each corner's support
+                           into connected components (Section 4.2; one thread per corner, corners with
+                           more than 64 triangles labelled on the host).  The prolongation and the
+                           contribution lists stay on the host.  The pieces agree with the host's up to
+                           FMA contraction in the plane intersections, the labels exactly.  Needs a GPU
+                           (LBMG_CUDA_ERROR otherwise), also for lbmg_host_build */
 } lbmg_options;
 
 typedef struct lbmg_stats {

@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblbmg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU = ["assemble.cu", "relax.cu", "packed.cu", "persist.cu", "narrow.cu", "learned.cu", "noalloc.cu", "cmcf.cu", "lobpcg.cu", "tune.cu", "clip.cu", "api.cu"]
+CU = ["assemble.cu", "relax.cu", "packed.cu", "persist.cu", "narrow.cu", "learned.cu", "noalloc.cu", "cmcf.cu", "lobpcg.cu", "tune.cu", "clip.cu", "basis.cu", "api.cu"]
 CPP = ["hier.cpp", "batch.cpp"]
 
 

@@ -846,6 +846,9 @@ static int build_single_host(const double *V, int nv, const int *F, int nt, int 
     } catch (const std::bad_alloc &) {
         st = LBMG_OUT_OF_MEMORY;
         err = "host memory exhausted";
+    } catch (const BuildCudaError &e) {
+        st = LBMG_CUDA_ERROR;
+        err = e.what();
     } catch (const std::exception &e) {
         st = LBMG_INVALID_ARG;
         err = e.what();
@@ -904,6 +907,9 @@ static int build_batch_host(const double *const *V, const int *nv, const int *co
                 } catch (const std::bad_alloc &) {
                     sti[i] = LBMG_OUT_OF_MEMORY;
                     erri[i] = "host memory exhausted";
+                } catch (const BuildCudaError &e) {
+                    sti[i] = LBMG_CUDA_ERROR;
+                    erri[i] = e.what();
                 } catch (const std::exception &e) {
                     sti[i] = LBMG_INVALID_ARG;
                     erri[i] = e.what();

@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <memory>
 #include <numeric>
 #include <stdexcept>
 
@@ -28,28 +29,6 @@
 
 namespace lbmg {
 namespace {
-
-inline uint64_t spread3(uint32_t v) {
-    uint64_t x = v & 0x1fffff;
-    x = (x | x << 32) & 0x1f00000000ffffULL;
-    x = (x | x << 16) & 0x1f0000ff0000ffULL;
-    x = (x | x << 8) & 0x100f00f00f00f00fULL;
-    x = (x | x << 4) & 0x10c30c30c30c30c3ULL;
-    x = (x | x << 2) & 0x1249249249249249ULL;
-    return x;
-}
-inline uint64_t morton(int x, int y, int z) {
-    return spread3((uint32_t)x) | (spread3((uint32_t)y) << 1) | (spread3((uint32_t)z) << 2);
-}
-inline uint32_t compact3(uint64_t x) {
-    x &= 0x1249249249249249ULL;
-    x = (x ^ (x >> 2)) & 0x10c30c30c30c30c3ULL;
-    x = (x ^ (x >> 4)) & 0x100f00f00f00f00fULL;
-    x = (x ^ (x >> 8)) & 0x1f0000ff0000ffULL;
-    x = (x ^ (x >> 16)) & 0x1f00000000ffffULL;
-    x = (x ^ (x >> 32)) & 0x1fffff;
-    return (uint32_t)x;
-}
 
 struct Pt { double v[3]; };
 using Poly = std::vector<Pt>;
@@ -203,7 +182,7 @@ int lookup_dof(const HostLevel &L, uint64_t key, int tri) {
 // split basis of one level from its (voxel, triangle) cells
 void build_level_basis(HostHierarchy &H, HostLevel &L, const std::vector<KT> &cells,
                        const std::vector<int32_t> &adj_ptr, const std::vector<int32_t> &adj,
-                       const std::vector<int32_t> &vt_ptr, const std::vector<int32_t> &vt) {
+                       const std::vector<int32_t> &vt_ptr, const std::vector<int32_t> &vt, const GpuBasis *gb) {
     const int shift = H.D - L.d;
     const double s = (double)(1 << shift);
     // (corner, triangle) pairs
@@ -212,7 +191,16 @@ void build_level_basis(HostHierarchy &H, HostLevel &L, const std::vector<KT> &ce
     // key and triangle fit one 64-bit word, the pairs are sorted as such words (same order)
     int tbits = 1;
     while (tbits < 31 && (1LL << tbits) < (int64_t)H.nt) tbits++;
-    if (3 * (L.d + 1) + tbits <= 64) {
+    std::vector<uint64_t> gw;   // the GPU's sorted unique words (gb only)
+    const bool on_gpu = gb != nullptr && 3 * (L.d + 1) + tbits <= 64;
+    if (on_gpu) {
+        std::string err;
+        if (!gpu_corner_pairs(cells, tbits, 3 * (L.d + 1), gw, err)) throw BuildCudaError(err);
+        ct.resize(gw.size());
+        const uint64_t tmask = (1ULL << tbits) - 1;
+#pragma omp parallel for schedule(static)
+        for (long i = 0; i < (long)gw.size(); i++) ct[i] = KT{gw[i] >> tbits, (int32_t)(gw[i] & tmask)};
+    } else if (3 * (L.d + 1) + tbits <= 64) {
         std::vector<uint64_t> w(cells.size() * 8);
 #pragma omp parallel for schedule(static)
         for (long i = 0; i < (long)cells.size(); i++) {
@@ -248,8 +236,16 @@ void build_level_basis(HostHierarchy &H, HostLevel &L, const std::vector<KT> &ce
     std::vector<int32_t> ncomp(ng);
     // Corners are taken largest first, one at a time: on coarse levels a few corners hold
     // most of the mesh each, and they must not queue behind one another on one thread.
-    std::vector<int64_t> order(ng);
-    std::iota(order.begin(), order.end(), (int64_t)0);
+    // With the GPU labelling the host takes only the runs the GPU leaves (ncomp < 0).
+    std::vector<int64_t> order;
+    if (on_gpu) {
+        std::string err;
+        if (!gpu_run_components(gb, gw, gstart, tbits, H.split, s, comp, ncomp, err)) throw BuildCudaError(err);
+        for (int64_t g = 0; g < ng; g++) if (ncomp[g] < 0) order.push_back(g);
+    } else {
+        order.resize(ng);
+        std::iota(order.begin(), order.end(), (int64_t)0);
+    }
     std::sort(order.begin(), order.end(), [&](int64_t x, int64_t y) {
         const int64_t sx = gstart[x + 1] - gstart[x], sy = gstart[y + 1] - gstart[y];
         return sx > sy || (sx == sy && x < y);
@@ -260,7 +256,7 @@ void build_level_basis(HostHierarchy &H, HostLevel &L, const std::vector<KT> &ce
         // position of each triangle within the current corner's list, -1 when absent
         std::vector<int32_t> slot_of(H.nt, -1);
 #pragma omp for schedule(dynamic, 1)
-        for (int64_t o = 0; o < ng; o++) {
+        for (int64_t o = 0; o < (int64_t)order.size(); o++) {
             const int64_t g = order[o];
             const int64_t b = gstart[g], e = gstart[g + 1];
             const int n = (int)(e - b);
@@ -489,6 +485,12 @@ int build_host_hierarchy(const double *V, int nv, const int *F, int nt, int dept
             for (int e = 0; e < 3; e++) vt[fill[F[3 * t + e]]++] = t;
     }
 
+    // the mesh on the device for the GPU labelling of row a2 (with gpu_clip)
+    std::unique_ptr<GpuBasis, void (*)(GpuBasis *)> gbase(nullptr, gpu_basis_free);
+    if (gpu_clip) {
+        gbase.reset(gpu_basis_setup(H, adj_ptr, adj, vt_ptr, vt, err));
+        if (!gbase) return 7;   // LBMG_CUDA_ERROR
+    }
     // finest fragments
     std::vector<FragOut> frags;
     if (gpu_clip) {
@@ -546,7 +548,7 @@ int build_host_hierarchy(const double *V, int nv, const int *F, int nt, int dept
     for (;;) {
         HostLevel &L = H.lev[d];
         L.d = d;
-        build_level_basis(H, L, cells, adj_ptr, adj, vt_ptr, vt);
+        build_level_basis(H, L, cells, adj_ptr, adj, vt_ptr, vt, gbase.get());
         if (min_depth >= 0) { if (d <= min_depth) break; }
         else if (L.ndof <= coarse_max) break;
         if (d == 0) break;

@@ -2,6 +2,7 @@
 // (Chuang & Kazhdan, Sections 3.2 and 4), in the layout the CUDA kernels use.
 #pragma once
 #include <cstdint>
+#include <stdexcept>
 #include <string>
 #include <vector>
 
@@ -19,6 +20,36 @@ constexpr uint32_t kGalMask = (1u << kGalShift) - 1u;
 // one finest piece of a triangle: its voxel's Morton key, the triangle, the voxel and the
 // polygon's vertices in voxel-local coordinates (x, y, z per vertex)
 struct FragOut { uint64_t key; int tri; int vox[3]; std::vector<double> poly; };
+
+// Morton keys of grid cells and corners (21 bits per axis), for host and device code alike
+#ifdef __CUDACC__
+#define LBMG_HD __host__ __device__
+#else
+#define LBMG_HD
+#endif
+LBMG_HD inline uint64_t spread3(uint32_t v) {
+    uint64_t x = v & 0x1fffff;
+    x = (x | x << 32) & 0x1f00000000ffffULL;
+    x = (x | x << 16) & 0x1f0000ff0000ffULL;
+    x = (x | x << 8) & 0x100f00f00f00f00fULL;
+    x = (x | x << 4) & 0x10c30c30c30c30c3ULL;
+    x = (x | x << 2) & 0x1249249249249249ULL;
+    return x;
+}
+LBMG_HD inline uint64_t morton(int x, int y, int z) {
+    return spread3((uint32_t)x) | (spread3((uint32_t)y) << 1) | (spread3((uint32_t)z) << 2);
+}
+LBMG_HD inline uint32_t compact3(uint64_t x) {
+    x &= 0x1249249249249249ULL;
+    x = (x ^ (x >> 2)) & 0x10c30c30c30c30c3ULL;
+    x = (x ^ (x >> 4)) & 0x100f00f00f00f00fULL;
+    x = (x ^ (x >> 8)) & 0x1f0000ff0000ffULL;
+    x = (x ^ (x >> 16)) & 0x1f00000000ffffULL;
+    x = (x ^ (x >> 32)) & 0x1fffff;
+    return (uint32_t)x;
+}
+
+
 
 struct CornerTri {
     uint64_t key;   // Morton key of a grid corner
@@ -110,5 +141,22 @@ int build_host_hierarchy(const double *V, int nv, const int *F, int nt, int dept
 // with a message in err (no device, a failed allocation, or a piece with more vertices than the
 // kernel holds, which a triangle clipped by a box cannot have).
 int gpu_cut_triangles(const HostHierarchy &H, int N, std::vector<FragOut> &out, std::string &err);
+
+// Row a2 on the GPU (basis.cu): the mesh arrays on the device, the sorted unique (corner,
+// triangle) words of a level's cells (morton(corner) << tbits | tri, key_bits bits of corner
+// key), and the component labels of the runs of one corner in those words (ncomp = -1 for runs
+// of more than 64 triangles, which the host labels).  A CUDA failure throws BuildCudaError.
+struct BuildCudaError : std::runtime_error {
+    explicit BuildCudaError(const std::string &m) : std::runtime_error(m) {}
+};
+struct GpuBasis;
+GpuBasis *gpu_basis_setup(const HostHierarchy &H, const std::vector<int32_t> &adj_ptr, const std::vector<int32_t> &adj,
+                          const std::vector<int32_t> &vt_ptr, const std::vector<int32_t> &vt, std::string &err);
+void gpu_basis_free(GpuBasis *G);
+bool gpu_corner_pairs(const std::vector<CornerTri> &cells, int tbits, int key_bits, std::vector<uint64_t> &words,
+                      std::string &err);
+bool gpu_run_components(const GpuBasis *G, const std::vector<uint64_t> &words, const std::vector<int64_t> &gstart,
+                        int tbits, int split, double s, std::vector<int32_t> &comp, std::vector<int32_t> &ncomp,
+                        std::string &err);
 
 }  // namespace lbmg

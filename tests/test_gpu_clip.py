@@ -1,10 +1,11 @@
-"""Row a1 of the hierarchy build on the GPU (options.gpu_clip = 1): the triangles cut into
-finest-voxel pieces by one thread per triangle, against the host builder's cut.
+"""Steps of the hierarchy build on the GPU (options.gpu_clip = 1), against the host builder:
+the triangles cut into finest-voxel pieces (row a1, one thread per triangle) and, on every
+level, the sorted (corner, triangle) pairs and the split labelling of each corner's support
+into connected components (row a2, one thread per corner).
 
-The labelling, prolongation and contribution lists stay on the host, so a build from the
-GPU's pieces must give the same split functions, patterns and prolongation as a build from
-the host's pieces, exactly; the matrices assembled from the two agree to 1e-13 of their
-largest entry (the pieces' vertices differ at most by FMA contraction in the plane
+The build from the GPU's pieces and labels must give the same split functions, patterns and
+prolongation as the host's, exactly; the matrices assembled from the two agree to 1e-13 of
+their largest entry (the pieces' vertices differ at most by FMA contraction in the plane
 intersections, a few units of the last place).  The seeded meshes include nearly touching
 sheets (heavy splitting) and a (3,5) knot on the bench's depth-10 grid."""
 import time
@@ -36,7 +37,7 @@ def test_gpu_pieces_give_the_host_builders_hierarchy(mesh):
     hg = L.lbmg_host_build(V, F, depth, gpu_clip=1)
     t2 = time.perf_counter()
     try:
-        print(f"\n{mesh}: host build {t1 - t0:.2f} s with host pieces, {t2 - t1:.2f} s with GPU pieces")
+        print(f"\n{mesh}: host build {t1 - t0:.2f} s on the host cores, {t2 - t1:.2f} s with the GPU steps")
         assert L.lbmg_host_levels(hc) == L.lbmg_host_levels(hg)
         d0, D = L.lbmg_host_levels(hc)
         for d in range(d0, D + 1):
