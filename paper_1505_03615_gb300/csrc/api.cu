@@ -494,10 +494,20 @@ int build_cond_graph(Ctx &c, int R, int precision, bool pcg, cudaGraphExec_t *ou
     const bool batch = c.ninst > 1;
     cudaGraph_t g = nullptr;
     LBMG_CK(cudaGraphCreate(&g, 0));
+    // on an error return: end a capture still open into the graph or its body, then free the graph
     struct GraphGuard {
         cudaGraph_t g;
-        ~GraphGuard() { if (g) cudaGraphDestroy(g); }
-    } guard{g};
+        cudaStream_t cs;
+        ~GraphGuard() {
+            cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+            if (cudaStreamIsCapturing(cs, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
+                cudaGraph_t part = nullptr;   // the captured-to graph itself: owned by g
+                cudaStreamEndCapture(cs, &part);
+            }
+            cudaGetLastError();
+            if (g) cudaGraphDestroy(g);
+        }
+    } guard{g, cs};
     cudaGraphConditionalHandle hc;
     LBMG_CK(cudaGraphConditionalHandleCreate(&hc, g, 0, cudaGraphCondAssignDefault));
     LBMG_CK(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
@@ -540,13 +550,7 @@ int get_cond_graph(lbmg_handle h, int R, int precision, bool pcg, cudaGraphExec_
     if (g.exec) { cudaGraphExecDestroy(g.exec); g.exec = nullptr; }
     int e = build_cond_graph(c, R, precision, pcg, &g.exec);
     if (e != LBMG_OK) {
-        // end a capture the failure may have left open, then report
-        cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
-        if (cudaStreamIsCapturing(c.capture_stream, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
-            cudaGraph_t junk = nullptr;
-            cudaStreamEndCapture(c.capture_stream, &junk);
-            if (junk) cudaGraphDestroy(junk);
-        }
+        // (the builder has ended any capture it left open)
         cudaGetLastError();
         g.exec = nullptr;
         return e;
@@ -781,7 +785,7 @@ int upload_hierarchy(lbmg_handle h) {
         return LBMG_OK;
     }
     if (narrow_views_setup(c) != 0) return LBMG_CUDA_ERROR;
-    if (c.ninst == 1 && narrow_smem_setup(c, 200 * 1024) != 0) {
+    if (c.ninst == 1 && narrow_smem_setup(c, narrow_smem_budget()) != 0) {
         cudaGetLastError();
         c.narrow.dn = c.d0 - 1;   // the bottom then runs from global memory
     }

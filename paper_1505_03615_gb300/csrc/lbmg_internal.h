@@ -107,7 +107,9 @@ struct NarrowLevel {
     int n = 0, ns = 0, nnz = 0, cb0 = 0, ncb = 0;
     int cs[9] = {0};
     // byte offsets in shared memory (blob part, then vectors); -1 = absent
-    int o_rp = -1, o_ci = -1, o_A = -1, o_dinv = -1, o_par = -1, o_npl2 = -1, o_crp = -1, o_cch = -1;
+    // (parents: o_pof [n + 1] offsets into o_par, the parents of each row in order; r: one
+    // buffer shared by all levels, live only between a level's residual and its restriction)
+    int o_rp = -1, o_ci = -1, o_A = -1, o_dinv = -1, o_par = -1, o_pof = -1, o_crp = -1, o_cch = -1;
     int o_x = -1, o_b = -1, o_r = -1;
 };
 struct NarrowParams {
@@ -246,6 +248,7 @@ struct Ctx {
 
 // ----- shared-memory bottom cycle (narrow.cu) -----
 int narrow_smem_setup(Ctx &c, size_t smem_budget);
+size_t narrow_smem_budget();   // dynamic shared memory a block of the bottom kernel may take
 void narrow_smem_refresh(const Ctx &c, cudaStream_t s);
 void launch_narrow_smem(const Ctx &c, int R, cudaStream_t s, Chain *ch = nullptr);
 

@@ -14,6 +14,7 @@
 // keeps each phase short: a phase is a chain of dependent shared-memory loads.
 // Only the dense coarse inverse and the top level's right-hand side and
 // correction touch global memory.
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -75,7 +76,7 @@ __device__ __forceinline__ void sst<4>(float *p, const float (&v)[4]) {
 struct SLev {
     const uint16_t *rp, *ci, *par, *crp, *cch;
     const float *A, *dinv;
-    const uint8_t *npl2;
+    const uint16_t *pof;
     float *x, *b, *r;
 };
 
@@ -86,7 +87,7 @@ __device__ SLev slev(const NarrowLevel &h, unsigned char *sm) {
     s.A = reinterpret_cast<const float *>(sm + h.o_A);
     s.dinv = reinterpret_cast<const float *>(sm + h.o_dinv);
     s.par = h.o_par >= 0 ? reinterpret_cast<const uint16_t *>(sm + h.o_par) : nullptr;
-    s.npl2 = h.o_npl2 >= 0 ? reinterpret_cast<const uint8_t *>(sm + h.o_npl2) : nullptr;
+    s.pof = h.o_pof >= 0 ? reinterpret_cast<const uint16_t *>(sm + h.o_pof) : nullptr;
     s.crp = h.o_crp >= 0 ? reinterpret_cast<const uint16_t *>(sm + h.o_crp) : nullptr;
     s.cch = h.o_cch >= 0 ? reinterpret_cast<const uint16_t *>(sm + h.o_cch) : nullptr;
     s.x = reinterpret_cast<float *>(sm + h.o_x);
@@ -303,14 +304,14 @@ __global__ void __launch_bounds__(1024, 1) narrow_smem_kernel(const unsigned cha
         const NarrowLevel &H = p.lev[d - p.d0];
         const SLev L = slev(H, sm), C = slev(p.lev[d - 1 - p.d0], sm);
         for (int i = threadIdx.x; i < H.ns; i += blockDim.x) {
-            const int np = 1 << L.npl2[i];
+            const int k0 = L.pof[i], np = L.pof[i + 1] - k0;
             float acc[R], v[R];
 #pragma unroll
             for (int q = 0; q < R; q++) acc[q] = 0.f;
 #pragma unroll
             for (int q2 = 0; q2 < 8; q2++) {
                 if (q2 < np) {
-                    sld<R>(C.x + (size_t)L.par[8 * i + q2] * R, v);
+                    sld<R>(C.x + (size_t)L.par[k0 + q2] * R, v);
 #pragma unroll
                     for (int q = 0; q < R; q++) acc[q] += v[q];
                 }
@@ -345,18 +346,25 @@ int narrow_smem_setup(Ctx &c, size_t smem_budget) {
     size_t best_blob = 0, best_vec = 0;
     int best_dn = c.d0 - 1;
     for (int dn = c.d0; dn <= c.D && dn - c.d0 < kMaxNarrow; dn++) {
-        size_t blob = 0, vec = 0;
+        size_t blob = 0, vec = 0, rmax = 0;
         bool ok = true;
         for (int d = c.d0; d <= dn && ok; d++) {
             const HostLevel &L = H.lev[d];
             const size_t nnz = L.rp.empty() ? 0 : (size_t)L.rp[L.ndof];
             if (nnz >= 65535 || L.ndof >= 16384) { ok = false; break; }
             blob += align16(2 * (L.ndof + 1)) + align16(2 * nnz) + align16(4 * nnz) + align16(4 * (size_t)L.ndof);
-            if (d > c.d0) blob += align16(16 * (size_t)L.ndof) + align16(L.ndof);
+            if (d > c.d0) {
+                size_t np = 0;
+                for (int i = 0; i < L.ndof; i++) np += (size_t)1 << L.npar_log2[i];
+                if (np >= 65535) ok = false;
+                blob += align16(2 * (L.ndof + 1)) + align16(2 * np);
+            }
             if (d < dn) blob += align16(2 * (L.ndof + 1)) + align16(2 * L.cch.size());
             if (d < dn && L.cch.size() >= 65535) ok = false;
-            vec += 3 * align16(16 * (size_t)L.ndof);   // x, b, r with room for 4 lanes
+            vec += 2 * align16(16 * (size_t)L.ndof);   // x, b with room for 4 lanes
+            rmax = std::max(rmax, align16(16 * (size_t)L.ndof));
         }
+        vec += rmax;   // one residual buffer for all levels
         if (!ok || blob + vec > smem_budget) break;
         best_dn = dn; best_blob = blob; best_vec = vec;
     }
@@ -387,16 +395,20 @@ int narrow_smem_setup(Ctx &c, size_t smem_budget) {
         o.o_A = (int)off; off += align16(4 * nnz);            // values: refreshed after every assembly
         o.o_dinv = (int)off; off += align16(4 * (size_t)L.ndof);
         o.nnz = (int)nnz;
-        o.o_par = o.o_npl2 = o.o_crp = o.o_cch = -1;
+        o.o_par = o.o_pof = o.o_crp = o.o_cch = -1;
         if (d > c.d0) {
-            std::vector<uint16_t> par16(8 * (size_t)L.ndof, 0);
-            std::vector<uint8_t> npl(L.ndof, 0);
+            // the first 1 << npar_log2 of a row's 8 parent slots are its parents
+            std::vector<uint16_t> pof16(L.ndof + 1), par16;
             for (int i = 0; i < L.ndof; i++) {
-                npl[i] = (uint8_t)L.npar_log2[i];
-                for (int q = 0; q < 8; q++) par16[8 * (size_t)i + q] = L.par[8 * (size_t)i + q] < 0 ? 0 : (uint16_t)L.par[8 * (size_t)i + q];
+                pof16[i] = (uint16_t)par16.size();
+                for (int q = 0; q < (1 << L.npar_log2[i]); q++) {
+                    if (L.par[8 * (size_t)i + q] < 0) return 1;
+                    par16.push_back((uint16_t)L.par[8 * (size_t)i + q]);
+                }
             }
+            pof16[L.ndof] = (uint16_t)par16.size();
+            o.o_pof = put(pof16.data(), 2 * pof16.size());
             o.o_par = put(par16.data(), 2 * par16.size());
-            o.o_npl2 = put(npl.data(), npl.size());
         }
         if (d < best_dn) {
             std::vector<uint16_t> crp16(L.ndof + 1), cch16(L.cch.size());
@@ -410,19 +422,38 @@ int narrow_smem_setup(Ctx &c, size_t smem_budget) {
         }
         o.o_x = (int)voff; voff += align16(16 * (size_t)L.ndof);
         o.o_b = (int)voff; voff += align16(16 * (size_t)L.ndof);
-        o.o_r = (int)voff; voff += align16(16 * (size_t)L.ndof);
     }
+    for (int d = c.d0; d <= best_dn; d++) p.lev[d - c.d0].o_r = (int)voff;   // the shared residual buffer
     if (off != best_blob) return 1;
     if (cudaMalloc((void **)&c.narrow.blob, best_blob) != cudaSuccess) { cudaGetLastError(); c.narrow.blob = nullptr; return 1; }
 
     if (cudaMemcpy(c.narrow.blob, buf.data(), best_blob, cudaMemcpyHostToDevice) != cudaSuccess) return 1;
     c.narrow.blob_bytes = (int)best_blob;
     c.narrow.vec_bytes = (int)best_vec;
-    for (auto *k : {(const void *)narrow_smem_kernel<1>, (const void *)narrow_smem_kernel<2>, (const void *)narrow_smem_kernel<4>})
-        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(best_blob + best_vec)) != cudaSuccess)
+    // the limit is a property of the kernel, shared by every handle of the process: only ever raised,
+    // so that a handle set up later with a smaller bottom does not lower it below this one's
+    for (auto *k : {(const void *)narrow_smem_kernel<1>, (const void *)narrow_smem_kernel<2>, (const void *)narrow_smem_kernel<4>}) {
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, k) != cudaSuccess) return 1;
+        if (fa.maxDynamicSharedSizeBytes < (int)(best_blob + best_vec) &&
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(best_blob + best_vec)) != cudaSuccess)
             return 1;
+    }
     c.narrow.dn = best_dn;
     return 0;
+}
+
+size_t narrow_smem_budget() {
+    // the opt-in limit per block, less the kernel's static shared memory (its level table)
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, narrow_smem_kernel<4>) != cudaSuccess || optin <= (int)fa.sharedSizeBytes) {
+        cudaGetLastError();
+        return 200 * 1024;
+    }
+    return (size_t)optin - fa.sharedSizeBytes;
 }
 
 // copy the current FP32 values and inverse diagonals of the narrow levels into the blob

@@ -390,6 +390,38 @@ def test_bounded_barrier_wait_reports_timeout_and_context_stays_usable():
         L.lbmg_destroy(good)
 
 
+def test_a_later_handle_with_a_smaller_bottom_leaves_an_earlier_one_working():
+    """The shared-memory bottom kernel's dynamic shared-memory limit belongs to the kernel, so
+    every handle of the process shares it: a handle set up later with a smaller bottom must not
+    lower it below what an earlier handle needs (whose mixed cycles would then fail to launch).
+    The earlier handle's solve is the same, bit for bit, before and after the later build."""
+    Vk, Fk = meshgen.torus_knot_tube(2, 3, 1.0, 0.12, 48, 8, 1e-6, 3)
+    Vs, Fs = meshgen.icosphere(2, 1.0, 1e-3, 1)
+    big = L.lbmg_build_hierarchy(Vk, Fk, 5)
+    small = None
+    try:
+        L.lbmg_assemble(big, 1e-2)
+        n = L.lbmg_level_info(big, 5)[0]
+        rhs = torch.zeros((n, 3), dtype=torch.float64, device=DEV)
+        L.lbmg_project_rhs(big, _dev(Vk), rhs)
+        xs = []
+        for later in (False, True):
+            if later:
+                small = L.lbmg_build_hierarchy(Vs, Fs, 4)
+                L.lbmg_assemble(small, 1e-2)
+                # the default shape again: drops the cached solve graph, so the cycle is captured anew
+                L.lbmg_set_launch_shape(big, 5, L.LBMG_MIXED, 0, 4, 256)
+            x = torch.zeros_like(rhs)
+            code, st = L.lbmg_solve(big, rhs, x, 1e-6, 1000, L.LBMG_MIXED)
+            assert code == L.LBMG_OK and st.converged
+            xs.append(x)
+        assert torch.equal(xs[0], xs[1])
+    finally:
+        L.lbmg_destroy(big)
+        if small is not None:
+            L.lbmg_destroy(small)
+
+
 def test_bounded_copy_wait_reports_timeout_and_context_stays_usable():
     """Fault injected on the host: the shared-memory bottom kernel's bulk copy is told
     to wait for 16 bytes that never arrive.  Its bounded wait expires, the kernel sets
