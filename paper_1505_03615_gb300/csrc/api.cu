@@ -645,6 +645,19 @@ int upload_hierarchy(lbmg_handle h) {
                 for (size_t g = 0; g < gq2.size(); g++) gq2[g] = make_int2(gq[2 * g], gq[2 * g + 1]);
                 for (int q = 0; q < 10; q++)
                     L.pk_es[q] = L.pk_gs[q] < (int)gq2.size() ? (int64_t)(unsigned)gq2[L.pk_gs[q]].x * 32 : L.pk_total;
+                for (int col = 0; col < 8; col++) {
+                    PkRuns &pr = L.pk_runs[col];
+                    pr = PkRuns();
+                    for (int g = L.pk_gs[col]; g < L.pk_gs[col + 1]; g++) {
+                        if (pr.n > 0 && gq2[g].y == pr.q[pr.n - 1] &&
+                            gq2[g].x == pr.b[pr.n - 1] + (g - pr.g[pr.n - 1]) * pr.q[pr.n - 1])
+                            continue;   // continues the run
+                        if (pr.n == kPkRuns) { pr.n = -1; break; }
+                        pr.g[pr.n] = g; pr.b[pr.n] = gq2[g].x; pr.q[pr.n] = gq2[g].y;
+                        pr.n++;
+                    }
+                    if (pr.n < 0) pr = PkRuns();   // too many runs: the kernel reads the headers
+                }
                 LBMG_TRY(h->upload(&L.pk_gq, gq2));
                 LBMG_TRY(h->upload(&L.pk_rows, rows));
                 LBMG_TRY(h->upload(&L.pk_map, map));

@@ -63,6 +63,15 @@ inline void klaunch(void (*kernel)(KArgs...), unsigned grid, unsigned block, siz
     if (ch) ch->prev = true;
 }
 
+// The groups of one colour of the packed copy, sorted by quad count, as runs of equal quads: group g of
+// run k (g[k] <= g < g[k + 1]) starts at entry 32 (b[k] + (g - g[k]) q[k]) and has q[k] quads.  Passed to
+// the colour kernel by value, so that a group's position needs no load (n = 0: read the group header).
+constexpr int kPkRuns = 12;
+struct PkRuns {
+    int n = 0;
+    int g[kPkRuns] = {0}, b[kPkRuns] = {0}, q[kPkRuns] = {0};
+};
+
 struct DevLevel {
     int d = 0, n = 0;
     int ns = 0;                            // rows [0, ns) are smoothed; [ns, n) belong to coarsest blocks
@@ -96,6 +105,7 @@ struct DevLevel {
     int64_t pk_total = 0;
     int pk_gs[10] = {0};                   // group ranges of colours 0..7, then rows [ns, n)
     int64_t pk_es[10] = {0};               // entry offset of the first group of each range (pk_es[9]: total)
+    PkRuns pk_runs[8];                     // per colour (n = 0 when a colour has more than kPkRuns runs)
     LaunchShape shape[2][2];               // [FP64][kShapeSmooth / kShapeResidual], set by the autotuner
     float tuned_ms[2][2] = {{0, 0}, {0, 0}};   // device time of the chosen shape when the tuner timed it
 };

@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(512) pk_row_kernel(int g0, int g1, const int2 
                                                      const int *__restrict__ rows, PkMat<T> m,
                                                      const T *__restrict__ dinv, const T *__restrict__ b, T *x,
                                                      T *__restrict__ r, const char *__restrict__ pf, int64_t pf_bytes,
-                                                     int pf_chunk) {
+                                                     int pf_chunk, const PkRuns runs) {
     // the next colour's entries into L2 (static data, so before the grid-dependency wait):
     // one bulk prefetch of a 256-byte-aligned slice per block
     if (pf && threadIdx.x == 0) {
@@ -95,9 +95,26 @@ __global__ void __launch_bounds__(512) pk_row_kernel(int g0, int g1, const int2 
     const int lane = threadIdx.x & 31;
     const int g = g0 + (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
     if (g >= g1) return;   // whole warps only (blockDim is a multiple of 32)
-    const int2 hd = __ldg(gq + g);
-    const int64_t base = (int64_t)(unsigned)hd.x * 32;
-    const int Q = hd.y;
+    // the group's position: from the colour's runs (no load; unrolled over constant indices, so the
+    // table stays in the parameter bank), else from its header
+    int64_t base;
+    int Q;
+    if (runs.n > 0) {
+        int rg = runs.g[0], rb = runs.b[0], rq = runs.q[0];
+#pragma unroll
+        for (int t = 1; t < kPkRuns; t++) {
+            const bool in = t < runs.n && g >= runs.g[t];
+            rg = in ? runs.g[t] : rg;
+            rb = in ? runs.b[t] : rb;
+            rq = in ? runs.q[t] : rq;
+        }
+        base = ((int64_t)rb + (int64_t)(g - rg) * rq) * 32;
+        Q = rq;
+    } else {
+        const int2 hd = __ldg(gq + g);
+        base = (int64_t)(unsigned)hd.x * 32;
+        Q = hd.y;
+    }
     const int row = __ldg(rows + 8 * (size_t)g + (lane >> 2));
     const bool lead = row >= 0 && (lane & 3) == 0;
     int j[kPkPrefetch];
@@ -312,7 +329,8 @@ template <> const double *level_A<double>(const DevLevel &L) { return L.A64; }
 // 256-byte-aligned slices
 template <class T, bool kGs>
 void launch_rows(const DevLevel &L, int g0, int g1, const T *dinv, const T *b, T *x, T *r, int R, int tpb,
-                 cudaStream_t s, Chain *ch, const char *pf = nullptr, int64_t pf_bytes = 0) {
+                 cudaStream_t s, Chain *ch, const char *pf = nullptr, int64_t pf_bytes = 0,
+                 const PkRuns &runs = PkRuns()) {
     if (g1 <= g0) return;
     tpb = std::max(32, std::min(512, tpb / 32 * 32));
     const unsigned blocks = (unsigned)(((int64_t)(g1 - g0) * 32 + tpb - 1) / tpb);
@@ -326,7 +344,7 @@ void launch_rows(const DevLevel &L, int g0, int g1, const T *dinv, const T *b, T
     }
     auto k = R == 1 ? pk_row_kernel<T, 1, kGs> : R == 2 ? pk_row_kernel<T, 2, kGs> : pk_row_kernel<T, 4, kGs>;
     klaunch(k, blocks, (unsigned)tpb, 0, s, ch, g0, g1, (const int2 *)L.pk_gq, (const int *)L.pk_rows, pk_mat<T>(L),
-            dinv, b, x, r, pf, pf ? pf_bytes : (int64_t)0, chunk);
+            dinv, b, x, r, pf, pf ? pf_bytes : (int64_t)0, chunk, runs);
 }
 
 // ---- the finest level's whole sweep (all its colour steps) in one cooperative launch ----
@@ -589,7 +607,8 @@ bool launch_packed_smooth(const DevLevel &L, int colour, const T *A, const T *di
         pf = reinterpret_cast<const char *>(L.pk_e32 + L.pk_es[next]);
         pf_bytes = (L.pk_es[next + 1] - L.pk_es[next]) * (int64_t)sizeof(int2);
     }
-    launch_rows<T, true>(L, L.pk_gs[colour], L.pk_gs[colour + 1], dinv, b, x, nullptr, R, tpb, s, ch, pf, pf_bytes);
+    launch_rows<T, true>(L, L.pk_gs[colour], L.pk_gs[colour + 1], dinv, b, x, nullptr, R, tpb, s, ch, pf, pf_bytes,
+                         L.pk_runs[colour]);
     return true;
 }
 
