@@ -16,6 +16,8 @@
 // levels are the Galerkin products P^T A P of Eq. 4's prolongation, summed the
 // same way.
 #include <algorithm>
+#include <cmath>
+#include <vector>
 
 #include "lbmg_internal.h"
 
@@ -31,25 +33,55 @@ __constant__ double c_type[6][3] = {{1, 0, 0}, {1, -1, 0}, {0, 1, 0}, {1, -2, 1}
 
 static bool g_gl_ready = false;
 
-// Gauss-Legendre nodes/weights on [0,1] by Newton iteration on P_n
+// Gauss-Legendre rule on [0,1] by the Golub-Welsch method: the nodes on [-1,1] are the eigenvalues
+// of the symmetric tridiagonal Jacobi matrix of the Legendre three-term recurrence (zero diagonal,
+// off-diagonal k / sqrt(4k^2 - 1)), each weight is twice the squared first component of the unit
+// eigenvector; the eigenproblem is solved by cyclic Jacobi rotations (n is a handful).  Nodes
+// ascending.
 static void gauss_legendre01(int n, double *x, double *w) {
+    std::vector<double> A((size_t)n * n, 0.0), V((size_t)n * n, 0.0);
+    for (int i = 0; i < n; i++) V[(size_t)i * n + i] = 1.0;
+    for (int k = 1; k < n; k++) {
+        const double b = k / std::sqrt(4.0 * k * k - 1.0);
+        A[(size_t)(k - 1) * n + k] = A[(size_t)k * n + k - 1] = b;
+    }
+    for (int sweep = 0; sweep < 64; sweep++) {
+        double off = 0.0;
+        for (int p = 0; p < n; p++)
+            for (int q = p + 1; q < n; q++) off += A[(size_t)p * n + q] * A[(size_t)p * n + q];
+        if (off < 1e-60) break;
+        for (int p = 0; p < n; p++)
+            for (int q = p + 1; q < n; q++) {
+                const double apq = A[(size_t)p * n + q];
+                if (apq == 0.0) continue;
+                // the rotation in the (p, q) plane that zeroes A_pq: A <- J^T A J, V <- V J
+                const double th = (A[(size_t)q * n + q] - A[(size_t)p * n + p]) / (2.0 * apq);
+                const double t = (th >= 0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < n; k++) {
+                    const double akp = A[(size_t)k * n + p], akq = A[(size_t)k * n + q];
+                    A[(size_t)k * n + p] = c * akp - s * akq;
+                    A[(size_t)k * n + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < n; k++) {
+                    const double apk = A[(size_t)p * n + k], aqk = A[(size_t)q * n + k];
+                    A[(size_t)p * n + k] = c * apk - s * aqk;
+                    A[(size_t)q * n + k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < n; k++) {
+                    const double vkp = V[(size_t)k * n + p], vkq = V[(size_t)k * n + q];
+                    V[(size_t)k * n + p] = c * vkp - s * vkq;
+                    V[(size_t)k * n + q] = s * vkp + c * vkq;
+                }
+            }
+    }
+    std::vector<int> ord(n);
+    for (int i = 0; i < n; i++) ord[i] = i;
+    std::sort(ord.begin(), ord.end(), [&](int a, int b) { return A[(size_t)a * n + a] < A[(size_t)b * n + b]; });
     for (int i = 0; i < n; i++) {
-        double z = cos(3.14159265358979323846 * (i + 0.75) / (n + 0.5));
-        double pn = 0, dpn = 1;
-        for (int it = 0; it < 100; it++) {
-            double p0 = 1.0, p1 = z;
-            for (int k = 1; k < n; k++) { double p2 = ((2.0 * k + 1.0) * z * p1 - k * p0) / (k + 1.0); p0 = p1; p1 = p2; }
-            pn = p1;
-            dpn = n * (z * p1 - p0) / (z * z - 1.0);
-            double dz = pn / dpn;
-            z -= dz;
-            if (fabs(dz) < 1e-16) break;
-        }
-        double p0 = 1.0, p1 = z;
-        for (int k = 1; k < n; k++) { double p2 = ((2.0 * k + 1.0) * z * p1 - k * p0) / (k + 1.0); p0 = p1; p1 = p2; }
-        dpn = n * (z * p1 - p0) / (z * z - 1.0);
-        x[i] = 0.5 * (z + 1.0);
-        w[i] = 1.0 / ((1.0 - z * z) * dpn * dpn);
+        const int e = ord[i];
+        x[i] = 0.5 * (A[(size_t)e * n + e] + 1.0);
+        w[i] = V[e] * V[e];   // 2 v_0^2 on [-1, 1], halved on [0, 1]
     }
 }
 
