@@ -5,8 +5,8 @@
 // triangles is then split into the connected components of the corner's support on the
 // mesh (the functions b_k^i of Section 4.2): two triangles of the run are joined through a
 // shared edge that meets the open support cube, or a shared vertex inside it.  Runs of at
-// most kSmallRun triangles are labelled here, one thread per run; the few larger runs of the
-// coarse levels are labelled by the host.  Labels number a run's components in the order
+// most kSmallRun triangles are labelled here, one thread per run; the larger runs of the coarse
+// levels are labelled by the host.  Labels number a run's components in the order
 // of their smallest triangle, so they do not depend on the order of the unions.  The box
 // tests are divisions and comparisons only, exactly as on the host.
 #include <algorithm>
@@ -21,7 +21,9 @@ namespace {
 
 constexpr int kRT = 256, kRI = 16, kRTile = kRT * kRI;   // radix tile: 256 threads x 16 keys
 constexpr int kDigits = 16;                               // 4-bit digits
-constexpr int kSmallRun = 64;
+// a run's parents and labels in 8 bits each in the thread's local memory: positions and labels 0..254,
+// 255 marks "no label yet"
+constexpr int kSmallRun = 255;
 
 // the (corner, triangle) words of cell i: morton(corner) << tbits | tri
 __global__ void pairs_kernel(long long ncell, const uint64_t *__restrict__ ckey, const int *__restrict__ ctri,
@@ -194,22 +196,27 @@ __global__ void small_runs_kernel(long long ng, const long long *__restrict__ gs
     const int n = (int)(gs[g + 1] - b);
     if (n > kSmallRun) { ncomp[g] = -1; return; }
     const uint64_t tmask = (1ULL << tbits) - 1;
-    int tri[kSmallRun], par[kSmallRun], lab[kSmallRun];
-    for (int i = 0; i < n; i++) { tri[i] = (int)(ct[b + i] & tmask); par[i] = i; lab[i] = -1; }
-    auto local = [&](int t) -> int {   // position of triangle t in the run, -1 if absent
+    // parents and labels of the run's positions (at most kSmallRun of them)
+    uint8_t par[kSmallRun], lab[kSmallRun];
+    for (int i = 0; i < n; i++) { par[i] = (uint8_t)i; lab[i] = 0xff; }
+    auto tri = [&](int i) { return (int)(ct[b + i] & tmask); };
+    auto local = [&](int t) -> int {   // position of triangle t in the run (triangles ascending), -1 if absent
         int lo = 0, hi = n;
-        while (lo < hi) { const int mid = (lo + hi) >> 1; if (tri[mid] < t) lo = mid + 1; else hi = mid; }
-        return (lo < n && tri[lo] == t) ? lo : -1;
+        while (lo < hi) { const int mid = (lo + hi) >> 1; if (tri(mid) < t) lo = mid + 1; else hi = mid; }
+        return (lo < n && tri(lo) == t) ? lo : -1;
     };
     auto find = [&](int x) { while (par[x] != x) { par[x] = par[par[x]]; x = par[x]; } return x; };
-    auto unite = [&](int x, int y) { x = find(x); y = find(y); if (x != y) { if (x < y) par[y] = x; else par[x] = y; } };
+    auto unite = [&](int x, int y) {
+        x = find(x); y = find(y);
+        if (x != y) { if (x < y) par[y] = (uint8_t)x; else par[x] = (uint8_t)y; }
+    };
     if (split) {
         const uint64_t key = ct[b] >> tbits;
         const double c[3] = {(double)compact3(key), (double)compact3(key >> 1), (double)compact3(key >> 2)};
         double lo[3], hi[3];
         for (int a = 0; a < 3; a++) { lo[a] = (c[a] - 1.0) * s; hi[a] = (c[a] + 1.0) * s; }
         for (int i = 0; i < n; i++) {
-            const int t = tri[i];
+            const int t = tri(i);
             for (int e3 = 0; e3 < 3; e3++) {
                 const int va = F[3 * t + e3], vb = F[3 * t + (e3 + 1) % 3];
                 bool tested = false, hit = false;
@@ -238,7 +245,7 @@ __global__ void small_runs_kernel(long long ng, const long long *__restrict__ gs
     int nc = 0;
     for (int i = 0; i < n; i++) {
         const int r = find(i);
-        if (lab[r] < 0) lab[r] = nc++;
+        if (lab[r] == 0xff) lab[r] = (uint8_t)nc++;
         comp[b + i] = lab[r];
     }
     ncomp[g] = nc;
@@ -309,6 +316,7 @@ bool gpu_corner_pairs(const std::vector<CornerTri> &cells, int tbits, int key_bi
     if (e == cudaSuccess) {
         std::vector<uint64_t> hk(nc);
         std::vector<int> ht(nc);
+#pragma omp parallel for schedule(static)
         for (long long i = 0; i < nc; i++) { hk[i] = cells[i].key; ht[i] = cells[i].tri; }
         chk(cudaMemcpy(ckey, hk.data(), nc * sizeof(uint64_t), cudaMemcpyHostToDevice));
         chk(cudaMemcpy(ctri, ht.data(), nc * sizeof(int), cudaMemcpyHostToDevice));

@@ -221,14 +221,15 @@ int gpu_cut_triangles(const HostHierarchy &H, int N, std::vector<FragOut> &out, 
         return 7;
     }
     out.resize(nf);
-    long long vq = 0;
+    std::vector<long long> vq(nf + 1, 0);   // first polygon vertex of each piece
+    for (long long q = 0; q < nf; q++) vq[q + 1] = vq[q] + hnv[q];
+#pragma omp parallel for schedule(static)
     for (long long q = 0; q < nf; q++) {
         FragOut &f = out[q];
         f.key = 0;
         f.tri = htri[q];
         for (int a = 0; a < 3; a++) f.vox[a] = hvox[3 * q + a];
-        f.poly.assign(hpoly.begin() + 3 * vq, hpoly.begin() + 3 * (vq + hnv[q]));
-        vq += hnv[q];
+        f.poly.assign(hpoly.begin() + 3 * vq[q], hpoly.begin() + 3 * vq[q + 1]);
     }
     return 0;
 }
