@@ -102,8 +102,9 @@ typedef struct lbmg_options {
                            run on the GPU: the cut of the triangles into finest-voxel pieces (one thread
                            per triangle, the same sweep of axis planes) and, on every level, the sorted
                            (corner, triangle) pairs and the split labelling of each corner's support
-                           into connected components (Section 4.2; one thread per corner, corners with
-                           more than 255 triangles labelled on the host).  The prolongation and the
+                           into connected components (Section 4.2; one thread per corner of up to 255
+                           triangles, one thread per (corner, triangle) pair with a shared lock-free
+                           union-find for larger corners).  The dof numbering, prolongation and
                            contribution lists stay on the host.  The pieces agree with the host's up to
                            FMA contraction in the plane intersections, the labels exactly.  Needs a GPU
                            (LBMG_CUDA_ERROR otherwise), also for lbmg_host_build */

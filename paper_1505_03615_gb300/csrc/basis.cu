@@ -5,8 +5,8 @@
 // triangles is then split into the connected components of the corner's support on the
 // mesh (the functions b_k^i of Section 4.2): two triangles of the run are joined through a
 // shared edge that meets the open support cube, or a shared vertex inside it.  Runs of at
-// most kSmallRun triangles are labelled here, one thread per run; the larger runs of the coarse
-// levels are labelled by the host.  Labels number a run's components in the order
+// most kSmallRun triangles are labelled one thread per run; longer runs (the coarse levels'), one
+// thread per pair with a shared lock-free union-find.  Labels number a run's components in the order
 // of their smallest triangle, so they do not depend on the order of the unions.  The box
 // tests are divisions and comparisons only, exactly as on the host.
 #include <algorithm>
@@ -184,7 +184,7 @@ __device__ bool pt_in_open_box(const double *p, const double *lo, const double *
 }
 
 // run g = ct[gs[g] .. gs[g+1]) of one corner (triangles ascending): its component label per
-// entry and the run's component count; runs longer than kSmallRun get ncomp = -1 (host)
+// entry and the run's component count; runs longer than kSmallRun get ncomp = -1 (labelled below)
 __global__ void small_runs_kernel(long long ng, const long long *__restrict__ gs, const uint64_t *__restrict__ ct,
                                   int tbits, int split, double s, const int *__restrict__ F,
                                   const double *__restrict__ Vg, const int *__restrict__ adj_ptr,
@@ -249,6 +249,147 @@ __global__ void small_runs_kernel(long long ng, const long long *__restrict__ gs
         comp[b + i] = lab[r];
     }
     ncomp[g] = nc;
+}
+
+// ---- runs longer than kSmallRun: one thread per (corner, triangle) pair, a shared union-find ----
+// Every pair of a long run joins its edge and vertex neighbours in the run, as the thread-per-run
+// kernel does, into one parent array over all pairs.  Unions hook the larger root under the smaller
+// (compare-and-swap on a root), finds halve paths with plain stores of ancestors; parents only ever
+// decrease, so the forest stays acyclic, and every component's root is its smallest position, which
+// makes the labels (roots ranked in order) those of the sequential labelling.  Loops are bounded: on
+// a bound the status word is set and the host reports a failure.
+
+__device__ int uf_find(int *par, int x, int *status) {
+    volatile int *vp = par;
+    for (int it = 0; it < (1 << 26); it++) {
+        const int p = vp[x];
+        if (p == x) return x;
+        const int gp = vp[p];
+        if (gp != p) vp[x] = gp;
+        x = gp;
+    }
+    atomicExch(status, 1);
+    return x;
+}
+
+__device__ void uf_union(int *par, int a, int b, int *status) {
+    for (int it = 0; it < (1 << 20); it++) {
+        a = uf_find(par, a, status);
+        b = uf_find(par, b, status);
+        if (a == b) return;
+        if (a < b) { const int t = a; a = b; b = t; }
+        if (atomicCAS(par + a, a, b) == a) return;
+    }
+    atomicExch(status, 1);
+}
+
+// run of each pair (-1 when its run was labelled by the thread-per-run kernel); parents initialised
+__global__ void long_init_kernel(long long m, long long ng, const long long *__restrict__ gs,
+                                 const int *__restrict__ ncomp, int *__restrict__ rid, int *__restrict__ par) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    long long lo = 0, hi = ng;   // the run g with gs[g] <= i < gs[g + 1]
+    while (hi - lo > 1) { const long long mid = (lo + hi) >> 1; if (gs[mid] <= i) lo = mid; else hi = mid; }
+    rid[i] = ncomp[lo] < 0 ? (int)lo : -1;
+    par[i] = (int)i;
+}
+
+__global__ void long_union_kernel(long long m, const long long *__restrict__ gs, const uint64_t *__restrict__ ct,
+                                  const int *__restrict__ rid, int tbits, int split, double s,
+                                  const int *__restrict__ F, const double *__restrict__ Vg,
+                                  const int *__restrict__ adj_ptr, const int *__restrict__ adj,
+                                  const int *__restrict__ vt_ptr, const int *__restrict__ vt, int *par, int *status) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const int g = rid[i];
+    if (g < 0) return;
+    const long long b = gs[g], e = gs[g + 1];
+    if (!split) { uf_union(par, (int)i, (int)b, status); return; }
+    const uint64_t tmask = (1ULL << tbits) - 1;
+    auto local = [&](int t) -> long long {   // position of triangle t in the run, -1 if absent
+        long long lo = b, hi = e;
+        while (lo < hi) {
+            const long long mid = (lo + hi) >> 1;
+            if ((int)(ct[mid] & tmask) < t) lo = mid + 1; else hi = mid;
+        }
+        return (lo < e && (int)(ct[lo] & tmask) == t) ? lo : -1;
+    };
+    const uint64_t key = ct[i] >> tbits;
+    const int t = (int)(ct[i] & tmask);
+    const double c[3] = {(double)compact3(key), (double)compact3(key >> 1), (double)compact3(key >> 2)};
+    double lo[3], hi[3];
+    for (int a = 0; a < 3; a++) { lo[a] = (c[a] - 1.0) * s; hi[a] = (c[a] + 1.0) * s; }
+    for (int e3 = 0; e3 < 3; e3++) {
+        const int va = F[3 * t + e3], vb = F[3 * t + (e3 + 1) % 3];
+        bool tested = false, hit = false;
+        for (int q = adj_ptr[3 * t + e3]; q < adj_ptr[3 * t + e3 + 1]; q++) {
+            const long long j = local(adj[q]);
+            if (j < 0) continue;
+            if (!tested) {
+                hit = seg_hits_open_box(Vg + 3 * (size_t)va, Vg + 3 * (size_t)vb, lo, hi);
+                tested = true;
+            }
+            if (hit) uf_union(par, (int)i, (int)j, status);
+        }
+    }
+    for (int e3 = 0; e3 < 3; e3++) {
+        const int v = F[3 * t + e3];
+        if (!pt_in_open_box(Vg + 3 * (size_t)v, lo, hi)) continue;
+        for (int q = vt_ptr[v]; q < vt_ptr[v + 1]; q++) {
+            const long long j = local(vt[q]);
+            if (j >= 0) uf_union(par, (int)i, (int)j, status);
+        }
+    }
+}
+
+// roots (parents fully compressed) and the flags of the roots of long runs
+__global__ void long_root_kernel(long long m, const int *__restrict__ rid, int *par, unsigned *__restrict__ flag,
+                                 int *status) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    if (rid[i] < 0) { flag[i] = 0u; return; }
+    const int r = uf_find(par, (int)i, status);
+    par[i] = r;
+    flag[i] = r == (int)i ? 1u : 0u;
+}
+
+// exclusive prefix of the flags: tile offset (scanned tile sums) + the flags before i in the tile
+__global__ void __launch_bounds__(kRT) rank_kernel(const unsigned *__restrict__ f, long long n,
+                                                   const unsigned *__restrict__ toff, unsigned *__restrict__ rank) {
+    __shared__ unsigned sh[kRT];
+    const long long base = (long long)blockIdx.x * kRTile + (long long)threadIdx.x * kRI;
+    unsigned c = 0;
+    for (int q = 0; q < kRI; q++) if (base + q < n) c += f[base + q];
+    sh[threadIdx.x] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned run = 0;
+        for (int t = 0; t < kRT; t++) { const unsigned v = sh[t]; sh[t] = run; run += v; }
+    }
+    __syncthreads();
+    unsigned p = toff[blockIdx.x] + sh[threadIdx.x];
+    for (int q = 0; q < kRI; q++) {
+        const long long i = base + q;
+        if (i < n) { rank[i] = p; p += f[i]; }
+    }
+}
+
+// labels of the long runs' pairs (their root's rank within the run) and the runs' component counts
+__global__ void long_label_kernel(long long m, const long long *__restrict__ gs, const int *__restrict__ rid,
+                                  const int *__restrict__ par, const unsigned *__restrict__ rank, int *__restrict__ comp) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const int g = rid[i];
+    if (g < 0) return;
+    comp[i] = (int)(rank[par[i]] - rank[gs[g]]);
+}
+
+__global__ void long_count_kernel(long long ng, long long m, const long long *__restrict__ gs,
+                                  const unsigned *__restrict__ rank, unsigned total, int *__restrict__ ncomp) {
+    const long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (g >= ng || ncomp[g] >= 0) return;
+    const unsigned end = gs[g + 1] < m ? rank[gs[g + 1]] : total;
+    ncomp[g] = (int)(end - rank[gs[g]]);
 }
 
 template <class T>
@@ -354,7 +495,7 @@ bool gpu_corner_pairs(const std::vector<CornerTri> &cells, int tbits, int key_bi
 }
 
 // component labels of the runs gstart[g] .. gstart[g+1] of the sorted words (ncomp[g] = -1: a
-// run the host labels); false on a CUDA failure
+// run left to the host, only when the pairs do not fit 31-bit positions); false on a CUDA failure
 bool gpu_run_components(const GpuBasis *G, const std::vector<uint64_t> &words, const std::vector<int64_t> &gstart,
                         int tbits, int split, double s, std::vector<int32_t> &comp, std::vector<int32_t> &ncomp,
                         std::string &err) {
@@ -373,20 +514,61 @@ bool gpu_run_components(const GpuBasis *G, const std::vector<uint64_t> &words, c
         chk(cudaMemcpy(gs, gstart.data(), (ng + 1) * sizeof(long long), cudaMemcpyHostToDevice));
         chk(cudaMemset(dcomp, 0, m * sizeof(int)));
     }
+    int *rid = nullptr, *par = nullptr, *status = nullptr;
+    unsigned *flag = nullptr, *rank = nullptr, *tsum = nullptr;
+    int hstatus = 0;
     if (e == cudaSuccess && ng > 0) {
         small_runs_kernel<<<(unsigned)((ng + 127) / 128), 128>>>(ng, gs, ct, tbits, split, s, G->F, G->Vg, G->adj_ptr,
                                                                  G->adj, G->vt_ptr, G->vt, dcomp, dn);
         chk(cudaDeviceSynchronize());
-        comp.resize(m);
         ncomp.resize(ng);
-        chk(cudaMemcpy(comp.data(), dcomp, m * sizeof(int), cudaMemcpyDeviceToHost));
         chk(cudaMemcpy(ncomp.data(), dn, ng * sizeof(int), cudaMemcpyDeviceToHost));
+        bool any_long = false;
+        for (long long g = 0; g < ng && e == cudaSuccess; g++) if (ncomp[g] < 0) { any_long = true; break; }
+        if (any_long && e == cudaSuccess && m < (long long)INT32_MAX) {
+            const int nb = (int)((m + kRTile - 1) / kRTile);
+            chk(balloc(&rid, m));
+            chk(balloc(&par, m));
+            chk(balloc(&flag, m));
+            chk(balloc(&rank, m));
+            chk(balloc(&tsum, nb));
+            chk(balloc(&status, 1));
+            if (e == cudaSuccess) chk(cudaMemset(status, 0, sizeof(int)));
+            if (e == cudaSuccess) {
+                const unsigned bm = (unsigned)((m + 255) / 256);
+                long_init_kernel<<<bm, 256>>>(m, ng, gs, dn, rid, par);
+                long_union_kernel<<<bm, 256>>>(m, gs, ct, rid, tbits, split, s, G->F, G->Vg, G->adj_ptr, G->adj,
+                                               G->vt_ptr, G->vt, par, status);
+                long_root_kernel<<<bm, 256>>>(m, rid, par, flag, status);
+                tile_sum_kernel<<<nb, kRT>>>(flag, m, tsum);
+                chk(cudaDeviceSynchronize());
+                std::vector<unsigned> hs(nb), toff(nb);
+                chk(cudaMemcpy(hs.data(), tsum, nb * sizeof(unsigned), cudaMemcpyDeviceToHost));
+                unsigned total = 0;
+                for (int q = 0; q < nb; q++) { toff[q] = total; total += hs[q]; }
+                chk(cudaMemcpy(tsum, toff.data(), nb * sizeof(unsigned), cudaMemcpyHostToDevice));
+                if (e == cudaSuccess) {
+                    rank_kernel<<<nb, kRT>>>(flag, m, tsum, rank);
+                    long_label_kernel<<<bm, 256>>>(m, gs, rid, par, rank, dcomp);
+                    long_count_kernel<<<(unsigned)((ng + 255) / 256), 256>>>(ng, m, gs, rank, total, dn);
+                    chk(cudaDeviceSynchronize());
+                    chk(cudaMemcpy(&hstatus, status, sizeof(int), cudaMemcpyDeviceToHost));
+                    chk(cudaMemcpy(ncomp.data(), dn, ng * sizeof(int), cudaMemcpyDeviceToHost));
+                }
+            }
+        }
+        comp.resize(m);
+        chk(cudaMemcpy(comp.data(), dcomp, m * sizeof(int), cudaMemcpyDeviceToHost));
     }
-    void *ptrs[] = {ct, gs, dcomp, dn};
+    void *ptrs[] = {ct, gs, dcomp, dn, rid, par, flag, rank, tsum, status};
     for (void *q : ptrs) if (q) cudaFree(q);
     if (e != cudaSuccess) {
         err = std::string("GPU labelling: ") + cudaGetErrorString(e);
         cudaGetLastError();
+        return false;
+    }
+    if (hstatus != 0) {
+        err = "GPU labelling: a union-find loop reached its bound";
         return false;
     }
     return true;

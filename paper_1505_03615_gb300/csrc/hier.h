@@ -144,8 +144,10 @@ int gpu_cut_triangles(const HostHierarchy &H, int N, std::vector<FragOut> &out, 
 
 // Row a2 on the GPU (basis.cu): the mesh arrays on the device, the sorted unique (corner,
 // triangle) words of a level's cells (morton(corner) << tbits | tri, key_bits bits of corner
-// key), and the component labels of the runs of one corner in those words (ncomp = -1 for runs
-// of more than 255 triangles, which the host labels).  A CUDA failure throws BuildCudaError.
+// key), and the component labels of the runs of one corner in those words (runs of up to 255
+// triangles one thread per run, longer ones one thread per pair with a shared union-find; ncomp =
+// -1, labelled by the host, only when a level's pairs exceed 31-bit positions).  A CUDA failure
+// throws BuildCudaError.
 struct BuildCudaError : std::runtime_error {
     explicit BuildCudaError(const std::string &m) : std::runtime_error(m) {}
 };
