@@ -311,17 +311,24 @@ void build_level_basis(HostHierarchy &H, HostLevel &L, const std::vector<KT> &ce
     }
     // dofs: one per (corner, component); order by colour, Morton key, smallest triangle
     struct DofRec { int colour; uint64_t key; int32_t mintri; int64_t group; int32_t comp; };
-    std::vector<DofRec> dofs;
+    std::vector<int64_t> gbase(ng + 1, 0);
+    for (int64_t g = 0; g < ng; g++) gbase[g + 1] = gbase[g] + ncomp[g];
+    std::vector<DofRec> dofs(gbase[ng]);
+#pragma omp parallel for schedule(static)
     for (int64_t g = 0; g < ng; g++) {
         const int64_t b = gstart[g];
-        uint64_t key = ct[b].key;
-        int colour = (compact3(key) & 1) | ((compact3(key >> 1) & 1) << 1) | ((compact3(key >> 2) & 1) << 2);
-        std::vector<int32_t> first(ncomp[g], -1);
-        for (int64_t i = b; i < gstart[g + 1]; i++)
-            if (first[comp[i]] < 0) first[comp[i]] = ct[i].tri;   // triangles ascending: first = min
-        for (int c = 0; c < ncomp[g]; c++) dofs.push_back(DofRec{colour, key, first[c], g, c});
+        const uint64_t key = ct[b].key;
+        const int colour = (compact3(key) & 1) | ((compact3(key >> 1) & 1) << 1) | ((compact3(key >> 2) & 1) << 2);
+        // labels number the components in the order of their first (smallest) triangle, so the first
+        // occurrences of labels 0, 1, 2, ... come in that order along the run
+        int next = 0;
+        for (int64_t i = b; i < gstart[g + 1] && next < ncomp[g]; i++)
+            if (comp[i] == next) {
+                dofs[gbase[g] + next] = DofRec{colour, key, ct[i].tri, g, next};
+                next++;
+            }
     }
-    std::sort(dofs.begin(), dofs.end(), [](const DofRec &a, const DofRec &b) {
+    LBMG_SORT(dofs.begin(), dofs.end(), [](const DofRec &a, const DofRec &b) {
         if (a.colour != b.colour) return a.colour < b.colour;
         if (a.key != b.key) return a.key < b.key;
         return a.mintri < b.mintri;
@@ -330,19 +337,17 @@ void build_level_basis(HostHierarchy &H, HostLevel &L, const std::vector<KT> &ce
     L.corner.resize(3 * (size_t)L.ndof);
     L.mintri.resize(L.ndof);
     for (int c = 0; c <= 8; c++) L.colour_start[c] = 0;
-    std::vector<std::vector<int32_t>> dof_of_group_comp(0);
-    std::vector<int64_t> gbase(ng + 1, 0);
-    for (int64_t g = 0; g < ng; g++) gbase[g + 1] = gbase[g] + ncomp[g];
     std::vector<int32_t> dof_id(gbase[ng]);
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < L.ndof; i++) {
         const DofRec &r = dofs[i];
         L.corner[3 * i] = (int)compact3(r.key);
         L.corner[3 * i + 1] = (int)compact3(r.key >> 1);
         L.corner[3 * i + 2] = (int)compact3(r.key >> 2);
         L.mintri[i] = r.mintri;
-        L.colour_start[r.colour + 1]++;
         dof_id[gbase[r.group] + r.comp] = i;
     }
+    for (int i = 0; i < L.ndof; i++) L.colour_start[dofs[i].colour + 1]++;
     for (int c = 0; c < 8; c++) L.colour_start[c + 1] += L.colour_start[c];
     L.ct_dof.resize(m);
 #pragma omp parallel for schedule(static)
