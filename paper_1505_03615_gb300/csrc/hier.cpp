@@ -501,7 +501,8 @@ int build_host_hierarchy(const double *V, int nv, const int *F, int nt, int dept
     if (gpu_clip) {
         const int st = gpu_cut_triangles(H, N, frags, err);
         if (st) return st;
-        for (auto &f : frags) f.key = morton(f.vox[0], f.vox[1], f.vox[2]);
+#pragma omp parallel for schedule(static)
+        for (long q = 0; q < (long)frags.size(); q++) frags[q].key = morton(frags[q].vox[0], frags[q].vox[1], frags[q].vox[2]);
     } else {
 #ifdef _OPENMP
         int nth = omp_get_max_threads();
@@ -536,6 +537,7 @@ int build_host_hierarchy(const double *V, int nv, const int *F, int nt, int dept
     H.frag_pstart[0] = 0;
     for (int f = 0; f < H.nfrag; f++) H.frag_pstart[f + 1] = H.frag_pstart[f] + (int32_t)(frags[f].poly.size() / 3);
     H.frag_poly.resize(3 * (size_t)H.frag_pstart[H.nfrag]);
+#pragma omp parallel for schedule(static)
     for (int f = 0; f < H.nfrag; f++) {
         H.frag_tri[f] = frags[f].tri;
         for (int a = 0; a < 3; a++) H.frag_vox[3 * f + a] = frags[f].vox[a];
@@ -545,7 +547,11 @@ int build_host_hierarchy(const double *V, int nv, const int *F, int nt, int dept
     // levels from the finest down
     H.lev.assign(depth + 1, HostLevel());
     std::vector<KT> cells(H.nfrag);
-    for (int f = 0; f < H.nfrag; f++) cells[f] = KT{frags[f].key, frags[f].tri};
+#pragma omp parallel for schedule(static)
+    for (int f = 0; f < H.nfrag; f++) {
+        cells[f] = KT{frags[f].key, frags[f].tri};
+        std::vector<double>().swap(frags[f].poly);   // the pieces' polygons are freed by all threads
+    }
     frags.clear();
     frags.shrink_to_fit();
     cells.erase(std::unique(cells.begin(), cells.end(), [](const KT &a, const KT &b) { return a.key == b.key && a.tri == b.tri; }), cells.end());
