@@ -501,10 +501,11 @@ def test_nan_right_hand_side_is_reported_as_divergence(path):
 def test_mixed_precision_skips_sliver_functions_below_fp32_range():
     """A torus of the seeded 64-mesh batch (34k triangles, depth 7) has split functions whose
     supports meet it in slivers where the hat and its tangential gradient nearly vanish: their
-    diagonals reach 1e-40 of the level's mean, below the assembly's rounding error and FP32's
-    range.  Relaxation leaves such rows (diagonal under 1e-20 of the mean, or not positive)
-    alone instead of dividing by them; the mixed solve, V-cycles or CG, then reaches 1e-6,
-    checked by the residual recomputed on the host."""
+    diagonals are the assembly's rounding noise, 1e-27 to 1e-40 of the level's mean depending on
+    the rounding of the quadrature (and down to FP32's range or below).  Relaxation leaves such
+    rows (diagonal under 1e-20 of the mean, or not positive) alone instead of dividing by them;
+    the mixed solve, V-cycles or CG, then reaches 1e-6, checked by the residual recomputed on
+    the host."""
     V, F, depth = meshgen.batch_mix(39)[38]
     t = 1e-4
     h = L.lbmg_build_hierarchy(V, F, depth)
@@ -514,7 +515,7 @@ def test_mixed_precision_skips_sliver_functions_below_fp32_range():
         n = len(rp) - 1
         A = sp.csr_matrix((M, ci, rp), shape=(n, n)) + t * sp.csr_matrix((Lm, ci, rp), shape=(n, n))
         dg = A.diagonal()
-        assert dg.min() < 1e-30 * dg.mean()          # the case this test is about
+        assert dg.min() < 1e-25 * dg.mean()          # the case this test is about: far below the skip rule's 1e-20
         rhs = torch.zeros((n, 3), dtype=torch.float64, device=DEV)
         L.lbmg_project_rhs(h, _dev(V), rhs)
         b = rhs.cpu().numpy()
