@@ -239,7 +239,7 @@ template <> struct P<double> {
 };
 
 template <class T>
-void enqueue_smooth(Ctx &c, DevLevel &L, int R, int sweeps, bool forward, cudaStream_t s, Chain *ch) {
+void enqueue_smooth(Ctx &c, DevLevel &L, int R, int sweeps, bool forward, cudaStream_t s, Chain *ch, int skip = 0) {
     if (c.smoother == LBMG_JACOBI) {
         for (int sw = 0; sw < sweeps; sw++) {
             launch_residual<T>(L, P<T>::A(L), P<T>::b(L), P<T>::x(L), P<T>::r(L), R, s, L.ns, ch);
@@ -247,7 +247,7 @@ void enqueue_smooth(Ctx &c, DevLevel &L, int R, int sweeps, bool forward, cudaSt
             if (ch) ch->cut();
         }
     } else {
-        launch_sweeps<T>(c, L, sweeps, forward, P<T>::A(L), P<T>::dinv(L), P<T>::b(L), P<T>::x(L), R, s, ch);
+        launch_sweeps<T>(c, L, sweeps, forward, P<T>::A(L), P<T>::dinv(L), P<T>::b(L), P<T>::x(L), R, s, ch, skip);
     }
 }
 
@@ -276,16 +276,21 @@ void enqueue_vcycle(Ctx &c, int R, cudaStream_t s, bool timed, Chain *ch, int to
         if (c.narrow.dn >= c.d0 && c.narrow.dn <= top) { bottom = kSmem; dn = c.narrow.dn; }
         else if (std::min(c.persist_dn, top) >= c.d0) { bottom = kL2; dn = std::min(c.persist_dn, top); }
     }
+    int skip = 0;   // colour steps of the next level's first sweep that its restriction did
     for (int d = top; d > dn; d--) {
         DevLevel &L = c.lev[d], &Lc = c.lev[d - 1];
         launch_coarse_apply<T>(c, L, P<T>::inv(c), P<T>::b(L), P<T>::x(L), R, s, ch);
         if (timed && d == top) record(c.ev_smooth[0], s, ch);
-        enqueue_smooth<T>(c, L, R, c.nu1, true, s, ch);
+        enqueue_smooth<T>(c, L, R, c.nu1, true, s, ch, skip);
         if (timed && d == top) record(c.ev_smooth[1], s, ch);
         launch_residual<T>(L, P<T>::A(L), P<T>::b(L), P<T>::x(L), P<T>::r(L), R, s, L.ns, ch);
         // the shared-memory bottom starts level dn from zero itself; the dense solve overwrites d0
         const bool zero = bottom == kSmem ? d - 1 > dn : (bottom == kL2 || d - 1 > c.d0);
-        launch_restrict<T>(Lc, P<T>::r(L), P<T>::b(Lc), R, s, zero ? P<T>::x(Lc) : (T *)nullptr, ch);
+        // a level that this loop smooths next (Gauss-Seidel, from zero) gets its first colour step
+        // from the restriction that zeroes it
+        const bool fuse = zero && d - 1 > dn && c.smoother != LBMG_JACOBI && c.nu1 > 0;
+        launch_restrict<T>(Lc, P<T>::r(L), P<T>::b(Lc), R, s, zero ? P<T>::x(Lc) : (T *)nullptr, ch, fuse);
+        skip = fuse ? 1 : 0;
     }
     if (bottom == kSmem) launch_narrow_smem(c, R, s, ch);
     else if (bottom == kL2) { launch_narrow_cycle(c, 1, R, dn, s); ch->cut(); }

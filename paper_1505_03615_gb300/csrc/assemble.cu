@@ -325,10 +325,10 @@ void launch_galerkin(const Ctx &c, int dc, double t, cudaStream_t s) {
 
 // Relaxation skips rows whose diagonal is below this fraction of the level's mean
 // diagonal (or not positive).  Such functions meet the mesh in slivers where the hat
-// and its tangential gradient nearly vanish: their diagonals, down to 1e-40 of the mean,
-// lie below the rounding error of the moment contraction that produced them (so they can
-// even come out negative), below FP32's range (1/a_ii overflows), and they carry no
-// measurable mass or stiffness.  Their coefficients stay at zero correction; the residual
+// and its tangential gradient nearly vanish: their diagonals (1e-27 to 1e-40 of the mean,
+// depending on the rounding of the quadrature) lie below the rounding error of the moment
+// contraction that produced them (so they can even come out negative), down to FP32's range
+// (1/a_ii overflows), and they carry no measurable mass or stiffness.  Their coefficients stay at zero correction; the residual
 // still includes their rows.
 constexpr double kDiagFloor = 1e-20;
 constexpr int kDiagBlocks = 256;

@@ -341,9 +341,11 @@ int packed_sweep_blocks(int R);   // the grid of the sweep kernel (resident bloc
 // vectors below are [n][R] with stride R in {1, 2, 4} (3 right-hand sides padded to 4)
 // `sweeps` Gauss-Seidel sweeps of level L (colours 0..7, or 7..0 backwards): one cooperative
 // launch per call when the level's tuned shape is the whole-sweep kernel (FP32), else one
-// launch per colour, each prefetching the next colour's entries
+// launch per colour, each prefetching the next colour's entries.  skip: colour steps of the
+// first sweep already done (1: the restriction applied colour 0's step from a zero start)
 template <class T> void launch_sweeps(const Ctx &c, const DevLevel &L, int sweeps, bool forward, const T *A,
-                                      const T *dinv, const T *b, T *x, int R, cudaStream_t s, Chain *ch);
+                                      const T *dinv, const T *b, T *x, int R, cudaStream_t s, Chain *ch,
+                                      int skip = 0);
 // next: the colour launched after this one on the same level (-1: none); its packed entries
 // are prefetched into L2 while this colour runs
 template <class T> void launch_smooth_colour(const DevLevel &L, int colour, const T *A, const T *dinv,
@@ -353,9 +355,11 @@ template <class T> void launch_residual(const DevLevel &L, const T *A, const T *
                                         cudaStream_t s, int nrows = -1, Chain *ch = nullptr);
 template <class T> void launch_jacobi_update(const DevLevel &L, const T *dinv, const T *r, T *x, T omega, int R,
                                              cudaStream_t s);
-// bc = P^T rf; when xc is given, the coarse correction xc is zeroed in the same pass
+// bc = P^T rf; when xc is given, the coarse correction xc is zeroed in the same pass, or, with
+// first_colour, given the first Gauss-Seidel colour step from zero: x_i = 0 + b_i / a_ii on the rows
+// of colour 0 (the colour kernels' arithmetic with x = 0, bit for bit), zero elsewhere
 template <class T> void launch_restrict(const DevLevel &Lc, const T *rf, T *bc, int R, cudaStream_t s,
-                                        T *xc = nullptr, Chain *ch = nullptr);
+                                        T *xc = nullptr, Chain *ch = nullptr, bool first_colour = false);
 template <class T> void launch_prolong_add(const DevLevel &Lf, const T *xc, T *xf, int R, cudaStream_t s,
                                            Chain *ch = nullptr);
 struct Ctx;

@@ -7,6 +7,8 @@
 // of equal-parity corners are disjoint and the components of one corner are
 // disjoint, so a colour is relaxed in parallel with exact Gauss-Seidel updates.
 // A group of G threads shares one matrix row.
+#include <algorithm>
+
 #include "lbmg_internal.h"
 
 namespace lbmg {
@@ -162,21 +164,22 @@ ResidualFn<T> residual_fn(int tpr) {
 
 template <class T>
 void launch_sweeps(const Ctx &c, const DevLevel &L, int sweeps, bool forward, const T *A, const T *dinv, const T *b,
-                   T *x, int R, cudaStream_t s, Chain *ch) {
+                   T *x, int R, cudaStream_t s, Chain *ch, int skip) {
     if (sweeps <= 0) return;
+    skip = std::max(0, std::min(skip, 8));
     const LaunchShape &sh = L.shape[sizeof(T) == 8][kShapeSmooth];
     if (sizeof(T) == 4 && sh.tpb == kSweepShapeTpb && 8 * sweeps <= 32 && c.sweep_bar && A == (const T *)L.A32) {
         int seq[32];
-        for (int q = 0; q < 8 * sweeps; q++) seq[q] = forward ? q % 8 : 7 - q % 8;
+        for (int q = skip; q < 8 * sweeps; q++) seq[q - skip] = forward ? q % 8 : 7 - q % 8;
         const int blocks = sh.grid > 0 && sh.grid < c.sweep_blocks[R] ? sh.grid : c.sweep_blocks[R];
         if (ch) ch->cut();   // a cooperative launch takes no programmatic serialisation
-        if (launch_packed_sweep(L, seq, 8 * sweeps, (const float *)dinv, (const float *)b, (float *)x, R, c.sweep_bar,
-                                c.narrow.status, blocks, s))
+        if (launch_packed_sweep(L, seq, 8 * sweeps - skip, (const float *)dinv, (const float *)b, (float *)x, R,
+                                c.sweep_bar, c.narrow.status, blocks, s))
             return;
         cudaGetLastError();   // refused: the per-colour launches below
     }
     for (int sw = 0; sw < sweeps; sw++)
-        for (int q = 0; q < 8; q++) {
+        for (int q = sw == 0 ? skip : 0; q < 8; q++) {
             const int colour = forward ? q : 7 - q;
             // the colour that follows on this level: the next of this sweep, or the first of the next sweep
             const int nq = q < 7 ? q + 1 : (sw + 1 < sweeps ? 0 : -1);
@@ -234,12 +237,15 @@ constexpr int kPreChildren = 16;
 
 template <class T, int R>
 __global__ void restrict_kernel(int nc, const int *__restrict__ crp, const uint32_t *__restrict__ cch,
-                                const T *__restrict__ rf, T *__restrict__ bc, T *__restrict__ xc) {
+                                const T *__restrict__ rf, T *__restrict__ bc, T *__restrict__ xc,
+                                const T *__restrict__ dinv, int c1) {
     const int J = blockIdx.x * blockDim.x + threadIdx.x;
     const bool active = J < nc;
     int k0 = 0, k1 = 0;
     uint32_t e[kPreChildren];
     if (active) { k0 = __ldg(crp + J); k1 = __ldg(crp + J + 1); }
+    // colour 0 (rows [0, c1)) of the first sweep, fused: its inverse diagonal
+    const T d = (active && dinv && J < c1) ? __ldg(dinv + J) : T(0);
 #pragma unroll
     for (int u = 0; u < kPreChildren; u++) e[u] = k0 + u < k1 ? __ldg(cch + k0 + u) : 0u;
     grid_dep_wait();
@@ -262,17 +268,25 @@ __global__ void restrict_kernel(int nc, const int *__restrict__ crp, const uint3
 #pragma unroll
     for (int r = 0; r < R; r++) bc[(size_t)J * R + r] = acc[r];
     if (xc) {
+        if (dinv && J < c1) {
+            // the colour kernels' step x = x + (b - A x) / a_ii with x = 0 (so A x = +0): 0 + b d
 #pragma unroll
-        for (int r = 0; r < R; r++) xc[(size_t)J * R + r] = T(0);
+            for (int r = 0; r < R; r++) xc[(size_t)J * R + r] = T(0) + (acc[r] - T(0)) * d;
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; r++) xc[(size_t)J * R + r] = T(0);
+        }
     }
 }
 
 template <class T>
-void launch_restrict(const DevLevel &Lc, const T *rf, T *bc, int R, cudaStream_t s, T *xc, Chain *ch) {
+void launch_restrict(const DevLevel &Lc, const T *rf, T *bc, int R, cudaStream_t s, T *xc, Chain *ch,
+                     bool first_colour) {
     if (Lc.n == 0) return;
     const unsigned blocks = (unsigned)((Lc.n + 255) / 256);
     auto k = R == 1 ? restrict_kernel<T, 1> : R == 2 ? restrict_kernel<T, 2> : restrict_kernel<T, 4>;
-    klaunch(k, blocks, 256u, 0, s, ch, Lc.n, Lc.crp, Lc.cch, rf, bc, xc);
+    const T *dinv = first_colour && xc ? (sizeof(T) == 4 ? (const T *)Lc.dinv32 : (const T *)Lc.dinv64) : nullptr;
+    klaunch(k, blocks, 256u, 0, s, ch, Lc.n, Lc.crp, Lc.cch, rf, bc, xc, dinv, dinv ? Lc.cs[1] : 0);
 }
 
 // x_f[i] += (sum of parent values) / #parents(i)
@@ -766,13 +780,13 @@ void launch_add_double(double *x, const double *e, int64_t n, cudaStream_t s) {
 // explicit instantiations
 #define LBMG_INST(T)                                                                                           \
     template void launch_sweeps<T>(const Ctx &, const DevLevel &, int, bool, const T *, const T *, const T *, T *, \
-                                   int, cudaStream_t, Chain *);                                               \
+                                   int, cudaStream_t, Chain *, int);                                          \
     template void launch_smooth_colour<T>(const DevLevel &, int, const T *, const T *, const T *, T *, int,   \
                                           cudaStream_t, Chain *, int);                                         \
     template void launch_residual<T>(const DevLevel &, const T *, const T *, const T *, T *, int, cudaStream_t, int, \
                                      Chain *);                                                                 \
     template void launch_jacobi_update<T>(const DevLevel &, const T *, const T *, T *, T, int, cudaStream_t);   \
-    template void launch_restrict<T>(const DevLevel &, const T *, T *, int, cudaStream_t, T *, Chain *);       \
+    template void launch_restrict<T>(const DevLevel &, const T *, T *, int, cudaStream_t, T *, Chain *, bool); \
     template void launch_prolong_add<T>(const DevLevel &, const T *, T *, int, cudaStream_t, Chain *);         \
     template void launch_coarse_apply<T>(const Ctx &, const DevLevel &, const T *, const T *, T *, int, cudaStream_t, \
                                          Chain *);
