@@ -1749,8 +1749,18 @@ int lbmg_launch_counts(lbmg_handle h, int precision, int *assemble, int *project
         const bool smem = c.narrow.dn >= c.d0 && c.smoother != LBMG_JACOBI && precision == LBMG_MIXED;
         const int bottom = smem ? c.narrow.dn : (narrow ? c.persist_dn : c.d0);
         cyc = 1;   // the one-block bottom cycle, or the coarse apply
-        for (int d = bottom + 1; d <= c.D; d++)   // sweeps, residual, restriction, prolongation
-            cyc += (c.nu1 + c.nu2) * per_sweep(c.lev[d].cs) + 3 + (c.lev[d].ncb > 0);
+        for (int d = bottom + 1; d <= c.D; d++) {   // sweeps, residual, restriction, prolongation
+            const DevLevel &L = c.lev[d];
+            const bool whole = precision == LBMG_MIXED && c.smoother != LBMG_JACOBI &&
+                               L.shape[0][kShapeSmooth].tpb == kSweepShapeTpb && L.pk_map && c.sweep_bar;
+            if (whole) cyc += (c.nu1 > 0) + (c.nu2 > 0);   // one cooperative launch per smoothing
+            else {
+                cyc += (c.nu1 + c.nu2) * per_sweep(L.cs);
+                // below the finest level the restriction does colour 0 of the first sweep
+                if (d < c.D && c.smoother != LBMG_JACOBI && c.nu1 > 0 && L.cs[1] > L.cs[0]) cyc -= 1;
+            }
+            cyc += 3 + (L.ncb > 0);
+        }
     } else {
         // the general cycle: gamma visits of each coarser level
         long visit = c.coarse_smooth ? (long)(c.nu1 + c.nu2) * per_sweep(c.lev[c.d0].cs_all) : 1;
