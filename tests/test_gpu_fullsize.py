@@ -19,6 +19,7 @@ import meshgen
 import oracle
 import paper_1505_03615_gb300 as L
 from tests._match import permutation
+from tests._stretch import complete_sample, oracle_to_library, stretch
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -168,3 +169,45 @@ def test_full_size_headline_mixed_and_learned_solves_reach_tolerance(knot35):
         cycles[mode] = st.cycles
     L.lbmg_learned_enable(h, False)
     assert cycles["learned"] < 0.85 * cycles["plain"], cycles
+
+
+def test_full_size_headline_rows_match_oracle_on_a_stretch(knot35):
+    """The headline workload's finest level against the oracle, where the oracle can be built: 80,000
+    consecutive triangles from the middle of the 4M-triangle knot, on the full mesh's grid.  On 400
+    functions whose support and neighbours' supports no outside triangle can meet, the library's rows
+    of M and L (every stored entry) and the projected right-hand side match the oracle's to 1e-12."""
+    V, F, depth, t, f, tol, h = knot35
+    t0, ntri = F.shape[0] // 2, 80_000
+    S, centre = L.lbmg_embedding(h)
+    So, co = oracle.embedding_of(V)
+    assert abs(S - So) <= 1e-14 * So and np.abs(centre - co).max() <= 1e-14 * So
+    Vp, Fp = stretch(V, F, t0, ntri)
+    o = oracle.Hierarchy(Vp, Fp, depth, min_depth=depth, embedding=(S, centre))
+    oc, om = o.dofs(depth)
+    pick = complete_sample(V, F, t0, ntri, S, centre, depth, oc, om, 400)
+    assert len(pick) >= 300
+    lc, lm = L.lbmg_get_dofs(h, depth)
+    to_lib = oracle_to_library(oc, om.astype(np.int64) + t0, lc, lm, F.shape[0])
+    rp, ci, M, Lm = L.lbmg_get_matrix(h, depth)
+    Mo, Lo = (A.tocsr() for A in o.matrices(depth))
+    mmax, lmax = abs(Mo).max(), abs(Lo).max()
+    for io in pick:
+        il = to_lib[io]
+        assert il >= 0, io
+        cols_o = Mo.indices[Mo.indptr[io]:Mo.indptr[io + 1]]
+        mapped = to_lib[cols_o]
+        assert (mapped >= 0).all(), io
+        k0, k1 = rp[il], rp[il + 1]
+        order = np.argsort(mapped)
+        assert np.array_equal(mapped[order], ci[k0:k1]), io   # library columns are sorted
+        assert np.abs(M[k0:k1] - Mo.data[Mo.indptr[io]:Mo.indptr[io + 1]][order]).max() <= 1e-12 * mmax
+        lo_row = Lo[io].toarray().ravel()[cols_o]
+        assert np.abs(Lm[k0:k1] - lo_row[order]).max() <= 1e-12 * lmax
+    n = L.lbmg_level_info(h, depth)[0]
+    rhs = torch.zeros((n, f.shape[1]), dtype=torch.float64, device="cuda:0")
+    L.lbmg_project_rhs(h, torch.tensor(f, device="cuda:0"), rhs)
+    used = np.unique(F[t0:t0 + ntri])
+    ro = o.project_rhs(np.ascontiguousarray(f[used]))
+    rl = rhs.cpu().numpy()
+    assert np.abs(rl[to_lib[pick]] - ro[pick]).max() <= 1e-12 * np.abs(ro).max()
+
