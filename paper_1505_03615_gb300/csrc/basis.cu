@@ -342,15 +342,13 @@ __global__ void long_union_kernel(long long m, const long long *__restrict__ gs,
     }
 }
 
-// roots (parents fully compressed) and the flags of the roots of long runs
+// the flags of the roots of long runs (the forest no longer changes, only paths are halved)
 __global__ void long_root_kernel(long long m, const int *__restrict__ rid, int *par, unsigned *__restrict__ flag,
                                  int *status) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= m) return;
     if (rid[i] < 0) { flag[i] = 0u; return; }
-    const int r = uf_find(par, (int)i, status);
-    par[i] = r;
-    flag[i] = r == (int)i ? 1u : 0u;
+    flag[i] = uf_find(par, (int)i, status) == (int)i ? 1u : 0u;
 }
 
 // exclusive prefix of the flags: tile offset (scanned tile sums) + the flags before i in the tile
@@ -374,14 +372,15 @@ __global__ void __launch_bounds__(kRT) rank_kernel(const unsigned *__restrict__ 
     }
 }
 
-// labels of the long runs' pairs (their root's rank within the run) and the runs' component counts
+// labels of the long runs' pairs (their root's rank within the run) and the runs' component counts;
+// the root comes from a find, since concurrent path halving may leave a pair's parent an ancestor below it
 __global__ void long_label_kernel(long long m, const long long *__restrict__ gs, const int *__restrict__ rid,
-                                  const int *__restrict__ par, const unsigned *__restrict__ rank, int *__restrict__ comp) {
+                                  int *par, const unsigned *__restrict__ rank, int *__restrict__ comp, int *status) {
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= m) return;
     const int g = rid[i];
     if (g < 0) return;
-    comp[i] = (int)(rank[par[i]] - rank[gs[g]]);
+    comp[i] = (int)(rank[uf_find(par, (int)i, status)] - rank[gs[g]]);
 }
 
 __global__ void long_count_kernel(long long ng, long long m, const long long *__restrict__ gs,
@@ -549,7 +548,7 @@ bool gpu_run_components(const GpuBasis *G, const std::vector<uint64_t> &words, c
                 chk(cudaMemcpy(tsum, toff.data(), nb * sizeof(unsigned), cudaMemcpyHostToDevice));
                 if (e == cudaSuccess) {
                     rank_kernel<<<nb, kRT>>>(flag, m, tsum, rank);
-                    long_label_kernel<<<bm, 256>>>(m, gs, rid, par, rank, dcomp);
+                    long_label_kernel<<<bm, 256>>>(m, gs, rid, par, rank, dcomp, status);
                     long_count_kernel<<<(unsigned)((ng + 255) / 256), 256>>>(ng, m, gs, rank, total, dn);
                     chk(cudaDeviceSynchronize());
                     chk(cudaMemcpy(&hstatus, status, sizeof(int), cudaMemcpyDeviceToHost));
