@@ -5,8 +5,10 @@
 // colours per Gauss-Seidel sweep, residual, restriction, prolongation) is pure
 // latency: as separate launches each costs a launch gap, and even inside one
 // block each phase waits on three dependent memory loads.  Here the static data
-// of those levels (16-bit row pointers, column indices, parents and children,
-// FP32 values and inverse diagonals) are packed once into a compact blob; every
+// of those levels (16-bit row pointers, column indices, children, and parents
+// behind per-row offsets, FP32 values and inverse diagonals) are packed once into a
+// compact blob, sized with x and b per level and one residual buffer shared by the
+// levels to the block's opt-in shared memory; every
 // cycle one block pulls the blob into shared memory with TMA bulk copies (issued
 // before the kernel waits for its predecessor, so the copy overlaps the previous
 // kernel), runs the bottom V-cycle there with block barriers between phases, and
